@@ -1,0 +1,186 @@
+"""Oracle for the all-pairs posterior stage -- TEST INFRASTRUCTURE ONLY.
+
+Plain FP64 log-space CPU implementation (``oracle.c``) of what the posterior
+stage computes (paper, Methods, stage I): pair-HMM and partition-function
+posteriors, their combination, the sparse matrix at threshold theta, the MEA
+score and the MEA distance.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+this package.  It shares no code with the CUDA path and imports nothing from
+it; both sides take their inputs from ``synth`` only.
+
+Every function here is pinned by tests against brute-force enumeration,
+closed forms, limits and invariants (tests/test_oracle_*.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+COMBINE = {"rms": 0, "mean": 1, "hmm": 2, "pf": 3}
+_LUT = np.full(256, 255, dtype=np.uint8)
+for _i, _c in enumerate("ACDEFGHIKLMNPQRSTVWY"):
+    _LUT[ord(_c)] = _i
+    _LUT[ord(_c.lower())] = _i
+
+
+class OrParams(ctypes.Structure):
+    _fields_ = [
+        ("pi", ctypes.c_double * 5),
+        ("delta1", ctypes.c_double), ("eps1", ctypes.c_double),
+        ("delta2", ctypes.c_double), ("eps2", ctypes.c_double),
+        ("emit_pair", ctypes.c_double * 400),
+        ("emit_bg", ctypes.c_double * 20),
+        ("end_w", ctypes.c_double * 5),
+        ("score", ctypes.c_double * 400),
+        ("gap_open", ctypes.c_double), ("gap_ext", ctypes.c_double),
+        ("temperature", ctypes.c_double),
+        ("combine", ctypes.c_int32), ("pad_", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc -O2, no fast-math)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            dp = ctypes.POINTER(ctypes.c_double)
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            lib.or_pair.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int,
+                                    ctypes.POINTER(OrParams), dp, dp, dp, dp, dp,
+                                    dp, dp, dp, dp, dp]
+            lib.or_pair.restype = ctypes.c_int
+            lib.or_pairs.argtypes = [u8p, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                     ctypes.POINTER(OrParams), ctypes.c_double,
+                                     ctypes.c_int, dp, dp, dp,
+                                     ctypes.POINTER(ctypes.c_int64)]
+            lib.or_pairs.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def to_struct(prm) -> OrParams:
+    """Copy a synth.ModelParams into the oracle's own parameter layout."""
+    s = OrParams()
+    s.pi[:] = [float(v) for v in prm.pi]
+    s.delta1, s.eps1 = float(prm.delta1), float(prm.eps1)
+    s.delta2, s.eps2 = float(prm.delta2), float(prm.eps2)
+    s.emit_pair[:] = [float(v) for v in np.asarray(prm.emit_pair).reshape(-1)]
+    s.emit_bg[:] = [float(v) for v in prm.emit_bg]
+    s.end_w[:] = [float(v) for v in prm.end_w]
+    s.score[:] = [float(v) for v in np.asarray(prm.score).reshape(-1)]
+    s.gap_open, s.gap_ext = float(prm.gap_open), float(prm.gap_ext)
+    s.temperature = float(prm.temperature)
+    s.combine = COMBINE[prm.combine] if isinstance(prm.combine, str) else int(prm.combine)
+    return s
+
+
+def encode(seq) -> np.ndarray:
+    """Residue letters (str or uint8 ASCII array) -> codes 0..19."""
+    if isinstance(seq, str):
+        seq = np.frombuffer(seq.encode("ascii"), dtype=np.uint8)
+    c = _LUT[np.asarray(seq, dtype=np.uint8)]
+    if (c == 255).any():
+        raise ValueError("residue outside the 20-letter alphabet")
+    return c
+
+
+def _as_codes(s) -> np.ndarray:
+    """Letters (str / ASCII bytes) or an array of codes 0..19 -> codes."""
+    if isinstance(s, np.ndarray) and s.dtype != np.uint8:
+        s = s.astype(np.uint8)
+    if isinstance(s, np.ndarray) and s.size and int(s.max()) < 20:
+        return np.ascontiguousarray(s, dtype=np.uint8)
+    return np.ascontiguousarray(encode(s), dtype=np.uint8)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def pair(x, y, prm) -> dict:
+    """All outputs of one pair (x, y are residue codes or letters)."""
+    lib = _load()
+    x = _as_codes(x)
+    y = _as_codes(y)
+    m, n = int(x.size), int(y.size)
+    if m < 1 or n < 1:
+        raise ValueError("empty sequence")
+    st = to_struct(prm)
+    out = {k: np.zeros((m, n)) for k in ("P_hmm", "P_pf", "P")}
+    gx_h, gy_h, gx_p, gy_p = np.zeros(m), np.zeros(n), np.zeros(m), np.zeros(n)
+    logz = np.zeros(4)
+    mea = np.zeros(1)
+    dist = np.zeros(1)
+    dp = ctypes.c_double
+    rc = lib.or_pair(_ptr(x, ctypes.c_uint8), m, _ptr(y, ctypes.c_uint8), n,
+                     ctypes.byref(st), _ptr(out["P_hmm"], dp), _ptr(out["P_pf"], dp),
+                     _ptr(out["P"], dp), _ptr(gx_h, dp), _ptr(gy_h, dp),
+                     _ptr(gx_p, dp), _ptr(gy_p, dp), _ptr(logz, dp),
+                     _ptr(mea, dp), _ptr(dist, dp))
+    if rc != 0:
+        raise MemoryError("oracle: out of memory")
+    out.update(gx_hmm=gx_h, gy_hmm=gy_h, gx_pf=gx_p, gy_pf=gy_p,
+               logz_hmm=logz[0], logz_hmm_bwd=logz[1], logz_pf=logz[2],
+               logz_pf_bwd=logz[3], mea=float(mea[0]), dist=float(dist[0]))
+    return out
+
+
+def sparsify(P: np.ndarray, theta: float):
+    """Entries with P >= theta as CSR (row_ptr, col, val), columns ascending."""
+    m = P.shape[0]
+    keep = P >= theta
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(keep.sum(axis=1))
+    rows, cols = np.nonzero(keep)
+    return row_ptr, cols.astype(np.int64), P[rows, cols]
+
+
+def pairs(family, pair_list, prm, threads: int | None = None, theta: float | None = None) -> dict:
+    """Per-pair log Z (HMM, PF), MEA score, distance and nnz for the listed
+    pairs of ``family``, on a thread pool of ``threads`` host cores."""
+    lib = _load()
+    threads = os.cpu_count() if threads is None else threads
+    codes = encode(family.residues)
+    off = np.ascontiguousarray(family.offsets, dtype=np.int64)
+    pl = np.asarray(list(pair_list), dtype=np.int32).reshape(-1, 2)
+    pa = np.ascontiguousarray(pl[:, 0])
+    pb = np.ascontiguousarray(pl[:, 1])
+    npairs = pl.shape[0]
+    logz = np.zeros(2 * npairs)
+    mea = np.zeros(npairs)
+    dist = np.zeros(npairs)
+    nnz = np.zeros(npairs, dtype=np.int64)
+    theta = prm.threshold if theta is None else theta
+    st = to_struct(prm)
+    dp = ctypes.c_double
+    rc = lib.or_pairs(_ptr(codes, ctypes.c_uint8), _ptr(off, ctypes.c_int64),
+                      _ptr(pa, ctypes.c_int32), _ptr(pb, ctypes.c_int32), npairs,
+                      ctypes.byref(st), float(theta), int(threads), _ptr(logz, dp),
+                      _ptr(mea, dp), _ptr(dist, dp), _ptr(nnz, ctypes.c_int64))
+    if rc != 0:
+        raise MemoryError("oracle: out of memory")
+    return dict(logz_hmm=logz[0::2].copy(), logz_pf=logz[1::2].copy(), mea=mea,
+                dist=dist, nnz=nnz, threads=threads)
