@@ -1,0 +1,333 @@
+"""Benchmark of the all-pairs posterior stage (one JSON line on stdout).
+
+Workload (default): one family of 64 synthetic protein sequences, lengths
+200-400 (seeded star-tree evolution, 40% substitution), all 2016 pairs in one
+length-ordered persistent launch, FP32 scaled recurrences, threshold 0.01 CSR
+output and the MEA distance matrix.  A step is one complete pass of the
+posterior stage over the family.
+
+Metric: posterior-stage GCUPS = sum over pairs of m*n / step time / 1e9, where
+one cell update is the whole per-cell work of pair-HMM forward and backward,
+partition-function forward and backward, combination, threshold and MEA.
+
+  value : residues resident on the device, results left on the device;
+          device time of each step (CUDA events on the launch stream), L2
+          flushed (256 MiB write) before every step, outside the timed window.
+  e2e   : the same call with host buffers: residues copied from pinned host
+          memory, every result array copied back, wall time of the call.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--config c1|c2|c3|c5] [--precision f32|f64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+ALU_OPS_PER_CELL = 61          # algorithmic FP32/INT issue slots per cell update
+FP32_LANES_PER_SM = 128
+CONFIG_DESC = {
+    "c1": "8 seqs, lengths 100-150, star tree s=0.30, 28 pairs",
+    "c2": "64 seqs, lengths 200-400, star tree s=0.40, 2016 pairs",
+    "c3": "500 seqs, lengths 150-500, random tree s~U[0.05,0.25], 124750 pairs",
+    "c5": "100 seqs, lengths 2000-4000, 3-domain roots, 4950 pairs",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIG_DESC))
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(s[0]) for s in self.samples if num(s[0]) is not None]
+        mx = [num(s[1]) for s in self.samples if num(s[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for nm, v in zip(names, s[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def cpu_baseline(fam, prm, budget_s: float, seed: int = 0):
+    """The FP64 oracle on the host cores, on a bounded seeded sample of pairs."""
+    import oracle
+    pl = list(fam.pairs())
+    rng = np.random.Generator(np.random.PCG64(seed))
+    order = rng.permutation(len(pl))
+    threads = os.cpu_count() or 1
+    L = fam.lengths.astype(np.int64)
+    # calibrate on a few pairs, then size the sample to the time budget
+    probe = [pl[i] for i in order[:threads]]
+    t0 = time.perf_counter()
+    oracle.pairs(fam, probe, prm, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    cells_probe = float(sum(L[a] * L[b] for a, b in probe))
+    want_cells = cells_probe / dt * budget_s
+    sample, cells = [], 0.0
+    for i in order[len(probe):]:
+        if cells >= want_cells:
+            break
+        a, b = pl[i]
+        sample.append((a, b))
+        cells += float(L[a] * L[b])
+    if not sample:
+        sample, cells = probe, cells_probe
+    t0 = time.perf_counter()
+    oracle.pairs(fam, sample, prm, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{len(sample)} seeded random pairs of the family ({cells:.3g} cells), "
+                      f"FP64 log-space, {threads} threads, {dt:.1f} s"}
+
+
+def run_reference(args, fam, prm, rank):
+    """--impl reference: the FP64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    threads = os.cpu_count() or 1
+    pl = list(fam.pairs())
+    rng = np.random.Generator(np.random.PCG64(args.seed + 100))
+    L = fam.lengths.astype(np.int64)
+    probe = [pl[i] for i in rng.permutation(len(pl))[:threads]]
+    t0 = time.perf_counter()
+    oracle.pairs(fam, probe, prm, threads=threads)
+    rate = sum(L[a] * L[b] for a, b in probe) / max(time.perf_counter() - t0, 1e-3)
+    step_cells = rate * 6.0          # about 6 s of host work per step
+    times, cells_done = [], []
+    for step in range(args.warmup + args.steps):
+        sample, c = [], 0.0
+        for i in rng.permutation(len(pl)):
+            if c >= step_cells:
+                break
+            sample.append(pl[i])
+            c += float(L[pl[i][0]] * L[pl[i][1]])
+        t0 = time.perf_counter()
+        oracle.pairs(fam, sample, prm, threads=threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            cells_done.append(c)
+    value = sum(cells_done) / sum(times) / 1e9
+    line = {
+        "impl": "reference", "metric": "posterior-stage GCUPS", "value": value, "unit": "GCUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: {CONFIG_DESC[args.config]}", "threshold": prm.threshold,
+                   "sample_per_step": "seeded random pairs, about 6 s of host work per step"},
+        "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"~{statistics.mean(cells_done):.3g} cells per step, FP64 log-space"},
+        "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    fam = synth.make_family(args.config, args.seed)
+    prm = synth.default_params(threshold=0.01, precision=args.precision)
+    if args.impl == "reference":
+        return run_reference(args, fam, prm, rank)
+
+    import torch
+    import paper_1512_07437_b300 as qp
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cells = fam.cells()
+    d_res = torch.from_numpy(fam.residues).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    params = qp.make_params(prm, device=local, stream=stream)
+
+    def step_dev():
+        return qp.qp_posteriors(d_res, fam.offsets, params, out_on_device=True)
+
+    for _ in range(max(3, args.warmup)):
+        step_dev().free()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident timing
+    times, kms, launches, fallbacks, nnz = [], [], 0, 0, 0
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step_dev()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            kms.append(r.kernel_ms[0])
+            fallbacks += r.n_fallback
+            # k_setup, k_encode, k_seqlogq, k_posterior_f32, k_scan_nnz, k_compact (+ k_posterior_f64)
+            launches += 6 + (1 if r.n_fallback else 0)
+            nnz = r.nnz
+            r.free()
+    torch.cuda.synchronize()
+    barrier()
+    ms = statistics.mean(times)
+    t_tot = sum(times) / 1e3
+    if world > 1:
+        t = torch.tensor([t_tot], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_tot = float(t.item())
+    value = cells * args.steps * world / t_tot / 1e9
+
+    # ---- end to end through the public API with host buffers
+    h_res = torch.from_numpy(fam.residues).pin_memory().numpy()
+    e2e_times = []
+    d2h = 0
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = qp.qp_posteriors(h_res, fam.offsets, params, out_on_device=False)
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = (8 * (r.n_pairs + 1) * 2 + 4 * r.n_rows + 8 * r.nnz + 12 * r.k * r.k + 28 * r.n_pairs)
+        r.free()
+    e2e_val = cells * world / statistics.mean(e2e_times) / 1e9
+    h2d = int(fam.residues.nbytes + fam.offsets.nbytes)
+
+    # ---- roofline of the dominant kernel (k_posterior_f32)
+    clocks = clk.summary()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    max_mhz = float(clocks["sm_max_mhz"] or peaks.get("sm_max_mhz", 2032.0))
+    peak_tops = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
+    kernel_ms = statistics.mean(kms)
+    achieved = cells * ALU_OPS_PER_CELL / (kernel_ms * 1e-3) / 1e12
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(f"{args.config}-{args.precision}")
+    except Exception:
+        pass
+    line = {
+        "metric": "posterior-stage GCUPS",
+        "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "f32" else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: {CONFIG_DESC[args.config]}", "seed": args.seed,
+                   "pairs": fam.n_pairs, "cells_per_step": cells, "threshold": prm.threshold,
+                   "combine": "rms", "precision": args.precision,
+                   "l2": "flushed (256 MiB write) before each timed step", "nnz": int(nnz),
+                   "fp64_fallback_pairs": fallbacks},
+        "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tissue/s",
+                     "frac": achieved / peak_tops, "traffic": traffic,
+                     "kernel": "k_posterior_f32" if args.precision == "f32" else "k_posterior_f64",
+                     "kernel_ms": kernel_ms,
+                     "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz",
+                     "ops_per_cell": ALU_OPS_PER_CELL},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(fam, prm, args.cpu_sample_s)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * qp.h -- C ABI of the all-pairs posterior stage (libqp.so, sm_103a).
+ *
+ * Operation (paper, Methods, stage I): for every pair of sequences of a
+ * family, posterior probability matrices are computed from a pair hidden
+ * Markov model and a partition function; maximum expected accuracy (MEA)
+ * alignment scores on those matrices give the pairwise distances that feed
+ * the guide tree.  The matrices are kept sparse (Methods, "Selective
+ * consistency", footnote: sparsity coefficient beta < 1).
+ *
+ * The paper prints neither models nor parameters.  This library computes,
+ * for each pair (x, y) with lengths m, n:
+ *   - the 5-state pair-HMM (M, X, Y, X2, Y2) forward/backward and the match
+ *     posterior P_hmm(i,j);
+ *   - the 3-state affine partition function forward/backward and the
+ *     aligned-pair posterior P_pf(i,j);
+ *   - the combination P(i,j) (root mean square by default);
+ *   - the sparse matrix {(i,j): P(i,j) >= threshold} in CSR form;
+ *   - the MEA score A = max over monotone matchings of sum P, and the
+ *     distance d = 1 - A / min(m, n).
+ *
+ * Conventions
+ *   Pairs: a < b, linear index p = a*k - a(a+1)/2 + (b - a - 1).  Rows of
+ *   pair p index sequence a (row i-1 <-> residue x_i), columns index
+ *   sequence b.  The pair (b, a) is the transpose.
+ *   Residues: ASCII letters of the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY
+ *   (lower case accepted).  Any other byte -> QP_EINVAL.
+ *   Ownership: inputs are borrowed for the duration of the call.  A
+ *   qp_result is owned by the library and released with qp_result_free.
+ *   Errors: every entry point returns a qp_status; qp_last_error() gives a
+ *   thread-local message for the last failure on the calling thread.
+ *   Streams: work is issued on params->stream (a cudaStream_t), or on a
+ *   library-owned stream of params->device when it is NULL.  qp_posteriors
+ *   returns after the results are complete on the device.
+ */
+#ifndef QP_H
+#define QP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QP_OK = 0,
+    QP_EINVAL = 1,      /* malformed family or parameters */
+    QP_ENOMEM = 2,      /* device or host allocation failed */
+    QP_ECUDA = 3,       /* a CUDA call failed (message has the CUDA error) */
+    QP_ETIMEOUT = 4,    /* a bounded wait ran out (server poll) */
+    QP_ECANCELLED = 5,  /* the request was cancelled or the server shut down */
+    QP_ENOTREADY = 6    /* server poll: the request has not finished yet */
+} qp_status;
+
+enum { QP_COMBINE_RMS = 0, QP_COMBINE_MEAN = 1, QP_COMBINE_HMM = 2, QP_COMBINE_PF = 3 };
+enum { QP_F32_SCALED = 0, QP_F64_PLAIN = 1 };
+
+/* A family of k sequences laid out as one buffer.
+ *   residues : concatenated ASCII residues, offsets[k] bytes; host memory,
+ *              or device memory of params->device when residues_on_device.
+ *   offsets  : HOST array of k+1 int64, offsets[0] = 0, strictly increasing
+ *              (every sequence non-empty).  2 <= k <= 46340. */
+typedef struct qp_family {
+    int32_t k;
+    int32_t residues_on_device;
+    const uint8_t* residues;
+    const int64_t* offsets;
+} qp_family;
+
+/* Model and run parameters (all host memory).
+ *   Pair-HMM: start distribution pi over (M, X, Y, X2, Y2); M->M = 1 - 2 d1 - 2 d2,
+ *   M->X = M->Y = delta1, M->X2 = M->Y2 = delta2, X->X = Y->Y = eps1,
+ *   X2->X2 = Y2->Y2 = eps2, every gap state returns to M; emit_pair[a*20+b]
+ *   = p(a,b) (sums to 1), emit_bg[a] = q(a) > 0 (sums to 1), end weights
+ *   end_w[s] >= 0.
+ *   Partition function: score[a*20+b] = s(a,b), weight exp(s/T); a gap of
+ *   length g weighs exp((gap_open + (g-1) gap_ext)/T); temperature T > 0;
+ *   end_gap_mode must be 0 (terminal gaps scored as internal ones).
+ *   combine: QP_COMBINE_*.  threshold: keep P >= threshold, 0 < threshold <= 1.
+ *   precision: QP_F32_SCALED (FP32 recurrences with power-of-two rescaling,
+ *   FP64 totals) or QP_F64_PLAIN (FP64 recurrences, one CTA per pair).
+ *   device: CUDA ordinal.  stream: cudaStream_t or NULL. */
+typedef struct qp_params {
+    double pi[5];
+    double delta1, eps1, delta2, eps2;
+    double emit_pair[400];
+    double emit_bg[20];
+    double end_w[5];
+    double score[400];
+    double gap_open, gap_ext, temperature;
+    int32_t end_gap_mode;
+    int32_t combine;
+    double threshold;
+    int32_t precision;
+    int32_t device;
+    void* stream;
+} qp_params;
+
+/* Results.  When on_device, every pointer is device memory of the call's
+ * device; otherwise host memory.  Layout:
+ *   pair_row_off [n_pairs+1] : row_ptr block of pair p starts at
+ *                              pair_row_off[p] and has m_a + 1 entries;
+ *   row_ptr      [n_rows]    : within pair p, CSR row r (residue x_{r+1})
+ *                              holds entries [row_ptr[o+r], row_ptr[o+r+1])
+ *                              counted from pair_nnz_off[p];
+ *   pair_nnz_off [n_pairs+1] : first entry of pair p in col / val;
+ *   col          [nnz]       : 0-based column (residue y_{c+1}), ascending
+ *                              within a row;
+ *   val          [nnz]       : P(i,j) as float;
+ *   val64        [nnz]       : P(i,j) as double (QP_F64_PLAIN only, else NULL);
+ *   dist, dist64 [k*k]       : symmetric MEA distances, zero diagonal;
+ *   mea          [n_pairs]   : MEA score A(m, n);
+ *   log_z_hmm    [n_pairs]   : natural log of the pair-HMM total probability;
+ *   log_z_pf     [n_pairs]   : natural log of the partition function;
+ *   pair_flags   [n_pairs]   : bit 0 set when an FP32 range guard fired and
+ *                              the pair was recomputed by the FP64 form; bits
+ *                              2.. name the guard;
+ *   kernel_ms[0..3]           : device time of the posterior kernel, the FP64
+ *                              kernel, the CSR compaction and the whole call;
+ *   n_fallback                : pairs recomputed by the FP64 form;
+ *   guard_info[12]            : the first FP32 range-guard event of the call
+ *                              (site, strip, step, lane, HMM exponent and its
+ *                              neighbour's, PF exponent and its neighbour's,
+ *                              m, n), all zero when no guard fired. */
+typedef struct qp_result {
+    int32_t k;
+    int32_t on_device;
+    int32_t precision;
+    int32_t device;
+    int64_t n_pairs;
+    int64_t n_rows;
+    int64_t nnz;
+    int64_t* pair_row_off;
+    int32_t* row_ptr;
+    int64_t* pair_nnz_off;
+    int32_t* col;
+    float* val;
+    double* val64;
+    float* dist;
+    double* dist64;
+    double* mea;
+    double* log_z_hmm;
+    double* log_z_pf;
+    int32_t* pair_flags;
+    double kernel_ms[4];
+    int64_t n_fallback;
+    int32_t guard_info[12];
+    void* owner_;            /* library bookkeeping; do not touch */
+} qp_result;
+
+/* All-pairs posterior stage of one family (Methods, stage I).
+ * On success *out holds a complete result (device or host per
+ * out_on_device).  Errors: QP_EINVAL (family/params), QP_ENOMEM, QP_ECUDA.
+ * On error *out is NULL. */
+int qp_posteriors(const qp_family* family, const qp_params* params,
+                  int32_t out_on_device, qp_result** out);
+
+/* Releases a result and everything it points to.  NULL is ignored. */
+void qp_result_free(qp_result* result);
+
+/* Serving loop (bulk processing of many families, Methods, "Other
+ * algorithmic improvements": bulk mode; memory limit by sparsity).
+ * A server owns one device stream and a worker thread.  Families submitted
+ * while others run are admitted as soon as their worst-case device memory
+ * fits in mem_budget bytes, and their pairs join the work already queued on
+ * the device.
+ *   qp_server_create : params as for qp_posteriors (precision must be
+ *                      QP_F32_SCALED); mem_budget > 0.
+ *   qp_server_submit : copies the family; returns a ticket.  QP_EINVAL for a
+ *                      malformed family or one that can never fit the budget.
+ *   qp_server_poll   : waits up to timeout_ms (0: no wait, <0: forever) for
+ *                      the ticket; QP_ENOTREADY / QP_ETIMEOUT when not done.
+ *                      The result is host-resident and owned by the caller.
+ *   qp_server_cancel : cancels a pending ticket (QP_ECANCELLED on poll).
+ *   qp_server_destroy: stops the worker, cancels pending work, frees memory. */
+typedef struct qp_server qp_server;
+int qp_server_create(const qp_params* params, size_t mem_budget, qp_server** out);
+int qp_server_submit(qp_server* server, const qp_family* family, uint64_t* ticket);
+int qp_server_poll(qp_server* server, uint64_t ticket, int32_t timeout_ms,
+                   qp_result** out);
+int qp_server_cancel(qp_server* server, uint64_t ticket);
+void qp_server_destroy(qp_server* server);
+
+/* Thread-local message of the last failure on the calling thread. */
+const char* qp_last_error(void);
+
+/* Library version string. */
+const char* qp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QP_H */

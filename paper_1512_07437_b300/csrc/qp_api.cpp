@@ -1,0 +1,668 @@
+// C ABI of the all-pairs posterior stage: validation, per-device context,
+// planning of the persistent launch, result assembly.
+#include "../../include/qp.h"
+#include "qp_internal.h"
+#include "qp_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+namespace qph {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(QP_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+const char* last_error() { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ buffers
+DevBuf::~DevBuf() { release(); }
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+cudaError_t DevBuf::ensure(size_t need) {
+    if (need <= bytes && ptr) return cudaSuccess;
+    release();
+    size_t want = std::max<size_t>(need, 256);
+    cudaError_t e = cudaMalloc(&ptr, want);
+    if (e != cudaSuccess) { ptr = nullptr; cudaGetLastError(); return e; }
+    bytes = want;
+    return cudaSuccess;
+}
+
+HostBuf::~HostBuf() { if (ptr) cudaFreeHost(ptr); }
+cudaError_t HostBuf::ensure(size_t need) {
+    if (need <= bytes && ptr) return cudaSuccess;
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMallocHost(&ptr, std::max<size_t>(need, 256));
+    if (e != cudaSuccess) { ptr = nullptr; cudaGetLastError(); return e; }
+    bytes = std::max<size_t>(need, 256);
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------ validation
+int validate_family(const qp_family* f) {
+    if (!f) return fail(QP_EINVAL, "family is NULL");
+    if (f->k < 2) return fail(QP_EINVAL, "family needs k >= 2 sequences (k = %d)", f->k);
+    if (f->k > kMaxK) return fail(QP_EINVAL, "k = %d exceeds the limit %d", f->k, kMaxK);
+    if (!f->offsets) return fail(QP_EINVAL, "offsets is NULL");
+    if (!f->residues) return fail(QP_EINVAL, "residues is NULL");
+    if (f->offsets[0] != 0) return fail(QP_EINVAL, "offsets[0] must be 0");
+    for (int a = 0; a < f->k; ++a) {
+        const int64_t L = f->offsets[a + 1] - f->offsets[a];
+        if (L < 1) return fail(QP_EINVAL, "sequence %d is empty", a);
+        if (L > kMaxLen) return fail(QP_EINVAL, "sequence %d is longer than %lld", a, (long long)kMaxLen);
+    }
+    return QP_OK;
+}
+
+static bool near1(double s) { return std::fabs(s - 1.0) <= 1e-9; }
+
+int validate_params(const qp_params* p) {
+    if (!p) return fail(QP_EINVAL, "params is NULL");
+    double s = 0;
+    for (int i = 0; i < 5; ++i) {
+        if (!(p->pi[i] >= 0.0)) return fail(QP_EINVAL, "pi[%d] must be >= 0", i);
+        s += p->pi[i];
+    }
+    if (!near1(s)) return fail(QP_EINVAL, "pi must sum to 1 (sum %.12g)", s);
+    if (!(p->delta1 >= 0 && p->delta2 >= 0 && 2 * p->delta1 + 2 * p->delta2 <= 1.0))
+        return fail(QP_EINVAL, "need delta1, delta2 >= 0 and 2 delta1 + 2 delta2 <= 1");
+    if (!(p->eps1 >= 0 && p->eps1 < 1 && p->eps2 >= 0 && p->eps2 < 1))
+        return fail(QP_EINVAL, "eps1, eps2 must be in [0, 1)");
+    s = 0;
+    for (int i = 0; i < 400; ++i) {
+        if (!(p->emit_pair[i] >= 0.0)) return fail(QP_EINVAL, "emit_pair[%d] must be >= 0", i);
+        s += p->emit_pair[i];
+    }
+    if (!near1(s)) return fail(QP_EINVAL, "emit_pair must sum to 1 (sum %.12g)", s);
+    s = 0;
+    for (int i = 0; i < 20; ++i) {
+        if (!(p->emit_bg[i] > 0.0)) return fail(QP_EINVAL, "emit_bg[%d] must be > 0", i);
+        s += p->emit_bg[i];
+    }
+    if (!near1(s)) return fail(QP_EINVAL, "emit_bg must sum to 1 (sum %.12g)", s);
+    double te = 0;
+    for (int i = 0; i < 5; ++i) {
+        if (!(p->end_w[i] >= 0.0 && std::isfinite(p->end_w[i])))
+            return fail(QP_EINVAL, "end_w[%d] must be finite and >= 0", i);
+        te += p->end_w[i];
+    }
+    if (!(te > 0)) return fail(QP_EINVAL, "end_w must not be all zero");
+    for (int i = 0; i < 400; ++i)
+        if (!std::isfinite(p->score[i])) return fail(QP_EINVAL, "score[%d] is not finite", i);
+    if (!(p->temperature > 0 && std::isfinite(p->temperature))) return fail(QP_EINVAL, "temperature must be > 0");
+    if (!std::isfinite(p->gap_open) || !std::isfinite(p->gap_ext)) return fail(QP_EINVAL, "gap penalties must be finite");
+    if (p->end_gap_mode != 0) return fail(QP_EINVAL, "only end_gap_mode 0 is supported");
+    if (p->combine < 0 || p->combine > 3) return fail(QP_EINVAL, "combine must be one of QP_COMBINE_*");
+    if (!(p->threshold > 0.0 && p->threshold <= 1.0)) return fail(QP_EINVAL, "threshold must be in (0, 1]");
+    if (p->precision != QP_F32_SCALED && p->precision != QP_F64_PLAIN)
+        return fail(QP_EINVAL, "precision must be QP_F32_SCALED or QP_F64_PLAIN");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "cudaGetDeviceCount"); }
+    if (p->device < 0 || p->device >= ndev) return fail(QP_EINVAL, "device %d does not exist (%d devices)", p->device, ndev);
+    return QP_OK;
+}
+
+// ------------------------------------------------------------------ derived constants
+void make_raw(const qp_params* p, qpk::RawParams* r) {
+    memcpy(r->pi, p->pi, sizeof r->pi);
+    r->delta1 = p->delta1; r->eps1 = p->eps1; r->delta2 = p->delta2; r->eps2 = p->eps2;
+    memcpy(r->emit_pair, p->emit_pair, sizeof r->emit_pair);
+    memcpy(r->emit_bg, p->emit_bg, sizeof r->emit_bg);
+    memcpy(r->end_w, p->end_w, sizeof r->end_w);
+    memcpy(r->score, p->score, sizeof r->score);
+    r->gap_open = p->gap_open; r->gap_ext = p->gap_ext; r->temperature = p->temperature;
+    r->threshold = p->threshold;
+    r->combine = p->combine;
+}
+
+void make_coef(const qp_params* p, qpk::Coef* c) {
+    c->tMM = (float)(1.0 - 2.0 * p->delta1 - 2.0 * p->delta2);
+    c->d1 = (float)p->delta1; c->d2 = (float)p->delta2;
+    c->e1 = (float)p->eps1; c->e2 = (float)p->eps2;
+    c->c1 = (float)(1.0 - p->eps1); c->c2 = (float)(1.0 - p->eps2);
+    c->Wo = (float)std::exp(p->gap_open / p->temperature);
+    c->We = (float)std::exp(p->gap_ext / p->temperature);
+    for (int s = 0; s < 5; ++s) { c->pi[s] = (float)p->pi[s]; c->tau[s] = (float)p->end_w[s]; }
+    c->theta = (float)p->threshold;
+    switch (p->combine) {
+        case QP_COMBINE_RMS: c->combine = 0; c->wh = 0.5f; c->wp = 0.5f; break;
+        case QP_COMBINE_MEAN: c->combine = 1; c->wh = 0.5f; c->wp = 0.5f; break;
+        case QP_COMBINE_HMM: c->combine = 1; c->wh = 1.f; c->wp = 0.f; break;
+        default: c->combine = 1; c->wh = 0.f; c->wp = 1.f; break;
+    }
+}
+
+int row_capacity(const qp_params* p, int max_len) {
+    // a row's combined posteriors sum to at most sqrt(2) (rms) or 1, so at most
+    // that many / theta entries reach the threshold
+    const double bound = (p->combine == QP_COMBINE_RMS) ? std::sqrt(2.0) : 1.0;
+    const double c = std::floor(bound / p->threshold) + 2.0;
+    const double lim = (double)max_len + 1.0;
+    return (int)std::min(c, lim);
+}
+
+// ------------------------------------------------------------------ planning
+std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
+    auto pl = std::make_shared<Plan>();
+    pl->k = k;
+    pl->lens.resize(k);
+    int maxL = 0;
+    for (int a = 0; a < k; ++a) {
+        pl->lens[a] = off[a + 1] - off[a];
+        maxL = std::max<int>(maxL, (int)pl->lens[a]);
+    }
+    pl->max_len = maxL;
+    const int64_t P = (int64_t)k * (k - 1) / 2;
+    pl->n_pairs = P;
+    pl->pairs.resize(P);
+    pl->row_off.resize(P + 1);
+    pl->strip_off.resize(P + 1);
+    pl->work.resize(P);
+    int64_t ro = 0, so = 0, q = 0;
+    int64_t bst = 0, bex = 0;
+    double work_sum = 0;
+    std::vector<std::pair<int64_t, int32_t>> order(P);
+    for (int a = 0; a < k; ++a) {
+        for (int b = a + 1; b < k; ++b, ++q) {
+            const int m = (int)pl->lens[a], n = (int)pl->lens[b];
+            pl->pairs[q] = make_int2(a, b);
+            pl->row_off[q] = ro;
+            pl->strip_off[q] = so;
+            const int ns = (m + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
+            ro += m + 1;
+            so += ns;
+            bst = std::max<int64_t>(bst, (int64_t)ns * qpk::kStripRows * (n + 32));
+            bex = std::max<int64_t>(bex, (int64_t)ns * ((n + 32 + qpk::kC - 1) / qpk::kC) * 32);
+            // swept lane-steps of the pair: strips x (columns + skew) x rows per lane
+            const int64_t w = (int64_t)(ns - 1) * 4 * (n + 32) +
+                              (int64_t)((m + 1 - (ns - 1) * qpk::kStripRows + 31) / 32) * (n + 32);
+            pl->work[q] = w;
+            order[q] = std::make_pair(-w, (int32_t)q);
+            work_sum += (double)w;
+        }
+    }
+    pl->row_off[P] = ro;
+    pl->strip_off[P] = so;
+    pl->n_rows = ro;
+    pl->n_strips = so;
+    pl->bst_stride = bst;
+    pl->bex_stride = bex;
+    pl->bnd_stride = 2 * (int64_t)(maxL + 1);
+    pl->work_sum = work_sum;
+    // longest first keeps the persistent workers balanced (greedy LPT)
+    std::stable_sort(order.begin(), order.end());
+    pl->order.resize(P);
+    for (int64_t i = 0; i < P; ++i) pl->order[i] = order[i].second;
+    return pl;
+}
+
+// ------------------------------------------------------------------ device context
+static std::mutex g_ctx_mu;
+static std::map<int, std::unique_ptr<Context>> g_ctx;
+
+Context* get_context(int device, int* status) {
+    std::lock_guard<std::mutex> g(g_ctx_mu);
+    auto it = g_ctx.find(device);
+    if (it != g_ctx.end()) return it->second.get();
+    std::unique_ptr<Context> c(new Context());
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { *status = cuda_fail(e, "cudaSetDevice"); return nullptr; }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { *status = cuda_fail(e, "cudaGetDeviceProperties"); return nullptr; }
+    c->sm_count = prop.multiProcessorCount;
+    c->cc_major = prop.major; c->cc_minor = prop.minor;
+    if (prop.major < 10) {
+        *status = fail(QP_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a", device, prop.major, prop.minor);
+        return nullptr;
+    }
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { *status = cuda_fail(e, "cudaStreamCreate"); return nullptr; }
+    for (auto& ev : c->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) { *status = cuda_fail(e, "cudaEventCreate"); return nullptr; }
+    }
+    int bps = 0;
+    qpk::posterior_f32_occupancy(4, &bps);
+    c->f32_blocks_per_sm = std::max(1, std::min(bps, 4));
+    int bps64 = 0;
+    qpk::posterior_f64_occupancy(&bps64);
+    c->f64_blocks_per_sm = std::max(1, std::min(bps64, 2));
+    Context* raw = c.get();
+    g_ctx[device] = std::move(c);
+    return raw;
+}
+
+std::shared_ptr<Plan> Context::plan_for(int k, const int64_t* off, int* status) {
+    // cache keyed by the length vector
+    std::vector<int64_t> lens(k);
+    for (int a = 0; a < k; ++a) lens[a] = off[a + 1] - off[a];
+    for (auto& pl : plans)
+        if (pl->k == k && pl->lens == lens) return pl;
+    auto pl = build_plan(k, off);
+    const int64_t P = pl->n_pairs;
+    std::vector<int2> items(P);
+    for (int64_t i = 0; i < P; ++i) items[i] = make_int2(0, pl->order[i]);
+    cudaError_t e;
+    if ((e = pl->d_pairs.ensure(sizeof(int2) * P)) != cudaSuccess ||
+        (e = pl->d_row_off.ensure(sizeof(int64_t) * (P + 1))) != cudaSuccess ||
+        (e = pl->d_strip_off.ensure(sizeof(int64_t) * (P + 1))) != cudaSuccess ||
+        (e = pl->d_items.ensure(sizeof(int2) * P)) != cudaSuccess) {
+        *status = fail(QP_ENOMEM, "plan allocation failed: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    cudaMemcpy(pl->d_pairs.ptr, pl->pairs.data(), sizeof(int2) * P, cudaMemcpyHostToDevice);
+    cudaMemcpy(pl->d_row_off.ptr, pl->row_off.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(pl->d_strip_off.ptr, pl->strip_off.data(), sizeof(int64_t) * (P + 1), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(pl->d_items.ptr, items.data(), sizeof(int2) * P, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { *status = cuda_fail(e, "plan upload"); return nullptr; }
+    plans.push_back(pl);
+    if (plans.size() > 8) plans.erase(plans.begin());
+    return pl;
+}
+
+// ------------------------------------------------------------------ one family
+struct ResultOwner {
+    int device = 0;
+    bool on_device = true;
+    void* dev_a = nullptr;   // fixed-size part
+    void* dev_b = nullptr;   // col / val part
+    void* host = nullptr;
+};
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
+               qp_result** out) {
+    cudaError_t e;
+    const int k = f->k;
+    cudaStream_t st = prm->stream ? (cudaStream_t)prm->stream : C->stream;
+    int status = QP_OK;
+    auto pl = C->plan_for(k, f->offsets, &status);
+    if (!pl) return status;
+    const int64_t P = pl->n_pairs;
+    const int64_t total_res = f->offsets[k];
+    const bool f64 = prm->precision == QP_F64_PLAIN;
+    const int cap = row_capacity(prm, pl->max_len);
+
+    e = cudaEventRecord(C->ev[0], st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    // ---- inputs
+    if ((e = C->codes.ensure(total_res)) != cudaSuccess ||
+        (!f->residues_on_device && (e = C->ascii.ensure(total_res)) != cudaSuccess) ||
+        (e = C->off.ensure(sizeof(int64_t) * (k + 1))) != cudaSuccess ||
+        (e = C->seqlogq.ensure(sizeof(double) * k)) != cudaSuccess ||
+        (e = C->cst.ensure(sizeof(qpk::Consts))) != cudaSuccess ||
+        (e = C->status.ensure(sizeof(qpk::Status))) != cudaSuccess ||
+        (e = C->fam.ensure(sizeof(qpk::FamDesc))) != cudaSuccess ||
+        (e = C->h_status.ensure(sizeof(qpk::Status))) != cudaSuccess ||
+        (e = C->h_fam.ensure(sizeof(qpk::FamDesc))) != cudaSuccess ||
+        (e = C->h_off.ensure(sizeof(int64_t) * (k + 1))) != cudaSuccess)
+        return fail(QP_ENOMEM, "workspace allocation failed: %s", cudaGetErrorString(e));
+    memcpy(C->h_off.ptr, f->offsets, sizeof(int64_t) * (k + 1));
+    cudaMemcpyAsync(C->off.ptr, C->h_off.ptr, sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, st);
+    const uint8_t* d_ascii = f->residues;
+    if (!f->residues_on_device) {
+        e = cudaMemcpyAsync(C->ascii.ptr, f->residues, total_res, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy residues");
+        d_ascii = (const uint8_t*)C->ascii.ptr;
+    }
+    cudaMemsetAsync(C->status.ptr, 0, sizeof(qpk::Status), st);
+    qpk::RawParams raw;
+    make_raw(prm, &raw);
+    if ((e = qpk::launch_setup(&raw, (qpk::Consts*)C->cst.ptr, st)) != cudaSuccess) return cuda_fail(e, "k_setup");
+    if ((e = qpk::launch_encode(d_ascii, (uint8_t*)C->codes.ptr, total_res, (const int64_t*)C->off.ptr, k,
+                                (double*)C->seqlogq.ptr, (const qpk::Consts*)C->cst.ptr,
+                                (qpk::Status*)C->status.ptr, st)) != cudaSuccess)
+        return cuda_fail(e, "k_encode");
+
+    // ---- result, fixed part
+    ResultOwner* own = new ResultOwner();
+    own->device = C->device;
+    auto bail = [&](int code) {
+        if (own->dev_a) cudaFreeAsync(own->dev_a, st);
+        if (own->dev_b) cudaFreeAsync(own->dev_b, st);
+        cudaStreamSynchronize(st);
+        delete own;
+        return code;
+    };
+    size_t o_pro, o_rp, o_pno, o_dist, o_d64, o_mea, o_lh, o_lp, o_fl, sz = 0;
+    o_pro = sz; sz += align_up(sizeof(int64_t) * (P + 1));
+    o_rp = sz;  sz += align_up(sizeof(int32_t) * pl->n_rows);
+    o_pno = sz; sz += align_up(sizeof(int64_t) * (P + 1));
+    o_dist = sz; sz += align_up(sizeof(float) * (size_t)k * k);
+    o_d64 = sz; sz += align_up(sizeof(double) * (size_t)k * k);
+    o_mea = sz; sz += align_up(sizeof(double) * P);
+    o_lh = sz;  sz += align_up(sizeof(double) * P);
+    o_lp = sz;  sz += align_up(sizeof(double) * P);
+    o_fl = sz;  sz += align_up(sizeof(int32_t) * P);
+    e = cudaMallocAsync(&own->dev_a, sz, st);
+    if (e != cudaSuccess) { own->dev_a = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation (%zu bytes) failed", sz)); }
+    char* A = (char*)own->dev_a;
+    cudaMemcpyAsync(A + o_pro, pl->d_row_off.ptr, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(A + o_dist, 0, sizeof(float) * (size_t)k * k, st);
+    cudaMemsetAsync(A + o_d64, 0, sizeof(double) * (size_t)k * k, st);
+    cudaMemsetAsync(A + o_fl, 0, sizeof(int32_t) * P, st);
+
+    // ---- workspace
+    if ((e = C->row_cnt.ensure(sizeof(int32_t) * pl->n_rows)) != cudaSuccess ||
+        (e = C->chunk_off.ensure(sizeof(int64_t) * pl->n_strips)) != cudaSuccess ||
+        (e = C->pair_nnz.ensure(sizeof(int64_t) * P)) != cudaSuccess ||
+        (e = C->fallback.ensure(sizeof(int2) * P)) != cudaSuccess)
+        return bail(fail(QP_ENOMEM, "workspace allocation failed: %s", cudaGetErrorString(e)));
+    {
+        // pool estimate; grown and rerun on overflow
+        const double per_row = std::min<double>(pl->max_len + 1.0, 4.0 + 0.04 / prm->threshold);
+        int64_t est = (int64_t)(per_row * (double)pl->n_rows) + 4096;
+        est = std::max<int64_t>(est, C->pool_hint);
+        if ((e = C->pool.ensure(sizeof(int2) * est)) != cudaSuccess)
+            return bail(fail(QP_ENOMEM, "pool allocation failed"));
+        C->pool_cap = (int64_t)(C->pool.bytes / sizeof(int2));
+        if (f64 && (e = C->pool64.ensure(sizeof(double) * C->pool_cap)) != cudaSuccess)
+            return bail(fail(QP_ENOMEM, "pool allocation failed"));
+    }
+
+    qpk::Status* d_status = (qpk::Status*)C->status.ptr;
+    qpk::FamDesc fd;
+    memset(&fd, 0, sizeof fd);
+    fd.codes = (const uint8_t*)C->codes.ptr;
+    fd.seq_off = (const int64_t*)C->off.ptr;
+    fd.seq_logq = (const double*)C->seqlogq.ptr;
+    fd.pairs = (const int2*)pl->d_pairs.ptr;
+    fd.pair_row_off = (const int64_t*)pl->d_row_off.ptr;
+    fd.pair_strip_off = (const int64_t*)pl->d_strip_off.ptr;
+    fd.k = k;
+    fd.row_cnt = (int32_t*)C->row_cnt.ptr;
+    fd.chunk_off = (int64_t*)C->chunk_off.ptr;
+    fd.pair_nnz = (int64_t*)C->pair_nnz.ptr;
+    fd.mea = (double*)(A + o_mea);
+    fd.logz_h = (double*)(A + o_lh);
+    fd.logz_p = (double*)(A + o_lp);
+    fd.dist = (float*)(A + o_dist);
+    fd.dist64 = (double*)(A + o_d64);
+    fd.pair_flags = (int32_t*)(A + o_fl);
+    fd.pool_used = &d_status->pool_used;
+    fd.pool_base = 0;
+    fd.n_done = nullptr;
+
+    qpk::Problem Pb;
+    memset(&Pb, 0, sizeof Pb);
+    make_coef(prm, &Pb.cf);
+    Pb.cst = (const qpk::Consts*)C->cst.ptr;
+    Pb.fams = (const qpk::FamDesc*)C->fam.ptr;
+    Pb.items = (const int2*)pl->d_items.ptr;
+    Pb.n_work = (int32_t)P;
+    Pb.cap = cap;
+    Pb.status = d_status;
+    Pb.fallback = (int2*)C->fallback.ptr;
+    Pb.max_len = pl->max_len;
+
+    qpk::Status hs;
+    memset(&hs, 0, sizeof hs);
+    for (int attempt = 0;; ++attempt) {
+        fd.pool_cap = C->pool_cap;
+        memcpy(C->h_fam.ptr, &fd, sizeof fd);
+        cudaMemcpyAsync(C->fam.ptr, C->h_fam.ptr, sizeof fd, cudaMemcpyHostToDevice, st);
+        Pb.pool = (int2*)C->pool.ptr;
+        Pb.pool64 = f64 ? (double*)C->pool64.ptr : nullptr;
+        if (attempt > 0) {
+            // rerun after a pool overflow: clear the counters, keep the rest
+            cudaMemsetAsync(&d_status->pool_used, 0, sizeof(unsigned long long), st);
+            cudaMemsetAsync(&d_status->pool_overflow, 0, sizeof(int32_t) * 2, st);
+            cudaMemsetAsync(&d_status->work_f32, 0, sizeof(int32_t) * 2, st);
+            cudaMemsetAsync(A + o_fl, 0, sizeof(int32_t) * P, st);
+        }
+        cudaEventRecord(C->ev[1], st);
+        int f64_grid = 0;
+        if (!f64) {
+            const int wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 4;
+            const int bps = C->tune.blocks_per_sm > 0 ? C->tune.blocks_per_sm : C->f32_blocks_per_sm;
+            int64_t grid = (int64_t)C->sm_count * bps;
+            grid = std::min<int64_t>(grid, (P + wpb - 1) / wpb);
+            grid = std::max<int64_t>(grid, 1);
+            const int64_t warps = grid * wpb;
+            if ((e = C->bst.ensure(sizeof(float2) * pl->bst_stride * warps)) != cudaSuccess ||
+                (e = C->bex.ensure(sizeof(int2) * pl->bex_stride * warps)) != cudaSuccess ||
+                (e = C->bnd.ensure(sizeof(float4) * pl->bnd_stride * warps)) != cudaSuccess ||
+                (e = C->stg.ensure(sizeof(int2) * (int64_t)qpk::kStripRows * cap * warps)) != cudaSuccess)
+                return bail(fail(QP_ENOMEM, "FP32 scratch allocation failed"));
+            Pb.bst = (float2*)C->bst.ptr; Pb.bst_stride = pl->bst_stride;
+            Pb.bex = (int2*)C->bex.ptr; Pb.bex_stride = pl->bex_stride;
+            Pb.bnd = (float4*)C->bnd.ptr; Pb.bnd_stride = pl->bnd_stride;
+            Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = (int64_t)qpk::kStripRows * cap;
+            if ((e = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st)) != cudaSuccess)
+                return bail(cuda_fail(e, "k_posterior_f32 launch"));
+            cudaEventRecord(C->ev[2], st);
+            e = cudaMemcpyAsync(C->h_status.ptr, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return bail(cuda_fail(e, "k_posterior_f32"));
+            memcpy(&hs, C->h_status.ptr, sizeof hs);
+            if (hs.bad_residue)
+                return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
+            f64_grid = hs.n_fallback > 0 ? std::min<int>(hs.n_fallback, C->sm_count * C->f64_blocks_per_sm) : 0;
+            Pb.f64_all = 0;
+        } else {
+            cudaEventRecord(C->ev[2], st);
+            f64_grid = (int)std::min<int64_t>(P, (int64_t)C->sm_count * C->f64_blocks_per_sm);
+            Pb.f64_all = 1;
+        }
+        if (f64_grid > 0) {
+            const int64_t L = pl->max_len + 1;
+            const int64_t db = L * L;
+            if ((e = C->d_b.ensure(sizeof(double2) * db * f64_grid)) != cudaSuccess ||
+                (e = C->d_diag.ensure(sizeof(double) * 3 * qpk::kNS * L * f64_grid)) != cudaSuccess ||
+                (e = C->d_cnt.ensure(sizeof(int32_t) * (5 * L + 8) * f64_grid)) != cudaSuccess ||
+                (e = C->d_stg.ensure(sizeof(int2) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess ||
+                (e = C->d_stg64.ensure(sizeof(double) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess)
+                return bail(fail(QP_ENOMEM, "FP64 scratch allocation failed"));
+            Pb.d_b = (double2*)C->d_b.ptr; Pb.d_b_stride = db;
+            Pb.d_diag = (double*)C->d_diag.ptr; Pb.d_diag_stride = 3 * qpk::kNS * L;
+            Pb.d_cnt = (int32_t*)C->d_cnt.ptr; Pb.d_cnt_stride = 5 * L + 8;
+            Pb.d_stg = (int2*)C->d_stg.ptr; Pb.d_stg64 = (double*)C->d_stg64.ptr;
+            Pb.d_stg_stride = (int64_t)pl->max_len * cap;
+            if ((e = qpk::launch_posterior_f64(Pb, f64_grid, st)) != cudaSuccess)
+                return bail(cuda_fail(e, "k_posterior_f64 launch"));
+        }
+        cudaEventRecord(C->ev[3], st);
+        e = cudaMemcpyAsync(C->h_status.ptr, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "posterior kernels"));
+        memcpy(&hs, C->h_status.ptr, sizeof hs);
+        if (hs.bad_residue)
+            return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
+        if (hs.stage_overflow) return bail(fail(QP_ECUDA, "internal: a row exceeded its entry capacity"));
+        if (!hs.pool_overflow) break;
+        if (attempt >= 2) return bail(fail(QP_ENOMEM, "the entry pool kept overflowing"));
+        // grow the pool to what was asked for, and run again
+        const int64_t need = (int64_t)(hs.pool_used * 5 / 4) + 4096;
+        C->pool_hint = need;
+        if ((e = C->pool.ensure(sizeof(int2) * need)) != cudaSuccess ||
+            (f64 && (e = C->pool64.ensure(sizeof(double) * need)) != cudaSuccess))
+            return bail(fail(QP_ENOMEM, "pool allocation (%lld entries) failed", (long long)need));
+        C->pool_cap = (int64_t)(C->pool.bytes / sizeof(int2));
+    }
+    const int64_t nnz_bound = (int64_t)hs.pool_used;
+    // ---- CSR assembly
+    const size_t ob_col = 0, ob_val = align_up(sizeof(int32_t) * nnz_bound),
+                 ob_v64 = ob_val + align_up(sizeof(float) * nnz_bound);
+    const size_t szb = ob_v64 + (f64 ? align_up(sizeof(double) * nnz_bound) : 0);
+    e = cudaMallocAsync(&own->dev_b, std::max<size_t>(szb, 256), st);
+    if (e != cudaSuccess) { own->dev_b = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation failed")); }
+    char* B = (char*)own->dev_b;
+    int32_t* d_col = (int32_t*)(B + ob_col);
+    float* d_val = (float*)(B + ob_val);
+    double* d_val64 = f64 ? (double*)(B + ob_v64) : nullptr;
+    if ((e = qpk::launch_scan_nnz(fd.pair_nnz, P, (int64_t*)(A + o_pno), st)) != cudaSuccess ||
+        (e = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
+                                 fd.chunk_off, (const int2*)C->pool.ptr, Pb.pool64, P, (int64_t*)(A + o_pno),
+                                 (int32_t*)(A + o_rp), d_col, d_val, d_val64, st)) != cudaSuccess)
+        return bail(cuda_fail(e, "CSR assembly"));
+    cudaEventRecord(C->ev[4], st);
+    int64_t nnz = 0;
+    e = cudaMemcpyAsync(C->h_status.ptr, A + o_pno + sizeof(int64_t) * P, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "CSR assembly"));
+    memcpy(&nnz, C->h_status.ptr, sizeof nnz);
+
+    qp_result* r = (qp_result*)calloc(1, sizeof(qp_result));
+    if (!r) return bail(fail(QP_ENOMEM, "host allocation failed"));
+    r->k = k;
+    r->on_device = 1;
+    r->precision = prm->precision;
+    r->device = C->device;
+    r->n_pairs = P;
+    r->n_rows = pl->n_rows;
+    r->nnz = nnz;
+    r->pair_row_off = (int64_t*)(A + o_pro);
+    r->row_ptr = (int32_t*)(A + o_rp);
+    r->pair_nnz_off = (int64_t*)(A + o_pno);
+    r->col = d_col;
+    r->val = d_val;
+    r->val64 = d_val64;
+    r->dist = (float*)(A + o_dist);
+    r->dist64 = (double*)(A + o_d64);
+    r->mea = (double*)(A + o_mea);
+    r->log_z_hmm = (double*)(A + o_lh);
+    r->log_z_pf = (double*)(A + o_lp);
+    r->pair_flags = (int32_t*)(A + o_fl);
+    r->n_fallback = f64 ? 0 : hs.n_fallback;
+    for (int i = 0; i < 10; ++i) r->guard_info[i] = hs.diag[i];
+    float ms = 0;
+    cudaEventElapsedTime(&ms, C->ev[1], C->ev[2]); r->kernel_ms[0] = ms;
+    cudaEventElapsedTime(&ms, C->ev[2], C->ev[3]); r->kernel_ms[1] = ms;
+    cudaEventElapsedTime(&ms, C->ev[3], C->ev[4]); r->kernel_ms[2] = ms;
+    cudaEventElapsedTime(&ms, C->ev[0], C->ev[4]); r->kernel_ms[3] = ms;
+    r->owner_ = own;
+    if (!out_on_device) {
+        int rc = to_host(r, st);
+        if (rc != QP_OK) { qp_result_free(r); return rc; }
+    }
+    *out = r;
+    return QP_OK;
+}
+
+int to_host(qp_result* r, cudaStream_t st) {
+    ResultOwner* own = (ResultOwner*)r->owner_;
+    const int64_t P = r->n_pairs;
+    const size_t k2 = (size_t)r->k * r->k;
+    struct Part { void** field; size_t bytes; };
+    Part parts[] = {
+        {(void**)&r->pair_row_off, sizeof(int64_t) * (P + 1)},
+        {(void**)&r->row_ptr, sizeof(int32_t) * r->n_rows},
+        {(void**)&r->pair_nnz_off, sizeof(int64_t) * (P + 1)},
+        {(void**)&r->col, sizeof(int32_t) * r->nnz},
+        {(void**)&r->val, sizeof(float) * r->nnz},
+        {(void**)&r->val64, r->val64 ? sizeof(double) * r->nnz : 0},
+        {(void**)&r->dist, sizeof(float) * k2},
+        {(void**)&r->dist64, sizeof(double) * k2},
+        {(void**)&r->mea, sizeof(double) * P},
+        {(void**)&r->log_z_hmm, sizeof(double) * P},
+        {(void**)&r->log_z_pf, sizeof(double) * P},
+        {(void**)&r->pair_flags, sizeof(int32_t) * P},
+    };
+    size_t tot = 0;
+    for (auto& p : parts) tot += align_up(p.bytes);
+    char* h = (char*)malloc(std::max<size_t>(tot, 64));
+    if (!h) return fail(QP_ENOMEM, "host result allocation (%zu bytes) failed", tot);
+    size_t o = 0;
+    cudaError_t e = cudaSuccess;
+    for (auto& p : parts) {
+        if (*p.field) {
+            if (p.bytes) {
+                e = cudaMemcpyAsync(h + o, *p.field, p.bytes, cudaMemcpyDeviceToHost, st);
+                if (e != cudaSuccess) break;
+            }
+            *p.field = h + o;
+        }
+        o += align_up(p.bytes);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { free(h); return cuda_fail(e, "copy result to host"); }
+    if (own->dev_a) cudaFreeAsync(own->dev_a, st);
+    if (own->dev_b) cudaFreeAsync(own->dev_b, st);
+    own->dev_a = own->dev_b = nullptr;
+    own->host = h;
+    own->on_device = false;
+    r->on_device = 0;
+    return QP_OK;
+}
+
+void free_result(qp_result* r) {
+    if (!r) return;
+    ResultOwner* own = (ResultOwner*)r->owner_;
+    if (own) {
+        if (own->dev_a || own->dev_b) {
+            int cur = 0, rc = 0;
+            cudaGetDevice(&cur);
+            cudaSetDevice(own->device);
+            Context* C = get_context(own->device, &rc);
+            cudaStream_t s = C ? C->stream : nullptr;
+            if (own->dev_a) cudaFreeAsync(own->dev_a, s);
+            if (own->dev_b) cudaFreeAsync(own->dev_b, s);
+            cudaSetDevice(cur);
+        }
+        free(own->host);
+        delete own;
+    }
+    free(r);
+}
+
+}  // namespace qph
+
+// ================================================================== C ABI
+extern "C" {
+
+int qp_posteriors(const qp_family* family, const qp_params* params, int32_t out_on_device,
+                  qp_result** out) {
+    using namespace qph;
+    if (!out) return fail(QP_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_family(family);
+    if (rc != QP_OK) return rc;
+    rc = validate_params(params);
+    if (rc != QP_OK) return rc;
+    cudaError_t e = cudaSetDevice(params->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    Context* C = get_context(params->device, &rc);
+    if (!C) return rc;
+    std::lock_guard<std::mutex> g(C->mu);
+    return run_family(C, family, params, out_on_device, out);
+}
+
+void qp_result_free(qp_result* result) { qph::free_result(result); }
+
+const char* qp_last_error(void) { return qph::last_error(); }
+
+const char* qp_version(void) { return "qp-b300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Host-side internals of libqp: device context, plans, buffers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qp.h"
+#include "qp_internal.h"
+
+namespace qph {
+
+constexpr int kMaxK = 46340;            // k(k-1)/2 stays below 2^30
+constexpr int64_t kMaxLen = 1 << 20;    // per-sequence length limit
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf();
+    void release();
+    cudaError_t ensure(size_t need);    // grow-only; contents are not kept
+};
+
+struct HostBuf {                        // pinned host memory
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    HostBuf() = default;
+    HostBuf(const HostBuf&) = delete;
+    HostBuf& operator=(const HostBuf&) = delete;
+    ~HostBuf();
+    cudaError_t ensure(size_t need);
+};
+
+// Work plan of one family shape (the vector of sequence lengths).
+struct Plan {
+    int k = 0;
+    std::vector<int64_t> lens;
+    int max_len = 0;
+    int64_t n_pairs = 0, n_rows = 0, n_strips = 0;
+    int64_t bst_stride = 0, bex_stride = 0, bnd_stride = 0;   // per-warp FP32 scratch
+    std::vector<int2> pairs;
+    std::vector<int64_t> row_off, strip_off;
+    std::vector<int32_t> order;          // pair ids, longest first
+    std::vector<int64_t> work;           // swept lane-steps per pair
+    double work_sum = 0;
+    DevBuf d_pairs, d_row_off, d_strip_off, d_items;
+};
+
+struct LaunchOverride {                  // autotuner / benchmark knobs
+    int warps_per_block = 0;
+    int blocks_per_sm = 0;
+};
+
+struct Context {
+    int device = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    int f32_blocks_per_sm = 3;
+    int f64_blocks_per_sm = 2;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev[6] = {};
+    std::mutex mu;
+    std::vector<std::shared_ptr<Plan>> plans;
+    // workspace (grow-only)
+    DevBuf ascii, codes, off, seqlogq, cst, status, fam;
+    DevBuf row_cnt, chunk_off, pair_nnz, fallback, pool, pool64;
+    DevBuf bst, bex, bnd, stg;
+    DevBuf d_b, d_diag, d_cnt, d_stg, d_stg64;
+    HostBuf h_status, h_off, h_fam;
+    int64_t pool_cap = 0;
+    int64_t pool_hint = 0;
+    LaunchOverride tune;
+    std::shared_ptr<Plan> plan_for(int k, const int64_t* off, int* status);
+};
+
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+const char* last_error();
+int validate_family(const qp_family* f);
+int validate_params(const qp_params* p);
+void make_raw(const qp_params* p, qpk::RawParams* r);
+void make_coef(const qp_params* p, qpk::Coef* c);
+int row_capacity(const qp_params* p, int max_len);
+std::shared_ptr<Plan> build_plan(int k, const int64_t* off);
+Context* get_context(int device, int* status);
+int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
+               qp_result** out);
+int to_host(qp_result* r, cudaStream_t st);
+void free_result(qp_result* r);
+
+}  // namespace qph

@@ -1,0 +1,136 @@
+// Internal definitions shared by the host orchestration (qp_api.cpp) and the
+// kernels (qp_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qpk {
+
+constexpr int kWarp = 32;
+constexpr int kRmax = 4;                     // DP rows per lane in a full strip
+constexpr int kStripRows = kWarp * kRmax;    // 128 DP rows per strip
+constexpr int kC = 16;                       // renormalisation period (steps); divides 32
+constexpr int kTab = 21;                     // 20 residues + the empty row/column code
+constexpr int kEmpty = 20;
+constexpr int kNS = 9;                       // FP64 form: values per diagonal slot
+
+// Per-call derived constants, written by k_setup on the device.
+struct Consts {
+    // (odds p(a,b)/(q(a)q(b)), Boltzmann weight exp(s(a,b)/T)), indexed [y][x]
+    float2 ow[kTab * kTab];
+    // FP64 form
+    double tMMd, d1d, d2d, e1d, e2d, c1d, c2d, Wod, Wed;
+    double pid[5], taud[5];
+    double thetad;
+    double oddsd[kTab * kTab];   // [y][x]
+    double wd[kTab * kTab];      // [y][x]
+    double logq[20];
+    int32_t combine;
+    int32_t err;
+};
+
+// Host-side copy of the parameters the setup kernel needs (plain doubles).
+struct RawParams {
+    double pi[5], delta1, eps1, delta2, eps2;
+    double emit_pair[400], emit_bg[20], end_w[5], score[400];
+    double gap_open, gap_ext, temperature, threshold;
+    int32_t combine;
+};
+
+// Status words written by the kernels (device memory, zeroed per call).
+struct Status {
+    unsigned long long pool_used;   // entries reserved in the pool (single-family calls)
+    int32_t pool_overflow;          // a reservation did not fit
+    int32_t n_fallback;             // pairs queued for the FP64 form
+    int32_t stage_overflow;         // a row had more entries than its staging
+    int32_t bad_residue;            // encode saw a byte outside the alphabet
+    int32_t work_f32;               // work counters of the persistent kernels
+    int32_t work_f64;
+    int32_t pad[2];
+    int32_t diag[16];               // first guard event: site, strip, step, lane, exponents, m, n
+};
+
+// Scalar coefficients passed by value (they live in the constant bank).
+struct Coef {
+    float tMM, d1, d2, e1, e2, c1, c2, Wo, We;
+    float pi[5];        // M, X, Y, X2, Y2
+    float tau[5];
+    float theta;
+    float wh, wp;       // combination weights
+    int32_t combine;    // 0 rms-family (sqrt(wh Ph^2 + wp Pp^2)), 1 linear (wh Ph + wp Pp)
+};
+
+// One family resident on the device: inputs, plan and outputs.
+struct FamDesc {
+    const uint8_t* codes;          // residue codes 0..19, concatenated
+    const int64_t* seq_off;        // [k+1]
+    const double* seq_logq;        // [k] sum of log q over each sequence
+    const int2* pairs;             // [n_pairs] (a, b), a < b
+    const int64_t* pair_row_off;   // [n_pairs+1] first CSR row slot of the pair
+    const int64_t* pair_strip_off; // [n_pairs+1] first strip slot of the pair
+    int32_t k;
+    int32_t pad0;
+    int32_t* row_cnt;              // entries per CSR row, at pair_row_off[p] + r
+    int64_t* chunk_off;            // absolute pool offset of each strip's entries
+    int64_t* pair_nnz;             // [n_pairs]
+    double* mea;                   // [n_pairs]
+    double* logz_h;                // [n_pairs]
+    double* logz_p;                // [n_pairs]
+    float* dist;                   // [k*k]
+    double* dist64;                // [k*k]
+    int32_t* pair_flags;           // [n_pairs]
+    // region of the shared entry pool owned by this family
+    unsigned long long* pool_used; // entries reserved in the region
+    int64_t pool_base;             // absolute first entry of the region
+    int64_t pool_cap;              // entries in the region
+    int32_t* n_done;               // pairs completed (atomic), may be null
+};
+
+struct Problem {
+    Coef cf;
+    const Consts* cst;
+    const FamDesc* fams;           // family table
+    const int2* items;             // [n_work] (family, pair), longest first
+    int32_t n_work;
+    int32_t cap;                   // staging capacity per row
+    // pool of sparse entries (shared by all families)
+    int2* pool;                    // (col, float bits of P)
+    double* pool64;                // FP64 values (F64 form) or null
+    Status* status;
+    int2* fallback;                // (family, pair) items for the FP64 form
+    // FP32 per-warp scratch
+    float2* bst;  int64_t bst_stride;      // stored backward values
+    int2* bex;    int64_t bex_stride;      // backward exponents per chunk
+    float4* bnd;  int64_t bnd_stride;      // strip boundary rows (2 float4 / column)
+    int2* stg;    int64_t stg_stride;      // staging of entries, [kStripRows][cap]
+    // FP64 per-CTA scratch
+    double2* d_b; int64_t d_b_stride;      // dense backward (B_M, Zm_b)
+    double* d_diag; int64_t d_diag_stride; // rotating diagonals
+    int32_t* d_cnt; int64_t d_cnt_stride;  // per-row entry counts and exponents
+    int2* d_stg;  double* d_stg64; int64_t d_stg_stride;
+    int32_t f64_all;               // 1: F64 form over the whole item list
+    int32_t max_len;
+};
+
+// launch wrappers (qp_kernels.cu)
+cudaError_t launch_setup(const RawParams* host_raw, Consts* dev_cst, cudaStream_t s);
+cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
+                          const int64_t* seq_off, int32_t k, double* seq_logq,
+                          const Consts* cst, Status* status, cudaStream_t s);
+cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block,
+                                 cudaStream_t s);
+cudaError_t launch_posterior_f64(const Problem& P, int grid, cudaStream_t s);
+cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
+                           const int64_t* pair_row_off, const int64_t* pair_strip_off,
+                           const int32_t* row_cnt, const int64_t* chunk_off, const int2* pool,
+                           const double* pool64, int64_t n_pairs, const int64_t* pair_nnz_off,
+                           int32_t* row_ptr, int32_t* col, float* val, double* val64,
+                           cudaStream_t s);
+cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,
+                            cudaStream_t s);
+int posterior_f32_regs();
+int posterior_f32_occupancy(int warps_per_block, int* blocks_per_sm);
+int posterior_f64_occupancy(int* blocks_per_sm);
+size_t posterior_f32_smem(int warps_per_block);
+
+}  // namespace qpk

@@ -1,0 +1,1183 @@
+// Kernels of the all-pairs posterior stage (paper, Methods, stage I) for sm_103a.
+//
+//   k_setup            derived tables: pair-HMM odds p(a,b)/(q(a)q(b)) and
+//                      partition-function weights exp(s(a,b)/T)
+//   k_encode           ASCII residues -> codes 0..19, alphabet check
+//   k_seqlogq          per-sequence sum of log q (turns the odds-scaled total
+//                      back into the pair-HMM probability)
+//   k_posterior_f32    the hot path: one warp per pair, FP32 recurrences with
+//                      per-lane power-of-two rescaling; pass 1 = backward of both
+//                      models (stored), pass 2 = forward of both models fused
+//                      with posterior, combination, threshold, MEA, distance
+//   k_posterior_f64    plain FP64 form (one CTA per pair, anti-diagonal
+//                      wavefront, per-diagonal rescaling); also recomputes pairs
+//                      whose FP32 range guards fired
+//   k_scan_nnz / k_compact   CSR assembly from the per-strip entry chunks
+//
+// Model (the reading this library documents; the paper prints no model):
+// a 5-state pair-HMM (M, X, Y, X2, Y2) with emissions taken relative to the
+// background (M: p(a,b)/(q(a)q(b)), gap states: 1; every path emits every
+// residue once, so posteriors are unchanged and the total differs by the
+// product of q over both sequences), and a 3-state affine partition function
+// (Zm, Ze, Zf) with Boltzmann weights.
+#include "qp_internal.h"
+
+#include <cstdio>
+
+namespace qpk {
+
+#define FULL 0xffffffffu
+
+// 2^e as a float for e in [-126, 127]; 0 below -126, 2^127 above.
+__device__ __forceinline__ float pow2f(int e) {
+    if (e < -126) return 0.f;
+    if (e > 127) e = 127;
+    return __int_as_float((e + 127) << 23);
+}
+
+// floor(log2 v) for a positive normal float; -127 for zero / denormal.
+__device__ __forceinline__ int ilog2f(float v) {
+    return ((__float_as_int(v) >> 23) & 0xff) - 127;
+}
+
+// ---------------------------------------------------------------- set-up
+__global__ void k_setup(RawParams raw, Consts* c) {
+    const int t = threadIdx.x;
+    for (int idx = t; idx < kTab * kTab; idx += blockDim.x) {
+        const int y = idx / kTab, x = idx % kTab;
+        double o = 0.0, w = 0.0;
+        if (x < 20 && y < 20) {
+            o = raw.emit_pair[x * 20 + y] / (raw.emit_bg[x] * raw.emit_bg[y]);
+            w = exp(raw.score[x * 20 + y] / raw.temperature);
+        }
+        c->ow[idx] = make_float2((float)o, (float)w);
+        c->oddsd[idx] = o;
+        c->wd[idx] = w;
+    }
+    if (t < 20) c->logq[t] = log(raw.emit_bg[t]);
+    if (t == 0) {
+        c->tMMd = 1.0 - 2.0 * raw.delta1 - 2.0 * raw.delta2;
+        c->d1d = raw.delta1; c->d2d = raw.delta2;
+        c->e1d = raw.eps1;   c->e2d = raw.eps2;
+        c->c1d = 1.0 - raw.eps1; c->c2d = 1.0 - raw.eps2;
+        c->Wod = exp(raw.gap_open / raw.temperature);
+        c->Wed = exp(raw.gap_ext / raw.temperature);
+        for (int s = 0; s < 5; ++s) { c->pid[s] = raw.pi[s]; c->taud[s] = raw.end_w[s]; }
+        c->thetad = raw.threshold;
+        c->combine = raw.combine;
+        c->err = 0;
+    }
+}
+
+cudaError_t launch_setup(const RawParams* raw, Consts* cst, cudaStream_t s) {
+    k_setup<<<1, 512, 0, s>>>(*raw, cst);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- encode
+__global__ void k_encode(const uint8_t* __restrict__ ascii, uint8_t* __restrict__ codes,
+                         int64_t n, Status* st) {
+    __shared__ uint8_t lut[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = 255;
+    __syncthreads();
+    if (threadIdx.x < 20) {
+        const char* A = "ACDEFGHIKLMNPQRSTVWY";
+        const int c = A[threadIdx.x];
+        lut[c] = (uint8_t)threadIdx.x;
+        lut[c + 32] = (uint8_t)threadIdx.x;   // lower case
+    }
+    __syncthreads();
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint8_t c = lut[ascii[i]];
+        if (c == 255) { bad = 1; c = 0; }
+        codes[i] = c;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->bad_residue, 1);
+}
+
+__global__ void k_seqlogq(const uint8_t* __restrict__ codes, const int64_t* __restrict__ off,
+                          int k, const Consts* __restrict__ c, double* __restrict__ out) {
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= k) return;
+    double s = 0.0;
+    for (int64_t i = off[w] + lane; i < off[w + 1]; i += 32) s += c->logq[codes[i]];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) out[w] = s;
+}
+
+cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
+                          const int64_t* seq_off, int32_t k, double* seq_logq,
+                          const Consts* cst, Status* status, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_encode<<<blocks, 256, 0, s>>>(ascii, codes, n, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_seqlogq<<<(k * 32 + 255) / 256, 256, 0, s>>>(codes, seq_off, k, cst, seq_logq);
+    return cudaGetLastError();
+}
+
+// ================================================================ FP32 path
+//
+// Geometry.  The DP grid has rows 0..m (row 0 and column 0 are the empty
+// prefixes; their residue code is kEmpty, whose odds and weights are 0) and
+// columns 0..n.  Rows are cut into strips of 128; in a strip lane l owns the
+// R consecutive rows row0 + l*R + r (R = 4, fewer in a short last strip).
+// A strip is swept column by column with the lanes skewed by one column:
+// in the forward pass lane l is at column t - l at step t, so one step of the
+// warp covers an anti-diagonal segment and the value a lane needs from the row
+// above was produced by lane l-1 one step earlier (one shuffle per value).
+// The row above lane 0 (the previous strip's last row) comes from a boundary
+// row in global memory written by lane 31 of that strip.  The backward pass
+// mirrors this (lane 31 leads, values come from lane l+1).
+//
+// Storage.  Pass 1 stores (B_M, Zm_b) of every cell in blocks indexed by the
+// forward step T = j + l at which pass 2 visits the cell; a block is 32*R
+// float2 in lane-major order, so both passes touch 256*R contiguous bytes per
+// step.
+//
+// Scaling.  Every lane carries one power-of-two exponent per model.  All
+// lanes renormalise on the same steps (every kC steps): the lane's largest
+// carried value is brought into [1, 2).  Values received from the row above
+// are converted with 2^(e_above - e_me), which only changes on those steps.
+// A lane whose upstream neighbour is zero for good (padding rows below row m
+// in the backward pass, the missing row above the first strip in the forward
+// pass) keeps the neighbour's exponent equal to its own.  Pass 1 records its
+// exponent per lane and kC-step chunk; pass 2 combines the two exponents and
+// the totals into one factor per lane and chunk, so the posterior of a cell
+// is (F_M * factor) * B_M.
+//
+// Range guards (the pair is recomputed by the FP64 form when one fires), for
+// lanes that own a row of the pair: a carried maximum >= 2^100 or not finite,
+// an exponent gap beyond the float range, a posterior factor beyond the float
+// range, a posterior above 1.001, forward and backward totals that disagree by
+// more than 1e-3 in log.
+
+struct PairCtx {
+    const FamDesc* fd;
+    Status* st;
+    const uint8_t* x;
+    const uint8_t* y;
+    int m, n, p, nch;
+    float2* bst;
+    int2* bex;
+    float4* bnd;
+    int2* stg;
+};
+
+constexpr float kBig = 1.2676506002282294e30f;   // 2^100
+
+// Records the first guard event of a launch (site code and context) so that a
+// fallback can be explained from the host.
+__device__ __forceinline__ void note_guard(Status* st, int site, int s, int t, int lane, int a, int b,
+                                           int c, int d, int m, int n) {
+    if (atomicCAS(&st->diag[0], 0, site) == 0) {
+        st->diag[1] = s; st->diag[2] = t; st->diag[3] = lane;
+        st->diag[4] = a; st->diag[5] = b; st->diag[6] = c; st->diag[7] = d;
+        st->diag[8] = m; st->diag[9] = n;
+    }
+}
+
+// Reasons an FP32 pair is handed to the FP64 form (pair_flags bits 2..).
+enum : int {
+    kGuardRange = 1 << 2,    // a carried maximum >= 2^100 or not finite
+    kGuardGap = 1 << 3,      // exponent gap between neighbouring lanes beyond float range
+    kGuardFactor = 1 << 4,   // posterior factor 2^(eF + eB - eZ) beyond float range
+    kGuardPost = 1 << 5,     // a posterior above 1.001
+    kGuardAgreeH = 1 << 6,   // pair-HMM forward and backward totals disagree
+    kGuardAgreeP = 1 << 7,   // partition-function totals disagree
+    kGuardTotal = 1 << 8,    // a total is zero or not finite
+    kGuardCorner = 1 << 9,   // a corner cell was reached with a non-zero exponent
+    kGuardStage = 1 << 10,   // a row exceeded its staging capacity
+    kGuardPool = 1 << 11,    // the entry pool region was full
+};
+
+// ---------------------------------------------------------------- pass 1
+template <int R, bool SPEC>
+__device__ __forceinline__ void bwd_step(
+    const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int t, int lane,
+    int Lend, int rend, bool first_strip,
+    float (&Mn)[R], float (&BXo)[R], float (&BX2o)[R], float (&BYo)[R], float (&BY2o)[R],
+    float (&Dpo)[R], float (&ZEo)[R], float (&ZFo)[R], const int (&xo)[R],
+    float& dMn, float& dDp, float cvH, float cvP, float2* __restrict__ bst_strip,
+    const float4* __restrict__ bnd_in, float4* __restrict__ bnd_out, int eH, int eP,
+    float& Zh, float& Zp, int& eZh, int& eZp, int& flag)
+{
+    const int n = c.n;
+    const int j = n + 31 - lane - t;
+    const bool act = (j >= 0) && (j <= n);
+    // values of the row below (lane+1's top row; lane 31: the boundary row)
+    float rMn = __shfl_down_sync(FULL, Mn[0], 1);
+    float rBX = __shfl_down_sync(FULL, BXo[0], 1);
+    float rBX2 = __shfl_down_sync(FULL, BX2o[0], 1);
+    float rDp = __shfl_down_sync(FULL, Dpo[0], 1);
+    float rZE = __shfl_down_sync(FULL, ZEo[0], 1);
+    if (lane == 31) {
+        if (act && bnd_in) {
+            const float4 v0 = bnd_in[2 * j];
+            const float4 v1 = bnd_in[2 * j + 1];
+            rMn = v0.x; rBX = v0.y; rBX2 = v0.z; rDp = v0.w; rZE = v1.x;
+        } else {
+            rMn = rBX = rBX2 = rDp = rZE = 0.f;
+        }
+    }
+    rMn *= cvH; rBX *= cvH; rBX2 *= cvH; rDp *= cvP; rZE *= cvP;
+    const int yc = (j >= 1 && j <= n) ? (int)__ldg(c.y + j - 1) : kEmpty;
+    const float2* __restrict__ owr = s_ow + yc * kTab;
+    float D = dMn, Dp = dDp;
+    float Xb = rBX, X2b = rBX2, Eb = rZE;
+    dMn = rMn; dDp = rDp;
+    float2* blk = bst_strip + (int64_t)(j + lane) * (kWarp * R) + lane * R;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+        const float Yb = BYo[r], Y2b = BY2o[r], Fb = ZFo[r];
+        float BM = cf.tMM * D + cf.d1 * (Xb + Yb) + cf.d2 * (X2b + Y2b);
+        float BX = cf.c1 * D + cf.e1 * Xb;
+        float BX2 = cf.c2 * D + cf.e2 * X2b;
+        float BY = cf.c1 * D + cf.e1 * Yb;
+        float BY2 = cf.c2 * D + cf.e2 * Y2b;
+        float ZMB = Dp + cf.Wo * (Eb + Fb);
+        float ZEB = Dp + cf.We * Eb;
+        float ZFB = Dp + cf.We * Fb;
+        if (SPEC) {
+            if (lane == Lend && r == rend && j == n) {
+                // end of every path: B_s(m, n) = tau_s; the partition function ends with weight 1
+                BM = cf.tau[0]; BX = cf.tau[1]; BY = cf.tau[2]; BX2 = cf.tau[3]; BY2 = cf.tau[4];
+                ZMB = ZEB = ZFB = 1.f;
+                if (eH != 0 || eP != 0) flag |= kGuardCorner;
+            }
+            if (first_strip && lane == 0 && r == 0 && j == 0) {
+                // totals seen from the start: pi_s times the first emission of s
+                Zh = cf.pi[0] * D + cf.pi[1] * Xb + cf.pi[2] * Yb + cf.pi[3] * X2b + cf.pi[4] * Y2b;
+                Zp = ZMB;
+                eZh = eH; eZp = eP;
+            }
+        }
+        const float2 w = owr[xo[r]];
+        const float nMn = w.x * BM, nDp = w.y * ZMB;
+        if (act) blk[r] = make_float2(BM, ZMB);
+        D = Mn[r]; Dp = Dpo[r];
+        Xb = BX; X2b = BX2; Eb = ZEB;
+        Mn[r] = nMn; BXo[r] = BX; BX2o[r] = BX2; BYo[r] = BY; BY2o[r] = BY2;
+        Dpo[r] = nDp; ZEo[r] = ZEB; ZFo[r] = ZFB;
+    }
+    if (lane == 0 && act && bnd_out) {
+        bnd_out[2 * j] = make_float4(Mn[0], BXo[0], BX2o[0], Dpo[0]);
+        bnd_out[2 * j + 1] = make_float4(ZEo[0], 0.f, __int_as_float(eH), __int_as_float(eP));
+    }
+}
+
+template <int R>
+__device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c,
+                          int s, int nstrips, float& Zh, float& Zp, int& eZh, int& eZp, int& flag)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = c.m, n = c.n;
+    const int row0 = s * kStripRows;
+    const bool last_strip = (s == nstrips - 1);
+    const bool first_strip = (s == 0);
+    int xo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = row0 + lane * R + r;
+        xo[r] = (i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty;
+    }
+    float Mn[R], BXo[R], BX2o[R], BYo[R], BY2o[R], Dpo[R], ZEo[R], ZFo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { Mn[r] = BXo[r] = BX2o[r] = BYo[r] = BY2o[r] = Dpo[r] = ZEo[r] = ZFo[r] = 0.f; }
+    float dMn = 0.f, dDp = 0.f;
+    // the boundary row below this strip (none for the last strip)
+    const float4* bnd_in = last_strip ? nullptr : c.bnd;
+    float4* bnd_out = first_strip ? nullptr : c.bnd;
+    const bool owns_row = row0 + lane * R <= m;
+    // the neighbour below is zero for good: padding rows, or no strip below
+    const bool up_zero = (lane == 31) ? (bnd_in == nullptr) : (row0 + (lane + 1) * R > m);
+    int eH = 0, eP = 0;
+    if (bnd_in) { const float4 e = bnd_in[2 * n + 1]; eH = __float_as_int(e.z); eP = __float_as_int(e.w); }
+    int eUpH = eH, eUpP = eP;
+    float cvH = 1.f, cvP = 1.f;
+    const int Lend = last_strip ? (m - row0) / R : -1;
+    const int rend = last_strip ? (m - row0) % R : -1;
+    const int t_end = last_strip ? 31 - Lend : -1;
+    const int t_start = first_strip ? n + 31 : -1;
+    float2* bst_strip = c.bst + (int64_t)s * kStripRows * (n + 32);
+    int2* bex = c.bex + (int64_t)s * c.nch * 32;
+    const int nsteps = n + 32;
+    for (int t = 0; t < nsteps; ++t) {
+        const int ph = t & (kC - 1);
+        if (ph == 0) {
+            // renormalise: bring the lane's largest carried value into [1, 2)
+            float mh = fmaxf(dMn, 0.f), mp = fmaxf(dDp, 0.f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                mh = fmaxf(mh, fmaxf(fmaxf(Mn[r], BXo[r]), fmaxf(BX2o[r], fmaxf(BYo[r], BY2o[r]))));
+                mp = fmaxf(mp, fmaxf(Dpo[r], fmaxf(ZEo[r], ZFo[r])));
+            }
+            const int j = n + 31 - lane - t;
+            const bool live = owns_row && (j >= -1) && (j <= n);
+            if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
+            if (mh > 0.f) {
+                const int k = max(-126, min(126, ilog2f(mh)));
+                const float sc = pow2f(-k);
+#pragma unroll
+                for (int r = 0; r < R; ++r) { Mn[r] *= sc; BXo[r] *= sc; BX2o[r] *= sc; BYo[r] *= sc; BY2o[r] *= sc; }
+                dMn *= sc;
+                eH += k;
+            } else {
+                eH = eUpH;
+            }
+            if (mp > 0.f) {
+                const int k = max(-126, min(126, ilog2f(mp)));
+                const float sc = pow2f(-k);
+#pragma unroll
+                for (int r = 0; r < R; ++r) { Dpo[r] *= sc; ZEo[r] *= sc; ZFo[r] *= sc; }
+                dDp *= sc;
+                eP += k;
+            } else {
+                eP = eUpP;
+            }
+            const int uH = __shfl_down_sync(FULL, eH, 1);
+            const int uP = __shfl_down_sync(FULL, eP, 1);
+            if (lane != 31) { eUpH = uH; eUpP = uP; }
+            if (up_zero) { eUpH = eH; eUpP = eP; }
+            bex[(t / kC) * 32 + lane] = make_int2(eH, eP);
+            const int gh = eUpH - eH, gp = eUpP - eP;
+            if (live && (gh > 127 || gp > 127)) {
+                flag |= kGuardGap;
+                note_guard(c.st, 1, s, t, lane, eH, eUpH, eP, eUpP, m, n);
+            }
+            cvH = pow2f(gh); cvP = pow2f(gp);
+        } else if (ph == 1) {
+            // the boundary row's exponent changes on these steps
+            if (lane == 31 && bnd_in) {
+                const int j = n - t;
+                if (j >= 0) {
+                    const float4 e = bnd_in[2 * j + 1];
+                    eUpH = __float_as_int(e.z); eUpP = __float_as_int(e.w);
+                    const int gh = eUpH - eH, gp = eUpP - eP;
+                    if (owns_row && (gh > 127 || gp > 127)) {
+                        flag |= kGuardGap;
+                        note_guard(c.st, 2, s, t, lane, eH, eUpH, eP, eUpP, m, n);
+                    }
+                    cvH = pow2f(gh); cvP = pow2f(gp);
+                }
+            }
+        }
+        if (t == t_end || t == t_start)
+            bwd_step<R, true>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Mn, BXo, BX2o, BYo, BY2o,
+                              Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip, bnd_in, bnd_out, eH, eP,
+                              Zh, Zp, eZh, eZp, flag);
+        else
+            bwd_step<R, false>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Mn, BXo, BX2o, BYo, BY2o,
+                               Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip, bnd_in, bnd_out, eH, eP,
+                               Zh, Zp, eZh, eZp, flag);
+    }
+}
+
+// ---------------------------------------------------------------- pass 2
+struct FwdOut {      // per-lane results captured at the end corner
+    float Zh, Zp;
+    int eZh, eZp;
+    int A;
+};
+
+template <int R, bool SPEC>
+__device__ __forceinline__ void fwd_step(
+    const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int t, int lane,
+    int Lend, int rend, bool first_strip,
+    float (&Md)[R], float (&Xi)[R], float (&X2i)[R], float (&Yi)[R], float (&Y2i)[R],
+    float (&Zd)[R], float (&Ei)[R], float (&Fi)[R], int (&Aa)[R], int (&cnt)[R],
+    const int (&xo)[R], const float (&thr)[R],
+    float& uMd, float& uZd, int& uA, float cvH, float cvP, float psH, float psP, float scaleA,
+    const float2 (&bs)[R], const float4* __restrict__ bnd_in, float4* __restrict__ bnd_out,
+    int2* __restrict__ stg, int cap, int eH, int eP, float& pmax, FwdOut& fo, int& flag)
+{
+    const int n = c.n;
+    const int j = t - lane;
+    const bool act = (j >= 0) && (j <= n);
+    float rMd = __shfl_up_sync(FULL, Md[R - 1], 1);
+    float rXi = __shfl_up_sync(FULL, Xi[R - 1], 1);
+    float rX2i = __shfl_up_sync(FULL, X2i[R - 1], 1);
+    float rZd = __shfl_up_sync(FULL, Zd[R - 1], 1);
+    float rEi = __shfl_up_sync(FULL, Ei[R - 1], 1);
+    int rA = __shfl_up_sync(FULL, Aa[R - 1], 1);
+    if (lane == 0) {
+        if (act && bnd_in) {
+            const float4 v0 = bnd_in[2 * j];
+            const float4 v1 = bnd_in[2 * j + 1];
+            rMd = v0.x; rXi = v0.y; rX2i = v0.z; rZd = v0.w; rEi = v1.x; rA = __float_as_int(v1.y);
+        } else {
+            rMd = rXi = rX2i = rZd = rEi = 0.f; rA = 0;
+        }
+    }
+    rMd *= cvH; rXi *= cvH; rX2i *= cvH; rZd *= cvP; rEi *= cvP;
+    const int yc = (j >= 1 && j <= n) ? (int)__ldg(c.y + j - 1) : kEmpty;
+    const float2* __restrict__ owr = s_ow + yc * kTab;
+    float dMd = uMd, dZd = uZd;
+    int dA = uA;
+    float aXi = rXi, aX2i = rX2i, aEi = rEi;
+    int aA = rA;
+    uMd = rMd; uZd = rZd; uA = rA;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float2 w = owr[xo[r]];
+        const float FM = w.x * dMd, FX = aXi, FX2 = aX2i, FY = Yi[r], FY2 = Y2i[r];
+        const float ZM = w.y * dZd, ZE = aEi, ZF = Fi[r];
+        float nMd = cf.tMM * FM + cf.c1 * (FX + FY) + cf.c2 * (FX2 + FY2);
+        float nXi = cf.d1 * FM + cf.e1 * FX;
+        float nX2i = cf.d2 * FM + cf.e2 * FX2;
+        float nYi = cf.d1 * FM + cf.e1 * FY;
+        float nY2i = cf.d2 * FM + cf.e2 * FY2;
+        float nZd = ZM + ZE + ZF;
+        float nEi = cf.Wo * ZM + cf.We * ZE;
+        float nFi = cf.Wo * ZM + cf.We * ZF;
+        // posteriors of the cell and their combination
+        const float Ph = (FM * psH) * bs[r].x;
+        const float Pp = (ZM * psP) * bs[r].y;
+        float P;
+        if (cf.combine == 0) P = sqrtf(cf.wh * (Ph * Ph) + cf.wp * (Pp * Pp));
+        else P = cf.wh * Ph + cf.wp * Pp;
+        pmax = fmaxf(pmax, P);
+        if (act && P >= thr[r]) {
+            const int q = cnt[r]++;
+            if (q < cap) stg[(lane * R + r) * cap + q] = make_int2(j - 1, __float_as_int(P));
+        }
+        // maximum expected accuracy, fixed point (scaleA * P < 2^22)
+        const int Pq = __float_as_int(fmaf(P, scaleA, 12582912.0f)) - 0x4B400000;
+        int nA = max(dA + Pq, max(aA, Aa[r]));
+        if (SPEC) {
+            if (first_strip && lane == 0 && r == 0 && j == 0) {
+                // empty prefixes: the start distribution and the empty alignment
+                nMd = cf.pi[0]; nXi = cf.pi[1]; nYi = cf.pi[2]; nX2i = cf.pi[3]; nY2i = cf.pi[4];
+                nZd = 1.f; nEi = cf.Wo; nFi = cf.Wo;
+                nA = 0;
+                if (eH != 0 || eP != 0) flag |= kGuardCorner;
+            }
+            if (lane == Lend && r == rend && j == n) {
+                fo.Zh = cf.tau[0] * FM + cf.tau[1] * FX + cf.tau[2] * FY + cf.tau[3] * FX2 + cf.tau[4] * FY2;
+                fo.Zp = ZM + ZE + ZF;
+                fo.eZh = eH; fo.eZp = eP;
+                fo.A = nA;
+            }
+        }
+        dMd = Md[r]; dZd = Zd[r]; dA = Aa[r];
+        aXi = nXi; aX2i = nX2i; aEi = nEi; aA = nA;
+        Md[r] = nMd; Xi[r] = nXi; X2i[r] = nX2i; Yi[r] = nYi; Y2i[r] = nY2i;
+        Zd[r] = nZd; Ei[r] = nEi; Fi[r] = nFi; Aa[r] = nA;
+    }
+    if (lane == 31 && act && bnd_out) {
+        bnd_out[2 * j] = make_float4(Md[R - 1], Xi[R - 1], X2i[R - 1], Zd[R - 1]);
+        bnd_out[2 * j + 1] = make_float4(Ei[R - 1], __int_as_float(Aa[R - 1]), __int_as_float(eH),
+                                         __int_as_float(eP));
+    }
+}
+
+template <int R>
+__device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, const PairCtx& c,
+                          int s, int nstrips, float invZh, float invZp, int eZh, int eZp,
+                          float scaleA, float& pmax, FwdOut& fo, int64_t& pair_tot, int& flag)
+{
+    const Coef& cf = Pb.cf;
+    const int lane = threadIdx.x & 31;
+    const int m = c.m, n = c.n;
+    const int row0 = s * kStripRows;
+    const bool last_strip = (s == nstrips - 1);
+    const bool first_strip = (s == 0);
+    int xo[R];
+    float thr[R];
+    int cnt[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = row0 + lane * R + r;
+        const bool valid = (i >= 1 && i <= m);
+        xo[r] = valid ? (int)__ldg(c.x + i - 1) : kEmpty;
+        thr[r] = valid ? cf.theta : __int_as_float(0x7f800000);
+        cnt[r] = 0;
+    }
+    float Md[R], Xi[R], X2i[R], Yi[R], Y2i[R], Zd[R], Ei[R], Fi[R];
+    int Aa[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { Md[r] = Xi[r] = X2i[r] = Yi[r] = Y2i[r] = Zd[r] = Ei[r] = Fi[r] = 0.f; Aa[r] = 0; }
+    float uMd = 0.f, uZd = 0.f;
+    int uA = 0;
+    const float4* bnd_in = first_strip ? nullptr : c.bnd;
+    float4* bnd_out = last_strip ? nullptr : c.bnd;
+    const bool owns_row = row0 + lane * R <= m;
+    const bool up_zero = (lane == 0) && (bnd_in == nullptr);
+    int eH = 0, eP = 0;
+    if (bnd_in) { const float4 e = bnd_in[1]; eH = __float_as_int(e.z); eP = __float_as_int(e.w); }
+    int eUpH = eH, eUpP = eP;
+    float cvH = 1.f, cvP = 1.f;
+    const int Lend = last_strip ? (m - row0) / R : -1;
+    const int rend = last_strip ? (m - row0) % R : -1;
+    const int t_end = last_strip ? n + Lend : -1;
+    const int t_start = first_strip ? 0 : -1;
+    const float2* bst_strip = c.bst + (int64_t)s * kStripRows * (n + 32);
+    const int2* bex = c.bex + (int64_t)s * c.nch * 32;
+    int2* stg = c.stg;
+    const int cap = Pb.cap;
+    const int nsteps = n + 32;
+    const int c2 = n & (kC - 1);
+    // posterior factor of this lane: 2^(eF + eB - eZ) / Z for each model
+    int2 eb = bex[((n + 31) / kC) * 32 + lane];
+    float psH, psP;
+    int t_ps = 0;
+    auto ps_update = [&]() {
+        const int Eh = eH + eb.x - eZh, Ep = eP + eb.y - eZp;
+        const int j0 = t_ps - lane;      // first column of the chunk for this lane
+        if (owns_row && (Eh > 126 || Ep > 126) && j0 <= n && j0 + kC >= 0) {
+            flag |= kGuardFactor;
+            note_guard(c.st, 5, s, t_ps, lane, eH, eb.x, eP, eb.y, m, n);
+        }
+        psH = pow2f(Eh) * invZh;
+        psP = pow2f(Ep) * invZp;
+    };
+    ps_update();
+    // stored backward values: two steps of prefetch
+    float2 bs0[R], bs1[R], bs2[R];
+    auto load_blk = [&](int T, float2 (&dst)[R]) {
+        const int jj = T - lane;
+        if (T < nsteps && jj >= 0 && jj <= n) {
+            const float2* src = bst_strip + (int64_t)T * (kWarp * R) + lane * R;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[r] = src[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[r] = make_float2(0.f, 0.f);
+        }
+    };
+    load_blk(0, bs0);
+    load_blk(1, bs1);
+    for (int t = 0; t < nsteps; ++t) {
+        load_blk(t + 2, bs2);
+        const int ph = (t - c2) & (kC - 1);
+        if (ph == 0) {
+            float mh = uMd, mp = uZd;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                mh = fmaxf(mh, fmaxf(fmaxf(Md[r], Xi[r]), fmaxf(X2i[r], fmaxf(Yi[r], Y2i[r]))));
+                mp = fmaxf(mp, fmaxf(Zd[r], fmaxf(Ei[r], Fi[r])));
+            }
+            const int j = t - lane;
+            const bool live = owns_row && (j >= 0) && (j <= n + 1);
+            if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
+            if (mh > 0.f) {
+                const int k = max(-126, min(126, ilog2f(mh)));
+                const float sc = pow2f(-k);
+#pragma unroll
+                for (int r = 0; r < R; ++r) { Md[r] *= sc; Xi[r] *= sc; X2i[r] *= sc; Yi[r] *= sc; Y2i[r] *= sc; }
+                uMd *= sc;
+                eH += k;
+            } else {
+                eH = eUpH;
+            }
+            if (mp > 0.f) {
+                const int k = max(-126, min(126, ilog2f(mp)));
+                const float sc = pow2f(-k);
+#pragma unroll
+                for (int r = 0; r < R; ++r) { Zd[r] *= sc; Ei[r] *= sc; Fi[r] *= sc; }
+                uZd *= sc;
+                eP += k;
+            } else {
+                eP = eUpP;
+            }
+            const int uH = __shfl_up_sync(FULL, eH, 1);
+            const int uP = __shfl_up_sync(FULL, eP, 1);
+            if (lane != 0) { eUpH = uH; eUpP = uP; }
+            if (up_zero) { eUpH = eH; eUpP = eP; }
+            const int gh = eUpH - eH, gp = eUpP - eP;
+            if (live && (gh > 127 || gp > 127)) {
+                flag |= kGuardGap;
+                note_guard(c.st, 3, s, t, lane, eH, eUpH, eP, eUpP, m, n);
+            }
+            cvH = pow2f(gh); cvP = pow2f(gp);
+            const int kc = (n + 31 - t) / kC;
+            eb = bex[kc * 32 + lane];
+            t_ps = t;
+            ps_update();
+        } else if (ph == 1) {
+            if (lane == 0 && bnd_in && t <= n) {
+                const float4 e = bnd_in[2 * t + 1];
+                eUpH = __float_as_int(e.z); eUpP = __float_as_int(e.w);
+                const int gh = eUpH - eH, gp = eUpP - eP;
+                if (gh > 127 || gp > 127) {
+                    flag |= kGuardGap;
+                    note_guard(c.st, 4, s, t, lane, eH, eUpH, eP, eUpP, m, n);
+                }
+                cvH = pow2f(gh); cvP = pow2f(gp);
+            }
+        }
+        if (t == t_end || t == t_start)
+            fwd_step<R, true>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Md, Xi, X2i, Yi, Y2i, Zd, Ei,
+                              Fi, Aa, cnt, xo, thr, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA, bs0,
+                              bnd_in, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
+        else
+            fwd_step<R, false>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Md, Xi, X2i, Yi, Y2i, Zd, Ei,
+                               Fi, Aa, cnt, xo, thr, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA, bs0,
+                               bnd_in, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
+#pragma unroll
+        for (int r = 0; r < R; ++r) { bs0[r] = bs1[r]; bs1[r] = bs2[r]; }
+    }
+    // ---- flush this strip's entries into the pool (row-major, columns ascending)
+    int tot = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (cnt[r] > cap) { flag |= kGuardStage; atomicExch(&Pb.status->stage_overflow, 1); cnt[r] = cap; }
+        tot += cnt[r];
+    }
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int strip_tot = __shfl_sync(FULL, incl, 31);
+    const FamDesc& fd = *c.fd;
+    unsigned long long off = 0;
+    if (lane == 0 && strip_tot > 0) off = atomicAdd(fd.pool_used, (unsigned long long)strip_tot);
+    off = __shfl_sync(FULL, off, 0);
+    const bool fits = (int64_t)off + strip_tot <= fd.pool_cap;
+    if (!fits) { flag |= kGuardPool; if (lane == 0) atomicExch(&Pb.status->pool_overflow, 1); }
+    const int64_t base = fd.pool_base + (int64_t)off;
+    int w = incl - tot;
+    const int64_t row_slot = fd.pair_row_off[c.p];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = row0 + lane * R + r;
+        if (i >= 1 && i <= m) fd.row_cnt[row_slot + i - 1] = cnt[r];
+        if (fits) {
+            const int2* src = stg + (lane * R + r) * cap;
+            for (int q = 0; q < cnt[r]; ++q) Pb.pool[base + w + q] = src[q];
+        }
+        w += cnt[r];
+    }
+    if (lane == 0) fd.chunk_off[fd.pair_strip_off[c.p] + s] = base;
+    pair_tot += strip_tot;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void bwd_dispatch(int Rs, const Coef& cf, const float2* s_ow, const PairCtx& c,
+                                             int s, int ns, float& Zh, float& Zp, int& eZh, int& eZp, int& flag) {
+    switch (Rs) {
+        case 1: bwd_strip<1>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        case 2: bwd_strip<2>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        case 3: bwd_strip<3>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        default: bwd_strip<4>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
+    }
+}
+
+__global__ void __launch_bounds__(128, 3) k_posterior_f32(Problem Pb) {
+    extern __shared__ float2 s_ow[];
+    for (int i = threadIdx.x; i < kTab * kTab; i += blockDim.x) s_ow[i] = Pb.cst->ow[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    PairCtx c;
+    c.bst = Pb.bst + gw * Pb.bst_stride;
+    c.bex = Pb.bex + gw * Pb.bex_stride;
+    c.bnd = Pb.bnd + gw * Pb.bnd_stride;
+    c.stg = Pb.stg + gw * Pb.stg_stride;
+    c.st = Pb.status;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(&Pb.status->work_f32, 1);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= Pb.n_work) break;
+        const int2 it = Pb.items[q];
+        const FamDesc& fd = Pb.fams[it.x];
+        const int p = it.y;
+        const int2 ab = fd.pairs[p];
+        const int64_t oa = fd.seq_off[ab.x], ob = fd.seq_off[ab.y];
+        c.fd = &fd;
+        c.m = (int)(fd.seq_off[ab.x + 1] - oa);
+        c.n = (int)(fd.seq_off[ab.y + 1] - ob);
+        c.x = fd.codes + oa;
+        c.y = fd.codes + ob;
+        c.p = p;
+        c.nch = (c.n + 32 + kC - 1) / kC;
+        const int m = c.m, n = c.n;
+        const int nstrips = (m + 1 + kStripRows - 1) / kStripRows;
+        int flag = 0;
+        // ---- pass 1: backward, bottom strip first
+        float Zh = 0.f, Zp = 0.f;
+        int eZh = 0, eZp = 0;
+        for (int s = nstrips - 1; s >= 0; --s) {
+            const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
+            const int Rs = (rows_in + 31) / 32;
+            bwd_dispatch(Rs, Pb.cf, s_ow, c, s, nstrips, Zh, Zp, eZh, eZp, flag);
+            __syncwarp();
+        }
+        Zh = __shfl_sync(FULL, Zh, 0); Zp = __shfl_sync(FULL, Zp, 0);
+        eZh = __shfl_sync(FULL, eZh, 0); eZp = __shfl_sync(FULL, eZp, 0);
+        // normalise the totals to [1, 2) * 2^e
+        if (!(Zh > 0.f) || !(Zp > 0.f) || !(Zh < kBig) || !(Zp < kBig)) flag |= kGuardTotal;
+        {
+            const int kh = ilog2f(fmaxf(Zh, 1e-30f)), kp = ilog2f(fmaxf(Zp, 1e-30f));
+            Zh *= pow2f(-kh); eZh += kh;
+            Zp *= pow2f(-kp); eZp += kp;
+        }
+        const float invZh = 1.f / Zh, invZp = 1.f / Zp;
+        // ---- pass 2: forward + posterior + threshold + MEA, top strip first
+        const int mn = min(m, n);
+        int sA = 30 - (32 - __clz(mn + 1));
+        if (sA > 21) sA = 21;
+        const float scaleA = (float)(1 << sA);
+        float pmax = 0.f;
+        FwdOut fo{0.f, 0.f, 0, 0, 0};
+        int64_t pair_tot = 0;
+        for (int s = 0; s < nstrips; ++s) {
+            const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
+            const int Rs = (rows_in + 31) / 32;
+            switch (Rs) {
+                case 1: fwd_strip<1>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                case 2: fwd_strip<2>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                case 3: fwd_strip<3>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                default: fwd_strip<4>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+            }
+        }
+        // ---- pair results (held by the lane that owns row m)
+        const int lastRs = (min(kStripRows, m + 1 - (nstrips - 1) * kStripRows) + 31) / 32;
+        const int Lend = (m - (nstrips - 1) * kStripRows) / lastRs;
+        const float fZh = __shfl_sync(FULL, fo.Zh, Lend), fZp = __shfl_sync(FULL, fo.Zp, Lend);
+        const int feh = __shfl_sync(FULL, fo.eZh, Lend), fep = __shfl_sync(FULL, fo.eZp, Lend);
+        const int Aend = __shfl_sync(FULL, fo.A, Lend);
+        if (pmax > 1.001f) flag |= kGuardPost;
+        flag = __reduce_or_sync(FULL, flag);
+        if (lane == 0) {
+            const double ln2 = 0.69314718055994530942;
+            const double lzb_h = log((double)Zh) + (double)eZh * ln2;
+            const double lzb_p = log((double)Zp) + (double)eZp * ln2;
+            const double lzf_h = log((double)fZh) + (double)feh * ln2;
+            const double lzf_p = log((double)fZp) + (double)fep * ln2;
+            if (!(fabs(lzb_h - lzf_h) <= 1e-3)) flag |= kGuardAgreeH;
+            if (!(fabs(lzb_p - lzf_p) <= 1e-3)) flag |= kGuardAgreeP;
+            if (flag != 0) {
+                fd.pair_flags[p] = flag;
+                const int slot = atomicAdd(&Pb.status->n_fallback, 1);
+                Pb.fallback[slot] = it;
+            } else {
+                const double A = (double)Aend / (double)(1 << sA);
+                fd.mea[p] = A;
+                fd.logz_h[p] = lzb_h + fd.seq_logq[ab.x] + fd.seq_logq[ab.y];
+                fd.logz_p[p] = lzb_p;
+                fd.pair_nnz[p] = pair_tot;
+                fd.pair_flags[p] = 0;
+                const double d = 1.0 - A / (double)mn;
+                const int64_t k = fd.k;
+                fd.dist[ab.x * k + ab.y] = (float)d;
+                fd.dist[ab.y * k + ab.x] = (float)d;
+                fd.dist64[ab.x * k + ab.y] = d;
+                fd.dist64[ab.y * k + ab.x] = d;
+                if (fd.n_done) { __threadfence(); atomicAdd(fd.n_done, 1); }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+int posterior_f32_regs() {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, k_posterior_f32) != cudaSuccess) return -1;
+    return a.numRegs;
+}
+
+size_t posterior_f32_smem(int) { return sizeof(float2) * kTab * kTab; }
+
+int posterior_f32_occupancy(int warps_per_block, int* blocks_per_sm) {
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, k_posterior_f32, warps_per_block * 32, posterior_f32_smem(warps_per_block));
+}
+
+cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block, cudaStream_t s) {
+    k_posterior_f32<<<grid, warps_per_block * 32, posterior_f32_smem(warps_per_block), s>>>(P);
+    return cudaGetLastError();
+}
+
+// ================================================================ FP64 form
+//
+// Plain FP64 evaluation: one CTA per pair, anti-diagonal wavefront over the
+// (m+1) x (n+1) grid, values of each diagonal rescaled by a power of two so
+// that its largest value is in [1, 2).  Pass 1 (backward) stores (B_M, Zm_b)
+// densely; pass 2 (forward) forms the posteriors, the combination, the
+// threshold and the MEA recurrence on each diagonal.
+constexpr int kF64Threads = 256;
+
+__device__ __forceinline__ double pow2d(int e) { return ldexp(1.0, e); }
+
+__device__ double block_max(double v, double* red) {
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double r = red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, red[i]);
+    return r;
+}
+
+__device__ int block_sum(int v, int* red) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    int r = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
+    __shared__ double sred[2][kF64Threads / 32];
+    __shared__ int ired[kF64Threads / 32];
+    __shared__ int s_q;
+    __shared__ unsigned long long s_base;
+    const Consts* __restrict__ C = Pb.cst;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double2* Bd = Pb.d_b + (int64_t)blockIdx.x * Pb.d_b_stride;
+    double* dg = Pb.d_diag + (int64_t)blockIdx.x * Pb.d_diag_stride;
+    int32_t* rc = Pb.d_cnt + (int64_t)blockIdx.x * Pb.d_cnt_stride;
+    int2* stg = Pb.d_stg + (int64_t)blockIdx.x * Pb.d_stg_stride;
+    double* stg64 = Pb.d_stg64 + (int64_t)blockIdx.x * Pb.d_stg_stride;
+    const int L = Pb.max_len + 1;   // diagonal slot length (indexed by row)
+    const int cap = Pb.cap;
+    const double tMM = C->tMMd, d1 = C->d1d, d2 = C->d2d, e1 = C->e1d, e2 = C->e2d;
+    const double c1 = C->c1d, c2 = C->c2d, Wo = C->Wod, We = C->Wed;
+    for (;;) {
+        if (tid == 0) s_q = atomicAdd(&Pb.status->work_f64, 1);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();
+        const int n_items = Pb.f64_all ? Pb.n_work : *(volatile int*)&Pb.status->n_fallback;
+        if (q >= n_items) break;
+        const int2 it = Pb.f64_all ? Pb.items[q] : Pb.fallback[q];
+        const FamDesc& fd = Pb.fams[it.x];
+        const int p = it.y;
+        const int2 ab = fd.pairs[p];
+        const int64_t oa = fd.seq_off[ab.x], ob = fd.seq_off[ab.y];
+        const int m = (int)(fd.seq_off[ab.x + 1] - oa), n = (int)(fd.seq_off[ab.y + 1] - ob);
+        const uint8_t* x = fd.codes + oa;
+        const uint8_t* y = fd.codes + ob;
+        auto X = [&](int i) { return (i >= 1 && i <= m) ? (int)x[i - 1] : kEmpty; };
+        auto Y = [&](int j) { return (j >= 1 && j <= n) ? (int)y[j - 1] : kEmpty; };
+        auto slot = [&](int d, int v) -> double* { return dg + ((int64_t)((d % 3 + 3) % 3) * kNS + v) * L; };
+        // ---- pass 1: backward over anti-diagonals d = m+n .. 0
+        // slot values: 0 B_M, 1 B_X, 2 B_X2, 3 B_Y, 4 B_Y2, 5 Zm_b, 6 Ze_b, 7 Zf_b
+        int Eh1 = 0, Ep1 = 0, Eh2 = 0, Ep2 = 0;   // exponents of diagonals d+1, d+2
+        double Zh = 0.0, Zp = 0.0;
+        int eZh = 0, eZp = 0;
+        int32_t* EB = rc + L;            // [m+n+1] HMM exponents per diagonal
+        int32_t* EP = EB + (2 * L + 2);  // [m+n+1] PF exponents per diagonal
+        for (int d = m + n; d >= 0; --d) {
+            const int ilo = max(0, d - n), ihi = min(m, d);
+            double* cur[8];
+            for (int v = 0; v < 8; ++v) cur[v] = slot(d, v);
+            double mh = 0.0, mp = 0.0;
+            const double f2 = pow2d(Eh2 - Eh1), g2 = pow2d(Ep2 - Ep1);
+            for (int i = ilo + tid; i <= ihi; i += nt) {
+                const int j = d - i;
+                double D = 0, Dp = 0, Xb = 0, X2b = 0, Eb = 0, Yb = 0, Y2b = 0, Fb = 0;
+                if (i < m && j < n) {
+                    const int o = Y(j + 1) * kTab + X(i + 1);
+                    D = C->oddsd[o] * slot(d + 2, 0)[i + 1] * f2;
+                    Dp = C->wd[o] * slot(d + 2, 5)[i + 1] * g2;
+                }
+                if (i < m) { Xb = slot(d + 1, 1)[i + 1]; X2b = slot(d + 1, 2)[i + 1]; Eb = slot(d + 1, 6)[i + 1]; }
+                if (j < n) { Yb = slot(d + 1, 3)[i]; Y2b = slot(d + 1, 4)[i]; Fb = slot(d + 1, 7)[i]; }
+                double BM = tMM * D + d1 * (Xb + Yb) + d2 * (X2b + Y2b);
+                double BX = c1 * D + e1 * Xb, BX2 = c2 * D + e2 * X2b;
+                double BY = c1 * D + e1 * Yb, BY2 = c2 * D + e2 * Y2b;
+                double ZMB = Dp + Wo * (Eb + Fb), ZEB = Dp + We * Eb, ZFB = Dp + We * Fb;
+                if (i == m && j == n) {
+                    BM = C->taud[0]; BX = C->taud[1]; BY = C->taud[2]; BX2 = C->taud[3]; BY2 = C->taud[4];
+                    ZMB = ZEB = ZFB = 1.0;
+                }
+                if (i == 0 && j == 0) {
+                    Zh = C->pid[0] * D + C->pid[1] * Xb + C->pid[2] * Yb + C->pid[3] * X2b + C->pid[4] * Y2b;
+                    Zp = ZMB;
+                }
+                cur[0][i] = BM; cur[1][i] = BX; cur[2][i] = BX2; cur[3][i] = BY; cur[4][i] = BY2;
+                cur[5][i] = ZMB; cur[6][i] = ZEB; cur[7][i] = ZFB;
+                mh = fmax(mh, fmax(fmax(BM, BX), fmax(BX2, fmax(BY, BY2))));
+                mp = fmax(mp, fmax(ZMB, fmax(ZEB, ZFB)));
+            }
+            const double MH = block_max(mh, sred[0]);
+            const double MP = block_max(mp, sred[1]);
+            int kh = 0, kp = 0;
+            if (d != m + n) {
+                if (MH > 0.0) { frexp(MH, &kh); kh -= 1; }
+                if (MP > 0.0) { frexp(MP, &kp); kp -= 1; }
+            }
+            const double sh = pow2d(-kh), sp = pow2d(-kp);
+            const int Ed = Eh1 + kh, Fd = Ep1 + kp;
+            for (int i = ilo + tid; i <= ihi; i += nt) {
+                const int j = d - i;
+                for (int v = 0; v < 5; ++v) cur[v][i] *= sh;
+                for (int v = 5; v < 8; ++v) cur[v][i] *= sp;
+                Bd[(int64_t)i * (n + 1) + j] = make_double2(cur[0][i], cur[5][i]);
+            }
+            if (tid == 0) { EB[d] = (d == m + n) ? 0 : Ed; EP[d] = (d == m + n) ? 0 : Fd; }
+            if (d == 0 && tid == 0) { eZh = Eh1; eZp = Ep1; }
+            Eh2 = Eh1; Ep2 = Ep1;
+            Eh1 = (d == m + n) ? 0 : Ed; Ep1 = (d == m + n) ? 0 : Fd;
+            __syncthreads();
+        }
+        // totals (thread 0 computed them at d = 0, in units of diagonal 1)
+        if (tid == 0) { sred[0][0] = Zh; sred[1][0] = Zp; ired[0] = eZh; ired[1] = eZp; }
+        __syncthreads();
+        Zh = sred[0][0]; Zp = sred[1][0]; eZh = ired[0]; eZp = ired[1];
+        __syncthreads();
+        // ---- pass 2: forward over d = 0 .. m+n
+        // slot values: 0 Mdiag, 1 Xin, 2 X2in, 3 Yin, 4 Y2in, 5 Zd, 6 Ein, 7 Fin, 8 A
+        for (int i = tid; i <= m; i += nt) rc[i] = 0;
+        __syncthreads();
+        int Fh1 = 0, Fp1 = 0, Fh2 = 0, Fp2 = 0;
+        double fZh = 0, fZp = 0, Aend = 0;
+        int feh = 0, fep = 0;
+        const double theta = C->thetad;
+        const int comb = C->combine;
+        for (int d = 0; d <= m + n; ++d) {
+            const int ilo = max(0, d - n), ihi = min(m, d);
+            double* cur[9];
+            for (int v = 0; v < 9; ++v) cur[v] = slot(d, v);
+            const double f2 = pow2d(Fh2 - Fh1), g2 = pow2d(Fp2 - Fp1);
+            double mh = 0.0, mp = 0.0;
+            // the thread for row i is fixed: i = tid (mod nt)
+            const int i0 = ilo + ((tid - ilo) % nt + nt) % nt;
+            for (int i = i0; i <= ihi; i += nt) {
+                const int j = d - i;
+                double Md = 0, Xi = 0, X2i = 0, Yi = 0, Y2i = 0, Zd = 0, Ei = 0, Fi = 0;
+                double Adg = 0, Aup = 0, Alf = 0;
+                if (i >= 1 && j >= 1) { Md = slot(d - 2, 0)[i - 1] * f2; Zd = slot(d - 2, 5)[i - 1] * g2; Adg = slot(d - 2, 8)[i - 1]; }
+                if (i >= 1) { Xi = slot(d - 1, 1)[i - 1]; X2i = slot(d - 1, 2)[i - 1]; Ei = slot(d - 1, 6)[i - 1]; Aup = slot(d - 1, 8)[i - 1]; }
+                if (j >= 1) { Yi = slot(d - 1, 3)[i]; Y2i = slot(d - 1, 4)[i]; Fi = slot(d - 1, 7)[i]; Alf = slot(d - 1, 8)[i]; }
+                const int o = Y(j) * kTab + X(i);
+                const double FM = C->oddsd[o] * Md, FX = Xi, FX2 = X2i, FY = Yi, FY2 = Y2i;
+                const double ZM = C->wd[o] * Zd, ZE = Ei, ZF = Fi;
+                double nMd = tMM * FM + c1 * (FX + FY) + c2 * (FX2 + FY2);
+                double nXi = d1 * FM + e1 * FX, nX2i = d2 * FM + e2 * FX2;
+                double nYi = d1 * FM + e1 * FY, nY2i = d2 * FM + e2 * FY2;
+                double nZd = ZM + ZE + ZF, nEi = Wo * ZM + We * ZE, nFi = Wo * ZM + We * ZF;
+                double A = 0.0;
+                if (i >= 1 && j >= 1) {
+                    const double2 b = Bd[(int64_t)i * (n + 1) + j];
+                    // F in units of the previous diagonal, B in units of its diagonal
+                    const double ph = ldexp(FM * b.x / Zh, Fh1 + EB[d] - eZh);
+                    const double pp = ldexp(ZM * b.y / Zp, Fp1 + EP[d] - eZp);
+                    double P;
+                    if (comb == 0) P = sqrt(0.5 * (ph * ph + pp * pp));
+                    else if (comb == 1) P = 0.5 * (ph + pp);
+                    else if (comb == 2) P = ph;
+                    else P = pp;
+                    if (P >= theta) {
+                        const int qq = rc[i]++;
+                        if (qq < cap) {
+                            stg[(int64_t)(i - 1) * cap + qq] = make_int2(j - 1, __float_as_int((float)P));
+                            stg64[(int64_t)(i - 1) * cap + qq] = P;
+                        }
+                    }
+                    A = fmax(Adg + P, fmax(Aup, Alf));
+                }
+                if (i == 0 && j == 0) {
+                    nMd = C->pid[0]; nXi = C->pid[1]; nYi = C->pid[2]; nX2i = C->pid[3]; nY2i = C->pid[4];
+                    nZd = 1.0; nEi = Wo; nFi = Wo;
+                }
+                if (i == m && j == n) {
+                    fZh = C->taud[0] * FM + C->taud[1] * FX + C->taud[2] * FY + C->taud[3] * FX2 + C->taud[4] * FY2;
+                    fZp = ZM + ZE + ZF;
+                    Aend = A;
+                    feh = Fh1; fep = Fp1;
+                }
+                cur[0][i] = nMd; cur[1][i] = nXi; cur[2][i] = nX2i; cur[3][i] = nYi; cur[4][i] = nY2i;
+                cur[5][i] = nZd; cur[6][i] = nEi; cur[7][i] = nFi; cur[8][i] = A;
+                mh = fmax(mh, fmax(fmax(nMd, nXi), fmax(nX2i, fmax(nYi, nY2i))));
+                mp = fmax(mp, fmax(nZd, fmax(nEi, nFi)));
+            }
+            const double MH = block_max(mh, sred[0]);
+            const double MP = block_max(mp, sred[1]);
+            int kh = 0, kp = 0;
+            if (MH > 0.0) { frexp(MH, &kh); kh -= 1; }
+            if (MP > 0.0) { frexp(MP, &kp); kp -= 1; }
+            const double sh = pow2d(-kh), sp = pow2d(-kp);
+            for (int i = i0; i <= ihi; i += nt) {
+                for (int v = 0; v < 5; ++v) cur[v][i] *= sh;
+                for (int v = 5; v < 8; ++v) cur[v][i] *= sp;
+            }
+            Fh2 = Fh1; Fp2 = Fp1;
+            Fh1 += kh; Fp1 += kp;
+            __syncthreads();
+        }
+        // gather the corner values from the thread that held row m
+        if (tid == m % nt) {
+            sred[0][0] = fZh; sred[1][0] = fZp; sred[0][1] = Aend; ired[0] = feh; ired[1] = fep;
+        }
+        __syncthreads();
+        fZh = sred[0][0]; fZp = sred[1][0]; Aend = sred[0][1]; feh = ired[0]; fep = ired[1];
+        __syncthreads();
+        // ---- flush entries per 128-row strip
+        const int nstrips = (m + 1 + kStripRows - 1) / kStripRows;
+        const int64_t row_slot = fd.pair_row_off[p];
+        int64_t pair_tot = 0;
+        for (int s = 0; s < nstrips; ++s) {
+            const int r0 = max(1, s * kStripRows), r1 = min(m, s * kStripRows + kStripRows - 1);
+            int my = 0;
+            for (int i = r0 + tid; i <= r1; i += nt) {
+                if (rc[i] > cap) { atomicExch(&Pb.status->stage_overflow, 1); rc[i] = cap; }
+                my += rc[i];
+            }
+            const int tot = block_sum(my, ired);
+            if (tid == 0) s_base = tot ? atomicAdd(fd.pool_used, (unsigned long long)tot) : 0ull;
+            __syncthreads();
+            const bool fits = (int64_t)s_base + tot <= fd.pool_cap;
+            const int64_t base = fd.pool_base + (int64_t)s_base;
+            if (!fits && tid == 0) atomicExch(&Pb.status->pool_overflow, 1);
+            // serial prefix over the strip's rows by thread 0 (plain form), then copy
+            if (tid == 0) {
+                int64_t w = 0;
+                for (int i = r0; i <= r1; ++i) {
+                    fd.row_cnt[row_slot + i - 1] = rc[i];
+                    const int c0 = rc[i];
+                    rc[i] = (int)w;   // reused as the row's offset within the strip
+                    w += c0;
+                }
+                fd.chunk_off[fd.pair_strip_off[p] + s] = base;
+            }
+            __syncthreads();
+            if (fits) {
+                for (int i = r0 + tid; i <= r1; i += nt) {
+                    const int cnt = fd.row_cnt[row_slot + i - 1];
+                    const int o = rc[i];
+                    for (int qq = 0; qq < cnt; ++qq) {
+                        Pb.pool[base + o + qq] = stg[(int64_t)(i - 1) * cap + qq];
+                        if (Pb.pool64) Pb.pool64[base + o + qq] = stg64[(int64_t)(i - 1) * cap + qq];
+                    }
+                }
+            }
+            pair_tot += tot;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const double ln2 = 0.69314718055994530942;
+            const double lzb_h = log(Zh) + (double)eZh * ln2;
+            const double lzb_p = log(Zp) + (double)eZp * ln2;
+            fd.mea[p] = Aend;
+            fd.logz_h[p] = lzb_h + fd.seq_logq[ab.x] + fd.seq_logq[ab.y];
+            fd.logz_p[p] = lzb_p;
+            fd.pair_nnz[p] = pair_tot;
+            const double lzf_h = log(fZh) + (double)feh * ln2;
+            const double lzf_p = log(fZp) + (double)fep * ln2;
+            const bool agree = fabs(lzb_h - lzf_h) <= 1e-8 * fmax(1.0, fabs(lzb_h)) &&
+                               fabs(lzb_p - lzf_p) <= 1e-8 * fmax(1.0, fabs(lzb_p));
+            fd.pair_flags[p] = (Pb.f64_all ? 0 : (fd.pair_flags[p] | 1)) | (agree ? 0 : 2);
+            const int mn = min(m, n);
+            const double dd = 1.0 - Aend / (double)mn;
+            const int64_t kk = fd.k;
+            fd.dist[ab.x * kk + ab.y] = (float)dd;
+            fd.dist[ab.y * kk + ab.x] = (float)dd;
+            fd.dist64[ab.x * kk + ab.y] = dd;
+            fd.dist64[ab.y * kk + ab.x] = dd;
+            if (fd.n_done) { __threadfence(); atomicAdd(fd.n_done, 1); }
+        }
+        __syncthreads();
+    }
+}
+
+int posterior_f64_occupancy(int* blocks_per_sm) {
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f64,
+                                                              kF64Threads, 0);
+}
+
+cudaError_t launch_posterior_f64(const Problem& P, int grid, cudaStream_t s) {
+    k_posterior_f64<<<grid, kF64Threads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+// ================================================================ CSR assembly
+__global__ void k_scan_nnz(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
+    // single CTA: each thread scans a contiguous segment, then the CTA scans
+    // the segment totals
+    __shared__ int64_t part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t per = (n + nt - 1) / nt;
+    const int64_t lo = min(n, per * tid), hi = min(n, lo + per);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += in[i];
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < nt; ++i) { const int64_t v = part[i]; part[i] = acc; acc += v; }
+        out[n] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[tid];
+    for (int64_t i = lo; i < hi; ++i) { out[i] = acc; acc += in[i]; }
+}
+
+__global__ void k_compact(const int2* __restrict__ pairs, const int64_t* __restrict__ seq_off,
+                          const int64_t* __restrict__ pair_row_off, const int64_t* __restrict__ pair_strip_off,
+                          const int32_t* __restrict__ row_cnt, const int64_t* __restrict__ chunk_off,
+                          const int2* __restrict__ pool, const double* __restrict__ pool64, int64_t n_pairs,
+                          const int64_t* __restrict__ pair_nnz_off, int32_t* __restrict__ row_ptr,
+                          int32_t* __restrict__ col, float* __restrict__ val, double* __restrict__ val64) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= n_pairs) return;
+    const int2 ab = pairs[p];
+    const int m = (int)(seq_off[ab.x + 1] - seq_off[ab.x]);
+    const int64_t ro = pair_row_off[p];
+    // row pointers: exclusive scan of the row counts, 32 rows at a time
+    int carry = 0;
+    for (int r0 = 0; r0 <= m; r0 += 32) {
+        const int r = r0 + lane;
+        const int v = (r < m) ? row_cnt[ro + r] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (r <= m) row_ptr[ro + r] = carry + incl - v;
+        carry += __shfl_sync(FULL, incl, 31);
+    }
+    __syncwarp();
+    const int64_t base = pair_nnz_off[p];
+    const int nstrips = (m + 1 + kStripRows - 1) / kStripRows;
+    for (int s = 0; s < nstrips; ++s) {
+        const int r0 = max(1, s * kStripRows) - 1;
+        const int r1 = min(m + 1, s * kStripRows + kStripRows) - 1;
+        const int beg = row_ptr[ro + r0], end = row_ptr[ro + r1];
+        const int64_t src = chunk_off[pair_strip_off[p] + s];
+        for (int e = lane; e < end - beg; e += 32) {
+            const int2 v = pool[src + e];
+            col[base + beg + e] = v.x;
+            val[base + beg + e] = __int_as_float(v.y);
+            if (val64) val64[base + beg + e] = pool64[src + e];
+        }
+    }
+}
+
+cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,
+                            cudaStream_t s) {
+    k_scan_nnz<<<1, 1024, 0, s>>>(pair_nnz, n_pairs, pair_nnz_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
+                           const int64_t* pair_row_off, const int64_t* pair_strip_off,
+                           const int32_t* row_cnt, const int64_t* chunk_off, const int2* pool,
+                           const double* pool64, int64_t n_pairs, const int64_t* pair_nnz_off,
+                           int32_t* row_ptr, int32_t* col, float* val, double* val64,
+                           cudaStream_t s) {
+    const int64_t threads = n_pairs * 32;
+    const int blocks = (int)((threads + 255) / 256);
+    if (blocks > 0)
+        k_compact<<<blocks, 256, 0, s>>>(pairs, seq_off, pair_row_off, pair_strip_off, row_cnt, chunk_off,
+                                         pool, pool64, n_pairs, pair_nnz_off, row_ptr, col, val, val64);
+    return cudaGetLastError();
+}
+
+}  // namespace qpk

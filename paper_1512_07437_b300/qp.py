@@ -1,0 +1,331 @@
+"""ctypes binding of libqp.so (include/qp.h), same names as the C entry points.
+
+Argument marshalling only: every step of the posterior stage runs in the
+library's CUDA kernels.  There is no fallback: if libqp.so is missing or no
+CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqp.so")
+
+QP_OK, QP_EINVAL, QP_ENOMEM, QP_ECUDA, QP_ETIMEOUT, QP_ECANCELLED, QP_ENOTREADY = range(7)
+QP_COMBINE = {"rms": 0, "mean": 1, "hmm": 2, "pf": 3}
+QP_PRECISION = {"f32": 0, "f64": 1}
+QP_F32_SCALED, QP_F64_PLAIN = 0, 1
+_STATUS_NAMES = {0: "QP_OK", 1: "QP_EINVAL", 2: "QP_ENOMEM", 3: "QP_ECUDA",
+                 4: "QP_ETIMEOUT", 5: "QP_ECANCELLED", 6: "QP_ENOTREADY"}
+GUARD_BITS = {2: "range", 3: "gap", 4: "factor", 5: "post", 6: "agree_hmm", 7: "agree_pf",
+              8: "total", 9: "corner", 10: "stage", 11: "pool"}
+
+
+class QpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qp_family(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("residues_on_device", ctypes.c_int32),
+                ("residues", ctypes.c_void_p), ("offsets", ctypes.POINTER(ctypes.c_int64))]
+
+
+class qp_params(ctypes.Structure):
+    _fields_ = [
+        ("pi", ctypes.c_double * 5),
+        ("delta1", ctypes.c_double), ("eps1", ctypes.c_double),
+        ("delta2", ctypes.c_double), ("eps2", ctypes.c_double),
+        ("emit_pair", ctypes.c_double * 400), ("emit_bg", ctypes.c_double * 20),
+        ("end_w", ctypes.c_double * 5), ("score", ctypes.c_double * 400),
+        ("gap_open", ctypes.c_double), ("gap_ext", ctypes.c_double),
+        ("temperature", ctypes.c_double),
+        ("end_gap_mode", ctypes.c_int32), ("combine", ctypes.c_int32),
+        ("threshold", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class qp_result(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int32), ("on_device", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("n_pairs", ctypes.c_int64), ("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64),
+        ("pair_row_off", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p),
+        ("pair_nnz_off", ctypes.c_void_p), ("col", ctypes.c_void_p),
+        ("val", ctypes.c_void_p), ("val64", ctypes.c_void_p),
+        ("dist", ctypes.c_void_p), ("dist64", ctypes.c_void_p),
+        ("mea", ctypes.c_void_p), ("log_z_hmm", ctypes.c_void_p),
+        ("log_z_pf", ctypes.c_void_p), ("pair_flags", ctypes.c_void_p),
+        ("kernel_ms", ctypes.c_double * 4), ("n_fallback", ctypes.c_int64),
+        ("guard_info", ctypes.c_int32 * 12), ("owner_", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libqp.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1512_07437_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        L.qp_posteriors.argtypes = [P(qp_family), P(qp_params), ctypes.c_int32, P(P(qp_result))]
+        L.qp_posteriors.restype = ctypes.c_int
+        L.qp_result_free.argtypes = [P(qp_result)]
+        L.qp_result_free.restype = None
+        L.qp_last_error.restype = ctypes.c_char_p
+        L.qp_version.restype = ctypes.c_char_p
+        L.qp_server_create.argtypes = [P(qp_params), ctypes.c_size_t, P(ctypes.c_void_p)]
+        L.qp_server_create.restype = ctypes.c_int
+        L.qp_server_submit.argtypes = [ctypes.c_void_p, P(qp_family), P(ctypes.c_uint64)]
+        L.qp_server_submit.restype = ctypes.c_int
+        L.qp_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, P(P(qp_result))]
+        L.qp_server_poll.restype = ctypes.c_int
+        L.qp_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+        L.qp_server_cancel.restype = ctypes.c_int
+        L.qp_server_destroy.argtypes = [ctypes.c_void_p]
+        L.qp_server_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def qp_last_error() -> str:
+    return lib().qp_last_error().decode()
+
+
+def qp_version() -> str:
+    return lib().qp_version().decode()
+
+
+def _check(rc: int):
+    if rc != QP_OK:
+        raise QpError(rc, qp_last_error())
+
+
+def make_params(prm, device: int = 0, stream=None, threshold: Optional[float] = None,
+                combine: Optional[str] = None, precision: Optional[str] = None) -> qp_params:
+    """qp_params from any object with the model fields (pi, delta1, ...)."""
+    p = qp_params()
+    p.pi[:] = [float(v) for v in prm.pi]
+    p.delta1, p.eps1 = float(prm.delta1), float(prm.eps1)
+    p.delta2, p.eps2 = float(prm.delta2), float(prm.eps2)
+    p.emit_pair[:] = [float(v) for v in np.asarray(prm.emit_pair).reshape(-1)]
+    p.emit_bg[:] = [float(v) for v in prm.emit_bg]
+    p.end_w[:] = [float(v) for v in prm.end_w]
+    p.score[:] = [float(v) for v in np.asarray(prm.score).reshape(-1)]
+    p.gap_open, p.gap_ext = float(prm.gap_open), float(prm.gap_ext)
+    p.temperature = float(prm.temperature)
+    p.end_gap_mode = int(getattr(prm, "end_gap_mode", 0))
+    c = combine if combine is not None else prm.combine
+    p.combine = QP_COMBINE[c] if isinstance(c, str) else int(c)
+    p.threshold = float(threshold if threshold is not None else prm.threshold)
+    pr = precision if precision is not None else prm.precision
+    p.precision = QP_PRECISION[pr] if isinstance(pr, str) else int(pr)
+    p.device = int(device)
+    if stream is None:
+        p.stream = None
+    elif isinstance(stream, int):
+        p.stream = stream
+    else:   # torch.cuda.Stream
+        p.stream = int(stream.cuda_stream)
+    return p
+
+
+def make_family(residues, offsets) -> tuple:
+    """qp_family from residues (numpy uint8 host array, or a torch CUDA uint8
+    tensor) and host int64 offsets.  Returns (struct, keep-alive tuple)."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    f = qp_family()
+    f.k = int(off.shape[0] - 1)
+    if hasattr(residues, "is_cuda") and residues.is_cuda:
+        f.residues_on_device = 1
+        f.residues = int(residues.data_ptr())
+        keep = (residues, off)
+    else:
+        res = np.ascontiguousarray(np.asarray(residues, dtype=np.uint8))
+        f.residues_on_device = 0
+        f.residues = res.ctypes.data
+        keep = (res, off)
+    f.offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    return f, keep
+
+
+class _DevArray:
+    """Exposes a device pointer through __cuda_array_interface__."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+            "version": 3, "strides": None, "stream": None}
+
+
+class Result:
+    """Owns a qp_result; arrays are numpy (host) or torch (device) views."""
+
+    _FIELDS = {
+        "pair_row_off": ("<i8", lambda r: r.n_pairs + 1),
+        "row_ptr": ("<i4", lambda r: r.n_rows),
+        "pair_nnz_off": ("<i8", lambda r: r.n_pairs + 1),
+        "col": ("<i4", lambda r: r.nnz),
+        "val": ("<f4", lambda r: r.nnz),
+        "val64": ("<f8", lambda r: r.nnz),
+        "dist": ("<f4", lambda r: r.k * r.k),
+        "dist64": ("<f8", lambda r: r.k * r.k),
+        "mea": ("<f8", lambda r: r.n_pairs),
+        "log_z_hmm": ("<f8", lambda r: r.n_pairs),
+        "log_z_pf": ("<f8", lambda r: r.n_pairs),
+        "pair_flags": ("<i4", lambda r: r.n_pairs),
+    }
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+        r = ptr.contents
+        self.k = r.k
+        self.on_device = bool(r.on_device)
+        self.n_pairs = r.n_pairs
+        self.n_rows = r.n_rows
+        self.nnz = r.nnz
+        self.kernel_ms = list(r.kernel_ms)
+        self.n_fallback = r.n_fallback
+        self.guard_info = list(r.guard_info)
+        self.precision = r.precision
+
+    def array(self, name):
+        r = self._ptr.contents
+        typestr, n = self._FIELDS[name]
+        n = int(n(r))
+        addr = getattr(r, name)
+        if not addr:
+            return None
+        shape = (self.k, self.k) if name in ("dist", "dist64") else (n,)
+        if self.on_device:
+            import torch
+            return torch.as_tensor(_DevArray(addr, shape, typestr, self), device=f"cuda:{r.device}")
+        dt = np.dtype(typestr)
+        if n == 0:
+            return np.zeros(shape, dtype=dt)
+        buf = (ctypes.c_char * (n * dt.itemsize)).from_address(addr)
+        return np.frombuffer(buf, dtype=dt, count=n).reshape(shape)
+
+    def __getattr__(self, name):
+        if name in Result._FIELDS:
+            return self.array(name)
+        raise AttributeError(name)
+
+    def pair_csr(self, p: int):
+        """(row_ptr, col, val, val64-or-None) of pair p as host numpy arrays."""
+        def h(x):
+            return x.cpu().numpy() if hasattr(x, "cpu") else x
+        pro = h(self.array("pair_row_off"))
+        pno = h(self.array("pair_nnz_off"))
+        rp = h(self.array("row_ptr"))[pro[p]:pro[p + 1]]
+        lo, hi = int(pno[p]), int(pno[p + 1])
+        col = h(self.array("col"))[lo:hi]
+        val = h(self.array("val"))[lo:hi]
+        v64 = self.array("val64")
+        v64 = h(v64)[lo:hi] if v64 is not None else None
+        return rp, col, val, v64
+
+    def free(self):
+        if self._ptr is not None:
+            lib().qp_result_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def qp_posteriors(residues, offsets, params, out_on_device: bool = False, device: int = 0,
+                  stream=None, **overrides) -> Result:
+    """All-pairs posteriors, sparse matrices and MEA distances of one family.
+
+    ``params`` is a qp_params or any object with the model fields."""
+    L = lib()
+    fam, keep = make_family(residues, offsets)
+    prm = params if isinstance(params, qp_params) else make_params(params, device=device,
+                                                                   stream=stream, **overrides)
+    out = ctypes.POINTER(qp_result)()
+    rc = L.qp_posteriors(ctypes.byref(fam), ctypes.byref(prm), int(bool(out_on_device)),
+                         ctypes.byref(out))
+    del keep
+    _check(rc)
+    return Result(out)
+
+
+def qp_result_free(result: Result):
+    result.free()
+
+
+class Server:
+    """Serving loop (qp_server_*)."""
+
+    def __init__(self, params, mem_budget: int, device: int = 0):
+        self._keep = params if isinstance(params, qp_params) else make_params(params, device=device)
+        h = ctypes.c_void_p()
+        _check(lib().qp_server_create(ctypes.byref(self._keep), int(mem_budget), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, residues, offsets) -> int:
+        fam, keep = make_family(residues, offsets)
+        t = ctypes.c_uint64()
+        rc = lib().qp_server_submit(self._h, ctypes.byref(fam), ctypes.byref(t))
+        del keep
+        _check(rc)
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_ms: int = -1) -> Optional[Result]:
+        out = ctypes.POINTER(qp_result)()
+        rc = lib().qp_server_poll(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(out))
+        if rc in (QP_ENOTREADY, QP_ETIMEOUT):
+            return None
+        _check(rc)
+        return Result(out)
+
+    def cancel(self, ticket: int):
+        _check(lib().qp_server_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            lib().qp_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def qp_server_create(params, mem_budget: int, device: int = 0) -> Server:
+    return Server(params, mem_budget, device)
+
+
+def qp_server_submit(server: Server, residues, offsets) -> int:
+    return server.submit(residues, offsets)
+
+
+def qp_server_poll(server: Server, ticket: int, timeout_ms: int = -1):
+    return server.poll(ticket, timeout_ms)
+
+
+def qp_server_cancel(server: Server, ticket: int):
+    server.cancel(ticket)
+
+
+def qp_server_destroy(server: Server):
+    server.destroy()

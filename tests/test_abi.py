@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    hdr = ""
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            hdr += open(os.path.join(inc, f)).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(qp_[a-z0-9_]+)\s*\(", hdr)))
+
+
+@pytest.fixture(scope="module")
+def libqp():
+    import paper_1512_07437_b300.build as b
+    b.build()
+    import paper_1512_07437_b300 as qp
+    return qp.lib()
+
+
+def test_library_exports_every_declared_entry_point(libqp):
+    names = _declared_symbols()
+    assert "qp_posteriors" in names and "qp_server_poll" in names
+    for n in names:
+        assert hasattr(libqp, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only",
+                          os.path.join(ROOT, "paper_1512_07437_b300", "libqp.so")],
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (qp_[a-z0-9_]+)", out))
+    assert set(names) <= exported
+
+
+def test_build_targets_sm_103a_only():
+    import paper_1512_07437_b300.build as b
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_struct_layout_matches_header(libqp):
+    """ctypes mirrors must match the C structs."""
+    import paper_1512_07437_b300.qp as q
+    assert ctypes.sizeof(q.qp_family) == 24
+    # pi..score: 5+4+400+20+5+400 doubles, 3 doubles, 2 ints, 1 double, 2 ints, 1 pointer
+    assert ctypes.sizeof(q.qp_params) == 8 * (5 + 4 + 400 + 20 + 5 + 400 + 3) + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(q.qp_result) == 4 * 4 + 8 * 3 + 8 * 12 + 8 * 4 + 8 + 4 * 12 + 8
+
+
+def test_no_device_fails_loudly(libqp):
+    """Without a usable GPU the product path raises; it never computes on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import synth
+    import paper_1512_07437_b300 as qp
+    fam = synth.star_family(1, 3, (20, 30), 0.3)
+    with pytest.raises(qp.QpError):
+        qp.qp_posteriors(fam.residues, fam.offsets, synth.default_params())
+
+
+def test_invalid_inputs_rejected_on_host(libqp):
+    """Malformed families and parameters are rejected before any device work."""
+    import synth
+    import paper_1512_07437_b300 as qp
+    prm = synth.default_params()
+    fam = synth.star_family(1, 3, (20, 30), 0.3)
+    bad_offsets = fam.offsets.copy()
+    bad_offsets[2] = bad_offsets[1]            # empty sequence
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_posteriors(fam.residues, bad_offsets, prm)
+    assert e.value.code == 1
+    with pytest.raises(qp.QpError) as e:      # k < 2
+        qp.qp_posteriors(fam.residues[:10], np.array([0, 10]), prm)
+    assert e.value.code == 1
+    for field, value in (("threshold", 0.0), ("threshold", 1.5), ("temperature", -1.0)):
+        bad = prm.replace(**{field: value})
+        with pytest.raises(qp.QpError) as e:
+            qp.qp_posteriors(fam.residues, fam.offsets, bad)
+        assert e.value.code == 1, field
+    bad = prm.replace(pi=np.array([0.5, 0.1, 0.1, 0.1, 0.1]))
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_posteriors(fam.residues, fam.offsets, bad)
+    assert e.value.code == 1

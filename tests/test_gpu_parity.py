@@ -1,0 +1,195 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP32 scaled form <= 1e-5 on every posterior and distance (the
+spec bar); FP64 plain form <= 1e-9.  Sparse patterns must match
+wherever |P - theta| > 1e-5.  FP32 results must come from the FP32 kernel:
+the tests assert that no pair was handed to the FP64 form unless stated.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import (TOL_F32, TOL_F64, TOL_LOGZ32, TOL_LOGZ64, compare_pair, dense_of,
+                      guard_report, host)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1512_07437_b300 as qp
+    qp.lib()
+    return qp
+
+
+DENSE = 1e-30     # threshold that keeps every non-negligible entry
+
+
+def _run(qp, fam, prm, **kw):
+    return qp.qp_posteriors(fam.residues, fam.offsets, prm, device=0, **kw)
+
+
+def _no_fallback(res):
+    assert res.n_fallback == 0, f"FP32 guards fired: {guard_report(res)} first event {res.guard_info}"
+
+
+@pytest.mark.parametrize("precision,tol,tlz", [("f32", TOL_F32, TOL_LOGZ32), ("f64", TOL_F64, TOL_LOGZ64)])
+def test_small_family_all_pairs_dense(qp, precision, tol, tlz):
+    """8 sequences, lengths 100-150 (the small configuration), every pair, every cell."""
+    fam = synth.make_family("c1", 1)
+    prm = synth.default_params(threshold=DENSE)
+    res = _run(qp, fam, prm, precision=precision)
+    assert res.n_pairs == 28
+    _no_fallback(res)
+    worst = 0.0
+    for p, (a, b) in enumerate(fam.pairs()):
+        worst = max(worst, compare_pair(res, fam, p, a, b, prm, tol, tlz)["p_err"])
+    print(f"{precision}: worst |dP| = {worst:.3e}")
+
+
+@pytest.mark.parametrize("precision,tol,tlz", [("f32", TOL_F32, TOL_LOGZ32), ("f64", TOL_F64, TOL_LOGZ64)])
+def test_small_family_threshold_pattern(qp, precision, tol, tlz):
+    fam = synth.make_family("c1", 2)
+    prm = synth.default_params(threshold=0.01)
+    res = _run(qp, fam, prm, precision=precision)
+    _no_fallback(res)
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(res, fam, p, a, b, prm, tol, tlz, dense=False)
+
+
+EDGE_LENGTHS = [1, 2, 3, 31, 32, 33, 95, 96, 97, 126, 127, 128, 129, 200, 255, 256, 257, 300]
+
+
+@pytest.mark.parametrize("precision,tol,tlz", [("f32", TOL_F32, TOL_LOGZ32), ("f64", TOL_F64, TOL_LOGZ64)])
+def test_edge_lengths(qp, precision, tol, tlz):
+    """Lengths at lane, rows-per-lane and strip boundaries, m >> n and n >> m."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    q = synth.background()
+    root = rng.choice(20, size=320, p=q).astype(np.uint8)
+    seqs = []
+    for L in EDGE_LENGTHS:
+        leaf = synth.evolve(rng, root[:L], 0.2, q)[:L]
+        if leaf.size < L:
+            leaf = np.concatenate([leaf, rng.choice(20, size=L - leaf.size, p=q).astype(np.uint8)])
+        seqs.append("".join(synth.ALPHABET[c] for c in leaf))
+    fam = synth.family_from_strings(seqs)
+    prm = synth.default_params(threshold=DENSE)
+    res = _run(qp, fam, prm, precision=precision)
+    _no_fallback(res)
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(res, fam, p, a, b, prm, tol, tlz)
+
+
+@pytest.mark.parametrize("combine", ["mean", "hmm", "pf"])
+def test_combination_modes(qp, combine):
+    fam = synth.star_family(5, 5, (80, 180), 0.3)
+    prm = synth.default_params(threshold=DENSE, combine=combine)
+    res = _run(qp, fam, prm)
+    _no_fallback(res)
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(res, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32)
+
+
+def test_nondefault_parameters(qp):
+    """Non-uniform start, unequal end weights, other gap constants."""
+    prm = synth.default_params(delta1=0.07, eps1=0.55, delta2=0.03, eps2=0.85,
+                               gap_open=-5.0, gap_ext=-2.0, temperature=2.0, threshold=DENSE)
+    prm = prm.replace(pi=np.array([0.6, 0.1, 0.15, 0.05, 0.1]),
+                      end_w=np.array([1.0, 0.7, 0.4, 0.9, 0.2]))
+    fam = synth.star_family(8, 5, (100, 260), 0.35)
+    for precision, tol, tlz in (("f32", TOL_F32, TOL_LOGZ32), ("f64", TOL_F64, TOL_LOGZ64)):
+        res = _run(qp, fam, prm, precision=precision)
+        _no_fallback(res)
+        for p, (a, b) in enumerate(fam.pairs()):
+            compare_pair(res, fam, p, a, b, prm, tol, tlz)
+
+
+def test_identical_and_unrelated_sequences(qp):
+    """Range stress for the FP32 rescaling: identical sequences (totals grow by
+    ~e^2.6 per residue) and unrelated random sequences."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    q = synth.background()
+    s = "".join(synth.ALPHABET[c] for c in rng.choice(20, size=400, p=q))
+    r1 = "".join(synth.ALPHABET[c] for c in rng.choice(20, size=380, p=q))
+    r2 = "".join(synth.ALPHABET[c] for c in rng.choice(20, size=350, p=q))
+    fam = synth.family_from_strings([s, s, r1, r2])
+    prm = synth.default_params(threshold=DENSE)
+    res = _run(qp, fam, prm)
+    _no_fallback(res)
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(res, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32)
+
+
+def test_swap_gives_transpose(qp):
+    fam = synth.star_family(12, 2, (150, 220), 0.3)
+    rev = synth.family_from_strings([fam.seq(1), fam.seq(0)])
+    prm = synth.default_params(threshold=DENSE)
+    r1 = _run(qp, fam, prm)
+    r2 = _run(qp, rev, prm)
+    m, n = fam.lengths
+    D1 = dense_of(r1, 0, m, n)
+    D2 = dense_of(r2, 0, n, m)
+    assert np.abs(D2 - D1.T).max() <= 2 * TOL_F32
+    assert abs(float(host(r1.dist64)[0, 1]) - float(host(r2.dist64)[0, 1])) <= 2 * TOL_F32
+
+
+def test_pair_alone_equals_pair_in_batch(qp):
+    """Batch invariance: a pair's FP32 result does not depend on what else is
+    in the launch (bitwise)."""
+    fam = synth.star_family(21, 10, (120, 300), 0.3)
+    prm = synth.default_params(threshold=0.001)
+    big = _run(qp, fam, prm)
+    _no_fallback(big)
+    a, b = 3, 7
+    p = synth.pair_index(a, b, fam.k)
+    alone = _run(qp, synth.family_from_strings([fam.seq(a), fam.seq(b)]), prm)
+    m, n = fam.lengths[a], fam.lengths[b]
+    assert np.array_equal(dense_of(big, p, m, n), dense_of(alone, 0, m, n))
+    assert float(host(big.mea)[p]) == float(host(alone.mea)[0])
+    assert float(host(big.log_z_hmm)[p]) == float(host(alone.log_z_hmm)[0])
+
+
+def test_medium_family_sampled_pairs(qp):
+    """64 sequences, lengths 200-400: the whole family in one launch (the
+    benchmark's configuration); a seeded sample of pairs against the oracle."""
+    fam = synth.make_family("c2", 1)
+    prm = synth.default_params(threshold=0.01)
+    res = _run(qp, fam, prm)
+    assert res.n_pairs == 2016
+    _no_fallback(res)
+    rng = np.random.Generator(np.random.PCG64(5))
+    pl = list(fam.pairs())
+    L = fam.lengths
+    longest = max(range(len(pl)), key=lambda q: L[pl[q][0]] * L[pl[q][1]])
+    shortest = min(range(len(pl)), key=lambda q: L[pl[q][0]] * L[pl[q][1]])
+    sample = sorted(set(rng.choice(len(pl), size=24, replace=False).tolist() + [longest, shortest]))
+    for q in sample:
+        a, b = pl[q]
+        compare_pair(res, fam, q, a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
+    dist = host(res.dist)
+    assert np.array_equal(dist, dist.T) and (np.diag(dist) == 0).all()
+    assert (dist >= -1e-6).all() and (dist <= 1 + 1e-6).all()
+
+
+def test_device_resident_input_and_output(qp):
+    """Residues already on the device, results left on the device (torch views)."""
+    import torch
+    fam = synth.star_family(31, 6, (90, 140), 0.3)
+    prm = synth.default_params(threshold=DENSE)
+    dres = torch.from_numpy(fam.residues).cuda()
+    r_dev = qp.qp_posteriors(dres, fam.offsets, prm, out_on_device=True, device=0)
+    assert r_dev.on_device and r_dev.val.is_cuda
+    r_host = _run(qp, fam, prm)
+    assert r_dev.nnz == r_host.nnz
+    assert np.array_equal(r_dev.val.cpu().numpy(), r_host.val)
+    assert np.array_equal(r_dev.col.cpu().numpy(), r_host.col)
+
+
+def test_invalid_residue_is_rejected(qp):
+    fam = synth.family_from_strings(["ACDEFGHIK", "ACDXFGHIK"])
+    with pytest.raises(qp.QpError) as e:
+        _run(qp, fam, synth.default_params())
+    assert e.value.code == 1
