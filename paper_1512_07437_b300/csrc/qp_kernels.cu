@@ -142,8 +142,11 @@ cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
 //
 // Scaling.  Every lane carries one power-of-two exponent per model.  All
 // lanes renormalise on the same steps (every kC steps): the lane's largest
-// carried value is brought into [1, 2).  Values received from the row above
-// are converted with 2^(e_above - e_me), which only changes on those steps.
+// carried value is brought into [1, 2); a lane that holds no value yet takes
+// the new exponent of the nearest upstream lane that does, so a lane starts
+// close to the magnitude of what will flow into it.  Values received from the
+// row above are converted with 2^(e_above - e_me), which only changes on those
+// steps.  A strip starts at the exponent of its boundary row's values.
 // A lane whose upstream neighbour is zero for good (padding rows below row m
 // in the backward pass, the missing row above the first strip in the forward
 // pass) keeps the neighbour's exponent equal to its own.  Pass 1 records its
@@ -170,6 +173,7 @@ struct PairCtx {
 };
 
 constexpr float kBig = 1.2676506002282294e30f;   // 2^100
+constexpr int kNoExp = (int)0x80000000;           // "no exponent yet" in the fill scan
 
 // Records the first guard event of a launch (site code and context) so that a
 // fallback can be explained from the host.
@@ -296,10 +300,18 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
     const bool owns_row = row0 + lane * R <= m;
     // the neighbour below is zero for good: padding rows, or no strip below
     const bool up_zero = (lane == 31) ? (bnd_in == nullptr) : (row0 + (lane + 1) * R > m);
-    int eH = 0, eP = 0;
-    if (bnd_in) { const float4 e = bnd_in[2 * n + 1]; eH = __float_as_int(e.z); eP = __float_as_int(e.w); }
-    int eUpH = eH, eUpP = eP;
-    float cvH = 1.f, cvP = 1.f;
+    // starting exponent: the boundary row's exponent, moved to the magnitude of
+    // its values at column n (every lane starts there)
+    int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
+    if (bnd_in) {
+        const float4 v0 = bnd_in[2 * n], v1 = bnd_in[2 * n + 1];
+        eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
+        const float bh = fmaxf(v0.x, fmaxf(v0.y, v0.z)), bp = fmaxf(v0.w, v1.x);
+        eH = eUpH + (bh > 0.f ? max(-126, min(126, ilog2f(bh))) : 0);
+        eP = eUpP + (bp > 0.f ? max(-126, min(126, ilog2f(bp))) : 0);
+        if (lane != 31) { eUpH = eH; eUpP = eP; }
+    }
+    float cvH = pow2f(eUpH - eH), cvP = pow2f(eUpP - eP);
     const int Lend = last_strip ? (m - row0) / R : -1;
     const int rend = last_strip ? (m - row0) % R : -1;
     const int t_end = last_strip ? 31 - Lend : -1;
@@ -320,15 +332,16 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
             const int j = n + 31 - lane - t;
             const bool live = owns_row && (j >= -1) && (j <= n);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
+            int fh = kNoExp, fp = kNoExp;
             if (mh > 0.f) {
                 const int k = max(-126, min(126, ilog2f(mh)));
                 const float sc = pow2f(-k);
 #pragma unroll
                 for (int r = 0; r < R; ++r) { Mn[r] *= sc; BXo[r] *= sc; BX2o[r] *= sc; BYo[r] *= sc; BY2o[r] *= sc; }
                 dMn *= sc;
-                eH += k;
-            } else {
-                eH = eUpH;
+                fh = eH + k;
+            } else if (lane == 31) {
+                fh = eH;
             }
             if (mp > 0.f) {
                 const int k = max(-126, min(126, ilog2f(mp)));
@@ -336,10 +349,21 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
 #pragma unroll
                 for (int r = 0; r < R; ++r) { Dpo[r] *= sc; ZEo[r] *= sc; ZFo[r] *= sc; }
                 dDp *= sc;
-                eP += k;
-            } else {
-                eP = eUpP;
+                fp = eP + k;
+            } else if (lane == 31) {
+                fp = eP;
             }
+            // a lane without state takes the new exponent of the nearest lane
+            // below it that has state (lane 31 keeps its own)
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int vh = __shfl_down_sync(FULL, fh, d), vp = __shfl_down_sync(FULL, fp, d);
+                if (lane + d < 32) {
+                    if (fh == kNoExp) fh = vh;
+                    if (fp == kNoExp) fp = vp;
+                }
+            }
+            eH = fh; eP = fp;
             const int uH = __shfl_down_sync(FULL, eH, 1);
             const int uP = __shfl_down_sync(FULL, eP, 1);
             if (lane != 31) { eUpH = uH; eUpP = uP; }
@@ -508,10 +532,18 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
     float4* bnd_out = last_strip ? nullptr : c.bnd;
     const bool owns_row = row0 + lane * R <= m;
     const bool up_zero = (lane == 0) && (bnd_in == nullptr);
-    int eH = 0, eP = 0;
-    if (bnd_in) { const float4 e = bnd_in[1]; eH = __float_as_int(e.z); eP = __float_as_int(e.w); }
-    int eUpH = eH, eUpP = eP;
-    float cvH = 1.f, cvP = 1.f;
+    // starting exponent: the boundary row's exponent, moved to the magnitude of
+    // its values at column 0 (every lane starts there)
+    int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
+    if (bnd_in) {
+        const float4 v0 = bnd_in[0], v1 = bnd_in[1];
+        eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
+        const float bh = fmaxf(v0.x, fmaxf(v0.y, v0.z)), bp = fmaxf(v0.w, v1.x);
+        eH = eUpH + (bh > 0.f ? max(-126, min(126, ilog2f(bh))) : 0);
+        eP = eUpP + (bp > 0.f ? max(-126, min(126, ilog2f(bp))) : 0);
+        if (lane != 0) { eUpH = eH; eUpP = eP; }
+    }
+    float cvH = pow2f(eUpH - eH), cvP = pow2f(eUpP - eP);
     const int Lend = last_strip ? (m - row0) / R : -1;
     const int rend = last_strip ? (m - row0) % R : -1;
     const int t_end = last_strip ? n + Lend : -1;
@@ -565,15 +597,16 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
             const int j = t - lane;
             const bool live = owns_row && (j >= 0) && (j <= n + 1);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
+            int fh = kNoExp, fp = kNoExp;
             if (mh > 0.f) {
                 const int k = max(-126, min(126, ilog2f(mh)));
                 const float sc = pow2f(-k);
 #pragma unroll
                 for (int r = 0; r < R; ++r) { Md[r] *= sc; Xi[r] *= sc; X2i[r] *= sc; Yi[r] *= sc; Y2i[r] *= sc; }
                 uMd *= sc;
-                eH += k;
-            } else {
-                eH = eUpH;
+                fh = eH + k;
+            } else if (lane == 0) {
+                fh = eH;
             }
             if (mp > 0.f) {
                 const int k = max(-126, min(126, ilog2f(mp)));
@@ -581,10 +614,21 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
 #pragma unroll
                 for (int r = 0; r < R; ++r) { Zd[r] *= sc; Ei[r] *= sc; Fi[r] *= sc; }
                 uZd *= sc;
-                eP += k;
-            } else {
-                eP = eUpP;
+                fp = eP + k;
+            } else if (lane == 0) {
+                fp = eP;
             }
+            // a lane without state takes the new exponent of the nearest lane
+            // above it that has state (lane 0 keeps its own)
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int vh = __shfl_up_sync(FULL, fh, d), vp = __shfl_up_sync(FULL, fp, d);
+                if (lane >= d) {
+                    if (fh == kNoExp) fh = vh;
+                    if (fp == kNoExp) fp = vp;
+                }
+            }
+            eH = fh; eP = fp;
             const int uH = __shfl_up_sync(FULL, eH, 1);
             const int uP = __shfl_up_sync(FULL, eP, 1);
             if (lane != 0) { eUpH = uH; eUpP = uP; }

@@ -193,3 +193,14 @@ def test_invalid_residue_is_rejected(qp):
     with pytest.raises(qp.QpError) as e:
         _run(qp, fam, synth.default_params())
     assert e.value.code == 1
+
+
+def test_long_pairs_stay_in_fp32(qp):
+    """Pairs of 500-700 residues (four to six strips): the per-lane exponents
+    must follow the values down the strip chain, so no range guard fires."""
+    fam = synth.star_family(44, 3, (560, 700), 0.3)
+    prm = synth.default_params(threshold=0.01)
+    res = _run(qp, fam, prm)
+    _no_fallback(res)
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(res, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
