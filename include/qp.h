@@ -182,6 +182,45 @@ int qp_server_poll(qp_server* server, uint64_t ticket, int32_t timeout_ms,
 int qp_server_cancel(qp_server* server, uint64_t ticket);
 void qp_server_destroy(qp_server* server);
 
+/* Allocation-free variant for callers that cannot allocate device memory.
+ * There is no counterpart in the paper: it exists for code that must not call
+ * cudaMalloc / cudaFree while it runs -- for instance a host program whose
+ * device memory is all handed to another allocator (a framework's caching
+ * pool or a fixed arena) so that a stray cudaMalloc can fail or fragment it,
+ * or a latency-critical loop that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree imply.
+ *
+ * It runs ONE pair (x, y) through the same FP32 posterior kernel as
+ * qp_posteriors, taking every piece of scratch memory from a fixed array
+ * compiled into libqp.so (about 5.5 MiB, held on every GPU that loads the
+ * library until the process exits).  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ *   residues : DEVICE memory of params->device, m + n ASCII residues: x
+ *              (m letters) immediately followed by y (n letters);
+ *   m, n     : 1 <= m, n <= QP_STATIC_MAX_LEN, else QP_EINVAL;
+ *   params   : as for qp_posteriors; precision must be QP_F32_SCALED;
+ *   row_ptr  : DEVICE int32[m + 1], CSR row pointers of P (rows = x);
+ *   col, val : DEVICE int32 / float [nnz_capacity], entries P >= threshold,
+ *              columns ascending within a row;
+ *   pair_out : DEVICE double[4] = MEA score, MEA distance, log Z_hmm, log Z_pf;
+ *   nnz_out  : HOST, the number of entries (also set when nnz_capacity is too
+ *              small, in which case QP_EINVAL is returned and the outputs are
+ *              left untouched).
+ * Values equal those of qp_posteriors for the same pair.  A pair that trips
+ * an FP32 range guard returns QP_ENOMEM (its FP64 recomputation needs more
+ * scratch than the fixed array holds; call qp_posteriors instead).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls share the one array: the call clears what has to
+ * start at zero, but two calls that overlap on the GPU (other host threads,
+ * other streams) race and corrupt each other.  The call returns after its
+ * work on params->stream (or the legacy default stream when NULL) is done. */
+#define QP_STATIC_MAX_LEN 512
+int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int32_t n,
+                              const qp_params* params, int32_t* row_ptr, int32_t* col,
+                              float* val, int64_t nnz_capacity, double* pair_out,
+                              int64_t* nnz_out);
+
 /* Thread-local message of the last failure on the calling thread. */
 const char* qp_last_error(void);
 

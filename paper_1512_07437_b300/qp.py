@@ -96,6 +96,11 @@ def lib():
         L.qp_server_cancel.restype = ctypes.c_int
         L.qp_server_destroy.argtypes = [ctypes.c_void_p]
         L.qp_server_destroy.restype = None
+        L.qp_pair_posteriors_static.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                                P(qp_params), ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                P(ctypes.c_int64)]
+        L.qp_pair_posteriors_static.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -265,6 +270,30 @@ def qp_posteriors(residues, offsets, params, out_on_device: bool = False, device
     del keep
     _check(rc)
     return Result(out)
+
+
+QP_STATIC_MAX_LEN = 512
+
+
+def qp_pair_posteriors_static(residues, m: int, n: int, params, row_ptr, col, val,
+                              pair_out, device: int = 0, stream=None) -> int:
+    """Allocation-free single-pair call (qp_pair_posteriors_static in qp.h).
+
+    For callers that may not allocate device memory while they run.  Every
+    array is a caller-owned CUDA tensor: ``residues`` uint8[m + n] (x then y,
+    ASCII), ``row_ptr`` int32[m + 1], ``col`` int32[cap], ``val`` float32[cap],
+    ``pair_out`` float64[4] (MEA score, distance, log Z_hmm, log Z_pf).
+    Returns the number of entries written."""
+    prm = params if isinstance(params, qp_params) else make_params(params, device=device,
+                                                                   stream=stream)
+    nnz = ctypes.c_int64(0)
+    cap = int(col.numel()) if col is not None else 0
+    rc = lib().qp_pair_posteriors_static(
+        int(residues.data_ptr()), int(m), int(n), ctypes.byref(prm), int(row_ptr.data_ptr()),
+        int(col.data_ptr()) if cap else None, int(val.data_ptr()) if cap else None, cap,
+        int(pair_out.data_ptr()), ctypes.byref(nnz))
+    _check(rc)
+    return int(nnz.value)
 
 
 def qp_result_free(result: Result):
