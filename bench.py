@@ -141,7 +141,8 @@ def cpu_baseline(fam, prm, budget_s: float, seed: int = 0):
     order = rng.permutation(len(pl))
     threads = os.cpu_count() or 1
     L = fam.lengths.astype(np.int64)
-    # calibrate on a few pairs, then size the sample to the time budget
+    # load the library, calibrate on a few pairs, then size the sample to the budget
+    oracle.pairs(fam, [pl[order[-1]]], prm, threads=1)
     probe = [pl[i] for i in order[:threads]]
     t0 = time.perf_counter()
     oracle.pairs(fam, probe, prm, threads=threads)
@@ -174,6 +175,7 @@ def run_reference(args, fam, prm, rank):
     pl = list(fam.pairs())
     rng = np.random.Generator(np.random.PCG64(args.seed + 100))
     L = fam.lengths.astype(np.int64)
+    oracle.pairs(fam, [pl[0]], prm, threads=1)
     probe = [pl[i] for i in rng.permutation(len(pl))[:threads]]
     t0 = time.perf_counter()
     oracle.pairs(fam, probe, prm, threads=threads)

@@ -252,9 +252,6 @@ Context* get_context(int device, int* status) {
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) { *status = cuda_fail(e, "cudaEventCreate"); return nullptr; }
     }
-    int bps = 0;
-    qpk::posterior_f32_occupancy(4, &bps);
-    c->f32_blocks_per_sm = std::max(1, std::min(bps, 4));
     int bps64 = 0;
     qpk::posterior_f64_occupancy(&bps64);
     c->f64_blocks_per_sm = std::max(1, std::min(bps64, 2));
@@ -446,7 +443,11 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         int f64_grid = 0;
         if (!f64) {
             const int wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 4;
-            const int bps = C->tune.blocks_per_sm > 0 ? C->tune.blocks_per_sm : C->f32_blocks_per_sm;
+            int bps = C->tune.blocks_per_sm;
+            if (bps <= 0) {
+                qpk::posterior_f32_occupancy(wpb, pl->max_len, &bps);
+                bps = std::max(1, std::min(bps, 8));
+            }
             int64_t grid = (int64_t)C->sm_count * bps;
             grid = std::min<int64_t>(grid, (P + wpb - 1) / wpb);
             grid = std::max<int64_t>(grid, 1);

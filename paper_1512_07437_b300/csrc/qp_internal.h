@@ -129,8 +129,8 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
 cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,
                             cudaStream_t s);
 int posterior_f32_regs();
-int posterior_f32_occupancy(int warps_per_block, int* blocks_per_sm);
+int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm);
 int posterior_f64_occupancy(int* blocks_per_sm);
-size_t posterior_f32_smem(int warps_per_block);
+size_t posterior_f32_smem(int warps_per_block, int max_len);
 
 }  // namespace qpk

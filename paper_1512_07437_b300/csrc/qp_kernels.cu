@@ -200,20 +200,54 @@ enum : int {
     kGuardPool = 1 << 11,    // the entry pool region was full
 };
 
+// ---------------------------------------------------------------- async copies
+// cp.async moves the stored backward blocks and the boundary row into a small
+// per-warp shared-memory ring kD steps ahead of their use.  Every lane copies
+// and later reads only its own bytes, so waiting on its own copy groups is the
+// only synchronisation needed.  A source size of 0 fills the slot with zeros.
+constexpr int kD = 4;
+
+#ifndef QP_F32_MIN_BLOCKS
+#define QP_F32_MIN_BLOCKS 4      // 4 blocks of 4 warps per SM: at most 128 registers
+#endif
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// per-warp shared memory: stored-block ring, boundary ring, column residues
+struct WarpSmem {
+    float2* ring_b;   // [kD][kWarp * kRmax]
+    float4* ring_e;   // [kD][2]
+    uint8_t* sy;      // [max_len]
+};
+
+constexpr int kOwBytes = ((kTab * kTab * 8 + 255) / 256) * 256;
+
+__host__ __device__ constexpr int warp_smem_bytes(int max_len) {
+    return kD * kWarp * kRmax * 8 + kD * 32 + ((max_len + 15) / 16) * 16;
+}
+
 // ---------------------------------------------------------------- pass 1
 template <int R, bool SPEC>
 __device__ __forceinline__ void bwd_step(
-    const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int t, int lane,
-    int Lend, int rend, bool first_strip,
+    const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
+    int Lend, int rend, bool first_strip, int yc,
     float (&Mn)[R], float (&BXo)[R], float (&BX2o)[R], float (&BYo)[R], float (&BY2o)[R],
     float (&Dpo)[R], float (&ZEo)[R], float (&ZFo)[R], const int (&xo)[R],
     float& dMn, float& dDp, float cvH, float cvP, float2* __restrict__ bst_strip,
-    const float4* __restrict__ bnd_in, float4* __restrict__ bnd_out, int eH, int eP,
+    const float4* __restrict__ ebnd, float4* __restrict__ bnd_out, int eH, int eP,
     float& Zh, float& Zp, int& eZh, int& eZp, int& flag)
 {
     const int n = c.n;
-    const int j = n + 31 - lane - t;
-    const bool act = (j >= 0) && (j <= n);
     // values of the row below (lane+1's top row; lane 31: the boundary row)
     float rMn = __shfl_down_sync(FULL, Mn[0], 1);
     float rBX = __shfl_down_sync(FULL, BXo[0], 1);
@@ -221,16 +255,10 @@ __device__ __forceinline__ void bwd_step(
     float rDp = __shfl_down_sync(FULL, Dpo[0], 1);
     float rZE = __shfl_down_sync(FULL, ZEo[0], 1);
     if (lane == 31) {
-        if (act && bnd_in) {
-            const float4 v0 = bnd_in[2 * j];
-            const float4 v1 = bnd_in[2 * j + 1];
-            rMn = v0.x; rBX = v0.y; rBX2 = v0.z; rDp = v0.w; rZE = v1.x;
-        } else {
-            rMn = rBX = rBX2 = rDp = rZE = 0.f;
-        }
+        const float4 v0 = ebnd[0], v1 = ebnd[1];
+        rMn = v0.x; rBX = v0.y; rBX2 = v0.z; rDp = v0.w; rZE = v1.x;
     }
     rMn *= cvH; rBX *= cvH; rBX2 *= cvH; rDp *= cvP; rZE *= cvP;
-    const int yc = (j >= 1 && j <= n) ? (int)__ldg(c.y + j - 1) : kEmpty;
     const float2* __restrict__ owr = s_ow + yc * kTab;
     float D = dMn, Dp = dDp;
     float Xb = rBX, X2b = rBX2, Eb = rZE;
@@ -277,7 +305,8 @@ __device__ __forceinline__ void bwd_step(
 
 template <int R>
 __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c,
-                          int s, int nstrips, float& Zh, float& Zp, int& eZh, int& eZp, int& flag)
+                          const WarpSmem& ws, int s, int nstrips, float& Zh, float& Zp, int& eZh,
+                          int& eZp, int& flag)
 {
     const int lane = threadIdx.x & 31;
     const int m = c.m, n = c.n;
@@ -319,7 +348,35 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
     float2* bst_strip = c.bst + (int64_t)s * kStripRows * (n + 32);
     int2* bex = c.bex + (int64_t)s * c.nch * 32;
     const int nsteps = n + 32;
+    // lane 31 streams the boundary row (column n - t at step t) into its ring
+    const bool streams = (lane == 31) && (bnd_in != nullptr);
+    auto fetch = [&](int t) {
+        if (streams) {
+            const int jb = n - t;
+            const bool ok = (t < nsteps) && jb >= 0;
+            const float4* src = bnd_in + 2 * (ok ? jb : 0);
+            float4* dst = ws.ring_e + 2 * (t % kD);
+            cp_async16(dst, src, ok ? 16 : 0);
+            cp_async16(dst + 1, src + 1, ok ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+    // without a strip below, lane 31 reads zeros from a ring slot
+    if (!streams && lane == 31) {
+#pragma unroll
+        for (int q = 0; q < 2 * kD; ++q) ws.ring_e[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < kD - 1; ++t) fetch(t);
+    // column residue of the lane, one step ahead
+    auto ycode = [&](int j) { return (j >= 1 && j <= n) ? (int)ws.sy[j - 1] : kEmpty; };
+    int yc = ycode(n + 31 - lane);
     for (int t = 0; t < nsteps; ++t) {
+        fetch(t + kD - 1);
+        cp_async_wait<kD - 1>();
+        const float4* ebnd = ws.ring_e + 2 * (streams ? (t % kD) : 0);
+        const int j = n + 31 - lane - t;
+        const bool act = (j >= 0) && (j <= n);
         const int ph = t & (kC - 1);
         if (ph == 0) {
             // renormalise: bring the lane's largest carried value into [1, 2)
@@ -329,7 +386,6 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
                 mh = fmaxf(mh, fmaxf(fmaxf(Mn[r], BXo[r]), fmaxf(BX2o[r], fmaxf(BYo[r], BY2o[r]))));
                 mp = fmaxf(mp, fmaxf(Dpo[r], fmaxf(ZEo[r], ZFo[r])));
             }
-            const int j = n + 31 - lane - t;
             const bool live = owns_row && (j >= -1) && (j <= n);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
             int fh = kNoExp, fp = kNoExp;
@@ -377,29 +433,29 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
             cvH = pow2f(gh); cvP = pow2f(gp);
         } else if (ph == 1) {
             // the boundary row's exponent changes on these steps
-            if (lane == 31 && bnd_in) {
-                const int j = n - t;
-                if (j >= 0) {
-                    const float4 e = bnd_in[2 * j + 1];
-                    eUpH = __float_as_int(e.z); eUpP = __float_as_int(e.w);
-                    const int gh = eUpH - eH, gp = eUpP - eP;
-                    if (owns_row && (gh > 127 || gp > 127)) {
-                        flag |= kGuardGap;
-                        note_guard(c.st, 2, s, t, lane, eH, eUpH, eP, eUpP, m, n);
-                    }
-                    cvH = pow2f(gh); cvP = pow2f(gp);
+            if (streams && n - t >= 0) {
+                const float4 e = ebnd[1];
+                eUpH = __float_as_int(e.z); eUpP = __float_as_int(e.w);
+                const int gh = eUpH - eH, gp = eUpP - eP;
+                if (owns_row && (gh > 127 || gp > 127)) {
+                    flag |= kGuardGap;
+                    note_guard(c.st, 2, s, t, lane, eH, eUpH, eP, eUpP, m, n);
                 }
+                cvH = pow2f(gh); cvP = pow2f(gp);
             }
         }
+        const int yc_now = yc;
+        yc = ycode(j - 1);
         if (t == t_end || t == t_start)
-            bwd_step<R, true>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Mn, BXo, BX2o, BYo, BY2o,
-                              Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip, bnd_in, bnd_out, eH, eP,
-                              Zh, Zp, eZh, eZp, flag);
+            bwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, BXo, BX2o,
+                              BYo, BY2o, Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
+                              ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
         else
-            bwd_step<R, false>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Mn, BXo, BX2o, BYo, BY2o,
-                               Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip, bnd_in, bnd_out, eH, eP,
-                               Zh, Zp, eZh, eZp, flag);
+            bwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, BXo, BX2o,
+                               BYo, BY2o, Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
+                               ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- pass 2
@@ -411,18 +467,16 @@ struct FwdOut {      // per-lane results captured at the end corner
 
 template <int R, bool SPEC>
 __device__ __forceinline__ void fwd_step(
-    const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int t, int lane,
-    int Lend, int rend, bool first_strip,
+    const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
+    int Lend, int rend, bool first_strip, int yc,
     float (&Md)[R], float (&Xi)[R], float (&X2i)[R], float (&Yi)[R], float (&Y2i)[R],
     float (&Zd)[R], float (&Ei)[R], float (&Fi)[R], int (&Aa)[R], int (&cnt)[R],
-    const int (&xo)[R], const float (&thr)[R],
+    const int (&xo)[R], int vmask,
     float& uMd, float& uZd, int& uA, float cvH, float cvP, float psH, float psP, float scaleA,
-    const float2 (&bs)[R], const float4* __restrict__ bnd_in, float4* __restrict__ bnd_out,
+    const float2* __restrict__ bs, const float4* __restrict__ ebnd, float4* __restrict__ bnd_out,
     int2* __restrict__ stg, int cap, int eH, int eP, float& pmax, FwdOut& fo, int& flag)
 {
     const int n = c.n;
-    const int j = t - lane;
-    const bool act = (j >= 0) && (j <= n);
     float rMd = __shfl_up_sync(FULL, Md[R - 1], 1);
     float rXi = __shfl_up_sync(FULL, Xi[R - 1], 1);
     float rX2i = __shfl_up_sync(FULL, X2i[R - 1], 1);
@@ -430,22 +484,19 @@ __device__ __forceinline__ void fwd_step(
     float rEi = __shfl_up_sync(FULL, Ei[R - 1], 1);
     int rA = __shfl_up_sync(FULL, Aa[R - 1], 1);
     if (lane == 0) {
-        if (act && bnd_in) {
-            const float4 v0 = bnd_in[2 * j];
-            const float4 v1 = bnd_in[2 * j + 1];
-            rMd = v0.x; rXi = v0.y; rX2i = v0.z; rZd = v0.w; rEi = v1.x; rA = __float_as_int(v1.y);
-        } else {
-            rMd = rXi = rX2i = rZd = rEi = 0.f; rA = 0;
-        }
+        // the previous strip's last row (zeros above the first strip)
+        const float4 v0 = ebnd[0], v1 = ebnd[1];
+        rMd = v0.x; rXi = v0.y; rX2i = v0.z; rZd = v0.w; rEi = v1.x; rA = __float_as_int(v1.y);
     }
     rMd *= cvH; rXi *= cvH; rX2i *= cvH; rZd *= cvP; rEi *= cvP;
-    const int yc = (j >= 1 && j <= n) ? (int)__ldg(c.y + j - 1) : kEmpty;
     const float2* __restrict__ owr = s_ow + yc * kTab;
     float dMd = uMd, dZd = uZd;
     int dA = uA;
     float aXi = rXi, aX2i = rX2i, aEi = rEi;
     int aA = rA;
     uMd = rMd; uZd = rZd; uA = rA;
+    float Pv[R];
+    bool any = false;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const float2 w = owr[xo[r]];
@@ -460,16 +511,15 @@ __device__ __forceinline__ void fwd_step(
         float nEi = cf.Wo * ZM + cf.We * ZE;
         float nFi = cf.Wo * ZM + cf.We * ZF;
         // posteriors of the cell and their combination
-        const float Ph = (FM * psH) * bs[r].x;
-        const float Pp = (ZM * psP) * bs[r].y;
+        const float2 b = bs[r];
+        const float Ph = (FM * psH) * b.x;
+        const float Pp = (ZM * psP) * b.y;
         float P;
         if (cf.combine == 0) P = sqrtf(cf.wh * (Ph * Ph) + cf.wp * (Pp * Pp));
         else P = cf.wh * Ph + cf.wp * Pp;
         pmax = fmaxf(pmax, P);
-        if (act && P >= thr[r]) {
-            const int q = cnt[r]++;
-            if (q < cap) stg[(lane * R + r) * cap + q] = make_int2(j - 1, __float_as_int(P));
-        }
+        Pv[r] = P;
+        any |= act && (P >= cf.theta) && ((vmask >> r) & 1);
         // maximum expected accuracy, fixed point (scaleA * P < 2^22)
         const int Pq = __float_as_int(fmaf(P, scaleA, 12582912.0f)) - 0x4B400000;
         int nA = max(dA + Pq, max(aA, Aa[r]));
@@ -493,6 +543,16 @@ __device__ __forceinline__ void fwd_step(
         Md[r] = nMd; Xi[r] = nXi; X2i[r] = nX2i; Yi[r] = nYi; Y2i[r] = nY2i;
         Zd[r] = nZd; Ei[r] = nEi; Fi[r] = nFi; Aa[r] = nA;
     }
+    // entries at or above the threshold are rare: one vote per step
+    if (__any_sync(FULL, any)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (act && Pv[r] >= cf.theta && ((vmask >> r) & 1)) {
+                const int q = cnt[r]++;
+                if (q < cap) stg[(lane * R + r) * cap + q] = make_int2(j - 1, __float_as_int(Pv[r]));
+            }
+        }
+    }
     if (lane == 31 && act && bnd_out) {
         bnd_out[2 * j] = make_float4(Md[R - 1], Xi[R - 1], X2i[R - 1], Zd[R - 1]);
         bnd_out[2 * j + 1] = make_float4(Ei[R - 1], __int_as_float(Aa[R - 1]), __int_as_float(eH),
@@ -502,8 +562,8 @@ __device__ __forceinline__ void fwd_step(
 
 template <int R>
 __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, const PairCtx& c,
-                          int s, int nstrips, float invZh, float invZp, int eZh, int eZp,
-                          float scaleA, float& pmax, FwdOut& fo, int64_t& pair_tot, int& flag)
+                          const WarpSmem& ws, int s, int nstrips, float invZh, float invZp, int eZh,
+                          int eZp, float scaleA, float& pmax, FwdOut& fo, int64_t& pair_tot, int& flag)
 {
     const Coef& cf = Pb.cf;
     const int lane = threadIdx.x & 31;
@@ -512,14 +572,14 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
     const bool last_strip = (s == nstrips - 1);
     const bool first_strip = (s == 0);
     int xo[R];
-    float thr[R];
     int cnt[R];
+    int vmask = 0;      // rows of this lane that belong to the pair (1..m)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + lane * R + r;
         const bool valid = (i >= 1 && i <= m);
         xo[r] = valid ? (int)__ldg(c.x + i - 1) : kEmpty;
-        thr[r] = valid ? cf.theta : __int_as_float(0x7f800000);
+        vmask |= valid ? (1 << r) : 0;
         cnt[r] = 0;
     }
     float Md[R], Xi[R], X2i[R], Yi[R], Y2i[R], Zd[R], Ei[R], Fi[R];
@@ -569,23 +629,48 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
         psP = pow2f(Ep) * invZp;
     };
     ps_update();
-    // stored backward values: two steps of prefetch
-    float2 bs0[R], bs1[R], bs2[R];
-    auto load_blk = [&](int T, float2 (&dst)[R]) {
+    // ring streams: this lane's stored block of step T, and (lane 0) the
+    // boundary row column T
+    const bool streams = (lane == 0) && (bnd_in != nullptr);
+    auto fetch = [&](int T) {
         const int jj = T - lane;
-        if (T < nsteps && jj >= 0 && jj <= n) {
-            const float2* src = bst_strip + (int64_t)T * (kWarp * R) + lane * R;
-#pragma unroll
-            for (int r = 0; r < R; ++r) dst[r] = src[r];
+        const bool ok = (T < nsteps) && jj >= 0 && jj <= n;
+        const float2* src = bst_strip + (ok ? ((int64_t)T * (kWarp * R) + lane * R) : 0);
+        float2* dst = ws.ring_b + (T % kD) * (kWarp * kRmax) + lane * R;
+        if (R == 4) {
+            cp_async16(dst, src, ok ? 16 : 0);
+            cp_async16(dst + 2, src + 2, ok ? 16 : 0);
+        } else if (R == 2) {
+            cp_async16(dst, src, ok ? 16 : 0);
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[r] = make_float2(0.f, 0.f);
+            for (int r = 0; r < R; ++r) cp_async8(dst + r, src + r, ok ? 8 : 0);
         }
+        if (streams) {
+            const bool okb = (T < nsteps) && T <= n;
+            const float4* sb = bnd_in + 2 * (okb ? T : 0);
+            float4* db = ws.ring_e + 2 * (T % kD);
+            cp_async16(db, sb, okb ? 16 : 0);
+            cp_async16(db + 1, sb + 1, okb ? 16 : 0);
+        }
+        cp_async_commit();
     };
-    load_blk(0, bs0);
-    load_blk(1, bs1);
+    // lanes without a boundary read zeros from their ring slots
+    if (!streams && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 2 * kD; ++q) ws.ring_e[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < kD - 1; ++t) fetch(t);
+    auto ycode = [&](int j) { return (j >= 1 && j <= n) ? (int)ws.sy[j - 1] : kEmpty; };
+    int yc = ycode(-lane);
     for (int t = 0; t < nsteps; ++t) {
-        load_blk(t + 2, bs2);
+        fetch(t + kD - 1);
+        cp_async_wait<kD - 1>();
+        const float2* bs = ws.ring_b + (t % kD) * (kWarp * kRmax) + lane * R;
+        const float4* ebnd = ws.ring_e + 2 * (streams ? (t % kD) : 0);
+        const int j = t - lane;
+        const bool act = (j >= 0) && (j <= n);
         const int ph = (t - c2) & (kC - 1);
         if (ph == 0) {
             float mh = uMd, mp = uZd;
@@ -594,7 +679,6 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
                 mh = fmaxf(mh, fmaxf(fmaxf(Md[r], Xi[r]), fmaxf(X2i[r], fmaxf(Yi[r], Y2i[r]))));
                 mp = fmaxf(mp, fmaxf(Zd[r], fmaxf(Ei[r], Fi[r])));
             }
-            const int j = t - lane;
             const bool live = owns_row && (j >= 0) && (j <= n + 1);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
             int fh = kNoExp, fp = kNoExp;
@@ -644,8 +728,8 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
             t_ps = t;
             ps_update();
         } else if (ph == 1) {
-            if (lane == 0 && bnd_in && t <= n) {
-                const float4 e = bnd_in[2 * t + 1];
+            if (streams && t <= n) {
+                const float4 e = ebnd[1];
                 eUpH = __float_as_int(e.z); eUpP = __float_as_int(e.w);
                 const int gh = eUpH - eH, gp = eUpP - eP;
                 if (gh > 127 || gp > 127) {
@@ -655,17 +739,18 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
                 cvH = pow2f(gh); cvP = pow2f(gp);
             }
         }
+        const int yc_now = yc;
+        yc = ycode(j + 1);
         if (t == t_end || t == t_start)
-            fwd_step<R, true>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Md, Xi, X2i, Yi, Y2i, Zd, Ei,
-                              Fi, Aa, cnt, xo, thr, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA, bs0,
-                              bnd_in, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
+            fwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, Xi, X2i, Yi,
+                              Y2i, Zd, Ei, Fi, Aa, cnt, xo, vmask, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
+                              bs, ebnd, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
         else
-            fwd_step<R, false>(cf, s_ow, c, t, lane, Lend, rend, first_strip, Md, Xi, X2i, Yi, Y2i, Zd, Ei,
-                               Fi, Aa, cnt, xo, thr, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA, bs0,
-                               bnd_in, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
-#pragma unroll
-        for (int r = 0; r < R; ++r) { bs0[r] = bs1[r]; bs1[r] = bs2[r]; }
+            fwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, Xi, X2i, Yi,
+                               Y2i, Zd, Ei, Fi, Aa, cnt, xo, vmask, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
+                               bs, ebnd, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
     }
+    cp_async_wait<0>();
     // ---- flush this strip's entries into the pool (row-major, columns ascending)
     int tot = 0;
 #pragma unroll
@@ -705,20 +790,30 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
 }
 
 __device__ __forceinline__ void bwd_dispatch(int Rs, const Coef& cf, const float2* s_ow, const PairCtx& c,
-                                             int s, int ns, float& Zh, float& Zp, int& eZh, int& eZp, int& flag) {
+                                             const WarpSmem& ws, int s, int ns, float& Zh, float& Zp,
+                                             int& eZh, int& eZp, int& flag) {
     switch (Rs) {
-        case 1: bwd_strip<1>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        case 2: bwd_strip<2>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        case 3: bwd_strip<3>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        default: bwd_strip<4>(cf, s_ow, c, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        case 1: bwd_strip<1>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        case 2: bwd_strip<2>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        case 3: bwd_strip<3>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        default: bwd_strip<4>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
     }
 }
 
-__global__ void __launch_bounds__(128, 3) k_posterior_f32(Problem Pb) {
-    extern __shared__ float2 s_ow[];
+__global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Problem Pb) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    float2* s_ow = (float2*)s_raw;
     for (int i = threadIdx.x; i < kTab * kTab; i += blockDim.x) s_ow[i] = Pb.cst->ow[i];
-    __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    WarpSmem ws;
+    {
+        unsigned char* p = s_raw + kOwBytes + (size_t)wib * warp_smem_bytes(Pb.max_len);
+        ws.ring_b = (float2*)p;
+        ws.ring_e = (float4*)(p + kD * kWarp * kRmax * 8);
+        ws.sy = p + kD * kWarp * kRmax * 8 + kD * 32;
+    }
+    __syncthreads();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     PairCtx c;
     c.bst = Pb.bst + gw * Pb.bst_stride;
@@ -745,6 +840,10 @@ __global__ void __launch_bounds__(128, 3) k_posterior_f32(Problem Pb) {
         c.nch = (c.n + 32 + kC - 1) / kC;
         const int m = c.m, n = c.n;
         const int nstrips = (m + 1 + kStripRows - 1) / kStripRows;
+        // the column residues of the pair, staged once
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) ws.sy[i] = c.y[i];
+        __syncwarp();
         int flag = 0;
         // ---- pass 1: backward, bottom strip first
         float Zh = 0.f, Zp = 0.f;
@@ -752,7 +851,7 @@ __global__ void __launch_bounds__(128, 3) k_posterior_f32(Problem Pb) {
         for (int s = nstrips - 1; s >= 0; --s) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = (rows_in + 31) / 32;
-            bwd_dispatch(Rs, Pb.cf, s_ow, c, s, nstrips, Zh, Zp, eZh, eZp, flag);
+            bwd_dispatch(Rs, Pb.cf, s_ow, c, ws, s, nstrips, Zh, Zp, eZh, eZp, flag);
             __syncwarp();
         }
         Zh = __shfl_sync(FULL, Zh, 0); Zp = __shfl_sync(FULL, Zp, 0);
@@ -777,10 +876,10 @@ __global__ void __launch_bounds__(128, 3) k_posterior_f32(Problem Pb) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = (rows_in + 31) / 32;
             switch (Rs) {
-                case 1: fwd_strip<1>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                case 2: fwd_strip<2>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                case 3: fwd_strip<3>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                default: fwd_strip<4>(Pb, s_ow, c, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                case 1: fwd_strip<1>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                case 2: fwd_strip<2>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                case 3: fwd_strip<3>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                default: fwd_strip<4>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
             }
         }
         // ---- pair results (held by the lane that owns row m)
@@ -829,15 +928,25 @@ int posterior_f32_regs() {
     return a.numRegs;
 }
 
-size_t posterior_f32_smem(int) { return sizeof(float2) * kTab * kTab; }
+size_t posterior_f32_smem(int warps_per_block, int max_len) {
+    return (size_t)kOwBytes + (size_t)warps_per_block * warp_smem_bytes(max_len);
+}
 
-int posterior_f32_occupancy(int warps_per_block, int* blocks_per_sm) {
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, k_posterior_f32, warps_per_block * 32, posterior_f32_smem(warps_per_block));
+int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm) {
+    const size_t smem = posterior_f32_smem(warps_per_block, max_len);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_posterior_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f32,
+                                                              warps_per_block * 32, smem);
 }
 
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block, cudaStream_t s) {
-    k_posterior_f32<<<grid, warps_per_block * 32, posterior_f32_smem(warps_per_block), s>>>(P);
+    const size_t smem = posterior_f32_smem(warps_per_block, P.max_len);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_posterior_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_posterior_f32<<<grid, warps_per_block * 32, smem, s>>>(P);
     return cudaGetLastError();
 }
 
