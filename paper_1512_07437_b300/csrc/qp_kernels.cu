@@ -35,6 +35,14 @@ __device__ __forceinline__ float pow2f(int e) {
     return __int_as_float((e + 127) << 23);
 }
 
+// Square root with the single hardware approximation (relative error of a
+// few ulp, far inside the 1e-5 posterior tolerance).
+__device__ __forceinline__ float sqrt_approx(float v) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // floor(log2 v) for a positive normal float; -127 for zero / denormal.
 __device__ __forceinline__ int ilog2f(float v) {
     return ((__float_as_int(v) >> 23) & 0xff) - 127;
@@ -304,7 +312,7 @@ __device__ __forceinline__ void bwd_step(
 }
 
 template <int R>
-__device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c,
+__device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c,
                           const WarpSmem& ws, int s, int nstrips, float& Zh, float& Zp, int& eZh,
                           int& eZp, int& flag)
 {
@@ -355,7 +363,7 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
             const int jb = n - t;
             const bool ok = (t < nsteps) && jb >= 0;
             const float4* src = bnd_in + 2 * (ok ? jb : 0);
-            float4* dst = ws.ring_e + 2 * (t % kD);
+            float4* dst = ws.ring_e + 2 * (t & (kD - 1));
             cp_async16(dst, src, ok ? 16 : 0);
             cp_async16(dst + 1, src + 1, ok ? 16 : 0);
         }
@@ -374,7 +382,7 @@ __device__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const
     for (int t = 0; t < nsteps; ++t) {
         fetch(t + kD - 1);
         cp_async_wait<kD - 1>();
-        const float4* ebnd = ws.ring_e + 2 * (streams ? (t % kD) : 0);
+        const float4* ebnd = ws.ring_e + 2 * (streams ? (t & (kD - 1)) : 0);
         const int j = n + 31 - lane - t;
         const bool act = (j >= 0) && (j <= n);
         const int ph = t & (kC - 1);
@@ -515,7 +523,7 @@ __device__ __forceinline__ void fwd_step(
         const float Ph = (FM * psH) * b.x;
         const float Pp = (ZM * psP) * b.y;
         float P;
-        if (cf.combine == 0) P = sqrtf(cf.wh * (Ph * Ph) + cf.wp * (Pp * Pp));
+        if (cf.combine == 0) P = sqrt_approx(cf.wh * (Ph * Ph) + cf.wp * (Pp * Pp));
         else P = cf.wh * Ph + cf.wp * Pp;
         pmax = fmaxf(pmax, P);
         Pv[r] = P;
@@ -561,7 +569,7 @@ __device__ __forceinline__ void fwd_step(
 }
 
 template <int R>
-__device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, const PairCtx& c,
+__device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, const PairCtx& c,
                           const WarpSmem& ws, int s, int nstrips, float invZh, float invZp, int eZh,
                           int eZp, float scaleA, float& pmax, FwdOut& fo, int64_t& pair_tot, int& flag)
 {
@@ -636,7 +644,7 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
         const int jj = T - lane;
         const bool ok = (T < nsteps) && jj >= 0 && jj <= n;
         const float2* src = bst_strip + (ok ? ((int64_t)T * (kWarp * R) + lane * R) : 0);
-        float2* dst = ws.ring_b + (T % kD) * (kWarp * kRmax) + lane * R;
+        float2* dst = ws.ring_b + (T & (kD - 1)) * (kWarp * kRmax) + lane * R;
         if (R == 4) {
             cp_async16(dst, src, ok ? 16 : 0);
             cp_async16(dst + 2, src + 2, ok ? 16 : 0);
@@ -649,7 +657,7 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
         if (streams) {
             const bool okb = (T < nsteps) && T <= n;
             const float4* sb = bnd_in + 2 * (okb ? T : 0);
-            float4* db = ws.ring_e + 2 * (T % kD);
+            float4* db = ws.ring_e + 2 * (T & (kD - 1));
             cp_async16(db, sb, okb ? 16 : 0);
             cp_async16(db + 1, sb + 1, okb ? 16 : 0);
         }
@@ -667,8 +675,8 @@ __device__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, co
     for (int t = 0; t < nsteps; ++t) {
         fetch(t + kD - 1);
         cp_async_wait<kD - 1>();
-        const float2* bs = ws.ring_b + (t % kD) * (kWarp * kRmax) + lane * R;
-        const float4* ebnd = ws.ring_e + 2 * (streams ? (t % kD) : 0);
+        const float2* bs = ws.ring_b + (t & (kD - 1)) * (kWarp * kRmax) + lane * R;
+        const float4* ebnd = ws.ring_e + 2 * (streams ? (t & (kD - 1)) : 0);
         const int j = t - lane;
         const bool act = (j >= 0) && (j <= n);
         const int ph = (t - c2) & (kC - 1);
@@ -795,7 +803,6 @@ __device__ __forceinline__ void bwd_dispatch(int Rs, const Coef& cf, const float
     switch (Rs) {
         case 1: bwd_strip<1>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
         case 2: bwd_strip<2>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        case 3: bwd_strip<3>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
         default: bwd_strip<4>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
     }
 }
@@ -850,7 +857,7 @@ __global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Proble
         int eZh = 0, eZp = 0;
         for (int s = nstrips - 1; s >= 0; --s) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
-            const int Rs = (rows_in + 31) / 32;
+            const int Rs = (rows_in + 31) / 32 == 3 ? 4 : (rows_in + 31) / 32;
             bwd_dispatch(Rs, Pb.cf, s_ow, c, ws, s, nstrips, Zh, Zp, eZh, eZp, flag);
             __syncwarp();
         }
@@ -874,16 +881,16 @@ __global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Proble
         int64_t pair_tot = 0;
         for (int s = 0; s < nstrips; ++s) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
-            const int Rs = (rows_in + 31) / 32;
+            const int Rs = (rows_in + 31) / 32 == 3 ? 4 : (rows_in + 31) / 32;
             switch (Rs) {
                 case 1: fwd_strip<1>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
                 case 2: fwd_strip<2>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                case 3: fwd_strip<3>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
                 default: fwd_strip<4>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
             }
         }
         // ---- pair results (held by the lane that owns row m)
-        const int lastRs = (min(kStripRows, m + 1 - (nstrips - 1) * kStripRows) + 31) / 32;
+        int lastRs = (min(kStripRows, m + 1 - (nstrips - 1) * kStripRows) + 31) / 32;
+        if (lastRs == 3) lastRs = 4;
         const int Lend = (m - (nstrips - 1) * kStripRows) / lastRs;
         const float fZh = __shfl_sync(FULL, fo.Zh, Lend), fZp = __shfl_sync(FULL, fo.Zp, Lend);
         const int feh = __shfl_sync(FULL, fo.eZh, Lend), fep = __shfl_sync(FULL, fo.eZp, Lend);
