@@ -203,8 +203,8 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
             bst = std::max<int64_t>(bst, (int64_t)ns * qpk::kStripRows * (n + 32));
             bex = std::max<int64_t>(bex, (int64_t)ns * ((n + 32 + qpk::kC - 1) / qpk::kC) * 32);
             // swept lane-steps of the pair: strips x (columns + skew) x rows per lane
-            const int64_t w = (int64_t)(ns - 1) * 4 * (n + 32) +
-                              (int64_t)((m + 1 - (ns - 1) * qpk::kStripRows + 31) / 32) * (n + 32);
+            const int last = (m + 1 - (ns - 1) * qpk::kStripRows + 31) / 32;
+            const int64_t w = ((int64_t)(ns - 1) * qpk::kRmax + (last <= 1 ? 1 : last <= 2 ? 2 : last <= 4 ? 4 : 8)) * (n + 32);
             pl->work[q] = w;
             order[q] = std::make_pair(-w, (int32_t)q);
             work_sum += (double)w;
@@ -223,6 +223,16 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
     pl->order.resize(P);
     for (int64_t i = 0; i < P; ++i) pl->order[i] = order[i].second;
     return pl;
+}
+
+// ------------------------------------------------------------------ autotuner key
+int64_t Context::tune_key(int64_t n_pairs, int max_len, double work) {
+    // buckets: pair count (half powers of two), longest sequence (64s), mean
+    // work per pair (powers of two)
+    const int pb = n_pairs > 0 ? (int)std::floor(2.0 * std::log2((double)n_pairs)) : 0;
+    const int lb = max_len / 64;
+    const int wb = n_pairs > 0 ? (int)std::floor(std::log2(1.0 + work / (double)n_pairs)) : 0;
+    return ((int64_t)pb << 40) | ((int64_t)lb << 16) | (int64_t)wb;
 }
 
 // ------------------------------------------------------------------ device context
@@ -255,6 +265,7 @@ Context* get_context(int device, int* status) {
     int bps64 = 0;
     qpk::posterior_f64_occupancy(&bps64);
     c->f64_blocks_per_sm = std::max(1, std::min(bps64, 2));
+    if (const char* v = getenv("QP_F32_VARIANT")) c->tune.variant = atoi(v);
     Context* raw = c.get();
     g_ctx[device] = std::move(c);
     return raw;
@@ -426,6 +437,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
 
     qpk::Status hs;
     memset(&hs, 0, sizeof hs);
+    int variant = 0;
     for (int attempt = 0;; ++attempt) {
         fd.pool_cap = C->pool_cap;
         memcpy(C->h_fam.ptr, &fd, sizeof fd);
@@ -443,9 +455,11 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         int f64_grid = 0;
         if (!f64) {
             const int wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 4;
+            const int64_t tkey = Context::tune_key(P, pl->max_len, pl->work_sum);
+            variant = C->tune.variant >= 0 ? C->tune.variant : C->tuner[tkey].choose();
             int bps = C->tune.blocks_per_sm;
             if (bps <= 0) {
-                qpk::posterior_f32_occupancy(wpb, pl->max_len, &bps);
+                qpk::posterior_f32_occupancy(wpb, pl->max_len, &bps, variant);
                 bps = std::max(1, std::min(bps, 8));
             }
             int64_t grid = (int64_t)C->sm_count * bps;
@@ -461,12 +475,19 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             Pb.bex = (int2*)C->bex.ptr; Pb.bex_stride = pl->bex_stride;
             Pb.bnd = (float4*)C->bnd.ptr; Pb.bnd_stride = pl->bnd_stride;
             Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = (int64_t)qpk::kStripRows * cap;
-            if ((e = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st)) != cudaSuccess)
+            if ((e = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st, variant)) != cudaSuccess)
                 return bail(cuda_fail(e, "k_posterior_f32 launch"));
             cudaEventRecord(C->ev[2], st);
             e = cudaMemcpyAsync(C->h_status.ptr, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return bail(cuda_fail(e, "k_posterior_f32"));
+            if (C->tune.variant < 0) {
+                float kms = 0.f;
+                if (cudaEventElapsedTime(&kms, C->ev[1], C->ev[2]) == cudaSuccess) {
+                    TuneEntry& te = C->tuner[Context::tune_key(P, pl->max_len, pl->work_sum)];
+                    te.ms[variant] = te.ms[variant] < 0 ? kms : std::min<double>(te.ms[variant], kms);
+                }
+            }
             memcpy(&hs, C->h_status.ptr, sizeof hs);
             if (hs.bad_residue)
                 return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));

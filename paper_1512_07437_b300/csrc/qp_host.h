@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -52,9 +53,26 @@ struct Plan {
     DevBuf d_pairs, d_row_off, d_strip_off, d_items;
 };
 
-struct LaunchOverride {                  // autotuner / benchmark knobs
+struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int warps_per_block = 0;
     int blocks_per_sm = 0;
+    int variant = -1;
+};
+
+// Online choice between the compiled variants of the FP32 kernel, per shape
+// bucket (pair count and longest sequence): each variant is timed once on a
+// real call, then the faster one is kept.
+struct TuneEntry {
+    double ms[qpk::kF32Variants];
+    TuneEntry() { for (auto& v : ms) v = -1.0; }
+    int choose() const {
+        for (int v = 0; v < qpk::kF32Variants; ++v)
+            if (ms[v] < 0) return v;
+        int best = 0;
+        for (int v = 1; v < qpk::kF32Variants; ++v)
+            if (ms[v] < ms[best]) best = v;
+        return best;
+    }
 };
 
 struct Context {
@@ -76,6 +94,8 @@ struct Context {
     int64_t pool_cap = 0;
     int64_t pool_hint = 0;
     LaunchOverride tune;
+    std::map<int64_t, TuneEntry> tuner;
+    static int64_t tune_key(int64_t n_pairs, int max_len, double work);
     std::shared_ptr<Plan> plan_for(int k, const int64_t* off, int* status);
 };
 

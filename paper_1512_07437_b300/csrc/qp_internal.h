@@ -7,8 +7,11 @@
 namespace qpk {
 
 constexpr int kWarp = 32;
-constexpr int kRmax = 4;                     // DP rows per lane in a full strip
-constexpr int kStripRows = kWarp * kRmax;    // 128 DP rows per strip
+#ifndef QP_RMAX
+#define QP_RMAX 4
+#endif
+constexpr int kRmax = QP_RMAX;               // DP rows per lane in a full strip (4 or 8)
+constexpr int kStripRows = kWarp * kRmax;    // 256 DP rows per strip
 constexpr int kC = 16;                       // renormalisation period (steps); divides 32
 constexpr int kTab = 21;                     // 20 residues + the empty row/column code
 constexpr int kEmpty = 20;
@@ -117,8 +120,11 @@ cudaError_t launch_setup(const RawParams* host_raw, Consts* dev_cst, cudaStream_
 cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
                           const int64_t* seq_off, int32_t k, double* seq_logq,
                           const Consts* cst, Status* status, cudaStream_t s);
+// variant: 0 = 4 blocks of 4 warps per SM (<= 128 registers),
+//          1 = 3 blocks of 4 warps per SM (no register cap below 168)
+constexpr int kF32Variants = 2;
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int variant = 0);
 cudaError_t launch_posterior_f64(const Problem& P, int grid, cudaStream_t s);
 cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const int64_t* pair_row_off, const int64_t* pair_strip_off,
@@ -128,8 +134,8 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            cudaStream_t s);
 cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,
                             cudaStream_t s);
-int posterior_f32_regs();
-int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm);
+int posterior_f32_regs(int variant = 0);
+int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant = 0);
 int posterior_f64_occupancy(int* blocks_per_sm);
 size_t posterior_f32_smem(int warps_per_block, int max_len);
 

@@ -215,9 +215,7 @@ enum : int {
 // only synchronisation needed.  A source size of 0 fills the slot with zeros.
 constexpr int kD = 4;
 
-#ifndef QP_F32_MIN_BLOCKS
-#define QP_F32_MIN_BLOCKS 4      // 4 blocks of 4 warps per SM: at most 128 registers
-#endif
+
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
@@ -240,8 +238,10 @@ struct WarpSmem {
 
 constexpr int kOwBytes = ((kTab * kTab * 8 + 255) / 256) * 256;
 
+constexpr int kYPad = 33;   // empty codes before column 1 of the staged residues
+
 __host__ __device__ constexpr int warp_smem_bytes(int max_len) {
-    return kD * kWarp * kRmax * 8 + kD * 32 + ((max_len + 15) / 16) * 16;
+    return kD * kWarp * kRmax * 8 + kD * 32 + ((max_len + 2 * kYPad + 15) / 16) * 16;
 }
 
 // ---------------------------------------------------------------- pass 1
@@ -249,8 +249,8 @@ template <int R, bool SPEC>
 __device__ __forceinline__ void bwd_step(
     const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
     int Lend, int rend, bool first_strip, int yc,
-    float (&Mn)[R], float (&BXo)[R], float (&BX2o)[R], float (&BYo)[R], float (&BY2o)[R],
-    float (&Dpo)[R], float (&ZEo)[R], float (&ZFo)[R], const int (&xo)[R],
+    float (&Mn)[R], float& tBX, float& tBX2, float (&BYo)[R], float (&BY2o)[R],
+    float (&Dpo)[R], float& tZE, float (&ZFo)[R], const int (&xo)[R],
     float& dMn, float& dDp, float cvH, float cvP, float2* __restrict__ bst_strip,
     const float4* __restrict__ ebnd, float4* __restrict__ bnd_out, int eH, int eP,
     float& Zh, float& Zp, int& eZh, int& eZp, int& flag)
@@ -258,10 +258,10 @@ __device__ __forceinline__ void bwd_step(
     const int n = c.n;
     // values of the row below (lane+1's top row; lane 31: the boundary row)
     float rMn = __shfl_down_sync(FULL, Mn[0], 1);
-    float rBX = __shfl_down_sync(FULL, BXo[0], 1);
-    float rBX2 = __shfl_down_sync(FULL, BX2o[0], 1);
+    float rBX = __shfl_down_sync(FULL, tBX, 1);
+    float rBX2 = __shfl_down_sync(FULL, tBX2, 1);
     float rDp = __shfl_down_sync(FULL, Dpo[0], 1);
-    float rZE = __shfl_down_sync(FULL, ZEo[0], 1);
+    float rZE = __shfl_down_sync(FULL, tZE, 1);
     if (lane == 31) {
         const float4 v0 = ebnd[0], v1 = ebnd[1];
         rMn = v0.x; rBX = v0.y; rBX2 = v0.z; rDp = v0.w; rZE = v1.x;
@@ -302,12 +302,13 @@ __device__ __forceinline__ void bwd_step(
         if (act) blk[r] = make_float2(BM, ZMB);
         D = Mn[r]; Dp = Dpo[r];
         Xb = BX; X2b = BX2; Eb = ZEB;
-        Mn[r] = nMn; BXo[r] = BX; BX2o[r] = BX2; BYo[r] = BY; BY2o[r] = BY2;
-        Dpo[r] = nDp; ZEo[r] = ZEB; ZFo[r] = ZFB;
+        Mn[r] = nMn; BYo[r] = BY; BY2o[r] = BY2;
+        Dpo[r] = nDp; ZFo[r] = ZFB;
+        if (r == 0) { tBX = BX; tBX2 = BX2; tZE = ZEB; }
     }
     if (lane == 0 && act && bnd_out) {
-        bnd_out[2 * j] = make_float4(Mn[0], BXo[0], BX2o[0], Dpo[0]);
-        bnd_out[2 * j + 1] = make_float4(ZEo[0], 0.f, __int_as_float(eH), __int_as_float(eP));
+        bnd_out[2 * j] = make_float4(Mn[0], tBX, tBX2, Dpo[0]);
+        bnd_out[2 * j + 1] = make_float4(tZE, 0.f, __int_as_float(eH), __int_as_float(eP));
     }
 }
 
@@ -327,9 +328,12 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
         const int i = row0 + lane * R + r;
         xo[r] = (i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty;
     }
-    float Mn[R], BXo[R], BX2o[R], BYo[R], BY2o[R], Dpo[R], ZEo[R], ZFo[R];
+    // carried across steps: diagonal and horizontal outflows of every row,
+    // vertical outflows of the top row (they go to the lane above)
+    float Mn[R], BYo[R], BY2o[R], Dpo[R], ZFo[R];
+    float tBX = 0.f, tBX2 = 0.f, tZE = 0.f;
 #pragma unroll
-    for (int r = 0; r < R; ++r) { Mn[r] = BXo[r] = BX2o[r] = BYo[r] = BY2o[r] = Dpo[r] = ZEo[r] = ZFo[r] = 0.f; }
+    for (int r = 0; r < R; ++r) { Mn[r] = BYo[r] = BY2o[r] = Dpo[r] = ZFo[r] = 0.f; }
     float dMn = 0.f, dDp = 0.f;
     // the boundary row below this strip (none for the last strip)
     const float4* bnd_in = last_strip ? nullptr : c.bnd;
@@ -376,8 +380,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     }
 #pragma unroll
     for (int t = 0; t < kD - 1; ++t) fetch(t);
-    // column residue of the lane, one step ahead
-    auto ycode = [&](int j) { return (j >= 1 && j <= n) ? (int)ws.sy[j - 1] : kEmpty; };
+    // column residue of the lane, one step ahead (padded: no range check)
+    auto ycode = [&](int j) { return (int)ws.sy[j + kYPad - 1]; };
     int yc = ycode(n + 31 - lane);
     for (int t = 0; t < nsteps; ++t) {
         fetch(t + kD - 1);
@@ -388,11 +392,11 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
         const int ph = t & (kC - 1);
         if (ph == 0) {
             // renormalise: bring the lane's largest carried value into [1, 2)
-            float mh = fmaxf(dMn, 0.f), mp = fmaxf(dDp, 0.f);
+            float mh = fmaxf(fmaxf(dMn, tBX), tBX2), mp = fmaxf(dDp, tZE);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                mh = fmaxf(mh, fmaxf(fmaxf(Mn[r], BXo[r]), fmaxf(BX2o[r], fmaxf(BYo[r], BY2o[r]))));
-                mp = fmaxf(mp, fmaxf(Dpo[r], fmaxf(ZEo[r], ZFo[r])));
+                mh = fmaxf(mh, fmaxf(Mn[r], fmaxf(BYo[r], BY2o[r])));
+                mp = fmaxf(mp, fmaxf(Dpo[r], ZFo[r]));
             }
             const bool live = owns_row && (j >= -1) && (j <= n);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
@@ -401,8 +405,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
                 const int k = max(-126, min(126, ilog2f(mh)));
                 const float sc = pow2f(-k);
 #pragma unroll
-                for (int r = 0; r < R; ++r) { Mn[r] *= sc; BXo[r] *= sc; BX2o[r] *= sc; BYo[r] *= sc; BY2o[r] *= sc; }
-                dMn *= sc;
+                for (int r = 0; r < R; ++r) { Mn[r] *= sc; BYo[r] *= sc; BY2o[r] *= sc; }
+                dMn *= sc; tBX *= sc; tBX2 *= sc;
                 fh = eH + k;
             } else if (lane == 31) {
                 fh = eH;
@@ -411,8 +415,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
                 const int k = max(-126, min(126, ilog2f(mp)));
                 const float sc = pow2f(-k);
 #pragma unroll
-                for (int r = 0; r < R; ++r) { Dpo[r] *= sc; ZEo[r] *= sc; ZFo[r] *= sc; }
-                dDp *= sc;
+                for (int r = 0; r < R; ++r) { Dpo[r] *= sc; ZFo[r] *= sc; }
+                dDp *= sc; tZE *= sc;
                 fp = eP + k;
             } else if (lane == 31) {
                 fp = eP;
@@ -455,12 +459,12 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
         const int yc_now = yc;
         yc = ycode(j - 1);
         if (t == t_end || t == t_start)
-            bwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, BXo, BX2o,
-                              BYo, BY2o, Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
+            bwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX, tBX2,
+                              BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
                               ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
         else
-            bwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, BXo, BX2o,
-                               BYo, BY2o, Dpo, ZEo, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
+            bwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX, tBX2,
+                               BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
                                ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
     }
     cp_async_wait<0>();
@@ -477,19 +481,19 @@ template <int R, bool SPEC>
 __device__ __forceinline__ void fwd_step(
     const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
     int Lend, int rend, bool first_strip, int yc,
-    float (&Md)[R], float (&Xi)[R], float (&X2i)[R], float (&Yi)[R], float (&Y2i)[R],
-    float (&Zd)[R], float (&Ei)[R], float (&Fi)[R], int (&Aa)[R], int (&cnt)[R],
-    const int (&xo)[R], int vmask,
+    float (&Md)[R], float& lXi, float& lX2i, float (&Yi)[R], float (&Y2i)[R],
+    float (&Zd)[R], float& lEi, float (&Fi)[R], int (&Aa)[R], int (&cnt)[R],
+    const int (&xo)[R],
     float& uMd, float& uZd, int& uA, float cvH, float cvP, float psH, float psP, float scaleA,
     const float2* __restrict__ bs, const float4* __restrict__ ebnd, float4* __restrict__ bnd_out,
     int2* __restrict__ stg, int cap, int eH, int eP, float& pmax, FwdOut& fo, int& flag)
 {
     const int n = c.n;
     float rMd = __shfl_up_sync(FULL, Md[R - 1], 1);
-    float rXi = __shfl_up_sync(FULL, Xi[R - 1], 1);
-    float rX2i = __shfl_up_sync(FULL, X2i[R - 1], 1);
+    float rXi = __shfl_up_sync(FULL, lXi, 1);
+    float rX2i = __shfl_up_sync(FULL, lX2i, 1);
     float rZd = __shfl_up_sync(FULL, Zd[R - 1], 1);
-    float rEi = __shfl_up_sync(FULL, Ei[R - 1], 1);
+    float rEi = __shfl_up_sync(FULL, lEi, 1);
     int rA = __shfl_up_sync(FULL, Aa[R - 1], 1);
     if (lane == 0) {
         // the previous strip's last row (zeros above the first strip)
@@ -527,10 +531,10 @@ __device__ __forceinline__ void fwd_step(
         else P = cf.wh * Ph + cf.wp * Pp;
         pmax = fmaxf(pmax, P);
         Pv[r] = P;
-        any |= act && (P >= cf.theta) && ((vmask >> r) & 1);
+        any |= (P >= cf.theta);
         // maximum expected accuracy, fixed point (scaleA * P < 2^22)
         const int Pq = __float_as_int(fmaf(P, scaleA, 12582912.0f)) - 0x4B400000;
-        int nA = max(dA + Pq, max(aA, Aa[r]));
+        int nA = __vimax3_s32(dA + Pq, aA, Aa[r]);
         if (SPEC) {
             if (first_strip && lane == 0 && r == 0 && j == 0) {
                 // empty prefixes: the start distribution and the empty alignment
@@ -548,22 +552,23 @@ __device__ __forceinline__ void fwd_step(
         }
         dMd = Md[r]; dZd = Zd[r]; dA = Aa[r];
         aXi = nXi; aX2i = nX2i; aEi = nEi; aA = nA;
-        Md[r] = nMd; Xi[r] = nXi; X2i[r] = nX2i; Yi[r] = nYi; Y2i[r] = nY2i;
-        Zd[r] = nZd; Ei[r] = nEi; Fi[r] = nFi; Aa[r] = nA;
+        Md[r] = nMd; Yi[r] = nYi; Y2i[r] = nY2i;
+        Zd[r] = nZd; Fi[r] = nFi; Aa[r] = nA;
+        if (r == R - 1) { lXi = nXi; lX2i = nX2i; lEi = nEi; }
     }
     // entries at or above the threshold are rare: one vote per step
     if (__any_sync(FULL, any)) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (act && Pv[r] >= cf.theta && ((vmask >> r) & 1)) {
+            if (Pv[r] >= cf.theta) {
                 const int q = cnt[r]++;
                 if (q < cap) stg[(lane * R + r) * cap + q] = make_int2(j - 1, __float_as_int(Pv[r]));
             }
         }
     }
     if (lane == 31 && act && bnd_out) {
-        bnd_out[2 * j] = make_float4(Md[R - 1], Xi[R - 1], X2i[R - 1], Zd[R - 1]);
-        bnd_out[2 * j + 1] = make_float4(Ei[R - 1], __int_as_float(Aa[R - 1]), __int_as_float(eH),
+        bnd_out[2 * j] = make_float4(Md[R - 1], lXi, lX2i, Zd[R - 1]);
+        bnd_out[2 * j + 1] = make_float4(lEi, __int_as_float(Aa[R - 1]), __int_as_float(eH),
                                          __int_as_float(eP));
     }
 }
@@ -579,21 +584,23 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     const int row0 = s * kStripRows;
     const bool last_strip = (s == nstrips - 1);
     const bool first_strip = (s == 0);
+    // rows outside 1..m get the empty code: their posteriors are 0, below any
+    // threshold, so they never produce an entry
     int xo[R];
     int cnt[R];
-    int vmask = 0;      // rows of this lane that belong to the pair (1..m)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + lane * R + r;
-        const bool valid = (i >= 1 && i <= m);
-        xo[r] = valid ? (int)__ldg(c.x + i - 1) : kEmpty;
-        vmask |= valid ? (1 << r) : 0;
+        xo[r] = (i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty;
         cnt[r] = 0;
     }
-    float Md[R], Xi[R], X2i[R], Yi[R], Y2i[R], Zd[R], Ei[R], Fi[R];
+    // carried across steps: diagonal and horizontal outflows of every row,
+    // vertical outflows of the bottom row (they go to the lane below)
+    float Md[R], Yi[R], Y2i[R], Zd[R], Fi[R];
+    float lXi = 0.f, lX2i = 0.f, lEi = 0.f;
     int Aa[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) { Md[r] = Xi[r] = X2i[r] = Yi[r] = Y2i[r] = Zd[r] = Ei[r] = Fi[r] = 0.f; Aa[r] = 0; }
+    for (int r = 0; r < R; ++r) { Md[r] = Yi[r] = Y2i[r] = Zd[r] = Fi[r] = 0.f; Aa[r] = 0; }
     float uMd = 0.f, uZd = 0.f;
     int uA = 0;
     const float4* bnd_in = first_strip ? nullptr : c.bnd;
@@ -640,12 +647,17 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     // ring streams: this lane's stored block of step T, and (lane 0) the
     // boundary row column T
     const bool streams = (lane == 0) && (bnd_in != nullptr);
+    const float2* bst_lane = bst_strip + lane * R;
+    float2* ring_lane = ws.ring_b + lane * R;
     auto fetch = [&](int T) {
-        const int jj = T - lane;
-        const bool ok = (T < nsteps) && jj >= 0 && jj <= n;
-        const float2* src = bst_strip + (ok ? ((int64_t)T * (kWarp * R) + lane * R) : 0);
-        float2* dst = ws.ring_b + (T & (kD - 1)) * (kWarp * kRmax) + lane * R;
-        if (R == 4) {
+        // the block of step T exists for this lane when 0 <= T - lane <= n
+        const bool ok = (unsigned)(T - lane) <= (unsigned)n;
+        const float2* src = ok ? bst_lane + T * (kWarp * R) : bst_lane;
+        float2* dst = ring_lane + (T & (kD - 1)) * (kWarp * kRmax);
+        if (R == 8) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cp_async16(dst + 2 * q, src + 2 * q, ok ? 16 : 0);
+        } else if (R == 4) {
             cp_async16(dst, src, ok ? 16 : 0);
             cp_async16(dst + 2, src + 2, ok ? 16 : 0);
         } else if (R == 2) {
@@ -670,7 +682,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     }
 #pragma unroll
     for (int t = 0; t < kD - 1; ++t) fetch(t);
-    auto ycode = [&](int j) { return (j >= 1 && j <= n) ? (int)ws.sy[j - 1] : kEmpty; };
+    auto ycode = [&](int j) { return (int)ws.sy[j + kYPad - 1]; };
     int yc = ycode(-lane);
     for (int t = 0; t < nsteps; ++t) {
         fetch(t + kD - 1);
@@ -681,11 +693,11 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
         const bool act = (j >= 0) && (j <= n);
         const int ph = (t - c2) & (kC - 1);
         if (ph == 0) {
-            float mh = uMd, mp = uZd;
+            float mh = fmaxf(fmaxf(uMd, lXi), lX2i), mp = fmaxf(uZd, lEi);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                mh = fmaxf(mh, fmaxf(fmaxf(Md[r], Xi[r]), fmaxf(X2i[r], fmaxf(Yi[r], Y2i[r]))));
-                mp = fmaxf(mp, fmaxf(Zd[r], fmaxf(Ei[r], Fi[r])));
+                mh = fmaxf(mh, fmaxf(Md[r], fmaxf(Yi[r], Y2i[r])));
+                mp = fmaxf(mp, fmaxf(Zd[r], Fi[r]));
             }
             const bool live = owns_row && (j >= 0) && (j <= n + 1);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
@@ -694,8 +706,8 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
                 const int k = max(-126, min(126, ilog2f(mh)));
                 const float sc = pow2f(-k);
 #pragma unroll
-                for (int r = 0; r < R; ++r) { Md[r] *= sc; Xi[r] *= sc; X2i[r] *= sc; Yi[r] *= sc; Y2i[r] *= sc; }
-                uMd *= sc;
+                for (int r = 0; r < R; ++r) { Md[r] *= sc; Yi[r] *= sc; Y2i[r] *= sc; }
+                uMd *= sc; lXi *= sc; lX2i *= sc;
                 fh = eH + k;
             } else if (lane == 0) {
                 fh = eH;
@@ -704,8 +716,8 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
                 const int k = max(-126, min(126, ilog2f(mp)));
                 const float sc = pow2f(-k);
 #pragma unroll
-                for (int r = 0; r < R; ++r) { Zd[r] *= sc; Ei[r] *= sc; Fi[r] *= sc; }
-                uZd *= sc;
+                for (int r = 0; r < R; ++r) { Zd[r] *= sc; Fi[r] *= sc; }
+                uZd *= sc; lEi *= sc;
                 fp = eP + k;
             } else if (lane == 0) {
                 fp = eP;
@@ -750,12 +762,12 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
         const int yc_now = yc;
         yc = ycode(j + 1);
         if (t == t_end || t == t_start)
-            fwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, Xi, X2i, Yi,
-                              Y2i, Zd, Ei, Fi, Aa, cnt, xo, vmask, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
+            fwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, lXi, lX2i, Yi,
+                              Y2i, Zd, lEi, Fi, Aa, cnt, xo, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
                               bs, ebnd, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
         else
-            fwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, Xi, X2i, Yi,
-                               Y2i, Zd, Ei, Fi, Aa, cnt, xo, vmask, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
+            fwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, lXi, lX2i, Yi,
+                               Y2i, Zd, lEi, Fi, Aa, cnt, xo, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
                                bs, ebnd, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
     }
     cp_async_wait<0>();
@@ -797,17 +809,25 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     __syncwarp();
 }
 
+// rows per lane of a strip with rows_in rows: the smallest of 1, 2, 4, 8 that covers it
+__device__ __forceinline__ int rows_per_lane(int rows_in) {
+    const int r = (rows_in + 31) / 32;
+    return r <= 1 ? 1 : r <= 2 ? 2 : (r <= 4 || kRmax == 4) ? 4 : 8;
+}
+
 __device__ __forceinline__ void bwd_dispatch(int Rs, const Coef& cf, const float2* s_ow, const PairCtx& c,
                                              const WarpSmem& ws, int s, int ns, float& Zh, float& Zp,
                                              int& eZh, int& eZp, int& flag) {
     switch (Rs) {
         case 1: bwd_strip<1>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
         case 2: bwd_strip<2>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        default: bwd_strip<4>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        case 4: bwd_strip<4>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        default: bwd_strip<kRmax>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
     }
 }
 
-__global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Problem Pb) {
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     float2* s_ow = (float2*)s_raw;
     for (int i = threadIdx.x; i < kTab * kTab; i += blockDim.x) s_ow[i] = Pb.cst->ow[i];
@@ -847,9 +867,13 @@ __global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Proble
         c.nch = (c.n + 32 + kC - 1) / kC;
         const int m = c.m, n = c.n;
         const int nstrips = (m + 1 + kStripRows - 1) / kStripRows;
-        // the column residues of the pair, staged once
+        // the column residues of the pair, staged once, with empty codes on
+        // both sides so that every skewed column index reads a valid byte
         __syncwarp();
-        for (int i = lane; i < n; i += 32) ws.sy[i] = c.y[i];
+        for (int i = lane; i < n + 2 * kYPad; i += 32) {
+            const int jj = i - kYPad;
+            ws.sy[i] = (jj >= 0 && jj < n) ? c.y[jj] : (uint8_t)kEmpty;
+        }
         __syncwarp();
         int flag = 0;
         // ---- pass 1: backward, bottom strip first
@@ -857,7 +881,7 @@ __global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Proble
         int eZh = 0, eZp = 0;
         for (int s = nstrips - 1; s >= 0; --s) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
-            const int Rs = (rows_in + 31) / 32 == 3 ? 4 : (rows_in + 31) / 32;
+            const int Rs = rows_per_lane(rows_in);
             bwd_dispatch(Rs, Pb.cf, s_ow, c, ws, s, nstrips, Zh, Zp, eZh, eZp, flag);
             __syncwarp();
         }
@@ -881,16 +905,16 @@ __global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Proble
         int64_t pair_tot = 0;
         for (int s = 0; s < nstrips; ++s) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
-            const int Rs = (rows_in + 31) / 32 == 3 ? 4 : (rows_in + 31) / 32;
+            const int Rs = rows_per_lane(rows_in);
             switch (Rs) {
                 case 1: fwd_strip<1>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
                 case 2: fwd_strip<2>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                default: fwd_strip<4>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                case 4: fwd_strip<4>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+                default: fwd_strip<kRmax>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
             }
         }
         // ---- pair results (held by the lane that owns row m)
-        int lastRs = (min(kStripRows, m + 1 - (nstrips - 1) * kStripRows) + 31) / 32;
-        if (lastRs == 3) lastRs = 4;
+        const int lastRs = rows_per_lane(min(kStripRows, m + 1 - (nstrips - 1) * kStripRows));
         const int Lend = (m - (nstrips - 1) * kStripRows) / lastRs;
         const float fZh = __shfl_sync(FULL, fo.Zh, Lend), fZp = __shfl_sync(FULL, fo.Zp, Lend);
         const int feh = __shfl_sync(FULL, fo.eZh, Lend), fep = __shfl_sync(FULL, fo.eZp, Lend);
@@ -929,31 +953,44 @@ __global__ void __launch_bounds__(128, QP_F32_MIN_BLOCKS) k_posterior_f32(Proble
     }
 }
 
-int posterior_f32_regs() {
+template <int MINB>
+static cudaError_t set_smem(size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_posterior_f32<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int posterior_f32_regs(int variant) {
     cudaFuncAttributes a;
-    if (cudaFuncGetAttributes(&a, k_posterior_f32) != cudaSuccess) return -1;
-    return a.numRegs;
+    const cudaError_t e = variant == 1 ? cudaFuncGetAttributes(&a, k_posterior_f32<3>)
+                                       : cudaFuncGetAttributes(&a, k_posterior_f32<4>);
+    return e == cudaSuccess ? a.numRegs : -1;
 }
 
 size_t posterior_f32_smem(int warps_per_block, int max_len) {
     return (size_t)kOwBytes + (size_t)warps_per_block * warp_smem_bytes(max_len);
 }
 
-int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm) {
+int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant) {
     const size_t smem = posterior_f32_smem(warps_per_block, max_len);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_posterior_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f32,
+    if (variant == 1) {
+        set_smem<3>(smem);
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f32<3>,
+                                                                  warps_per_block * 32, smem);
+    }
+    set_smem<4>(smem);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f32<4>,
                                                               warps_per_block * 32, smem);
 }
 
-cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block, cudaStream_t s) {
+cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block, cudaStream_t s,
+                                 int variant) {
     const size_t smem = posterior_f32_smem(warps_per_block, P.max_len);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_posterior_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_posterior_f32<<<grid, warps_per_block * 32, smem, s>>>(P);
+    cudaError_t e = variant == 1 ? set_smem<3>(smem) : set_smem<4>(smem);
+    if (e != cudaSuccess) return e;
+    if (variant == 1)
+        k_posterior_f32<3><<<grid, warps_per_block * 32, smem, s>>>(P);
+    else
+        k_posterior_f32<4><<<grid, warps_per_block * 32, smem, s>>>(P);
     return cudaGetLastError();
 }
 
