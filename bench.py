@@ -17,8 +17,19 @@ partition-function forward and backward, combination, threshold and MEA.
           copied from pinned host memory, the CSR left on the device, the
           MEA distance matrix copied back to pinned host memory; wall time.
 
+  f64_plain : the plain FP64 GPU form (one CTA per pair, no scaling tricks)
+          on the same family, device time, for comparison.
+
+Serving (--config c4): 200 families (10-1000 sequences, log-uniform; lengths
+50-1000) arrive as a Poisson process at 20/s and go through the serving loop
+(qp_server_*: memory-admitted, device-resident, pairs of all admitted families
+batched into shared persistent launches).  value = cells of all families /
+wall time from the first arrival to the last completion; latency_ms = p50 /
+p99 / max of submit-to-completion per family; e2e = the same wall-clock
+throughput (families from host memory, distance matrices read back).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--config c1|c2|c3|c5] [--precision f32|f64]
+       [--config c1|c2|c3|c4|c5] [--precision f32|f64]
 """
 from __future__ import annotations
 
@@ -44,6 +55,7 @@ CONFIG_DESC = {
     "c1": "8 seqs, lengths 100-150, star tree s=0.30, 28 pairs",
     "c2": "64 seqs, lengths 200-400, star tree s=0.40, 2016 pairs",
     "c3": "500 seqs, lengths 150-500, random tree s~U[0.05,0.25], 124750 pairs",
+    "c4": "serving: 200 families Poisson 20/s, 10-1000 seqs log-uniform, lengths 50-1000",
     "c5": "100 seqs, lengths 2000-4000, 3-domain roots, 4950 pairs",
 }
 
@@ -211,9 +223,149 @@ def run_reference(args, fam, prm, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank, world, local):
+    """--config c4: the serving loop under Poisson arrivals."""
+    import torch
+    import paper_1512_07437_b300 as qp
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prm = synth.default_params(threshold=0.01)
+    trace = synth.make_serving_trace(seed=4 + 1000 * rank)
+    free, total = torch.cuda.mem_get_info(dev)
+    budget = int(min(0.55 * free, 150e9))
+    srv = qp.Server(prm, budget, device=local, out_on_device=True)
+    # warm-up: a few small families (allocator pool, autotuner, module load)
+    warm = [synth.star_family(900 + i, 24, (200, 400), 0.3) for i in range(max(3, args.warmup))]
+    for f in warm:
+        srv.poll(srv.submit(f.residues, f.offsets), -1).free()
+    st0 = srv.stats()
+    lat, cells_done, fallbacks = [], 0.0, 0
+    pending = {}
+    lock = threading.Lock()
+    submitted = threading.Event()
+    errors = []
+
+    def poller():
+        try:
+            while True:
+                with lock:
+                    items = list(pending.items())
+                if not items and submitted.is_set():
+                    return
+                hit = False
+                for t, (fam, h_dist) in items:
+                    r = srv.poll(t, 0)
+                    if r is None:
+                        continue
+                    hit = True
+                    h_dist.copy_(r.dist)          # the guide tree's input comes back to the host
+                    lat.append(r.kernel_ms[3])
+                    nonlocal_state["cells"] += fam.cells()
+                    nonlocal_state["fallbacks"] += r.n_fallback
+                    r.free()
+                    with lock:
+                        del pending[t]
+                    nonlocal_state["t_last"] = time.perf_counter()
+                if not hit:
+                    time.sleep(0.0005)
+        except Exception as e:      # surfaced after the join
+            errors.append(e)
+
+    nonlocal_state = {"cells": 0.0, "fallbacks": 0, "t_last": 0.0}
+    th = threading.Thread(target=poller, daemon=True)
+    h2d = 0
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        th.start()
+        for t_arr, fam in trace:
+            d = t0 + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            h_dist = torch.empty((fam.k, fam.k), dtype=torch.float32).pin_memory()
+            t = srv.submit(fam.residues, fam.offsets)
+            h2d += int(fam.residues.nbytes + fam.offsets.nbytes)
+            with lock:
+                pending[t] = (fam, h_dist)
+        submitted.set()
+        th.join()
+    if errors:
+        raise errors[0]
+    wall = nonlocal_state["t_last"] - t0
+    st = srv.stats()
+    srv.destroy()
+    cells = nonlocal_state["cells"]
+    kernel_ms = st["kernel_ms"] - st0["kernel_ms"]
+    n_f32 = st["launches_f32"] - st0["launches_f32"]
+    n_f64 = st["launches_f64"] - st0["launches_f64"]
+    lat_s = sorted(lat)
+    q = lambda p: lat_s[min(len(lat_s) - 1, int(round(p * (len(lat_s) - 1))))]
+    value = cells / wall / 1e9
+    clocks = clk.summary()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(clocks["sm_max_mhz"] or 2032.0)
+    peak_tops = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
+    achieved = cells * ALU_OPS_PER_CELL / (kernel_ms * 1e-3) / 1e12
+    line = {
+        "metric": "posterior-stage GCUPS and p50/p99 family latency (serving)",
+        "value": value, "unit": "GCUPS", "n_gpus": world, "steps": 1, "warmup": len(warm),
+        "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"c4: {CONFIG_DESC['c4']}", "families": len(trace),
+                   "cells": cells, "mem_budget_bytes": budget, "threshold": prm.threshold,
+                   "l2": "inputs far larger than L2 (4e12 cells over 200 families)",
+                   "fp64_fallback_pairs": nonlocal_state["fallbacks"],
+                   "launch_target_ms": float(os.environ.get("QP_SERVER_LAUNCH_MS", 30)),
+                   "max_resident": st["max_resident"],
+                   "max_families_per_launch": st["max_families_per_launch"]},
+        "latency_ms": {"p50": q(0.50), "p99": q(0.99), "max": lat_s[-1], "min": lat_s[0]},
+        "busy_gcups": cells / (kernel_ms * 1e-3) / 1e9,
+        "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(sum(f.k * f.k * 4 for _, f in trace)),
+                "what": "families submitted from host memory at their arrival times; distance "
+                        "matrices read back; wall time first arrival -> last completion"},
+        "gpu_launches": int(n_f32 + n_f64 + 3 * len(trace)),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tissue/s",
+                     "frac": achieved / peak_tops, "traffic": None, "kernel": "k_posterior_f32",
+                     "kernel_ms": kernel_ms, "ops_per_cell": ALU_OPS_PER_CELL,
+                     "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz"},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def f64_plain(qp, torch, fam, prm, local, stream, steps=3):
+    """Device time of the plain FP64 GPU form on the same family."""
+    p64 = qp.make_params(prm.replace(precision="f64") if hasattr(prm, "replace") else prm,
+                         device=local, stream=stream)
+    d_res = torch.from_numpy(fam.residues).to(torch.device("cuda", local))
+    qp.qp_posteriors(d_res, fam.offsets, p64, out_on_device=True).free()
+    ts = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = qp.qp_posteriors(d_res, fam.offsets, p64, out_on_device=True)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        r.free()
+    ms = statistics.mean(ts)
+    return {"value": fam.cells() / (ms * 1e-3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
+            "steps": steps, "kernel": "k_posterior_f64"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.config == "c4":
+        if args.impl == "reference":
+            # the oracle on pairs of the trace's first families (same generator
+            # seeds as the full trace), the family of median size
+            fams = sorted((f for _, f in synth.make_serving_trace(seed=4, n_families=12)),
+                          key=lambda f: f.cells())
+            return run_reference(args, fams[len(fams) // 2], synth.default_params(), rank)
+        return run_serving(args, rank, world, local)
     fam = synth.make_family(args.config, args.seed)
     prm = synth.default_params(threshold=0.01, precision=args.precision)
     if args.impl == "reference":
@@ -330,6 +482,8 @@ def main():
                      "ops_per_cell": ALU_OPS_PER_CELL},
         "clocks": clocks,
     }
+    if args.precision == "f32" and args.config in ("c1", "c2"):
+        line["f64_plain"] = f64_plain(qp, torch, fam, prm, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fam, prm, args.cpu_sample_s)
     if rank == 0:

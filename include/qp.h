@@ -159,27 +159,70 @@ int qp_posteriors(const qp_family* family, const qp_params* params,
 /* Releases a result and everything it points to.  NULL is ignored. */
 void qp_result_free(qp_result* result);
 
-/* Serving loop (bulk processing of many families, Methods, "Other
- * algorithmic improvements": bulk mode; memory limit by sparsity).
- * A server owns one device stream and a worker thread.  Families submitted
- * while others run are admitted as soon as their worst-case device memory
- * fits in mem_budget bytes, and their pairs join the work already queued on
- * the device.
+/* Serving loop with continuous batching: many families in one run under a
+ * device memory limit (Methods, "Other algorithmic improvements": bulk mode
+ * and the user-specified memory limit).
+ *
+ * A server owns three streams of params->device and two threads.  Submitted
+ * families are admitted in arrival order while one of 64 family slots is
+ * free and mem_budget holds their bytes (sequences, pair plan, entry pool,
+ * results, plus the kernels' per-warp scratch, which grows with the longest
+ * admitted sequence).  Admitted families stay resident on the device.  The
+ * server keeps two persistent launches of the FP32 kernel queued back to
+ * back; every launch takes pairs from all admitted families (the family
+ * with the least remaining work first; families admitted more than an aging
+ * bound ago before all others), so a family that arrives while others run
+ * shares the next launch with them.  Results equal those of qp_posteriors
+ * on the same family and parameters.
+ *
  *   qp_server_create : params as for qp_posteriors (precision must be
- *                      QP_F32_SCALED); mem_budget > 0.
+ *                      QP_F32_SCALED; params->stream is ignored); mem_budget
+ *                      > 0 bytes; out_on_device 0: results are copied to host
+ *                      memory, 1: results stay in device memory (and no
+ *                      longer count against the budget once polled).
  *   qp_server_submit : copies the family; returns a ticket.  QP_EINVAL for a
- *                      malformed family or one that can never fit the budget.
+ *                      malformed family, a residue outside the alphabet, or
+ *                      a family that can never fit the budget.
  *   qp_server_poll   : waits up to timeout_ms (0: no wait, <0: forever) for
  *                      the ticket; QP_ENOTREADY / QP_ETIMEOUT when not done.
- *                      The result is host-resident and owned by the caller.
- *   qp_server_cancel : cancels a pending ticket (QP_ECANCELLED on poll).
- *   qp_server_destroy: stops the worker, cancels pending work, frees memory. */
+ *                      On success the caller owns *out (qp_result_free); a
+ *                      ticket is consumed by the poll that returns its end.
+ *                      Server results use kernel_ms as: [0] ms queued before
+ *                      admission, [1] ms from admission to the last pair,
+ *                      [2] ms of CSR assembly and copy-out, [3] ms from
+ *                      submit to completion.
+ *   qp_server_cancel : cancels a ticket not yet finished (QP_ECANCELLED on
+ *                      poll); pairs already on the device finish first.
+ *   qp_server_get_stats : counters below.
+ *   qp_server_destroy: cancels pending work, waits for the device, frees
+ *                      everything, including results never polled.
+ * Environment knobs: QP_SERVER_LAUNCH_MS (target device time of one launch,
+ * default 30), QP_SERVER_AGING_MS (aging bound, default 2000). */
 typedef struct qp_server qp_server;
-int qp_server_create(const qp_params* params, size_t mem_budget, qp_server** out);
+typedef struct qp_server_stats {
+    int64_t submitted;       /* tickets issued */
+    int64_t completed;       /* finished with a result */
+    int64_t failed;          /* finished with an error */
+    int64_t cancelled;
+    int64_t pairs_done;      /* pairs of completed families */
+    double cells_done;       /* sum of m*n over those pairs */
+    int64_t launches_f32;    /* persistent FP32 launches */
+    int64_t launches_f64;    /* FP64 follow-up launches */
+    double kernel_ms;        /* device time of all those launches */
+    int32_t resident;        /* families holding device memory now */
+    int32_t max_resident;    /* most families resident at once */
+    int32_t max_families_per_launch;  /* most families sharing one launch */
+    int32_t queued;          /* submitted and not yet admitted */
+    int64_t reserved_bytes;  /* device bytes held for admitted families */
+    int64_t scratch_bytes;   /* device bytes of the kernels' scratch */
+} qp_server_stats;
+int qp_server_create(const qp_params* params, size_t mem_budget, int32_t out_on_device,
+                     qp_server** out);
 int qp_server_submit(qp_server* server, const qp_family* family, uint64_t* ticket);
 int qp_server_poll(qp_server* server, uint64_t ticket, int32_t timeout_ms,
                    qp_result** out);
 int qp_server_cancel(qp_server* server, uint64_t ticket);
+int qp_server_get_stats(qp_server* server, qp_server_stats* out);
 void qp_server_destroy(qp_server* server);
 
 /* Allocation-free variant for callers that cannot allocate device memory.

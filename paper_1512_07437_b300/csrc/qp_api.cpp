@@ -300,15 +300,31 @@ std::shared_ptr<Plan> Context::plan_for(int k, const int64_t* off, int* status) 
 }
 
 // ------------------------------------------------------------------ one family
-struct ResultOwner {
-    int device = 0;
-    bool on_device = true;
-    void* dev_a = nullptr;   // fixed-size part
-    void* dev_b = nullptr;   // col / val part
-    void* host = nullptr;
-};
-
-static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+void fill_result(qp_result* r, ResultOwner* own, const ResultLayout& L, int k, int64_t n_pairs,
+                 int64_t n_rows, int64_t nnz_bound, bool f64, int precision, int device) {
+    char* A = (char*)own->dev_a;
+    char* B = (char*)own->dev_b;
+    r->k = k;
+    r->on_device = 1;
+    r->precision = precision;
+    r->device = device;
+    r->n_pairs = n_pairs;
+    r->n_rows = n_rows;
+    r->pair_row_off = (int64_t*)(A + L.o_pro);
+    r->row_ptr = (int32_t*)(A + L.o_rp);
+    r->pair_nnz_off = (int64_t*)(A + L.o_pno);
+    r->col = (int32_t*)B;
+    r->val = B ? (float*)(B + align256(sizeof(int32_t) * nnz_bound)) : nullptr;
+    r->val64 = (B && f64) ? (double*)(B + align256(sizeof(int32_t) * nnz_bound) +
+                                      align256(sizeof(float) * nnz_bound)) : nullptr;
+    r->dist = (float*)(A + L.o_dist);
+    r->dist64 = (double*)(A + L.o_d64);
+    r->mea = (double*)(A + L.o_mea);
+    r->log_z_hmm = (double*)(A + L.o_lh);
+    r->log_z_pf = (double*)(A + L.o_lp);
+    r->pair_flags = (int32_t*)(A + L.o_fl);
+    r->owner_ = own;
+}
 
 int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
                qp_result** out) {
@@ -364,23 +380,15 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         delete own;
         return code;
     };
-    size_t o_pro, o_rp, o_pno, o_dist, o_d64, o_mea, o_lh, o_lp, o_fl, sz = 0;
-    o_pro = sz; sz += align_up(sizeof(int64_t) * (P + 1));
-    o_rp = sz;  sz += align_up(sizeof(int32_t) * pl->n_rows);
-    o_pno = sz; sz += align_up(sizeof(int64_t) * (P + 1));
-    o_dist = sz; sz += align_up(sizeof(float) * (size_t)k * k);
-    o_d64 = sz; sz += align_up(sizeof(double) * (size_t)k * k);
-    o_mea = sz; sz += align_up(sizeof(double) * P);
-    o_lh = sz;  sz += align_up(sizeof(double) * P);
-    o_lp = sz;  sz += align_up(sizeof(double) * P);
-    o_fl = sz;  sz += align_up(sizeof(int32_t) * P);
+    const ResultLayout lay(P, pl->n_rows, k);
+    const size_t sz = lay.bytes;
     e = cudaMallocAsync(&own->dev_a, sz, st);
     if (e != cudaSuccess) { own->dev_a = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation (%zu bytes) failed", sz)); }
     char* A = (char*)own->dev_a;
-    cudaMemcpyAsync(A + o_pro, pl->d_row_off.ptr, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToDevice, st);
-    cudaMemsetAsync(A + o_dist, 0, sizeof(float) * (size_t)k * k, st);
-    cudaMemsetAsync(A + o_d64, 0, sizeof(double) * (size_t)k * k, st);
-    cudaMemsetAsync(A + o_fl, 0, sizeof(int32_t) * P, st);
+    cudaMemcpyAsync(A + lay.o_pro, pl->d_row_off.ptr, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(A + lay.o_dist, 0, sizeof(float) * (size_t)k * k, st);
+    cudaMemsetAsync(A + lay.o_d64, 0, sizeof(double) * (size_t)k * k, st);
+    cudaMemsetAsync(A + lay.o_fl, 0, sizeof(int32_t) * P, st);
 
     // ---- workspace
     if ((e = C->row_cnt.ensure(sizeof(int32_t) * pl->n_rows)) != cudaSuccess ||
@@ -413,12 +421,12 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     fd.row_cnt = (int32_t*)C->row_cnt.ptr;
     fd.chunk_off = (int64_t*)C->chunk_off.ptr;
     fd.pair_nnz = (int64_t*)C->pair_nnz.ptr;
-    fd.mea = (double*)(A + o_mea);
-    fd.logz_h = (double*)(A + o_lh);
-    fd.logz_p = (double*)(A + o_lp);
-    fd.dist = (float*)(A + o_dist);
-    fd.dist64 = (double*)(A + o_d64);
-    fd.pair_flags = (int32_t*)(A + o_fl);
+    fd.mea = (double*)(A + lay.o_mea);
+    fd.logz_h = (double*)(A + lay.o_lh);
+    fd.logz_p = (double*)(A + lay.o_lp);
+    fd.dist = (float*)(A + lay.o_dist);
+    fd.dist64 = (double*)(A + lay.o_d64);
+    fd.pair_flags = (int32_t*)(A + lay.o_fl);
     fd.pool_used = &d_status->pool_used;
     fd.pool_base = 0;
     fd.n_done = nullptr;
@@ -449,7 +457,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             cudaMemsetAsync(&d_status->pool_used, 0, sizeof(unsigned long long), st);
             cudaMemsetAsync(&d_status->pool_overflow, 0, sizeof(int32_t) * 2, st);
             cudaMemsetAsync(&d_status->work_f32, 0, sizeof(int32_t) * 2, st);
-            cudaMemsetAsync(A + o_fl, 0, sizeof(int32_t) * P, st);
+            cudaMemsetAsync(A + lay.o_fl, 0, sizeof(int32_t) * P, st);
         }
         cudaEventRecord(C->ev[1], st);
         int f64_grid = 0;
@@ -535,48 +543,30 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     }
     const int64_t nnz_bound = (int64_t)hs.pool_used;
     // ---- CSR assembly
-    const size_t ob_col = 0, ob_val = align_up(sizeof(int32_t) * nnz_bound),
-                 ob_v64 = ob_val + align_up(sizeof(float) * nnz_bound);
-    const size_t szb = ob_v64 + (f64 ? align_up(sizeof(double) * nnz_bound) : 0);
+    const size_t szb = ResultLayout::entry_bytes(nnz_bound, f64);
     e = cudaMallocAsync(&own->dev_b, std::max<size_t>(szb, 256), st);
     if (e != cudaSuccess) { own->dev_b = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation failed")); }
-    char* B = (char*)own->dev_b;
-    int32_t* d_col = (int32_t*)(B + ob_col);
-    float* d_val = (float*)(B + ob_val);
-    double* d_val64 = f64 ? (double*)(B + ob_v64) : nullptr;
-    if ((e = qpk::launch_scan_nnz(fd.pair_nnz, P, (int64_t*)(A + o_pno), st)) != cudaSuccess ||
-        (e = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
-                                 fd.chunk_off, (const int2*)C->pool.ptr, Pb.pool64, P, (int64_t*)(A + o_pno),
-                                 (int32_t*)(A + o_rp), d_col, d_val, d_val64, st)) != cudaSuccess)
-        return bail(cuda_fail(e, "CSR assembly"));
-    cudaEventRecord(C->ev[4], st);
-    int64_t nnz = 0;
-    e = cudaMemcpyAsync(C->h_status.ptr, A + o_pno + sizeof(int64_t) * P, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "CSR assembly"));
-    memcpy(&nnz, C->h_status.ptr, sizeof nnz);
-
     qp_result* r = (qp_result*)calloc(1, sizeof(qp_result));
     if (!r) return bail(fail(QP_ENOMEM, "host allocation failed"));
-    r->k = k;
-    r->on_device = 1;
-    r->precision = prm->precision;
-    r->device = C->device;
-    r->n_pairs = P;
-    r->n_rows = pl->n_rows;
+    fill_result(r, own, lay, k, P, pl->n_rows, nnz_bound, f64, prm->precision, C->device);
+    int32_t* d_col = r->col;
+    float* d_val = r->val;
+    double* d_val64 = r->val64;
+    if ((e = qpk::launch_scan_nnz(fd.pair_nnz, P, (int64_t*)(A + lay.o_pno), st)) != cudaSuccess ||
+        (e = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
+                                 fd.chunk_off, (const int2*)C->pool.ptr, Pb.pool64, P, (int64_t*)(A + lay.o_pno),
+                                 (int32_t*)(A + lay.o_rp), d_col, d_val, d_val64, st)) != cudaSuccess) {
+        free(r);
+        return bail(cuda_fail(e, "CSR assembly"));
+    }
+    cudaEventRecord(C->ev[4], st);
+    int64_t nnz = 0;
+    e = cudaMemcpyAsync(C->h_status.ptr, A + lay.o_pno + sizeof(int64_t) * P, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { free(r); return bail(cuda_fail(e, "CSR assembly")); }
+    memcpy(&nnz, C->h_status.ptr, sizeof nnz);
+
     r->nnz = nnz;
-    r->pair_row_off = (int64_t*)(A + o_pro);
-    r->row_ptr = (int32_t*)(A + o_rp);
-    r->pair_nnz_off = (int64_t*)(A + o_pno);
-    r->col = d_col;
-    r->val = d_val;
-    r->val64 = d_val64;
-    r->dist = (float*)(A + o_dist);
-    r->dist64 = (double*)(A + o_d64);
-    r->mea = (double*)(A + o_mea);
-    r->log_z_hmm = (double*)(A + o_lh);
-    r->log_z_pf = (double*)(A + o_lp);
-    r->pair_flags = (int32_t*)(A + o_fl);
     r->n_fallback = f64 ? 0 : hs.n_fallback;
     for (int i = 0; i < 10; ++i) r->guard_info[i] = hs.diag[i];
     float ms = 0;
@@ -584,7 +574,6 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     cudaEventElapsedTime(&ms, C->ev[2], C->ev[3]); r->kernel_ms[1] = ms;
     cudaEventElapsedTime(&ms, C->ev[3], C->ev[4]); r->kernel_ms[2] = ms;
     cudaEventElapsedTime(&ms, C->ev[0], C->ev[4]); r->kernel_ms[3] = ms;
-    r->owner_ = own;
     if (!out_on_device) {
         int rc = to_host(r, st);
         if (rc != QP_OK) { qp_result_free(r); return rc; }
@@ -613,7 +602,7 @@ int to_host(qp_result* r, cudaStream_t st) {
         {(void**)&r->pair_flags, sizeof(int32_t) * P},
     };
     size_t tot = 0;
-    for (auto& p : parts) tot += align_up(p.bytes);
+    for (auto& p : parts) tot += align256(p.bytes);
     char* h = (char*)malloc(std::max<size_t>(tot, 64));
     if (!h) return fail(QP_ENOMEM, "host result allocation (%zu bytes) failed", tot);
     size_t o = 0;
@@ -626,7 +615,7 @@ int to_host(qp_result* r, cudaStream_t st) {
             }
             *p.field = h + o;
         }
-        o += align_up(p.bytes);
+        o += align256(p.bytes);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { free(h); return cuda_fail(e, "copy result to host"); }

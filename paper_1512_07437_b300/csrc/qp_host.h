@@ -99,6 +99,48 @@ struct Context {
     std::shared_ptr<Plan> plan_for(int k, const int64_t* off, int* status);
 };
 
+// Device layout of a result's fixed-size part (one allocation): per-pair and
+// per-row arrays and the k x k distance matrices.  col / val live in a second
+// allocation sized by the entry count.
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+struct ResultLayout {
+    size_t o_pro = 0, o_rp = 0, o_pno = 0, o_dist = 0, o_d64 = 0, o_mea = 0, o_lh = 0, o_lp = 0, o_fl = 0;
+    size_t bytes = 0;
+    ResultLayout() = default;
+    ResultLayout(int64_t n_pairs, int64_t n_rows, int k) {
+        size_t sz = 0;
+        o_pro = sz;  sz += align256(sizeof(int64_t) * (n_pairs + 1));
+        o_rp = sz;   sz += align256(sizeof(int32_t) * n_rows);
+        o_pno = sz;  sz += align256(sizeof(int64_t) * (n_pairs + 1));
+        o_dist = sz; sz += align256(sizeof(float) * (size_t)k * k);
+        o_d64 = sz;  sz += align256(sizeof(double) * (size_t)k * k);
+        o_mea = sz;  sz += align256(sizeof(double) * n_pairs);
+        o_lh = sz;   sz += align256(sizeof(double) * n_pairs);
+        o_lp = sz;   sz += align256(sizeof(double) * n_pairs);
+        o_fl = sz;   sz += align256(sizeof(int32_t) * n_pairs);
+        bytes = sz;
+    }
+    // bytes of the col / val part for nnz entries
+    static size_t entry_bytes(int64_t nnz, bool f64) {
+        return align256(sizeof(int32_t) * nnz) + align256(sizeof(float) * nnz) +
+               (f64 ? align256(sizeof(double) * nnz) : 0);
+    }
+};
+
+// Owner of a result's memory (qp_result::owner_).
+struct ResultOwner {
+    int device = 0;
+    bool on_device = true;
+    void* dev_a = nullptr;   // fixed-size part (ResultLayout)
+    void* dev_b = nullptr;   // col / val part
+    void* host = nullptr;
+};
+
+// Fills the public result from the two device parts (B may be null when nnz = 0
+// is known in advance).  The caller sets nnz, n_fallback, guard_info, kernel_ms.
+void fill_result(qp_result* r, ResultOwner* own, const ResultLayout& L, int k, int64_t n_pairs,
+                 int64_t n_rows, int64_t nnz_bound, bool f64, int precision, int device);
+
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 const char* last_error();

@@ -82,7 +82,10 @@ struct FamDesc {
     float* dist;                   // [k*k]
     double* dist64;                // [k*k]
     int32_t* pair_flags;           // [n_pairs]
-    // region of the shared entry pool owned by this family
+    // entry pool of this family (null: the launch's shared pool) and the
+    // region of it that the family owns
+    int2* pool;
+    double* pool64;
     unsigned long long* pool_used; // entries reserved in the region
     int64_t pool_base;             // absolute first entry of the region
     int64_t pool_cap;              // entries in the region

@@ -794,13 +794,14 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     const int64_t base = fd.pool_base + (int64_t)off;
     int w = incl - tot;
     const int64_t row_slot = fd.pair_row_off[c.p];
+    int2* pool = fd.pool ? fd.pool : Pb.pool;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + lane * R + r;
         if (i >= 1 && i <= m) fd.row_cnt[row_slot + i - 1] = cnt[r];
         if (fits) {
             const int2* src = stg + (lane * R + r) * cap;
-            for (int q = 0; q < cnt[r]; ++q) Pb.pool[base + w + q] = src[q];
+            for (int q = 0; q < cnt[r]; ++q) pool[base + w + q] = src[q];
         }
         w += cnt[r];
     }
@@ -929,7 +930,9 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
             const double lzf_p = log((double)fZp) + (double)fep * ln2;
             if (!(fabs(lzb_h - lzf_h) <= 1e-3)) flag |= kGuardAgreeH;
             if (!(fabs(lzb_p - lzf_p) <= 1e-3)) flag |= kGuardAgreeP;
-            if (flag != 0) {
+            // a full entry pool is not a range problem: the pair keeps its FP32
+            // results, its flag tells the host to grow the pool and run again
+            if (flag & ~kGuardPool) {
                 fd.pair_flags[p] = flag;
                 const int slot = atomicAdd(&Pb.status->n_fallback, 1);
                 Pb.fallback[slot] = it;
@@ -939,7 +942,7 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
                 fd.logz_h[p] = lzb_h + fd.seq_logq[ab.x] + fd.seq_logq[ab.y];
                 fd.logz_p[p] = lzb_p;
                 fd.pair_nnz[p] = pair_tot;
-                fd.pair_flags[p] = 0;
+                fd.pair_flags[p] = flag;
                 const double d = 1.0 - A / (double)mn;
                 const int64_t k = fd.k;
                 fd.dist[ab.x * k + ab.y] = (float)d;
@@ -1245,12 +1248,14 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
             }
             __syncthreads();
             if (fits) {
+                int2* pool = fd.pool ? fd.pool : Pb.pool;
+                double* pool64 = fd.pool ? fd.pool64 : Pb.pool64;
                 for (int i = r0 + tid; i <= r1; i += nt) {
                     const int cnt = fd.row_cnt[row_slot + i - 1];
                     const int o = rc[i];
                     for (int qq = 0; qq < cnt; ++qq) {
-                        Pb.pool[base + o + qq] = stg[(int64_t)(i - 1) * cap + qq];
-                        if (Pb.pool64) Pb.pool64[base + o + qq] = stg64[(int64_t)(i - 1) * cap + qq];
+                        pool[base + o + qq] = stg[(int64_t)(i - 1) * cap + qq];
+                        if (pool64) pool64[base + o + qq] = stg64[(int64_t)(i - 1) * cap + qq];
                     }
                 }
             }

@@ -68,6 +68,19 @@ class qp_result(ctypes.Structure):
     ]
 
 
+class qp_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+        ("pairs_done", ctypes.c_int64), ("cells_done", ctypes.c_double),
+        ("launches_f32", ctypes.c_int64), ("launches_f64", ctypes.c_int64),
+        ("kernel_ms", ctypes.c_double),
+        ("resident", ctypes.c_int32), ("max_resident", ctypes.c_int32),
+        ("max_families_per_launch", ctypes.c_int32), ("queued", ctypes.c_int32),
+        ("reserved_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
+    ]
+
+
 _lib = None
 
 
@@ -86,7 +99,7 @@ def lib():
         L.qp_result_free.restype = None
         L.qp_last_error.restype = ctypes.c_char_p
         L.qp_version.restype = ctypes.c_char_p
-        L.qp_server_create.argtypes = [P(qp_params), ctypes.c_size_t, P(ctypes.c_void_p)]
+        L.qp_server_create.argtypes = [P(qp_params), ctypes.c_size_t, ctypes.c_int32, P(ctypes.c_void_p)]
         L.qp_server_create.restype = ctypes.c_int
         L.qp_server_submit.argtypes = [ctypes.c_void_p, P(qp_family), P(ctypes.c_uint64)]
         L.qp_server_submit.restype = ctypes.c_int
@@ -94,6 +107,8 @@ def lib():
         L.qp_server_poll.restype = ctypes.c_int
         L.qp_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
         L.qp_server_cancel.restype = ctypes.c_int
+        L.qp_server_get_stats.argtypes = [ctypes.c_void_p, P(qp_server_stats)]
+        L.qp_server_get_stats.restype = ctypes.c_int
         L.qp_server_destroy.argtypes = [ctypes.c_void_p]
         L.qp_server_destroy.restype = None
         L.qp_pair_posteriors_static.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -301,13 +316,20 @@ def qp_result_free(result: Result):
 
 
 class Server:
-    """Serving loop (qp_server_*)."""
+    """Serving loop with continuous batching (qp_server_* in qp.h)."""
 
-    def __init__(self, params, mem_budget: int, device: int = 0):
+    def __init__(self, params, mem_budget: int, device: int = 0, out_on_device: bool = False):
         self._keep = params if isinstance(params, qp_params) else make_params(params, device=device)
         h = ctypes.c_void_p()
-        _check(lib().qp_server_create(ctypes.byref(self._keep), int(mem_budget), ctypes.byref(h)))
+        self._h = None
+        _check(lib().qp_server_create(ctypes.byref(self._keep), int(mem_budget), int(bool(out_on_device)),
+                                      ctypes.byref(h)))
         self._h = h
+
+    def stats(self) -> dict:
+        st = qp_server_stats()
+        _check(lib().qp_server_get_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in qp_server_stats._fields_}
 
     def submit(self, residues, offsets) -> int:
         fam, keep = make_family(residues, offsets)
@@ -340,8 +362,8 @@ class Server:
             pass
 
 
-def qp_server_create(params, mem_budget: int, device: int = 0) -> Server:
-    return Server(params, mem_budget, device)
+def qp_server_create(params, mem_budget: int, device: int = 0, out_on_device: bool = False) -> Server:
+    return Server(params, mem_budget, device, out_on_device)
 
 
 def qp_server_submit(server: Server, residues, offsets) -> int:
@@ -354,6 +376,10 @@ def qp_server_poll(server: Server, ticket: int, timeout_ms: int = -1):
 
 def qp_server_cancel(server: Server, ticket: int):
     server.cancel(ticket)
+
+
+def qp_server_get_stats(server: Server) -> dict:
+    return server.stats()
 
 
 def qp_server_destroy(server: Server):

@@ -89,3 +89,13 @@ def test_invalid_inputs_rejected_on_host(libqp):
     with pytest.raises(qp.QpError) as e:
         qp.qp_posteriors(fam.residues, fam.offsets, bad)
     assert e.value.code == 1
+
+
+def test_server_without_device_fails_loudly(libqp):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import synth
+    import paper_1512_07437_b300 as qp
+    with pytest.raises(qp.QpError):
+        qp.Server(synth.default_params(), 1 << 30)
