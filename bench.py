@@ -239,7 +239,7 @@ def run_serving(args, rank, world, local):
     for f in warm:
         srv.poll(srv.submit(f.residues, f.offsets), -1).free()
     st0 = srv.stats()
-    lat, cells_done, fallbacks = [], 0.0, 0
+    lat, lat_k, cells_done, fallbacks = [], [], 0.0, 0
     pending = {}
     lock = threading.Lock()
     submitted = threading.Event()
@@ -260,6 +260,7 @@ def run_serving(args, rank, world, local):
                     hit = True
                     h_dist.copy_(r.dist)          # the guide tree's input comes back to the host
                     lat.append(r.kernel_ms[3])
+                    lat_k.append((fam.k, r.kernel_ms[3], r.kernel_ms[0]))
                     nonlocal_state["cells"] += fam.cells()
                     nonlocal_state["fallbacks"] += r.n_fallback
                     r.free()
@@ -300,6 +301,13 @@ def run_serving(args, rank, world, local):
     lat_s = sorted(lat)
     q = lambda p: lat_s[min(len(lat_s) - 1, int(round(p * (len(lat_s) - 1))))]
     value = cells / wall / 1e9
+    by_k = {}
+    for name, lo, hi in (("k<50", 0, 50), ("50<=k<200", 50, 200), ("k>=200", 200, 1 << 30)):
+        xs = sorted(l for k, l, _ in lat_k if lo <= k < hi)
+        ws = sorted(w for k, _, w in lat_k if lo <= k < hi)
+        if xs:
+            by_k[name] = {"n": len(xs), "p50": xs[len(xs) // 2], "max": xs[-1],
+                          "queued_p50": ws[len(ws) // 2]}
     clocks = clk.summary()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = float(clocks["sm_max_mhz"] or 2032.0)
@@ -318,6 +326,7 @@ def run_serving(args, rank, world, local):
                    "max_resident": st["max_resident"],
                    "max_families_per_launch": st["max_families_per_launch"]},
         "latency_ms": {"p50": q(0.50), "p99": q(0.99), "max": lat_s[-1], "min": lat_s[0]},
+        "latency_ms_by_k": by_k,
         "busy_gcups": cells / (kernel_ms * 1e-3) / 1e9,
         "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(sum(f.k * f.k * 4 for _, f in trace)),

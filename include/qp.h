@@ -164,16 +164,18 @@ void qp_result_free(qp_result* result);
  * and the user-specified memory limit).
  *
  * A server owns three streams of params->device and two threads.  Submitted
- * families are admitted in arrival order while one of 64 family slots is
- * free and mem_budget holds their bytes (sequences, pair plan, entry pool,
- * results, plus the kernels' per-warp scratch, which grows with the longest
- * admitted sequence).  Admitted families stay resident on the device.  The
- * server keeps two persistent launches of the FP32 kernel queued back to
- * back; every launch takes pairs from all admitted families (the family
- * with the least remaining work first; families admitted more than an aging
- * bound ago before all others), so a family that arrives while others run
- * shares the next launch with them.  Results equal those of qp_posteriors
- * on the same family and parameters.
+ * families are admitted while one of 64 family slots is free and mem_budget
+ * holds their bytes (sequences, pair plan, entry pool, results, plus the
+ * kernels' per-warp scratch, which grows with the longest admitted
+ * sequence): in arrival order, except that a family that does not fit is
+ * passed by later ones that do until it has waited past the aging bound.
+ * Admitted families stay resident on the device.  The server keeps two
+ * persistent launches of the FP32 kernel queued back to back; every launch
+ * takes pairs from all admitted families (the family with the least
+ * remaining work first; families admitted more than the aging bound ago
+ * get up to half of every launch, oldest first), so a family that arrives
+ * while others run shares the next launch with them.  Results equal those of qp_posteriors on the same
+ * family and parameters.
  *
  *   qp_server_create : params as for qp_posteriors (precision must be
  *                      QP_F32_SCALED; params->stream is ignored); mem_budget
@@ -197,7 +199,7 @@ void qp_result_free(qp_result* result);
  *   qp_server_destroy: cancels pending work, waits for the device, frees
  *                      everything, including results never polled.
  * Environment knobs: QP_SERVER_LAUNCH_MS (target device time of one launch,
- * default 30), QP_SERVER_AGING_MS (aging bound, default 2000). */
+ * default 30), QP_SERVER_AGING_MS (aging bound, default 5000). */
 typedef struct qp_server qp_server;
 typedef struct qp_server_stats {
     int64_t submitted;       /* tickets issued */

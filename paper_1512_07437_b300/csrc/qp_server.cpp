@@ -4,15 +4,17 @@
 //
 //   submit (caller's thread): checks and copies the family, builds its pair
 //     plan and the device bytes it will hold while resident; queues it.
-//   worker thread: admits queued families in arrival order while a family
-//     slot is free and the memory budget holds their bytes.  An admitted
+//   worker thread: admits queued families while a family slot is free and
+//     the memory budget holds their bytes (arrival order; later families
+//     that fit pass one that does not, until it has waited past the aging
+//     bound).  An admitted
 //     family's sequences, work arrays, entry pool and per-pair results stay
 //     in device memory until it completes.  The worker keeps two persistent
 //     launches of the FP32 posterior kernel queued back to back on its
 //     stream; each launch draws pairs from every admitted family (least
-//     remaining work first, families waiting longer than an aging bound
-//     first of all), so a family admitted while others run joins the next
-//     launch and shares it with them.  Pairs whose range guards fired go to
+//     remaining work first; families admitted longer ago than the aging
+//     bound get up to half of every launch), so a family admitted while
+//     others run joins the next launch and shares it with them.  Pairs whose range guards fired go to
 //     an FP64 follow-up launch.  When all pairs of a family are done its CSR
 //     is assembled on the device and the family moves to the finisher.
 //   finisher thread: reads the entry count, copies the result to the host
@@ -140,7 +142,7 @@ struct qp_server {
     int out_on_device = 0;
     Context* ctx = nullptr;
     cudaStream_t cs = nullptr, up = nullptr, down = nullptr;
-    double target_ms = 30.0, aging_s = 2.0;
+    double target_ms = 30.0, aging_s = 5.0;
     // device state
     qpk::Consts* d_cst = nullptr;
     qpk::FamDesc* d_fams = nullptr;
@@ -421,43 +423,55 @@ int admit_one(qp_server* S, const std::shared_ptr<Job>& J, int slot) {
     return QP_OK;
 }
 
+// Admission: families are taken in arrival order; one that does not fit the
+// budget is passed over by later ones that do (backfill) until it has waited
+// longer than the aging bound, after which nothing passes it.
 void admit(qp_server* S) {
     for (;;) {
         int slot = -1;
         for (int s = 0; s < kSlots; ++s)
             if (!S->fams[s]) { slot = s; break; }
         if (slot < 0) return;
-        std::shared_ptr<Job> J;
         int L = 0;
         bool any_resident = false;
         for (int s = 0; s < kSlots; ++s)
             if (S->fams[s]) { any_resident = true; L = std::max(L, S->fams[s]->job->plan->max_len); }
+        std::shared_ptr<Job> J;
+        int Ls = 0;
         {
             std::lock_guard<std::mutex> g(S->mu);
-            while (!S->queue.empty() && S->queue.front()->state != kQueued) S->queue.pop_front();
-            if (S->queue.empty()) return;
-            J = S->queue.front();
-            // scratch is grow-only while families are resident; with none
-            // resident it is kept when it covers the newcomer and fits, else
-            // resized to the newcomer
-            int Ls;
-            if (any_resident) {
-                Ls = std::max(std::max(L, J->plan->max_len), S->scratch_len);
-            } else {
-                Ls = J->plan->max_len;
-                if (S->scratch_len >= Ls && S->reserved + J->reserve + S->scratch_bytes <= S->budget)
-                    Ls = S->scratch_len;
+            const double t = now_s();
+            for (auto it = S->queue.begin(); it != S->queue.end();) {
+                if ((*it)->state != kQueued) { it = S->queue.erase(it); continue; }
+                const Job& C = **it;
+                // scratch is grow-only while families are resident; with none
+                // resident it is kept when it covers the newcomer and fits,
+                // else resized to the newcomer
+                int ls;
+                if (any_resident) {
+                    ls = std::max(std::max(L, C.plan->max_len), S->scratch_len);
+                } else {
+                    ls = C.plan->max_len;
+                    if (S->scratch_len >= ls && S->reserved + C.reserve + S->scratch_bytes <= S->budget)
+                        ls = S->scratch_len;
+                }
+                const size_t scratch = ls == S->scratch_len ? S->scratch_bytes
+                                                            : scratch_bytes_for(S, ls, nullptr, nullptr, nullptr);
+                if (S->reserved + C.reserve + scratch <= S->budget) {
+                    J = *it;
+                    Ls = ls;
+                    S->queue.erase(it);
+                    break;
+                }
+                if (t - C.t_submit > S->aging_s) break;     // hold the memory for this one
+                ++it;
             }
-            const size_t scratch = Ls == S->scratch_len ? S->scratch_bytes
-                                                        : scratch_bytes_for(S, Ls, nullptr, nullptr, nullptr);
-            if (S->reserved + J->reserve + scratch > S->budget) return;   // wait for memory
-            S->queue.pop_front();
+            if (!J) return;                                 // wait for memory
             S->reserved += J->reserve;
             J->state = kRunning;
             J->t_admit = now_s();
-            L = Ls;
         }
-        int rc = set_scratch(S, L);
+        int rc = set_scratch(S, Ls);
         if (rc != QP_OK) {
             std::lock_guard<std::mutex> g(S->mu);
             S->reserved -= J->reserve;
@@ -478,20 +492,22 @@ bool issue(qp_server* S) {
         if (S->recs[i].phase == 0 && ri < 0) ri = i;
     }
     if (inflight >= kInflight || ri < 0) return false;
-    // families with pairs to launch: aged ones by admission, then least remaining work
+    // families with pairs to launch.  Those admitted longer ago than the
+    // aging bound get up to half of the launch, oldest first; the rest of the
+    // launch goes to the family with the least remaining work first.
     const double t = now_s();
-    std::vector<Fam*> cand;
+    std::vector<Fam*> cand, aged;
     for (int s = 0; s < kSlots; ++s) {
         Fam* F = S->fams[s].get();
-        if (F && !F->failed && !F->job->cancel && F->next < F->job->plan->n_pairs) cand.push_back(F);
+        if (F && !F->failed && !F->job->cancel && F->next < F->job->plan->n_pairs) {
+            cand.push_back(F);
+            if (t - F->job->t_admit > S->aging_s) aged.push_back(F);
+        }
     }
     if (cand.empty()) return false;
-    std::stable_sort(cand.begin(), cand.end(), [&](const Fam* a, const Fam* b) {
-        const bool aa = t - a->job->t_admit > S->aging_s, ab = t - b->job->t_admit > S->aging_s;
-        if (aa != ab) return aa;
-        if (aa) return a->job->t_admit < b->job->t_admit;
-        return a->remaining < b->remaining;
-    });
+    std::stable_sort(aged.begin(), aged.end(),
+                     [](const Fam* a, const Fam* b) { return a->job->t_admit < b->job->t_admit; });
+    std::stable_sort(cand.begin(), cand.end(), [](const Fam* a, const Fam* b) { return a->remaining < b->remaining; });
     Rec& R = S->recs[ri];
     R.items.clear();
     R.per_fam.clear();
@@ -500,25 +516,31 @@ bool issue(qp_server* S) {
     R.cells = 0;
     const double budget = std::max(1.0, S->target_ms * S->rate);
     std::vector<std::pair<int64_t, int2>> take;
-    for (Fam* F : cand) {
-        if (R.work >= budget || (int64_t)take.size() >= kMaxItems) break;
-        const Plan& pl = *F->job->plan;
-        int64_t n = 0;
-        while (F->next < pl.n_pairs && (R.work < budget || take.empty()) && (int64_t)take.size() < kMaxItems) {
-            const int32_t q = pl.order[F->next++];
-            const int64_t w = pl.work[q];
-            take.push_back(std::make_pair(w, make_int2(F->slot, q)));
-            R.work += (double)w;
-            F->remaining -= (double)w;
-            const int2 ab = pl.pairs[q];
-            R.cells += (double)pl.lens[ab.x] * (double)pl.lens[ab.y];
-            ++n;
+    std::map<int, int64_t> per;
+    auto fill = [&](const std::vector<Fam*>& order, double limit) {
+        for (Fam* F : order) {
+            if (R.work >= limit || (int64_t)take.size() >= kMaxItems) break;
+            const Plan& pl = *F->job->plan;
+            int64_t n = 0;
+            while (F->next < pl.n_pairs && (R.work < limit || take.empty()) && (int64_t)take.size() < kMaxItems) {
+                const int32_t q = pl.order[F->next++];
+                const int64_t w = pl.work[q];
+                take.push_back(std::make_pair(w, make_int2(F->slot, q)));
+                R.work += (double)w;
+                F->remaining -= (double)w;
+                const int2 ab = pl.pairs[q];
+                R.cells += (double)pl.lens[ab.x] * (double)pl.lens[ab.y];
+                ++n;
+            }
+            if (n) {
+                per[F->slot] += n;
+                F->outstanding += n;
+            }
         }
-        if (n) {
-            R.per_fam.push_back(std::make_pair(F->slot, n));
-            F->outstanding += n;
-        }
-    }
+    };
+    fill(aged, 0.5 * budget);
+    fill(cand, budget);
+    R.per_fam.assign(per.begin(), per.end());
     // one longest-first order over the whole launch
     std::stable_sort(take.begin(), take.end(),
                      [](const std::pair<int64_t, int2>& a, const std::pair<int64_t, int2>& b) { return a.first > b.first; });
