@@ -464,7 +464,7 @@ def main():
     achieved = cells * ALU_OPS_PER_CELL / (kernel_ms * 1e-3) / 1e12
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "k_posterior_f32_traffic.json")) as f:
             traffic = json.load(f).get(f"{args.config}-{args.precision}")
     except Exception:
         pass

@@ -227,6 +227,24 @@ int qp_server_cancel(qp_server* server, uint64_t ticket);
 int qp_server_get_stats(qp_server* server, qp_server_stats* out);
 void qp_server_destroy(qp_server* server);
 
+/* Launch knobs of the FP32 kernel on one device, for benchmarks and tests
+ * (no counterpart in the paper).  value -1 (or 0 for the sizes) restores the
+ * automatic choice.  Names:
+ *   "variant"         0: 4 blocks of 4 warps per SM (at most 128 registers),
+ *                     1: 3 blocks of 4 warps per SM;
+ *   "ckpt"            0: stored form (pass 1 keeps the backward values of the
+ *                     whole matrix), 1: checkpointed form (pass 1 keeps one
+ *                     boundary row per 128-row strip; pass 2 recomputes each
+ *                     strip's backward values before its forward sweep);
+ *   "blocks_per_sm", "warps_per_block";
+ *   "scratch_bytes"   device bytes the kernels' scratch may take (default:
+ *                     45% of free memory, at most 48 GiB); the stored form is
+ *                     chosen while it fits a full grid, else the checkpointed
+ *                     form, on a grid cut to the budget if need be.
+ * Applies to later qp_posteriors calls and servers created afterwards.
+ * QP_EINVAL for an unknown name or device. */
+int qp_set_option(int32_t device, const char* name, int64_t value);
+
 /* Allocation-free variant for callers that cannot allocate device memory.
  * There is no counterpart in the paper: it exists for code that must not call
  * cudaMalloc / cudaFree while it runs -- for instance a host program whose

@@ -225,6 +225,14 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
     return pl;
 }
 
+int64_t scratch_budget(const LaunchOverride& t) {
+    if (t.scratch_bytes > 0) return t.scratch_bytes;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
+    const int64_t cap = (int64_t)48 << 30;
+    return std::max<int64_t>((int64_t)1 << 30, std::min<int64_t>(cap, (int64_t)(0.45 * (double)fr)));
+}
+
 // ------------------------------------------------------------------ autotuner key
 int64_t Context::tune_key(int64_t n_pairs, int max_len, double work) {
     // buckets: pair count (half powers of two), longest sequence (64s), mean
@@ -266,6 +274,8 @@ Context* get_context(int device, int* status) {
     qpk::posterior_f64_occupancy(&bps64);
     c->f64_blocks_per_sm = std::max(1, std::min(bps64, 2));
     if (const char* v = getenv("QP_F32_VARIANT")) c->tune.variant = atoi(v);
+    if (const char* v = getenv("QP_F32_CKPT")) c->tune.ckpt = atoi(v);
+    if (const char* v = getenv("QP_SCRATCH_BYTES")) c->tune.scratch_bytes = atoll(v);
     Context* raw = c.get();
     g_ctx[device] = std::move(c);
     return raw;
@@ -446,6 +456,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     qpk::Status hs;
     memset(&hs, 0, sizeof hs);
     int variant = 0;
+    bool last_ckpt = false;
     for (int attempt = 0;; ++attempt) {
         fd.pool_cap = C->pool_cap;
         memcpy(C->h_fam.ptr, &fd, sizeof fd);
@@ -463,26 +474,51 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         int f64_grid = 0;
         if (!f64) {
             const int wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 4;
-            const int64_t tkey = Context::tune_key(P, pl->max_len, pl->work_sum);
-            variant = C->tune.variant >= 0 ? C->tune.variant : C->tuner[tkey].choose();
-            int bps = C->tune.blocks_per_sm;
-            if (bps <= 0) {
-                qpk::posterior_f32_occupancy(wpb, pl->max_len, &bps, variant);
-                bps = std::max(1, std::min(bps, 8));
+            // stored form unless its scratch for a full grid exceeds the budget;
+            // then the checkpointed form, on a grid cut to the budget if need be
+            const int64_t budget = scratch_budget(C->tune);
+            auto occupancy = [&](int v, bool ck) {
+                int b = C->tune.blocks_per_sm;
+                if (b <= 0) {
+                    qpk::posterior_f32_occupancy(wpb, pl->max_len, &b, v, ck);
+                    b = std::max(1, std::min(b, 8));
+                }
+                return b;
+            };
+            const int64_t stored_warp = (int64_t)(sizeof(float2) * pl->bst_stride + sizeof(int2) * pl->bex_stride +
+                                                  sizeof(float4) * pl->bnd_stride +
+                                                  sizeof(int2) * (int64_t)qpk::kStripRows * cap);
+            bool ckpt = C->tune.ckpt >= 0 ? C->tune.ckpt != 0 : false;
+            const int64_t full_warps = (int64_t)C->sm_count * 8 * wpb;
+            if (C->tune.ckpt < 0) {
+                const int64_t pairs_warps = std::min<int64_t>(full_warps, ((P + wpb - 1) / wpb) * wpb);
+                ckpt = stored_warp * std::min<int64_t>(pairs_warps, (int64_t)C->sm_count * occupancy(0, false) * wpb) > budget;
             }
+            const int64_t tkey = Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)ckpt << 62);
+            variant = C->tune.variant >= 0 ? C->tune.variant : C->tuner[tkey].choose();
+            const int bps = occupancy(variant, ckpt);
+            const qpk::F32Scratch sz(pl->max_len, cap, ckpt);
+            const int64_t per_warp = ckpt ? (int64_t)sz.bytes() : stored_warp;
             int64_t grid = (int64_t)C->sm_count * bps;
             grid = std::min<int64_t>(grid, (P + wpb - 1) / wpb);
+            grid = std::min<int64_t>(grid, std::max<int64_t>(1, budget / (per_warp * wpb)));
             grid = std::max<int64_t>(grid, 1);
             const int64_t warps = grid * wpb;
-            if ((e = C->bst.ensure(sizeof(float2) * pl->bst_stride * warps)) != cudaSuccess ||
-                (e = C->bex.ensure(sizeof(int2) * pl->bex_stride * warps)) != cudaSuccess ||
+            const int64_t bst_stride = ckpt ? sz.bst : pl->bst_stride;
+            const int64_t bex_stride = ckpt ? sz.bex : pl->bex_stride;
+            if ((e = C->bst.ensure(sizeof(float2) * bst_stride * warps)) != cudaSuccess ||
+                (e = C->bex.ensure(sizeof(int2) * bex_stride * warps)) != cudaSuccess ||
                 (e = C->bnd.ensure(sizeof(float4) * pl->bnd_stride * warps)) != cudaSuccess ||
+                (ckpt && (e = C->bck.ensure(sizeof(float4) * sz.bck * warps)) != cudaSuccess) ||
                 (e = C->stg.ensure(sizeof(int2) * (int64_t)qpk::kStripRows * cap * warps)) != cudaSuccess)
                 return bail(fail(QP_ENOMEM, "FP32 scratch allocation failed"));
-            Pb.bst = (float2*)C->bst.ptr; Pb.bst_stride = pl->bst_stride;
-            Pb.bex = (int2*)C->bex.ptr; Pb.bex_stride = pl->bex_stride;
+            Pb.bst = (float2*)C->bst.ptr; Pb.bst_stride = bst_stride;
+            Pb.bex = (int2*)C->bex.ptr; Pb.bex_stride = bex_stride;
             Pb.bnd = (float4*)C->bnd.ptr; Pb.bnd_stride = pl->bnd_stride;
+            Pb.bck = ckpt ? (float4*)C->bck.ptr : nullptr; Pb.bck_stride = ckpt ? sz.bck : 0;
+            Pb.ckpt = ckpt ? 1 : 0;
             Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = (int64_t)qpk::kStripRows * cap;
+            last_ckpt = ckpt;
             if ((e = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st, variant)) != cudaSuccess)
                 return bail(cuda_fail(e, "k_posterior_f32 launch"));
             cudaEventRecord(C->ev[2], st);
@@ -492,7 +528,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             if (C->tune.variant < 0) {
                 float kms = 0.f;
                 if (cudaEventElapsedTime(&kms, C->ev[1], C->ev[2]) == cudaSuccess) {
-                    TuneEntry& te = C->tuner[Context::tune_key(P, pl->max_len, pl->work_sum)];
+                    TuneEntry& te = C->tuner[Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)last_ckpt << 62)];
                     te.ms[variant] = te.ms[variant] < 0 ? kms : std::min<double>(te.ms[variant], kms);
                 }
             }
@@ -509,6 +545,11 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         if (f64_grid > 0) {
             const int64_t L = pl->max_len + 1;
             const int64_t db = L * L;
+            // per-CTA scratch of the FP64 form; the grid is cut to the budget
+            const int64_t per_cta = (int64_t)(sizeof(double2) * db + sizeof(double) * 3 * qpk::kNS * L +
+                                              sizeof(int32_t) * (5 * L + 8) +
+                                              (sizeof(int2) + sizeof(double)) * (int64_t)pl->max_len * cap);
+            f64_grid = (int)std::max<int64_t>(1, std::min<int64_t>(f64_grid, scratch_budget(C->tune) / per_cta));
             if ((e = C->d_b.ensure(sizeof(double2) * db * f64_grid)) != cudaSuccess ||
                 (e = C->d_diag.ensure(sizeof(double) * 3 * qpk::kNS * L * f64_grid)) != cudaSuccess ||
                 (e = C->d_cnt.ensure(sizeof(int32_t) * (5 * L + 8) * f64_grid)) != cudaSuccess ||
@@ -671,6 +712,37 @@ int qp_posteriors(const qp_family* family, const qp_params* params, int32_t out_
 }
 
 void qp_result_free(qp_result* result) { qph::free_result(result); }
+
+int qp_set_option(int32_t device, const char* name, int64_t value) {
+    using namespace qph;
+    if (!name) return fail(QP_EINVAL, "name is NULL");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return fail(QP_ECUDA, "no CUDA device"); }
+    if (device < 0 || device >= ndev) return fail(QP_EINVAL, "device %d does not exist", device);
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    int rc = QP_OK;
+    Context* C = get_context(device, &rc);
+    if (!C) return rc;
+    std::lock_guard<std::mutex> g(C->mu);
+    const std::string n(name);
+    if (n == "variant") {
+        if (value >= qpk::kF32Variants) return fail(QP_EINVAL, "variant must be < %d", qpk::kF32Variants);
+        C->tune.variant = value < 0 ? -1 : (int)value;
+    } else if (n == "ckpt") {
+        C->tune.ckpt = value < 0 ? -1 : (value ? 1 : 0);
+    } else if (n == "blocks_per_sm") {
+        C->tune.blocks_per_sm = value > 0 ? (int)std::min<int64_t>(value, 32) : 0;
+    } else if (n == "warps_per_block") {
+        if (value > 8) return fail(QP_EINVAL, "warps_per_block must be <= 8");
+        C->tune.warps_per_block = value > 0 ? (int)value : 0;
+    } else if (n == "scratch_bytes") {
+        C->tune.scratch_bytes = value > 0 ? value : 0;
+    } else {
+        return fail(QP_EINVAL, "unknown option '%s'", name);
+    }
+    return QP_OK;
+}
 
 const char* qp_last_error(void) { return qph::last_error(); }
 

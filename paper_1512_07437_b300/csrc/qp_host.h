@@ -57,7 +57,13 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int warps_per_block = 0;
     int blocks_per_sm = 0;
     int variant = -1;
+    int ckpt = -1;                       // 0 stored form, 1 checkpointed form
+    int64_t scratch_bytes = 0;           // budget of the FP32 / FP64 scratch
 };
+
+// Device bytes the kernels' scratch may take: the override, else 45% of the
+// free device memory, at most 48 GiB.
+int64_t scratch_budget(const LaunchOverride& t);
 
 // Online choice between the compiled variants of the FP32 kernel, per shape
 // bucket (pair count and longest sequence): each variant is timed once on a
@@ -88,7 +94,7 @@ struct Context {
     // workspace (grow-only)
     DevBuf ascii, codes, off, seqlogq, cst, status, fam;
     DevBuf row_cnt, chunk_off, pair_nnz, fallback, pool, pool64;
-    DevBuf bst, bex, bnd, stg;
+    DevBuf bst, bex, bnd, bck, stg;
     DevBuf d_b, d_diag, d_cnt, d_stg, d_stg64;
     HostBuf h_status, h_off, h_fam;
     int64_t pool_cap = 0;

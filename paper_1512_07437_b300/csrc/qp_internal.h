@@ -109,6 +109,10 @@ struct Problem {
     int2* bex;    int64_t bex_stride;      // backward exponents per chunk
     float4* bnd;  int64_t bnd_stride;      // strip boundary rows (2 float4 / column)
     int2* stg;    int64_t stg_stride;      // staging of entries, [kStripRows][cap]
+    // checkpointed form (ckpt = 1): bst / bex hold one strip, bck the backward
+    // boundary row at the top of every strip
+    float4* bck;  int64_t bck_stride;
+    int32_t ckpt;
     // FP64 per-CTA scratch
     double2* d_b; int64_t d_b_stride;      // dense backward (B_M, Zm_b)
     double* d_diag; int64_t d_diag_stride; // rotating diagonals
@@ -124,10 +128,29 @@ cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
                           const int64_t* seq_off, int32_t k, double* seq_logq,
                           const Consts* cst, Status* status, cudaStream_t s);
 // variant: 0 = 4 blocks of 4 warps per SM (<= 128 registers),
-//          1 = 3 blocks of 4 warps per SM (no register cap below 168)
+//          1 = 3 blocks of 4 warps per SM (no register cap below 168);
+// P.ckpt picks the stored or the checkpointed form.
 constexpr int kF32Variants = 2;
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block,
                                  cudaStream_t s, int variant = 0);
+// Per-warp scratch of the FP32 kernel for sequences up to L (elements of each
+// buffer), in the stored or the checkpointed form.
+struct F32Scratch {
+    int64_t bst, bex, bnd, bck, stg;
+    F32Scratch(int L, int cap, bool ckpt) {
+        const int64_t ns = (L + 1 + kStripRows - 1) / kStripRows;
+        const int64_t strip = (int64_t)kStripRows * (L + 32);
+        const int64_t ex = (int64_t)((L + 32 + kC - 1) / kC) * 32;
+        bst = ckpt ? strip : ns * strip;
+        bex = ckpt ? ex : ns * ex;
+        bnd = 2 * (int64_t)(L + 1);
+        bck = ckpt ? ns * 2 * (int64_t)(L + 1) : 0;
+        stg = (int64_t)kStripRows * cap;
+    }
+    size_t bytes() const {
+        return sizeof(float2) * bst + sizeof(int2) * bex + sizeof(float4) * (bnd + bck) + sizeof(int2) * stg;
+    }
+};
 cudaError_t launch_posterior_f64(const Problem& P, int grid, cudaStream_t s);
 cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const int64_t* pair_row_off, const int64_t* pair_strip_off,
@@ -137,8 +160,9 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            cudaStream_t s);
 cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,
                             cudaStream_t s);
-int posterior_f32_regs(int variant = 0);
-int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant = 0);
+int posterior_f32_regs(int variant = 0, bool ckpt = false);
+int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant = 0,
+                            bool ckpt = false);
 int posterior_f64_occupancy(int* blocks_per_sm);
 size_t posterior_f32_smem(int warps_per_block, int max_len);
 

@@ -177,7 +177,18 @@ struct PairCtx {
     float2* bst;
     int2* bex;
     float4* bnd;
+    float4* bck;     // checkpointed form: the backward boundary row of every strip
     int2* stg;
+};
+
+// Where one strip sweep reads and writes: the boundary row it starts from
+// (null: none), the boundary row it leaves for the next strip (null: none),
+// and the stored backward values and exponents of the strip.
+struct StripIO {
+    const float4* bnd_in;
+    float4* bnd_out;
+    float2* bst;
+    int2* bex;
 };
 
 constexpr float kBig = 1.2676506002282294e30f;   // 2^100
@@ -245,7 +256,7 @@ __host__ __device__ constexpr int warp_smem_bytes(int max_len) {
 }
 
 // ---------------------------------------------------------------- pass 1
-template <int R, bool SPEC>
+template <int R, bool SPEC, bool STORE>
 __device__ __forceinline__ void bwd_step(
     const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
     int Lend, int rend, bool first_strip, int yc,
@@ -299,7 +310,7 @@ __device__ __forceinline__ void bwd_step(
         }
         const float2 w = owr[xo[r]];
         const float nMn = w.x * BM, nDp = w.y * ZMB;
-        if (act) blk[r] = make_float2(BM, ZMB);
+        if (STORE && act) blk[r] = make_float2(BM, ZMB);
         D = Mn[r]; Dp = Dpo[r];
         Xb = BX; X2b = BX2; Eb = ZEB;
         Mn[r] = nMn; BYo[r] = BY; BY2o[r] = BY2;
@@ -312,10 +323,10 @@ __device__ __forceinline__ void bwd_step(
     }
 }
 
-template <int R>
+template <int R, bool STORE>
 __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c,
-                          const WarpSmem& ws, int s, int nstrips, float& Zh, float& Zp, int& eZh,
-                          int& eZp, int& flag)
+                          const WarpSmem& ws, int s, int nstrips, const StripIO& io, float& Zh, float& Zp,
+                          int& eZh, int& eZp, int& flag)
 {
     const int lane = threadIdx.x & 31;
     const int m = c.m, n = c.n;
@@ -336,8 +347,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     for (int r = 0; r < R; ++r) { Mn[r] = BYo[r] = BY2o[r] = Dpo[r] = ZFo[r] = 0.f; }
     float dMn = 0.f, dDp = 0.f;
     // the boundary row below this strip (none for the last strip)
-    const float4* bnd_in = last_strip ? nullptr : c.bnd;
-    float4* bnd_out = first_strip ? nullptr : c.bnd;
+    const float4* bnd_in = io.bnd_in;
+    float4* bnd_out = io.bnd_out;
     const bool owns_row = row0 + lane * R <= m;
     // the neighbour below is zero for good: padding rows, or no strip below
     const bool up_zero = (lane == 31) ? (bnd_in == nullptr) : (row0 + (lane + 1) * R > m);
@@ -357,8 +368,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     const int rend = last_strip ? (m - row0) % R : -1;
     const int t_end = last_strip ? 31 - Lend : -1;
     const int t_start = first_strip ? n + 31 : -1;
-    float2* bst_strip = c.bst + (int64_t)s * kStripRows * (n + 32);
-    int2* bex = c.bex + (int64_t)s * c.nch * 32;
+    float2* bst_strip = io.bst;
+    int2* bex = io.bex;
     const int nsteps = n + 32;
     // lane 31 streams the boundary row (column n - t at step t) into its ring
     const bool streams = (lane == 31) && (bnd_in != nullptr);
@@ -436,7 +447,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
             const int uP = __shfl_down_sync(FULL, eP, 1);
             if (lane != 31) { eUpH = uH; eUpP = uP; }
             if (up_zero) { eUpH = eH; eUpP = eP; }
-            bex[(t / kC) * 32 + lane] = make_int2(eH, eP);
+            if (STORE) bex[(t / kC) * 32 + lane] = make_int2(eH, eP);
             const int gh = eUpH - eH, gp = eUpP - eP;
             if (live && (gh > 127 || gp > 127)) {
                 flag |= kGuardGap;
@@ -459,13 +470,13 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
         const int yc_now = yc;
         yc = ycode(j - 1);
         if (t == t_end || t == t_start)
-            bwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX, tBX2,
-                              BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
-                              ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
+            bwd_step<R, true, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX,
+                                     tBX2, BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
+                                     ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
         else
-            bwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX, tBX2,
-                               BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
-                               ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
+            bwd_step<R, false, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX,
+                                      tBX2, BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
+                                      ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
     }
     cp_async_wait<0>();
 }
@@ -575,8 +586,9 @@ __device__ __forceinline__ void fwd_step(
 
 template <int R>
 __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, const PairCtx& c,
-                          const WarpSmem& ws, int s, int nstrips, float invZh, float invZp, int eZh,
-                          int eZp, float scaleA, float& pmax, FwdOut& fo, int64_t& pair_tot, int& flag)
+                          const WarpSmem& ws, int s, int nstrips, const StripIO& io, float invZh,
+                          float invZp, int eZh, int eZp, float scaleA, float& pmax, FwdOut& fo,
+                          int64_t& pair_tot, int& flag)
 {
     const Coef& cf = Pb.cf;
     const int lane = threadIdx.x & 31;
@@ -603,8 +615,8 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     for (int r = 0; r < R; ++r) { Md[r] = Yi[r] = Y2i[r] = Zd[r] = Fi[r] = 0.f; Aa[r] = 0; }
     float uMd = 0.f, uZd = 0.f;
     int uA = 0;
-    const float4* bnd_in = first_strip ? nullptr : c.bnd;
-    float4* bnd_out = last_strip ? nullptr : c.bnd;
+    const float4* bnd_in = io.bnd_in;
+    float4* bnd_out = io.bnd_out;
     const bool owns_row = row0 + lane * R <= m;
     const bool up_zero = (lane == 0) && (bnd_in == nullptr);
     // starting exponent: the boundary row's exponent, moved to the magnitude of
@@ -623,8 +635,8 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     const int rend = last_strip ? (m - row0) % R : -1;
     const int t_end = last_strip ? n + Lend : -1;
     const int t_start = first_strip ? 0 : -1;
-    const float2* bst_strip = c.bst + (int64_t)s * kStripRows * (n + 32);
-    const int2* bex = c.bex + (int64_t)s * c.nch * 32;
+    const float2* bst_strip = io.bst;
+    const int2* bex = io.bex;
     int2* stg = c.stg;
     const int cap = Pb.cap;
     const int nsteps = n + 32;
@@ -816,18 +828,39 @@ __device__ __forceinline__ int rows_per_lane(int rows_in) {
     return r <= 1 ? 1 : r <= 2 ? 2 : (r <= 4 || kRmax == 4) ? 4 : 8;
 }
 
+template <bool STORE>
 __device__ __forceinline__ void bwd_dispatch(int Rs, const Coef& cf, const float2* s_ow, const PairCtx& c,
-                                             const WarpSmem& ws, int s, int ns, float& Zh, float& Zp,
-                                             int& eZh, int& eZp, int& flag) {
+                                             const WarpSmem& ws, int s, int ns, const StripIO& io,
+                                             float& Zh, float& Zp, int& eZh, int& eZp, int& flag) {
     switch (Rs) {
-        case 1: bwd_strip<1>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        case 2: bwd_strip<2>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        case 4: bwd_strip<4>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
-        default: bwd_strip<kRmax>(cf, s_ow, c, ws, s, ns, Zh, Zp, eZh, eZp, flag); break;
+        case 1: bwd_strip<1, STORE>(cf, s_ow, c, ws, s, ns, io, Zh, Zp, eZh, eZp, flag); break;
+        case 2: bwd_strip<2, STORE>(cf, s_ow, c, ws, s, ns, io, Zh, Zp, eZh, eZp, flag); break;
+        case 4: bwd_strip<4, STORE>(cf, s_ow, c, ws, s, ns, io, Zh, Zp, eZh, eZp, flag); break;
+        default: bwd_strip<kRmax, STORE>(cf, s_ow, c, ws, s, ns, io, Zh, Zp, eZh, eZp, flag); break;
     }
 }
 
-template <int MINB>
+__device__ __forceinline__ void fwd_dispatch(int Rs, const Problem& Pb, const float2* s_ow, const PairCtx& c,
+                                             const WarpSmem& ws, int s, int ns, const StripIO& io,
+                                             float invZh, float invZp, int eZh, int eZp, float scaleA,
+                                             float& pmax, FwdOut& fo, int64_t& pair_tot, int& flag) {
+    switch (Rs) {
+        case 1: fwd_strip<1>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+        case 2: fwd_strip<2>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+        case 4: fwd_strip<4>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+        default: fwd_strip<kRmax>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+    }
+}
+
+// CKPT = false (stored form): pass 1 stores (B_M, Zm_b) of every strip, pass 2
+// reads them back.  CKPT = true (checkpointed form, for long sequences): pass 1
+// keeps only the boundary row at the top of every strip; pass 2 recomputes the
+// backward values of one strip from the boundary row below it, then runs the
+// forward sweep of that strip, so the per-warp scratch holds one strip instead
+// of the whole matrix, for one more backward sweep of work.  Both forms give
+// the same values: the recomputed strip starts from the same boundary row and
+// runs the same instructions.
+template <int MINB, bool CKPT>
 __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     float2* s_ow = (float2*)s_raw;
@@ -847,6 +880,7 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     c.bst = Pb.bst + gw * Pb.bst_stride;
     c.bex = Pb.bex + gw * Pb.bex_stride;
     c.bnd = Pb.bnd + gw * Pb.bnd_stride;
+    c.bck = CKPT ? Pb.bck + gw * Pb.bck_stride : nullptr;
     c.stg = Pb.stg + gw * Pb.stg_stride;
     c.st = Pb.status;
     for (;;) {
@@ -880,10 +914,25 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
         // ---- pass 1: backward, bottom strip first
         float Zh = 0.f, Zp = 0.f;
         int eZh = 0, eZp = 0;
+        const int64_t strip_vals = (int64_t)kStripRows * (n + 32), strip_exps = (int64_t)c.nch * 32;
+        const int64_t row_len = 2 * (int64_t)(n + 1);
         for (int s = nstrips - 1; s >= 0; --s) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = rows_per_lane(rows_in);
-            bwd_dispatch(Rs, Pb.cf, s_ow, c, ws, s, nstrips, Zh, Zp, eZh, eZp, flag);
+            StripIO io;
+            if (CKPT) {
+                io.bnd_in = (s == nstrips - 1) ? nullptr : c.bck + (s + 1) * row_len;
+                io.bnd_out = (s == 0) ? nullptr : c.bck + s * row_len;
+                io.bst = nullptr;
+                io.bex = nullptr;
+                bwd_dispatch<false>(Rs, Pb.cf, s_ow, c, ws, s, nstrips, io, Zh, Zp, eZh, eZp, flag);
+            } else {
+                io.bnd_in = (s == nstrips - 1) ? nullptr : c.bnd;
+                io.bnd_out = (s == 0) ? nullptr : c.bnd;
+                io.bst = c.bst + s * strip_vals;
+                io.bex = c.bex + s * strip_exps;
+                bwd_dispatch<true>(Rs, Pb.cf, s_ow, c, ws, s, nstrips, io, Zh, Zp, eZh, eZp, flag);
+            }
             __syncwarp();
         }
         Zh = __shfl_sync(FULL, Zh, 0); Zp = __shfl_sync(FULL, Zp, 0);
@@ -907,12 +956,29 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
         for (int s = 0; s < nstrips; ++s) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = rows_per_lane(rows_in);
-            switch (Rs) {
-                case 1: fwd_strip<1>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                case 2: fwd_strip<2>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                case 4: fwd_strip<4>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-                default: fwd_strip<kRmax>(Pb, s_ow, c, ws, s, nstrips, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+            StripIO io;
+            io.bnd_in = (s == 0) ? nullptr : c.bnd;
+            io.bnd_out = (s == nstrips - 1) ? nullptr : c.bnd;
+            if (CKPT) {
+                // the strip's backward values again, from its checkpoint row
+                StripIO bio;
+                bio.bnd_in = (s == nstrips - 1) ? nullptr : c.bck + (s + 1) * row_len;
+                bio.bnd_out = nullptr;
+                bio.bst = c.bst;
+                bio.bex = c.bex;
+                float dZh = 0.f, dZp = 0.f;
+                int deZh = 0, deZp = 0;
+                bwd_dispatch<true>(Rs, Pb.cf, s_ow, c, ws, s, nstrips, bio, dZh, dZp, deZh, deZp, flag);
+                __syncwarp();
+                io.bst = c.bst;
+                io.bex = c.bex;
+            } else {
+                io.bst = c.bst + s * strip_vals;
+                io.bex = c.bex + s * strip_exps;
             }
+            fwd_dispatch(Rs, Pb, s_ow, c, ws, s, nstrips, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo,
+                         pair_tot, flag);
+            __syncwarp();
         }
         // ---- pair results (held by the lane that owns row m)
         const int lastRs = rows_per_lane(min(kStripRows, m + 1 - (nstrips - 1) * kStripRows));
@@ -956,16 +1022,21 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     }
 }
 
-template <int MINB>
-static cudaError_t set_smem(size_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_posterior_f32<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+using F32Kernel = void (*)(Problem);
+
+static F32Kernel f32_kernel(int variant, bool ckpt) {
+    if (ckpt) return variant == 1 ? k_posterior_f32<3, true> : k_posterior_f32<4, true>;
+    return variant == 1 ? k_posterior_f32<3, false> : k_posterior_f32<4, false>;
 }
 
-int posterior_f32_regs(int variant) {
+static cudaError_t set_smem(F32Kernel k, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int posterior_f32_regs(int variant, bool ckpt) {
     cudaFuncAttributes a;
-    const cudaError_t e = variant == 1 ? cudaFuncGetAttributes(&a, k_posterior_f32<3>)
-                                       : cudaFuncGetAttributes(&a, k_posterior_f32<4>);
+    const cudaError_t e = cudaFuncGetAttributes(&a, f32_kernel(variant, ckpt));
     return e == cudaSuccess ? a.numRegs : -1;
 }
 
@@ -973,27 +1044,20 @@ size_t posterior_f32_smem(int warps_per_block, int max_len) {
     return (size_t)kOwBytes + (size_t)warps_per_block * warp_smem_bytes(max_len);
 }
 
-int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant) {
+int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant, bool ckpt) {
     const size_t smem = posterior_f32_smem(warps_per_block, max_len);
-    if (variant == 1) {
-        set_smem<3>(smem);
-        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f32<3>,
-                                                                  warps_per_block * 32, smem);
-    }
-    set_smem<4>(smem);
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f32<4>,
-                                                              warps_per_block * 32, smem);
+    const F32Kernel k = f32_kernel(variant, ckpt);
+    set_smem(k, smem);
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, warps_per_block * 32, smem);
 }
 
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block, cudaStream_t s,
                                  int variant) {
     const size_t smem = posterior_f32_smem(warps_per_block, P.max_len);
-    cudaError_t e = variant == 1 ? set_smem<3>(smem) : set_smem<4>(smem);
+    const F32Kernel k = f32_kernel(variant, P.ckpt != 0);
+    cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
-    if (variant == 1)
-        k_posterior_f32<3><<<grid, warps_per_block * 32, smem, s>>>(P);
-    else
-        k_posterior_f32<4><<<grid, warps_per_block * 32, smem, s>>>(P);
+    k<<<grid, warps_per_block * 32, smem, s>>>(P);
     return cudaGetLastError();
 }
 

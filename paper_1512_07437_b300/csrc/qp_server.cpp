@@ -155,7 +155,8 @@ struct qp_server {
     int64_t scratch_warps = 0;
     int bps[qpk::kF32Variants] = {};
     size_t scratch_bytes = 0;
-    void *bst = nullptr, *bex = nullptr, *bnd = nullptr, *stg = nullptr;
+    bool ckpt = false;               // checkpointed form of the FP32 kernel
+    void *bst = nullptr, *bex = nullptr, *bnd = nullptr, *bck = nullptr, *stg = nullptr;
     void *d_b = nullptr, *d_diag = nullptr, *d_cnt = nullptr, *d_stg = nullptr, *d_stg64 = nullptr;
     // shared with the callers (mu)
     std::mutex mu;
@@ -180,35 +181,42 @@ struct qp_server {
 
 namespace {
 
-// Device bytes of the kernels' scratch for sequences up to L.
-size_t scratch_bytes_for(const qp_server* S, int L, int64_t* warps_out, int* bps_out, int* cap_out) {
+// Device bytes of the kernels' scratch for sequences up to L.  The stored
+// form is used while its scratch takes at most a third of the budget, else
+// the checkpointed form.
+size_t scratch_bytes_for(const qp_server* S, int L, int64_t* warps_out, int* bps_out, int* cap_out,
+                         bool* ckpt_out) {
     if (L <= 0) return 0;
-    int bmax = 1;
-    for (int v = 0; v < qpk::kF32Variants; ++v) {
-        int b = 0;
-        qpk::posterior_f32_occupancy(kWpb, L, &b, v);
-        b = std::max(1, std::min(b, 8));
-        if (bps_out) bps_out[v] = b;
-        bmax = std::max(bmax, b);
-    }
-    const int64_t warps = (int64_t)S->ctx->sm_count * bmax * kWpb;
     const int cap = row_capacity(&S->params, L);
-    const int64_t ns = (L + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
-    const int64_t bst = ns * qpk::kStripRows * (L + 32);
-    const int64_t bex = ns * ((L + 32 + qpk::kC - 1) / qpk::kC) * 32;
-    const int64_t bnd = 2 * (int64_t)(L + 1);
-    const int64_t stg = (int64_t)qpk::kStripRows * cap;
-    size_t b = (size_t)warps * (sizeof(float2) * bst + sizeof(int2) * bex + sizeof(float4) * bnd + sizeof(int2) * stg);
+    bool ckpt = false;
+    int64_t warps = 0;
+    size_t b = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int bmax = 1;
+        for (int v = 0; v < qpk::kF32Variants; ++v) {
+            int bb = 0;
+            qpk::posterior_f32_occupancy(kWpb, L, &bb, v, ckpt);
+            bb = std::max(1, std::min(bb, 8));
+            if (bps_out) bps_out[v] = bb;
+            bmax = std::max(bmax, bb);
+        }
+        warps = (int64_t)S->ctx->sm_count * bmax * kWpb;
+        b = (size_t)warps * qpk::F32Scratch(L, cap, ckpt).bytes();
+        if (ckpt || S->ctx->tune.ckpt == 0 || (S->ctx->tune.ckpt < 0 && b <= S->budget / 3)) break;
+        ckpt = true;
+    }
     const int64_t L1 = L + 1;
     b += (size_t)kF64Grid * (sizeof(double2) * L1 * L1 + sizeof(double) * 3 * qpk::kNS * L1 +
                              sizeof(int32_t) * (5 * L1 + 8) + (sizeof(int2) + sizeof(double)) * (size_t)L * cap);
     if (warps_out) *warps_out = warps;
     if (cap_out) *cap_out = cap;
+    if (ckpt_out) *ckpt_out = ckpt;
     return b;
 }
 
 void free_scratch(qp_server* S) {
-    for (void** p : {&S->bst, &S->bex, &S->bnd, &S->stg, &S->d_b, &S->d_diag, &S->d_cnt, &S->d_stg, &S->d_stg64}) {
+    for (void** p : {&S->bst, &S->bex, &S->bnd, &S->bck, &S->stg, &S->d_b, &S->d_diag, &S->d_cnt, &S->d_stg,
+                     &S->d_stg64}) {
         if (*p) cudaFreeAsync(*p, S->cs);
         *p = nullptr;
     }
@@ -223,14 +231,16 @@ int set_scratch(qp_server* S, int L) {
     free_scratch(S);
     int64_t warps = 0;
     int cap = 0;
-    const size_t bytes = scratch_bytes_for(S, L, &warps, S->bps, &cap);
-    const int64_t ns = (L + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
+    bool ckpt = false;
+    const size_t bytes = scratch_bytes_for(S, L, &warps, S->bps, &cap, &ckpt);
+    const qpk::F32Scratch sz(L, cap, ckpt);
     const int64_t L1 = L + 1;
     struct A { void** p; size_t b; } al[] = {
-        {&S->bst, sizeof(float2) * (size_t)(ns * qpk::kStripRows * (L + 32)) * warps},
-        {&S->bex, sizeof(int2) * (size_t)(ns * ((L + 32 + qpk::kC - 1) / qpk::kC) * 32) * warps},
-        {&S->bnd, sizeof(float4) * (size_t)(2 * L1) * warps},
-        {&S->stg, sizeof(int2) * (size_t)qpk::kStripRows * cap * warps},
+        {&S->bst, sizeof(float2) * (size_t)sz.bst * warps},
+        {&S->bex, sizeof(int2) * (size_t)sz.bex * warps},
+        {&S->bnd, sizeof(float4) * (size_t)sz.bnd * warps},
+        {&S->bck, sizeof(float4) * (size_t)sz.bck * warps},
+        {&S->stg, sizeof(int2) * (size_t)sz.stg * warps},
         {&S->d_b, sizeof(double2) * (size_t)(L1 * L1) * kF64Grid},
         {&S->d_diag, sizeof(double) * (size_t)(3 * qpk::kNS * L1) * kF64Grid},
         {&S->d_cnt, sizeof(int32_t) * (size_t)(5 * L1 + 8) * kF64Grid},
@@ -249,6 +259,7 @@ int set_scratch(qp_server* S, int L) {
     S->scratch_len = L;
     S->scratch_warps = warps;
     S->cap = cap;
+    S->ckpt = ckpt;
     S->scratch_bytes = bytes;
     return QP_OK;
 }
@@ -267,12 +278,14 @@ qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items) {
     Pb.status = R.d_status;
     Pb.fallback = R.d_fallback;
     const int L = S->scratch_len;
-    const int64_t ns = (L + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
     const int64_t L1 = L + 1;
-    Pb.bst = (float2*)S->bst; Pb.bst_stride = ns * qpk::kStripRows * (L + 32);
-    Pb.bex = (int2*)S->bex;   Pb.bex_stride = ns * ((L + 32 + qpk::kC - 1) / qpk::kC) * 32;
-    Pb.bnd = (float4*)S->bnd; Pb.bnd_stride = 2 * L1;
-    Pb.stg = (int2*)S->stg;   Pb.stg_stride = (int64_t)qpk::kStripRows * S->cap;
+    const qpk::F32Scratch sz(L, S->cap, S->ckpt);
+    Pb.bst = (float2*)S->bst; Pb.bst_stride = sz.bst;
+    Pb.bex = (int2*)S->bex;   Pb.bex_stride = sz.bex;
+    Pb.bnd = (float4*)S->bnd; Pb.bnd_stride = sz.bnd;
+    Pb.bck = (float4*)S->bck; Pb.bck_stride = sz.bck;
+    Pb.ckpt = S->ckpt ? 1 : 0;
+    Pb.stg = (int2*)S->stg;   Pb.stg_stride = sz.stg;
     Pb.d_b = (double2*)S->d_b; Pb.d_b_stride = L1 * L1;
     Pb.d_diag = (double*)S->d_diag; Pb.d_diag_stride = 3 * qpk::kNS * L1;
     Pb.d_cnt = (int32_t*)S->d_cnt; Pb.d_cnt_stride = 5 * L1 + 8;
@@ -456,7 +469,7 @@ void admit(qp_server* S) {
                         ls = S->scratch_len;
                 }
                 const size_t scratch = ls == S->scratch_len ? S->scratch_bytes
-                                                            : scratch_bytes_for(S, ls, nullptr, nullptr, nullptr);
+                                                            : scratch_bytes_for(S, ls, nullptr, nullptr, nullptr, nullptr);
                 if (S->reserved + C.reserve + scratch <= S->budget) {
                     J = *it;
                     Ls = ls;
@@ -555,7 +568,7 @@ bool issue(qp_server* S) {
         release_items(S, R.per_fam);
         return false;
     }
-    R.tkey = Context::tune_key(n_items, S->scratch_len, R.work);
+    R.tkey = Context::tune_key(n_items, S->scratch_len, R.work) ^ ((int64_t)S->ckpt << 62);
     R.variant = S->ctx->tune.variant >= 0 ? S->ctx->tune.variant : S->tuner[R.tkey].choose();
     int64_t grid = (int64_t)S->ctx->sm_count * S->bps[R.variant];
     grid = std::min<int64_t>(grid, (n_items + kWpb - 1) / kWpb);
@@ -963,7 +976,7 @@ int qp_server_submit(qp_server* S, const qp_family* family, uint64_t* ticket) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(S->device);
-    const size_t scratch = scratch_bytes_for(S, pl.max_len, nullptr, nullptr, nullptr);
+    const size_t scratch = scratch_bytes_for(S, pl.max_len, nullptr, nullptr, nullptr, nullptr);
     cudaSetDevice(cur);
     if (J->reserve + scratch > S->budget)
         return fail(QP_EINVAL, "the family needs %zu bytes (%zu resident + %zu kernel scratch), more than the budget %zu",

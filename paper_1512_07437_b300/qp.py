@@ -107,6 +107,8 @@ def lib():
         L.qp_server_poll.restype = ctypes.c_int
         L.qp_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
         L.qp_server_cancel.restype = ctypes.c_int
+        L.qp_set_option.argtypes = [ctypes.c_int32, ctypes.c_char_p, ctypes.c_int64]
+        L.qp_set_option.restype = ctypes.c_int
         L.qp_server_get_stats.argtypes = [ctypes.c_void_p, P(qp_server_stats)]
         L.qp_server_get_stats.restype = ctypes.c_int
         L.qp_server_destroy.argtypes = [ctypes.c_void_p]
@@ -313,6 +315,11 @@ def qp_pair_posteriors_static(residues, m: int, n: int, params, row_ptr, col, va
 
 def qp_result_free(result: Result):
     result.free()
+
+
+def qp_set_option(name: str, value: int, device: int = 0):
+    """Launch knob of the FP32 kernel (qp_set_option in qp.h); -1 = automatic."""
+    _check(lib().qp_set_option(int(device), name.encode(), int(value)))
 
 
 class Server:

@@ -204,3 +204,136 @@ def test_long_pairs_stay_in_fp32(qp):
     _no_fallback(res)
     for p, (a, b) in enumerate(fam.pairs()):
         compare_pair(res, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
+
+
+def _same_csr(a, b):
+    for name in ("pair_row_off", "row_ptr", "pair_nnz_off", "col", "val", "dist64", "mea",
+                 "log_z_hmm", "log_z_pf", "pair_flags"):
+        x, y = host(getattr(a, name)), host(getattr(b, name))
+        assert np.array_equal(x, y), name
+
+
+@pytest.mark.parametrize("which", ["edge", "long", "c1"])
+def test_checkpointed_form_equals_stored(qp, which):
+    """The checkpointed form recomputes each strip's backward values from the
+    boundary row kept for it; the result must be bit-identical to the stored
+    form (same start row, same instructions)."""
+    if which == "c1":
+        fam = synth.make_family("c1", 3)
+    elif which == "long":
+        fam = synth.star_family(45, 4, (560, 700), 0.3)
+    else:
+        rng = np.random.Generator(np.random.PCG64(78))
+        q = synth.background()
+        root = rng.choice(20, size=400, p=q).astype(np.uint8)
+        seqs = []
+        for L in (1, 33, 127, 128, 129, 255, 256, 257, 385):
+            leaf = synth.evolve(rng, root[:L], 0.2, q)[:L]
+            if leaf.size == 0:
+                leaf = root[:1]
+            seqs.append("".join(synth.ALPHABET[c] for c in leaf))
+        fam = synth.family_from_strings(seqs)
+    prm = synth.default_params(threshold=0.01)
+    try:
+        qp.qp_set_option("ckpt", 0)
+        stored = _run(qp, fam, prm)
+        qp.qp_set_option("ckpt", 1)
+        ckpt = _run(qp, fam, prm)
+    finally:
+        qp.qp_set_option("ckpt", -1)
+    _no_fallback(stored)
+    _no_fallback(ckpt)
+    _same_csr(stored, ckpt)
+    if which == "long":
+        for p, (a, b) in enumerate(fam.pairs()):
+            compare_pair(ckpt, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
+
+
+def test_checkpointed_form_under_a_small_scratch_budget(qp):
+    """A scratch budget too small for the stored form switches to the
+    checkpointed form and cuts the grid; results stay the same."""
+    fam = synth.make_family("c2", 2)
+    prm = synth.default_params(threshold=0.01)
+    ref = _run(qp, fam, prm)
+    try:
+        qp.qp_set_option("scratch_bytes", 256 << 20)
+        small = _run(qp, fam, prm)
+    finally:
+        qp.qp_set_option("scratch_bytes", 0)
+    _no_fallback(small)
+    _same_csr(ref, small)
+
+
+def test_long_family_sampled_pairs(qp):
+    """100 sequences of 2000-4000 residues (three-domain roots, 4950 pairs) in
+    one launch, in the form the library picks for them (checkpointed: the
+    stored form would need ~130 MB per warp).  Seeded pairs against the
+    oracle: totals, MEA score, distance and entry count for 12 pairs,
+    posteriors for 2."""
+    import concurrent.futures as cf
+    import os
+    import oracle
+    fam = synth.make_family("c5", 1)
+    prm = synth.default_params(threshold=0.01)
+    res = _run(qp, fam, prm)
+    assert res.n_pairs == 4950
+    _no_fallback(res)
+    pl = list(fam.pairs())
+    L = fam.lengths
+    rng = np.random.Generator(np.random.PCG64(9))
+    longest = max(range(len(pl)), key=lambda q: L[pl[q][0]] * L[pl[q][1]])
+    sample = sorted(set(rng.choice(len(pl), size=11, replace=False).tolist() + [longest]))
+    ref = oracle.pairs(fam, [pl[q] for q in sample], prm, threads=os.cpu_count())
+    lzh, lzp = host(res.log_z_hmm), host(res.log_z_pf)
+    mea, dist = host(res.mea), host(res.dist64)
+    pno = host(res.pair_nnz_off)
+    for i, q in enumerate(sample):
+        a, b = pl[q]
+        mn = min(L[a], L[b])
+        assert abs(lzh[q] - ref["logz_hmm"][i]) <= TOL_LOGZ32 * abs(ref["logz_hmm"][i])
+        assert abs(lzp[q] - ref["logz_pf"][i]) <= TOL_LOGZ32 * abs(ref["logz_pf"][i])
+        assert abs(mea[q] - ref["mea"][i]) <= TOL_F32 * mn
+        assert abs(dist[a, b] - ref["dist"][i]) <= TOL_F32
+        nnz = int(pno[q + 1] - pno[q])
+        assert abs(nnz - int(ref["nnz"][i])) <= 2 + nnz // 1000, (nnz, ref["nnz"][i])
+    dense = [longest, sample[0]]
+    with cf.ThreadPoolExecutor(len(dense)) as ex:
+        refs = list(ex.map(lambda q: oracle.pair(fam.codes(pl[q][0]), fam.codes(pl[q][1]), prm), dense))
+    for q, r in zip(dense, refs):
+        a, b = pl[q]
+        compare_pair(res, fam, q, a, b, prm, TOL_F32, TOL_LOGZ32, dense=False, ref=r)
+
+
+def test_large_family_sampled_pairs(qp):
+    """500 sequences of 150-500 residues (124,750 pairs, random-tree family)
+    in one launch; a seeded 0.5% sample of pairs (624) against the oracle:
+    totals, MEA score, distance and entry count; posteriors for 4 pairs."""
+    import os
+    import oracle
+    fam = synth.make_family("c3", 1)
+    prm = synth.default_params(threshold=0.01)
+    res = _run(qp, fam, prm)
+    assert res.n_pairs == 124750
+    _no_fallback(res)
+    pl = list(fam.pairs())
+    L = fam.lengths
+    rng = np.random.Generator(np.random.PCG64(11))
+    sample = np.sort(rng.choice(len(pl), size=624, replace=False))
+    ref = oracle.pairs(fam, [pl[q] for q in sample], prm, threads=os.cpu_count())
+    lzh, lzp = host(res.log_z_hmm), host(res.log_z_pf)
+    mea, dist = host(res.mea), host(res.dist64)
+    pno = host(res.pair_nnz_off)
+    a_s = np.array([pl[q][0] for q in sample])
+    b_s = np.array([pl[q][1] for q in sample])
+    mn = np.minimum(L[a_s], L[b_s])
+    assert np.all(np.abs(lzh[sample] - ref["logz_hmm"]) <= TOL_LOGZ32 * np.abs(ref["logz_hmm"]))
+    assert np.all(np.abs(lzp[sample] - ref["logz_pf"]) <= TOL_LOGZ32 * np.abs(ref["logz_pf"]))
+    assert np.all(np.abs(mea[sample] - ref["mea"]) <= TOL_F32 * mn)
+    assert np.abs(dist[a_s, b_s] - ref["dist"]).max() <= TOL_F32
+    nnz = pno[sample + 1] - pno[sample]
+    assert np.all(np.abs(nnz - ref["nnz"]) <= 2), np.abs(nnz - ref["nnz"]).max()
+    d = host(res.dist)
+    assert np.array_equal(d, d.T) and (np.diag(d) == 0).all()
+    for q in sample[:4]:
+        a, b = pl[q]
+        compare_pair(res, fam, int(q), a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)

@@ -236,3 +236,38 @@ def test_destroy_with_pending_work(qp):
         r.free()
     finally:
         srv.destroy()
+
+
+def test_serving_trace_sampled_pairs(qp):
+    """The first 12 families of the serving workload (Poisson arrivals,
+    28-930 sequences, lengths 11-1000), submitted at their arrival times;
+    one seeded pair per family against the oracle."""
+    import os
+    import oracle
+    prm = synth.default_params(threshold=0.01)
+    trace = synth.make_serving_trace(seed=4, n_families=12)
+    srv = qp.Server(prm, 120 << 30)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for t_arr, f in trace:
+            d = t0 + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(f.residues, f.offsets))
+        got = [srv.poll(t, 300000) for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["completed"] == 12 and st["max_families_per_launch"] >= 2, st
+    rng = np.random.Generator(np.random.PCG64(21))
+    for (_, f), r in zip(trace, got):
+        a, b = sorted(rng.choice(f.k, size=2, replace=False).tolist())
+        p = synth.pair_index(a, b, f.k)
+        ref = oracle.pairs(f, [(a, b)], prm, threads=1)
+        assert abs(host(r.log_z_hmm)[p] - ref["logz_hmm"][0]) <= TOL_LOGZ32 * abs(ref["logz_hmm"][0])
+        assert abs(host(r.log_z_pf)[p] - ref["logz_pf"][0]) <= TOL_LOGZ32 * abs(ref["logz_pf"][0])
+        assert abs(host(r.dist64)[a, b] - ref["dist"][0]) <= TOL_F32
+        pno = host(r.pair_nnz_off)
+        assert abs(int(pno[p + 1] - pno[p]) - int(ref["nnz"][0])) <= 2
+        r.free()
