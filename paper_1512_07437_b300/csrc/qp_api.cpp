@@ -153,6 +153,10 @@ void make_coef(const qp_params* p, qpk::Coef* c) {
     c->We = (float)std::exp(p->gap_ext / p->temperature);
     for (int s = 0; s < 5; ++s) { c->pi[s] = (float)p->pi[s]; c->tau[s] = (float)p->end_w[s]; }
     c->theta = (float)p->threshold;
+    c->k_open = make_float2(c->d1, c->Wo);
+    c->k_ext = make_float2(c->e1, c->We);
+    c->k_mm = make_float2(c->tMM, 1.f);
+    c->k_close = make_float2(c->c1, 1.f);
     switch (p->combine) {
         case QP_COMBINE_RMS: c->combine = 0; c->wh = 0.5f; c->wp = 0.5f; break;
         case QP_COMBINE_MEAN: c->combine = 1; c->wh = 0.5f; c->wp = 0.5f; break;
@@ -275,6 +279,7 @@ Context* get_context(int device, int* status) {
     c->f64_blocks_per_sm = std::max(1, std::min(bps64, 2));
     if (const char* v = getenv("QP_F32_VARIANT")) c->tune.variant = atoi(v);
     if (const char* v = getenv("QP_F32_CKPT")) c->tune.ckpt = atoi(v);
+    if (const char* v = getenv("QP_F32_BLOCKS")) c->tune.blocks_per_sm = atoi(v);
     if (const char* v = getenv("QP_SCRATCH_BYTES")) c->tune.scratch_bytes = atoll(v);
     Context* raw = c.get();
     g_ctx[device] = std::move(c);

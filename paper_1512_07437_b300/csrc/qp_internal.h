@@ -55,6 +55,10 @@ struct Status {
 
 // Scalar coefficients passed by value (they live in the constant bank).
 struct Coef {
+    // pairs for the packed (HMM, PF) updates: gap opening (delta1, Wo), gap
+    // extension (eps1, We), match continuation (1 - 2 delta1 - 2 delta2, 1),
+    // gap closing (1 - eps1, 1)
+    float2 k_open, k_ext, k_mm, k_close;
     float tMM, d1, d2, e1, e2, c1, c2, Wo, We;
     float pi[5];        // M, X, Y, X2, Y2
     float tau[5];

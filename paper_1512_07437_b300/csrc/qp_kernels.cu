@@ -260,66 +260,72 @@ template <int R, bool SPEC, bool STORE>
 __device__ __forceinline__ void bwd_step(
     const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
     int Lend, int rend, bool first_strip, int yc,
-    float (&Mn)[R], float& tBX, float& tBX2, float (&BYo)[R], float (&BY2o)[R],
-    float (&Dpo)[R], float& tZE, float (&ZFo)[R], const int (&xo)[R],
-    float& dMn, float& dDp, float cvH, float cvP, float2* __restrict__ bst_strip,
+    float2 (&DD)[R], float2& tV, float& tX2, float2 (&HB)[R], float (&BY2o)[R], const int (&xo)[R],
+    float2& dDD, float2 cv, float2* __restrict__ bst_strip,
     const float4* __restrict__ ebnd, float4* __restrict__ bnd_out, int eH, int eP,
     float& Zh, float& Zp, int& eZh, int& eZp, int& flag)
 {
     const int n = c.n;
-    // values of the row below (lane+1's top row; lane 31: the boundary row)
-    float rMn = __shfl_down_sync(FULL, Mn[0], 1);
-    float rBX = __shfl_down_sync(FULL, tBX, 1);
-    float rBX2 = __shfl_down_sync(FULL, tBX2, 1);
-    float rDp = __shfl_down_sync(FULL, Dpo[0], 1);
-    float rZE = __shfl_down_sync(FULL, tZE, 1);
+    // values of the row below (lane+1's top row; lane 31: the boundary row):
+    // (B_M, Zm_b) weighted by the emission of their cell, (B_X, Ze_b), B_X2
+    float2 rDD = make_float2(__shfl_down_sync(FULL, DD[0].x, 1), __shfl_down_sync(FULL, DD[0].y, 1));
+    float2 rV = make_float2(__shfl_down_sync(FULL, tV.x, 1), __shfl_down_sync(FULL, tV.y, 1));
+    float rX2 = __shfl_down_sync(FULL, tX2, 1);
     if (lane == 31) {
         const float4 v0 = ebnd[0], v1 = ebnd[1];
-        rMn = v0.x; rBX = v0.y; rBX2 = v0.z; rDp = v0.w; rZE = v1.x;
+        rDD = make_float2(v0.x, v0.y); rV = make_float2(v0.z, v0.w); rX2 = v1.x;
     }
-    rMn *= cvH; rBX *= cvH; rBX2 *= cvH; rDp *= cvP; rZE *= cvP;
+    rDD = __fmul2_rn(rDD, cv); rV = __fmul2_rn(rV, cv); rX2 *= cv.x;
     const float2* __restrict__ owr = s_ow + yc * kTab;
-    float D = dMn, Dp = dDp;
-    float Xb = rBX, X2b = rBX2, Eb = rZE;
-    dMn = rMn; dDp = rDp;
+    float2 D = dDD;
+    float2 V = rV;
+    float X2b = rX2;
+    dDD = rDD;
     float2* blk = bst_strip + (int64_t)(j + lane) * (kWarp * R) + lane * R;
 #pragma unroll
     for (int r = R - 1; r >= 0; --r) {
-        const float Yb = BYo[r], Y2b = BY2o[r], Fb = ZFo[r];
-        float BM = cf.tMM * D + cf.d1 * (Xb + Yb) + cf.d2 * (X2b + Y2b);
-        float BX = cf.c1 * D + cf.e1 * Xb;
-        float BX2 = cf.c2 * D + cf.e2 * X2b;
-        float BY = cf.c1 * D + cf.e1 * Yb;
-        float BY2 = cf.c2 * D + cf.e2 * Y2b;
-        float ZMB = Dp + cf.Wo * (Eb + Fb);
-        float ZEB = Dp + cf.We * Eb;
-        float ZFB = Dp + cf.We * Fb;
+        const float2 H = HB[r];             // (B_Y, Zf_b) of the cell to the right
+        const float Y2b = BY2o[r];
+        // (B_X, Ze_b) and (B_Y, Zf_b) of this cell: gap closed by the match
+        // below-right, or extended
+        // (the carried operand enters last: one operation per row on the
+        // vertical chain)
+        const float2 cD = __fmul2_rn(cf.k_close, D);
+        float2 nV = __ffma2_rn(cf.k_ext, V, cD);
+        float2 nH = __ffma2_rn(cf.k_ext, H, cD);
+        const float cX2 = cf.c2 * D.x;
+        float BX2 = fmaf(cf.e2, X2b, cX2);
+        float BY2 = fmaf(cf.e2, Y2b, cX2);
+        // (B_M, Zm_b): continue the match, or open a gap
+        float2 B = __ffma2_rn(cf.k_open, __fadd2_rn(V, H), __fmul2_rn(cf.k_mm, D));
+        B.x = fmaf(cf.d2, X2b + Y2b, B.x);
         if (SPEC) {
             if (lane == Lend && r == rend && j == n) {
                 // end of every path: B_s(m, n) = tau_s; the partition function ends with weight 1
-                BM = cf.tau[0]; BX = cf.tau[1]; BY = cf.tau[2]; BX2 = cf.tau[3]; BY2 = cf.tau[4];
-                ZMB = ZEB = ZFB = 1.f;
+                B = make_float2(cf.tau[0], 1.f);
+                nV = make_float2(cf.tau[1], 1.f);
+                nH = make_float2(cf.tau[2], 1.f);
+                BX2 = cf.tau[3]; BY2 = cf.tau[4];
                 if (eH != 0 || eP != 0) flag |= kGuardCorner;
             }
             if (first_strip && lane == 0 && r == 0 && j == 0) {
                 // totals seen from the start: pi_s times the first emission of s
-                Zh = cf.pi[0] * D + cf.pi[1] * Xb + cf.pi[2] * Yb + cf.pi[3] * X2b + cf.pi[4] * Y2b;
-                Zp = ZMB;
+                Zh = cf.pi[0] * D.x + cf.pi[1] * V.x + cf.pi[2] * H.x + cf.pi[3] * X2b + cf.pi[4] * Y2b;
+                Zp = B.y;
                 eZh = eH; eZp = eP;
             }
         }
         const float2 w = owr[xo[r]];
-        const float nMn = w.x * BM, nDp = w.y * ZMB;
-        if (STORE && act) blk[r] = make_float2(BM, ZMB);
-        D = Mn[r]; Dp = Dpo[r];
-        Xb = BX; X2b = BX2; Eb = ZEB;
-        Mn[r] = nMn; BYo[r] = BY; BY2o[r] = BY2;
-        Dpo[r] = nDp; ZFo[r] = ZFB;
-        if (r == 0) { tBX = BX; tBX2 = BX2; tZE = ZEB; }
+        if (STORE && act) blk[r] = B;
+        D = DD[r];
+        V = nV; X2b = BX2;
+        DD[r] = __fmul2_rn(w, B);
+        HB[r] = nH; BY2o[r] = BY2;
+        if (r == 0) { tV = nV; tX2 = BX2; }
     }
     if (lane == 0 && act && bnd_out) {
-        bnd_out[2 * j] = make_float4(Mn[0], tBX, tBX2, Dpo[0]);
-        bnd_out[2 * j + 1] = make_float4(tZE, 0.f, __int_as_float(eH), __int_as_float(eP));
+        bnd_out[2 * j] = make_float4(DD[0].x, DD[0].y, tV.x, tV.y);
+        bnd_out[2 * j + 1] = make_float4(tX2, 0.f, __int_as_float(eH), __int_as_float(eP));
     }
 }
 
@@ -339,13 +345,16 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
         const int i = row0 + lane * R + r;
         xo[r] = (i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty;
     }
-    // carried across steps: diagonal and horizontal outflows of every row,
-    // vertical outflows of the top row (they go to the lane above)
-    float Mn[R], BYo[R], BY2o[R], Dpo[R], ZFo[R];
-    float tBX = 0.f, tBX2 = 0.f, tZE = 0.f;
+    // carried across steps: the diagonal outflow (B_M, Zm_b) and the
+    // horizontal outflows (B_Y, Zf_b), B_Y2 of every row; the vertical
+    // outflows (B_X, Ze_b), B_X2 of the top row (they go to the lane above)
+    float2 DD[R], HB[R];
+    float BY2o[R];
+    float2 tV = make_float2(0.f, 0.f);
+    float tX2 = 0.f;
 #pragma unroll
-    for (int r = 0; r < R; ++r) { Mn[r] = BYo[r] = BY2o[r] = Dpo[r] = ZFo[r] = 0.f; }
-    float dMn = 0.f, dDp = 0.f;
+    for (int r = 0; r < R; ++r) { DD[r] = HB[r] = make_float2(0.f, 0.f); BY2o[r] = 0.f; }
+    float2 dDD = make_float2(0.f, 0.f);
     // the boundary row below this strip (none for the last strip)
     const float4* bnd_in = io.bnd_in;
     float4* bnd_out = io.bnd_out;
@@ -358,12 +367,12 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     if (bnd_in) {
         const float4 v0 = bnd_in[2 * n], v1 = bnd_in[2 * n + 1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
-        const float bh = fmaxf(v0.x, fmaxf(v0.y, v0.z)), bp = fmaxf(v0.w, v1.x);
+        const float bh = fmaxf(v0.x, fmaxf(v0.z, v1.x)), bp = fmaxf(v0.y, v0.w);
         eH = eUpH + (bh > 0.f ? max(-126, min(126, ilog2f(bh))) : 0);
         eP = eUpP + (bp > 0.f ? max(-126, min(126, ilog2f(bp))) : 0);
         if (lane != 31) { eUpH = eH; eUpP = eP; }
     }
-    float cvH = pow2f(eUpH - eH), cvP = pow2f(eUpP - eP);
+    float2 cv = make_float2(pow2f(eUpH - eH), pow2f(eUpP - eP));
     const int Lend = last_strip ? (m - row0) / R : -1;
     const int rend = last_strip ? (m - row0) % R : -1;
     const int t_end = last_strip ? 31 - Lend : -1;
@@ -403,35 +412,24 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
         const int ph = t & (kC - 1);
         if (ph == 0) {
             // renormalise: bring the lane's largest carried value into [1, 2)
-            float mh = fmaxf(fmaxf(dMn, tBX), tBX2), mp = fmaxf(dDp, tZE);
+            float mh = fmaxf(fmaxf(dDD.x, tV.x), tX2), mp = fmaxf(dDD.y, tV.y);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                mh = fmaxf(mh, fmaxf(Mn[r], fmaxf(BYo[r], BY2o[r])));
-                mp = fmaxf(mp, fmaxf(Dpo[r], ZFo[r]));
+                mh = fmaxf(mh, fmaxf(DD[r].x, fmaxf(HB[r].x, BY2o[r])));
+                mp = fmaxf(mp, fmaxf(DD[r].y, HB[r].y));
             }
             const bool live = owns_row && (j >= -1) && (j <= n);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
-            int fh = kNoExp, fp = kNoExp;
-            if (mh > 0.f) {
-                const int k = max(-126, min(126, ilog2f(mh)));
-                const float sc = pow2f(-k);
+            const int kh = mh > 0.f ? max(-126, min(126, ilog2f(mh))) : 0;
+            const int kp = mp > 0.f ? max(-126, min(126, ilog2f(mp))) : 0;
+            const float2 sc = make_float2(pow2f(-kh), pow2f(-kp));
 #pragma unroll
-                for (int r = 0; r < R; ++r) { Mn[r] *= sc; BYo[r] *= sc; BY2o[r] *= sc; }
-                dMn *= sc; tBX *= sc; tBX2 *= sc;
-                fh = eH + k;
-            } else if (lane == 31) {
-                fh = eH;
+            for (int r = 0; r < R; ++r) {
+                DD[r] = __fmul2_rn(DD[r], sc); HB[r] = __fmul2_rn(HB[r], sc); BY2o[r] *= sc.x;
             }
-            if (mp > 0.f) {
-                const int k = max(-126, min(126, ilog2f(mp)));
-                const float sc = pow2f(-k);
-#pragma unroll
-                for (int r = 0; r < R; ++r) { Dpo[r] *= sc; ZFo[r] *= sc; }
-                dDp *= sc; tZE *= sc;
-                fp = eP + k;
-            } else if (lane == 31) {
-                fp = eP;
-            }
+            dDD = __fmul2_rn(dDD, sc); tV = __fmul2_rn(tV, sc); tX2 *= sc.x;
+            int fh = mh > 0.f ? eH + kh : (lane == 31 ? eH : kNoExp);
+            int fp = mp > 0.f ? eP + kp : (lane == 31 ? eP : kNoExp);
             // a lane without state takes the new exponent of the nearest lane
             // below it that has state (lane 31 keeps its own)
 #pragma unroll
@@ -453,7 +451,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
                 flag |= kGuardGap;
                 note_guard(c.st, 1, s, t, lane, eH, eUpH, eP, eUpP, m, n);
             }
-            cvH = pow2f(gh); cvP = pow2f(gp);
+            cv = make_float2(pow2f(gh), pow2f(gp));
         } else if (ph == 1) {
             // the boundary row's exponent changes on these steps
             if (streams && n - t >= 0) {
@@ -464,19 +462,19 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
                     flag |= kGuardGap;
                     note_guard(c.st, 2, s, t, lane, eH, eUpH, eP, eUpP, m, n);
                 }
-                cvH = pow2f(gh); cvP = pow2f(gp);
+                cv = make_float2(pow2f(gh), pow2f(gp));
             }
         }
         const int yc_now = yc;
         yc = ycode(j - 1);
         if (t == t_end || t == t_start)
-            bwd_step<R, true, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX,
-                                     tBX2, BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
-                                     ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
+            bwd_step<R, true, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, DD, tV, tX2,
+                                     HB, BY2o, xo, dDD, cv, bst_strip, ebnd, bnd_out, eH, eP, Zh, Zp, eZh,
+                                     eZp, flag);
         else
-            bwd_step<R, false, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Mn, tBX,
-                                      tBX2, BYo, BY2o, Dpo, tZE, ZFo, xo, dMn, dDp, cvH, cvP, bst_strip,
-                                      ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp, flag);
+            bwd_step<R, false, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, DD, tV, tX2,
+                                      HB, BY2o, xo, dDD, cv, bst_strip, ebnd, bnd_out, eH, eP, Zh, Zp, eZh,
+                                      eZp, flag);
     }
     cp_async_wait<0>();
 }
@@ -492,54 +490,61 @@ template <int R, bool SPEC>
 __device__ __forceinline__ void fwd_step(
     const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
     int Lend, int rend, bool first_strip, int yc,
-    float (&Md)[R], float& lXi, float& lX2i, float (&Yi)[R], float (&Y2i)[R],
-    float (&Zd)[R], float& lEi, float (&Fi)[R], int (&Aa)[R], int (&cnt)[R],
-    const int (&xo)[R],
-    float& uMd, float& uZd, int& uA, float cvH, float cvP, float psH, float psP, float scaleA,
+    float2 (&MZ)[R], float2& lV, float& lX2, float2 (&HY)[R], float (&Y2i)[R], int (&Aa)[R], int (&cnt)[R],
+    const int (&xo)[R], float2& uMZ, int& uA, float2 cv, float2 ps, float scaleA,
     const float2* __restrict__ bs, const float4* __restrict__ ebnd, float4* __restrict__ bnd_out,
     int2* __restrict__ stg, int cap, int eH, int eP, float& pmax, FwdOut& fo, int& flag)
 {
     const int n = c.n;
-    float rMd = __shfl_up_sync(FULL, Md[R - 1], 1);
-    float rXi = __shfl_up_sync(FULL, lXi, 1);
-    float rX2i = __shfl_up_sync(FULL, lX2i, 1);
-    float rZd = __shfl_up_sync(FULL, Zd[R - 1], 1);
-    float rEi = __shfl_up_sync(FULL, lEi, 1);
+    // values of the row above (lane-1's bottom row; lane 0: the boundary row):
+    // the diagonal outflow (M, Zm), the vertical outflow (X, Ze), X2, MEA
+    float2 rMZ = make_float2(__shfl_up_sync(FULL, MZ[R - 1].x, 1), __shfl_up_sync(FULL, MZ[R - 1].y, 1));
+    float2 rV = make_float2(__shfl_up_sync(FULL, lV.x, 1), __shfl_up_sync(FULL, lV.y, 1));
+    float rX2 = __shfl_up_sync(FULL, lX2, 1);
     int rA = __shfl_up_sync(FULL, Aa[R - 1], 1);
     if (lane == 0) {
         // the previous strip's last row (zeros above the first strip)
         const float4 v0 = ebnd[0], v1 = ebnd[1];
-        rMd = v0.x; rXi = v0.y; rX2i = v0.z; rZd = v0.w; rEi = v1.x; rA = __float_as_int(v1.y);
+        rMZ = make_float2(v0.x, v0.y); rV = make_float2(v0.z, v0.w); rX2 = v1.x; rA = __float_as_int(v1.y);
     }
-    rMd *= cvH; rXi *= cvH; rX2i *= cvH; rZd *= cvP; rEi *= cvP;
+    rMZ = __fmul2_rn(rMZ, cv); rV = __fmul2_rn(rV, cv); rX2 *= cv.x;
     const float2* __restrict__ owr = s_ow + yc * kTab;
-    float dMd = uMd, dZd = uZd;
+    float2 dMZ = uMZ;
     int dA = uA;
-    float aXi = rXi, aX2i = rX2i, aEi = rEi;
+    float2 aV = rV;
+    float aX2 = rX2;
     int aA = rA;
-    uMd = rMd; uZd = rZd; uA = rA;
+    uMZ = rMZ; uA = rA;
     float Pv[R];
     bool any = false;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const float2 w = owr[xo[r]];
-        const float FM = w.x * dMd, FX = aXi, FX2 = aX2i, FY = Yi[r], FY2 = Y2i[r];
-        const float ZM = w.y * dZd, ZE = aEi, ZF = Fi[r];
-        float nMd = cf.tMM * FM + cf.c1 * (FX + FY) + cf.c2 * (FX2 + FY2);
-        float nXi = cf.d1 * FM + cf.e1 * FX;
-        float nX2i = cf.d2 * FM + cf.e2 * FX2;
-        float nYi = cf.d1 * FM + cf.e1 * FY;
-        float nY2i = cf.d2 * FM + cf.e2 * FY2;
-        float nZd = ZM + ZE + ZF;
-        float nEi = cf.Wo * ZM + cf.We * ZE;
-        float nFi = cf.Wo * ZM + cf.We * ZF;
+        const float2 F = __fmul2_rn(w, dMZ);     // (M, Zm) of the cell
+        const float2 V = aV, H = HY[r];         // (X, Ze), (Y, Zf) of the cell
+        const float FX2 = aX2, FY2 = Y2i[r];
+        // outflows: gaps opened from the match or extended; the match
+        // continued or closing a gap (diagonal, weighted by the next cell's
+        // emission when it is read)
+        // (the carried operand enters last: one operation per row on the
+        // vertical chain)
+        const float2 oF = __fmul2_rn(cf.k_open, F);
+        float2 nV = __ffma2_rn(cf.k_ext, V, oF);
+        float2 nH = __ffma2_rn(cf.k_ext, H, oF);
+        const float oX2 = cf.d2 * F.x;
+        float nX2 = fmaf(cf.e2, FX2, oX2);
+        float nY2 = fmaf(cf.e2, FY2, oX2);
+        float2 nMZ = __ffma2_rn(cf.k_close, __fadd2_rn(V, H), __fmul2_rn(cf.k_mm, F));
+        nMZ.x = fmaf(cf.c2, FX2 + FY2, nMZ.x);
         // posteriors of the cell and their combination
-        const float2 b = bs[r];
-        const float Ph = (FM * psH) * b.x;
-        const float Pp = (ZM * psP) * b.y;
+        const float2 Pq2 = __fmul2_rn(__fmul2_rn(F, ps), bs[r]);
         float P;
-        if (cf.combine == 0) P = sqrt_approx(cf.wh * (Ph * Ph) + cf.wp * (Pp * Pp));
-        else P = cf.wh * Ph + cf.wp * Pp;
+        if (cf.combine == 0) {
+            const float2 sq = __fmul2_rn(Pq2, Pq2);
+            P = sqrt_approx(fmaf(cf.wh, sq.x, cf.wp * sq.y));
+        } else {
+            P = fmaf(cf.wh, Pq2.x, cf.wp * Pq2.y);
+        }
         pmax = fmaxf(pmax, P);
         Pv[r] = P;
         any |= (P >= cf.theta);
@@ -549,23 +554,24 @@ __device__ __forceinline__ void fwd_step(
         if (SPEC) {
             if (first_strip && lane == 0 && r == 0 && j == 0) {
                 // empty prefixes: the start distribution and the empty alignment
-                nMd = cf.pi[0]; nXi = cf.pi[1]; nYi = cf.pi[2]; nX2i = cf.pi[3]; nY2i = cf.pi[4];
-                nZd = 1.f; nEi = cf.Wo; nFi = cf.Wo;
+                nMZ = make_float2(cf.pi[0], 1.f);
+                nV = make_float2(cf.pi[1], cf.Wo);
+                nH = make_float2(cf.pi[2], cf.Wo);
+                nX2 = cf.pi[3]; nY2 = cf.pi[4];
                 nA = 0;
                 if (eH != 0 || eP != 0) flag |= kGuardCorner;
             }
             if (lane == Lend && r == rend && j == n) {
-                fo.Zh = cf.tau[0] * FM + cf.tau[1] * FX + cf.tau[2] * FY + cf.tau[3] * FX2 + cf.tau[4] * FY2;
-                fo.Zp = ZM + ZE + ZF;
+                fo.Zh = cf.tau[0] * F.x + cf.tau[1] * V.x + cf.tau[2] * H.x + cf.tau[3] * FX2 + cf.tau[4] * FY2;
+                fo.Zp = F.y + V.y + H.y;
                 fo.eZh = eH; fo.eZp = eP;
                 fo.A = nA;
             }
         }
-        dMd = Md[r]; dZd = Zd[r]; dA = Aa[r];
-        aXi = nXi; aX2i = nX2i; aEi = nEi; aA = nA;
-        Md[r] = nMd; Yi[r] = nYi; Y2i[r] = nY2i;
-        Zd[r] = nZd; Fi[r] = nFi; Aa[r] = nA;
-        if (r == R - 1) { lXi = nXi; lX2i = nX2i; lEi = nEi; }
+        dMZ = MZ[r]; dA = Aa[r];
+        aV = nV; aX2 = nX2; aA = nA;
+        MZ[r] = nMZ; HY[r] = nH; Y2i[r] = nY2; Aa[r] = nA;
+        if (r == R - 1) { lV = nV; lX2 = nX2; }
     }
     // entries at or above the threshold are rare: one vote per step
     if (__any_sync(FULL, any)) {
@@ -578,9 +584,8 @@ __device__ __forceinline__ void fwd_step(
         }
     }
     if (lane == 31 && act && bnd_out) {
-        bnd_out[2 * j] = make_float4(Md[R - 1], lXi, lX2i, Zd[R - 1]);
-        bnd_out[2 * j + 1] = make_float4(lEi, __int_as_float(Aa[R - 1]), __int_as_float(eH),
-                                         __int_as_float(eP));
+        bnd_out[2 * j] = make_float4(MZ[R - 1].x, MZ[R - 1].y, lV.x, lV.y);
+        bnd_out[2 * j + 1] = make_float4(lX2, __int_as_float(Aa[R - 1]), __int_as_float(eH), __int_as_float(eP));
     }
 }
 
@@ -606,14 +611,17 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
         xo[r] = (i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty;
         cnt[r] = 0;
     }
-    // carried across steps: diagonal and horizontal outflows of every row,
-    // vertical outflows of the bottom row (they go to the lane below)
-    float Md[R], Yi[R], Y2i[R], Zd[R], Fi[R];
-    float lXi = 0.f, lX2i = 0.f, lEi = 0.f;
+    // carried across steps: the diagonal outflow (M, Zm) and the horizontal
+    // outflows (Y, Zf), Y2 of every row; the vertical outflows (X, Ze), X2 of
+    // the bottom row (they go to the lane below)
+    float2 MZ[R], HY[R];
+    float Y2i[R];
+    float2 lV = make_float2(0.f, 0.f);
+    float lX2 = 0.f;
     int Aa[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) { Md[r] = Yi[r] = Y2i[r] = Zd[r] = Fi[r] = 0.f; Aa[r] = 0; }
-    float uMd = 0.f, uZd = 0.f;
+    for (int r = 0; r < R; ++r) { MZ[r] = HY[r] = make_float2(0.f, 0.f); Y2i[r] = 0.f; Aa[r] = 0; }
+    float2 uMZ = make_float2(0.f, 0.f);
     int uA = 0;
     const float4* bnd_in = io.bnd_in;
     float4* bnd_out = io.bnd_out;
@@ -625,12 +633,12 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     if (bnd_in) {
         const float4 v0 = bnd_in[0], v1 = bnd_in[1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
-        const float bh = fmaxf(v0.x, fmaxf(v0.y, v0.z)), bp = fmaxf(v0.w, v1.x);
+        const float bh = fmaxf(v0.x, fmaxf(v0.z, v1.x)), bp = fmaxf(v0.y, v0.w);
         eH = eUpH + (bh > 0.f ? max(-126, min(126, ilog2f(bh))) : 0);
         eP = eUpP + (bp > 0.f ? max(-126, min(126, ilog2f(bp))) : 0);
         if (lane != 0) { eUpH = eH; eUpP = eP; }
     }
-    float cvH = pow2f(eUpH - eH), cvP = pow2f(eUpP - eP);
+    float2 cv = make_float2(pow2f(eUpH - eH), pow2f(eUpP - eP));
     const int Lend = last_strip ? (m - row0) / R : -1;
     const int rend = last_strip ? (m - row0) % R : -1;
     const int t_end = last_strip ? n + Lend : -1;
@@ -643,7 +651,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     const int c2 = n & (kC - 1);
     // posterior factor of this lane: 2^(eF + eB - eZ) / Z for each model
     int2 eb = bex[((n + 31) / kC) * 32 + lane];
-    float psH, psP;
+    float2 ps;
     int t_ps = 0;
     auto ps_update = [&]() {
         const int Eh = eH + eb.x - eZh, Ep = eP + eb.y - eZp;
@@ -652,8 +660,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
             flag |= kGuardFactor;
             note_guard(c.st, 5, s, t_ps, lane, eH, eb.x, eP, eb.y, m, n);
         }
-        psH = pow2f(Eh) * invZh;
-        psP = pow2f(Ep) * invZp;
+        ps = make_float2(pow2f(Eh) * invZh, pow2f(Ep) * invZp);
     };
     ps_update();
     // ring streams: this lane's stored block of step T, and (lane 0) the
@@ -705,35 +712,24 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
         const bool act = (j >= 0) && (j <= n);
         const int ph = (t - c2) & (kC - 1);
         if (ph == 0) {
-            float mh = fmaxf(fmaxf(uMd, lXi), lX2i), mp = fmaxf(uZd, lEi);
+            float mh = fmaxf(fmaxf(uMZ.x, lV.x), lX2), mp = fmaxf(uMZ.y, lV.y);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                mh = fmaxf(mh, fmaxf(Md[r], fmaxf(Yi[r], Y2i[r])));
-                mp = fmaxf(mp, fmaxf(Zd[r], Fi[r]));
+                mh = fmaxf(mh, fmaxf(MZ[r].x, fmaxf(HY[r].x, Y2i[r])));
+                mp = fmaxf(mp, fmaxf(MZ[r].y, HY[r].y));
             }
             const bool live = owns_row && (j >= 0) && (j <= n + 1);
             if (live && !(mh < kBig && mp < kBig)) flag |= kGuardRange;
-            int fh = kNoExp, fp = kNoExp;
-            if (mh > 0.f) {
-                const int k = max(-126, min(126, ilog2f(mh)));
-                const float sc = pow2f(-k);
+            const int kh = mh > 0.f ? max(-126, min(126, ilog2f(mh))) : 0;
+            const int kp = mp > 0.f ? max(-126, min(126, ilog2f(mp))) : 0;
+            const float2 sc = make_float2(pow2f(-kh), pow2f(-kp));
 #pragma unroll
-                for (int r = 0; r < R; ++r) { Md[r] *= sc; Yi[r] *= sc; Y2i[r] *= sc; }
-                uMd *= sc; lXi *= sc; lX2i *= sc;
-                fh = eH + k;
-            } else if (lane == 0) {
-                fh = eH;
+            for (int r = 0; r < R; ++r) {
+                MZ[r] = __fmul2_rn(MZ[r], sc); HY[r] = __fmul2_rn(HY[r], sc); Y2i[r] *= sc.x;
             }
-            if (mp > 0.f) {
-                const int k = max(-126, min(126, ilog2f(mp)));
-                const float sc = pow2f(-k);
-#pragma unroll
-                for (int r = 0; r < R; ++r) { Zd[r] *= sc; Fi[r] *= sc; }
-                uZd *= sc; lEi *= sc;
-                fp = eP + k;
-            } else if (lane == 0) {
-                fp = eP;
-            }
+            uMZ = __fmul2_rn(uMZ, sc); lV = __fmul2_rn(lV, sc); lX2 *= sc.x;
+            int fh = mh > 0.f ? eH + kh : (lane == 0 ? eH : kNoExp);
+            int fp = mp > 0.f ? eP + kp : (lane == 0 ? eP : kNoExp);
             // a lane without state takes the new exponent of the nearest lane
             // above it that has state (lane 0 keeps its own)
 #pragma unroll
@@ -754,7 +750,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
                 flag |= kGuardGap;
                 note_guard(c.st, 3, s, t, lane, eH, eUpH, eP, eUpP, m, n);
             }
-            cvH = pow2f(gh); cvP = pow2f(gp);
+            cv = make_float2(pow2f(gh), pow2f(gp));
             const int kc = (n + 31 - t) / kC;
             eb = bex[kc * 32 + lane];
             t_ps = t;
@@ -768,19 +764,19 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
                     flag |= kGuardGap;
                     note_guard(c.st, 4, s, t, lane, eH, eUpH, eP, eUpP, m, n);
                 }
-                cvH = pow2f(gh); cvP = pow2f(gp);
+                cv = make_float2(pow2f(gh), pow2f(gp));
             }
         }
         const int yc_now = yc;
         yc = ycode(j + 1);
         if (t == t_end || t == t_start)
-            fwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, lXi, lX2i, Yi,
-                              Y2i, Zd, lEi, Fi, Aa, cnt, xo, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
-                              bs, ebnd, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
+            fwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, MZ, lV, lX2, HY,
+                              Y2i, Aa, cnt, xo, uMZ, uA, cv, ps, scaleA, bs, ebnd, bnd_out, stg, cap, eH,
+                              eP, pmax, fo, flag);
         else
-            fwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, Md, lXi, lX2i, Yi,
-                               Y2i, Zd, lEi, Fi, Aa, cnt, xo, uMd, uZd, uA, cvH, cvP, psH, psP, scaleA,
-                               bs, ebnd, bnd_out, stg, cap, eH, eP, pmax, fo, flag);
+            fwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, MZ, lV, lX2, HY,
+                               Y2i, Aa, cnt, xo, uMZ, uA, cv, ps, scaleA, bs, ebnd, bnd_out, stg, cap, eH,
+                               eP, pmax, fo, flag);
     }
     cp_async_wait<0>();
     // ---- flush this strip's entries into the pool (row-major, columns ascending)
