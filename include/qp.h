@@ -236,6 +236,10 @@ void qp_server_destroy(qp_server* server);
  *                     whole matrix), 1: checkpointed form (pass 1 keeps one
  *                     boundary row per 128-row strip; pass 2 recomputes each
  *                     strip's backward values before its forward sweep);
+ *   "wpp"             warps sharing one pair: 1, or 2 (each takes every
+ *                     second 128-row strip, trailing the other through the
+ *                     boundary row between them); by default the autotuner
+ *                     tries 2 when pairs are too few to fill the grid;
  *   "blocks_per_sm", "warps_per_block";
  *   "scratch_bytes"   device bytes the kernels' scratch may take (default:
  *                     45% of free memory, at most 48 GiB); the stored form is

@@ -229,6 +229,23 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
     return pl;
 }
 
+unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, int warps_per_block,
+                         const LaunchOverride& t) {
+    unsigned mask = 0;
+    for (int cfg = 0; cfg < kTuneConfigs; ++cfg) {
+        const int v = config_variant(cfg), W = config_wpp(cfg);
+        if (t.variant >= 0 && v != t.variant) continue;
+        if (t.wpp > 0 && W != t.wpp) continue;
+        // W must divide the block; groups of several warps use named barriers 1, 2
+        if (warps_per_block % W || (W > 1 && warps_per_block / W > 2)) continue;
+        // two warps per pair only while the pairs fill at most half the grid
+        // (then they shorten each pair without halving the pairs in flight)
+        if (t.wpp <= 0 && W > 1 && (max_strips < W || n_pairs * W > warps_full)) continue;
+        mask |= 1u << cfg;
+    }
+    return mask ? mask : 1u;
+}
+
 int64_t scratch_budget(const LaunchOverride& t) {
     if (t.scratch_bytes > 0) return t.scratch_bytes;
     size_t fr = 0, tot = 0;
@@ -280,6 +297,7 @@ Context* get_context(int device, int* status) {
     if (const char* v = getenv("QP_F32_VARIANT")) c->tune.variant = atoi(v);
     if (const char* v = getenv("QP_F32_CKPT")) c->tune.ckpt = atoi(v);
     if (const char* v = getenv("QP_F32_BLOCKS")) c->tune.blocks_per_sm = atoi(v);
+    if (const char* v = getenv("QP_F32_WPP")) c->tune.wpp = atoi(v);
     if (const char* v = getenv("QP_SCRATCH_BYTES")) c->tune.scratch_bytes = atoll(v);
     Context* raw = c.get();
     g_ctx[device] = std::move(c);
@@ -461,6 +479,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     qpk::Status hs;
     memset(&hs, 0, sizeof hs);
     int variant = 0;
+    int last_cfg = 0;
     bool last_ckpt = false;
     for (int attempt = 0;; ++attempt) {
         fd.pool_cap = C->pool_cap;
@@ -482,47 +501,57 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             // stored form unless its scratch for a full grid exceeds the budget;
             // then the checkpointed form, on a grid cut to the budget if need be
             const int64_t budget = scratch_budget(C->tune);
-            auto occupancy = [&](int v, bool ck) {
+            auto occupancy = [&](int v, bool ck, int W = 1) {
                 int b = C->tune.blocks_per_sm;
                 if (b <= 0) {
-                    qpk::posterior_f32_occupancy(wpb, pl->max_len, &b, v, ck);
+                    qpk::posterior_f32_occupancy(wpb, pl->max_len, &b, v, ck, W);
                     b = std::max(1, std::min(b, 8));
                 }
                 return b;
             };
-            const int64_t stored_warp = (int64_t)(sizeof(float2) * pl->bst_stride + sizeof(int2) * pl->bex_stride +
-                                                  sizeof(float4) * pl->bnd_stride +
-                                                  sizeof(int2) * (int64_t)qpk::kStripRows * cap);
+            // bytes of a grid of `warps` warps, W warps per pair (the stored form
+            // keeps the plan's tighter per-pair sizes)
+            auto scratch_of = [&](bool ck, int W, int64_t warps) -> int64_t {
+                const qpk::F32Scratch sz(pl->max_len, cap, ck, W);
+                if (ck) return (int64_t)sz.bytes(warps);
+                const int64_t groups = warps / W;
+                return groups * (int64_t)(sizeof(float2) * pl->bst_stride + sizeof(int2) * pl->bex_stride +
+                                          sizeof(float4) * (sz.bnd + sz.bck)) +
+                       warps * (int64_t)(sizeof(int2) * sz.stg);
+            };
             bool ckpt = C->tune.ckpt >= 0 ? C->tune.ckpt != 0 : false;
-            const int64_t full_warps = (int64_t)C->sm_count * 8 * wpb;
-            if (C->tune.ckpt < 0) {
-                const int64_t pairs_warps = std::min<int64_t>(full_warps, ((P + wpb - 1) / wpb) * wpb);
-                ckpt = stored_warp * std::min<int64_t>(pairs_warps, (int64_t)C->sm_count * occupancy(0, false) * wpb) > budget;
-            }
+            const int64_t warps_full = (int64_t)C->sm_count * occupancy(0, false) * wpb;
+            if (C->tune.ckpt < 0)
+                ckpt = scratch_of(false, 1, std::min<int64_t>(warps_full, ((P + wpb - 1) / wpb) * wpb)) > budget;
+            const int max_strips = (pl->max_len + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
+            const unsigned allowed = allowed_configs(P, max_strips, warps_full, wpb, C->tune);
             const int64_t tkey = Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)ckpt << 62);
-            variant = C->tune.variant >= 0 ? C->tune.variant : C->tuner[tkey].choose();
-            const int bps = occupancy(variant, ckpt);
-            const qpk::F32Scratch sz(pl->max_len, cap, ckpt);
-            const int64_t per_warp = ckpt ? (int64_t)sz.bytes() : stored_warp;
+            last_cfg = C->tuner[tkey].choose(allowed);
+            variant = config_variant(last_cfg);
+            const int W = config_wpp(last_cfg);
+            const int bps = occupancy(variant, ckpt, W);
             int64_t grid = (int64_t)C->sm_count * bps;
-            grid = std::min<int64_t>(grid, (P + wpb - 1) / wpb);
-            grid = std::min<int64_t>(grid, std::max<int64_t>(1, budget / (per_warp * wpb)));
+            grid = std::min<int64_t>(grid, (P * W + wpb - 1) / wpb);
+            grid = std::min<int64_t>(grid, std::max<int64_t>(1, budget / std::max<int64_t>(1, scratch_of(ckpt, W, wpb))));
             grid = std::max<int64_t>(grid, 1);
-            const int64_t warps = grid * wpb;
+            const int64_t warps = grid * wpb, groups = warps / W;
+            const qpk::F32Scratch sz(pl->max_len, cap, ckpt, W);
             const int64_t bst_stride = ckpt ? sz.bst : pl->bst_stride;
             const int64_t bex_stride = ckpt ? sz.bex : pl->bex_stride;
-            if ((e = C->bst.ensure(sizeof(float2) * bst_stride * warps)) != cudaSuccess ||
-                (e = C->bex.ensure(sizeof(int2) * bex_stride * warps)) != cudaSuccess ||
-                (e = C->bnd.ensure(sizeof(float4) * pl->bnd_stride * warps)) != cudaSuccess ||
-                (ckpt && (e = C->bck.ensure(sizeof(float4) * sz.bck * warps)) != cudaSuccess) ||
-                (e = C->stg.ensure(sizeof(int2) * (int64_t)qpk::kStripRows * cap * warps)) != cudaSuccess)
+            const int64_t units = ckpt ? warps : groups;
+            if ((e = C->bst.ensure(sizeof(float2) * bst_stride * units)) != cudaSuccess ||
+                (e = C->bex.ensure(sizeof(int2) * bex_stride * units)) != cudaSuccess ||
+                (e = C->bnd.ensure(sizeof(float4) * sz.bnd * groups)) != cudaSuccess ||
+                (e = C->bck.ensure(sizeof(float4) * sz.bck * groups)) != cudaSuccess ||
+                (e = C->stg.ensure(sizeof(int2) * sz.stg * warps)) != cudaSuccess)
                 return bail(fail(QP_ENOMEM, "FP32 scratch allocation failed"));
             Pb.bst = (float2*)C->bst.ptr; Pb.bst_stride = bst_stride;
             Pb.bex = (int2*)C->bex.ptr; Pb.bex_stride = bex_stride;
-            Pb.bnd = (float4*)C->bnd.ptr; Pb.bnd_stride = pl->bnd_stride;
-            Pb.bck = ckpt ? (float4*)C->bck.ptr : nullptr; Pb.bck_stride = ckpt ? sz.bck : 0;
+            Pb.bnd = (float4*)C->bnd.ptr; Pb.bnd_stride = sz.bnd;
+            Pb.bck = (float4*)C->bck.ptr; Pb.bck_stride = sz.bck;
             Pb.ckpt = ckpt ? 1 : 0;
-            Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = (int64_t)qpk::kStripRows * cap;
+            Pb.wpp = W;
+            Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = sz.stg;
             last_ckpt = ckpt;
             if ((e = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st, variant)) != cudaSuccess)
                 return bail(cuda_fail(e, "k_posterior_f32 launch"));
@@ -530,11 +559,11 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             e = cudaMemcpyAsync(C->h_status.ptr, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return bail(cuda_fail(e, "k_posterior_f32"));
-            if (C->tune.variant < 0) {
+            {
                 float kms = 0.f;
                 if (cudaEventElapsedTime(&kms, C->ev[1], C->ev[2]) == cudaSuccess) {
-                    TuneEntry& te = C->tuner[Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)last_ckpt << 62)];
-                    te.ms[variant] = te.ms[variant] < 0 ? kms : std::min<double>(te.ms[variant], kms);
+                    C->tuner[Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)last_ckpt << 62)]
+                        .record(last_cfg, kms);
                 }
             }
             memcpy(&hs, C->h_status.ptr, sizeof hs);
@@ -736,6 +765,9 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
         C->tune.variant = value < 0 ? -1 : (int)value;
     } else if (n == "ckpt") {
         C->tune.ckpt = value < 0 ? -1 : (value ? 1 : 0);
+    } else if (n == "wpp") {
+        if (value > 0 && value != 1 && value != 2) return fail(QP_EINVAL, "wpp must be 1 or 2");
+        C->tune.wpp = value > 0 ? (int)value : 0;
     } else if (n == "blocks_per_sm") {
         C->tune.blocks_per_sm = value > 0 ? (int)std::min<int64_t>(value, 32) : 0;
     } else if (n == "warps_per_block") {

@@ -58,6 +58,7 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int blocks_per_sm = 0;
     int variant = -1;
     int ckpt = -1;                       // 0 stored form, 1 checkpointed form
+    int wpp = 0;                         // warps per pair (1, 2)
     int64_t scratch_bytes = 0;           // budget of the FP32 / FP64 scratch
 };
 
@@ -65,21 +66,42 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
 // free device memory, at most 48 GiB.
 int64_t scratch_budget(const LaunchOverride& t);
 
-// Online choice between the compiled variants of the FP32 kernel, per shape
-// bucket (pair count and longest sequence): each variant is timed once on a
-// real call, then the faster one is kept.
+// Launch configurations of the FP32 kernel the autotuner chooses from:
+// config = variant + kF32Variants * w, with w indexing kWpp (warps per pair).
+constexpr int kWpp[2] = {1, 2};
+constexpr int kTuneConfigs = qpk::kF32Variants * 2;
+inline int config_variant(int cfg) { return cfg % qpk::kF32Variants; }
+inline int config_wpp(int cfg) { return kWpp[cfg / qpk::kF32Variants]; }
+
+// Online choice among the allowed launch configurations, per shape bucket
+// (pair count, longest sequence, mean work): each is timed on kTuneSamples
+// real calls (the first of a configuration can pay for cold caches and fresh
+// scratch), then the fastest (best sample) is kept.
+constexpr int kTuneSamples = 2;
 struct TuneEntry {
-    double ms[qpk::kF32Variants];
-    TuneEntry() { for (auto& v : ms) v = -1.0; }
-    int choose() const {
-        for (int v = 0; v < qpk::kF32Variants; ++v)
-            if (ms[v] < 0) return v;
-        int best = 0;
-        for (int v = 1; v < qpk::kF32Variants; ++v)
-            if (ms[v] < ms[best]) best = v;
-        return best;
+    double ms[kTuneConfigs];
+    int n[kTuneConfigs];
+    TuneEntry() { for (int v = 0; v < kTuneConfigs; ++v) { ms[v] = -1.0; n[v] = 0; } }
+    int choose(unsigned allowed) const {
+        for (int v = 0; v < kTuneConfigs; ++v)
+            if ((allowed >> v & 1u) && n[v] < kTuneSamples) return v;
+        int best = -1;
+        for (int v = 0; v < kTuneConfigs; ++v)
+            if ((allowed >> v & 1u) && (best < 0 || ms[v] < ms[best])) best = v;
+        return best < 0 ? 0 : best;
+    }
+    void record(int v, double t) {
+        ms[v] = ms[v] < 0 ? t : (t < ms[v] ? t : ms[v]);
+        ++n[v];
     }
 };
+
+// Configurations worth trying for a launch of n_pairs pairs whose longest
+// sequence spans max_strips strips, on warps_full resident warps: several
+// warps per pair only when pairs are too few to balance the grid and pairs
+// have strips to share; wpp must divide warps_per_block.
+unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, int warps_per_block,
+                         const LaunchOverride& t);
 
 struct Context {
     int device = 0;

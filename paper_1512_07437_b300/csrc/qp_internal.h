@@ -113,10 +113,14 @@ struct Problem {
     int2* bex;    int64_t bex_stride;      // backward exponents per chunk
     float4* bnd;  int64_t bnd_stride;      // strip boundary rows (2 float4 / column)
     int2* stg;    int64_t stg_stride;      // staging of entries, [kStripRows][cap]
-    // checkpointed form (ckpt = 1): bst / bex hold one strip, bck the backward
-    // boundary row at the top of every strip
+    // backward boundary rows (bck) and forward ones (bnd), per group of warps
+    // sharing a pair: one row per strip when other warps or a recompute read
+    // them (checkpointed form, wpp > 1), else one row.  bst / bex: per group
+    // (stored form: every strip of the pair) or per warp (checkpointed form:
+    // one strip).
     float4* bck;  int64_t bck_stride;
     int32_t ckpt;
+    int32_t wpp;                   // warps per pair: 1, or 2 with at most 2 groups per block
     // FP64 per-CTA scratch
     double2* d_b; int64_t d_b_stride;      // dense backward (B_M, Zm_b)
     double* d_diag; int64_t d_diag_stride; // rotating diagonals
@@ -137,22 +141,29 @@ cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
 constexpr int kF32Variants = 2;
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block,
                                  cudaStream_t s, int variant = 0);
-// Per-warp scratch of the FP32 kernel for sequences up to L (elements of each
-// buffer), in the stored or the checkpointed form.
+// Scratch of the FP32 kernel for sequences up to L (elements of each buffer
+// per unit: bst / bex per group in the stored form and per warp in the
+// checkpointed form; bnd / bck per group; stg per warp), for wpp warps per pair.
 struct F32Scratch {
     int64_t bst, bex, bnd, bck, stg;
-    F32Scratch(int L, int cap, bool ckpt) {
+    bool ckpt;
+    int wpp;
+    F32Scratch(int L, int cap, bool ckpt_, int wpp_ = 1) : ckpt(ckpt_), wpp(wpp_ > 1 ? wpp_ : 1) {
         const int64_t ns = (L + 1 + kStripRows - 1) / kStripRows;
         const int64_t strip = (int64_t)kStripRows * (L + 32);
         const int64_t ex = (int64_t)((L + 32 + kC - 1) / kC) * 32;
+        const int64_t row = 2 * (int64_t)(L + 1);
         bst = ckpt ? strip : ns * strip;
         bex = ckpt ? ex : ns * ex;
-        bnd = 2 * (int64_t)(L + 1);
-        bck = ckpt ? ns * 2 * (int64_t)(L + 1) : 0;
+        bnd = (wpp > 1 ? ns : 1) * row;
+        bck = (ckpt || wpp > 1 ? ns : 1) * row;
         stg = (int64_t)kStripRows * cap;
     }
-    size_t bytes() const {
-        return sizeof(float2) * bst + sizeof(int2) * bex + sizeof(float4) * (bnd + bck) + sizeof(int2) * stg;
+    // bytes for a grid of `warps` warps
+    size_t bytes(int64_t warps) const {
+        const int64_t groups = warps / wpp, units = ckpt ? warps : groups;
+        return (size_t)units * (sizeof(float2) * bst + sizeof(int2) * bex) +
+               (size_t)groups * sizeof(float4) * (bnd + bck) + (size_t)warps * sizeof(int2) * stg;
     }
 };
 cudaError_t launch_posterior_f64(const Problem& P, int grid, cudaStream_t s);
@@ -166,7 +177,7 @@ cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* p
                             cudaStream_t s);
 int posterior_f32_regs(int variant = 0, bool ckpt = false);
 int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant = 0,
-                            bool ckpt = false);
+                            bool ckpt = false, int wpp = 1);
 int posterior_f64_occupancy(int* blocks_per_sm);
 size_t posterior_f32_smem(int warps_per_block, int max_len);
 

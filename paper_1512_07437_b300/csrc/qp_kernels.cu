@@ -189,7 +189,37 @@ struct StripIO {
     float4* bnd_out;
     float2* bst;
     int2* bex;
+    // strips of one pair shared by several warps: the progress word of the
+    // warp writing bnd_in and the value that marks its strip (null: the row
+    // is complete), and this warp's own progress word for bnd_out (null: no
+    // reader waits on it).  A word holds (strip tag << 32) | steps done.
+    const volatile long long* wait;
+    long long wait_tag;
+    volatile long long* pub;
+    long long pub_tag;
 };
+
+constexpr long long kStepsDone = 0x7fffffffLL;     // "strip complete" in a progress word
+constexpr long long kPass2Tag = 1LL << 20;         // strip tags of pass 2 start here
+constexpr int kSpinLimit = 1 << 22;                 // bounded wait for a progress word
+
+// Waits (warp-uniform) until the progress word reaches need.  A wait that runs
+// out sets the sync guard, so the pair goes to the FP64 form; it never hangs.
+__device__ __forceinline__ void wait_progress(const volatile long long* w, long long need, int& flag) {
+    if (!w) return;
+    int it = 0;
+    while (*w < need) {
+        if (++it > kSpinLimit) { flag |= (1 << 12); return; }
+        __nanosleep(64);
+    }
+    __threadfence_block();
+}
+
+// Publishes this warp's progress (called by the lane that writes the row).
+__device__ __forceinline__ void publish_progress(volatile long long* w, long long v) {
+    __threadfence_block();
+    *w = v;
+}
 
 constexpr float kBig = 1.2676506002282294e30f;   // 2^100
 constexpr int kNoExp = (int)0x80000000;           // "no exponent yet" in the fill scan
@@ -217,6 +247,7 @@ enum : int {
     kGuardCorner = 1 << 9,   // a corner cell was reached with a non-zero exponent
     kGuardStage = 1 << 10,   // a row exceeded its staging capacity
     kGuardPool = 1 << 11,    // the entry pool region was full
+    kGuardSync = 1 << 12,    // a wait for another warp's strip ran out
 };
 
 // ---------------------------------------------------------------- async copies
@@ -364,6 +395,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     // starting exponent: the boundary row's exponent, moved to the magnitude of
     // its values at column n (every lane starts there)
     int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
+    // the row below is written by another warp: wait for its first columns
+    wait_progress(io.wait, io.wait_tag | (64 + kD), flag);
     if (bnd_in) {
         const float4 v0 = bnd_in[2 * n], v1 = bnd_in[2 * n + 1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
@@ -377,6 +410,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     const int rend = last_strip ? (m - row0) % R : -1;
     const int t_end = last_strip ? 31 - Lend : -1;
     const int t_start = first_strip ? n + 31 : -1;
+    // column n - t of the row below is written at the writer's step t + 31 and
+    // fetched here kD - 1 steps ahead: stay 16 + kD + 32 steps behind it
     float2* bst_strip = io.bst;
     int2* bex = io.bex;
     const int nsteps = n + 32;
@@ -404,12 +439,16 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     auto ycode = [&](int j) { return (int)ws.sy[j + kYPad - 1]; };
     int yc = ycode(n + 31 - lane);
     for (int t = 0; t < nsteps; ++t) {
+        const int ph = t & (kC - 1);
+        if (ph == 0) {
+            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag);
+            if (io.pub && lane == 0) publish_progress(io.pub, io.pub_tag | t);
+        }
         fetch(t + kD - 1);
         cp_async_wait<kD - 1>();
         const float4* ebnd = ws.ring_e + 2 * (streams ? (t & (kD - 1)) : 0);
         const int j = n + 31 - lane - t;
         const bool act = (j >= 0) && (j <= n);
-        const int ph = t & (kC - 1);
         if (ph == 0) {
             // renormalise: bring the lane's largest carried value into [1, 2)
             float mh = fmaxf(fmaxf(dDD.x, tV.x), tX2), mp = fmaxf(dDD.y, tV.y);
@@ -477,6 +516,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
                                       eZp, flag);
     }
     cp_async_wait<0>();
+    if (io.pub && lane == 0) publish_progress(io.pub, io.pub_tag | kStepsDone);
 }
 
 // ---------------------------------------------------------------- pass 2
@@ -630,6 +670,8 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     // starting exponent: the boundary row's exponent, moved to the magnitude of
     // its values at column 0 (every lane starts there)
     int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
+    // the row above is written by another warp: wait for its first columns
+    wait_progress(io.wait, io.wait_tag | (64 + kD), flag);
     if (bnd_in) {
         const float4 v0 = bnd_in[0], v1 = bnd_in[1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
@@ -704,6 +746,12 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     auto ycode = [&](int j) { return (int)ws.sy[j + kYPad - 1]; };
     int yc = ycode(-lane);
     for (int t = 0; t < nsteps; ++t) {
+        // column T of the row above is written at the writer's step T + 31 and
+        // fetched here kD - 1 steps ahead: stay 16 + kD + 32 steps behind it
+        if ((t & (kC - 1)) == 0) {
+            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag);
+            if (io.pub && lane == 31) publish_progress(io.pub, io.pub_tag | t);
+        }
         fetch(t + kD - 1);
         cp_async_wait<kD - 1>();
         const float2* bs = ws.ring_b + (t & (kD - 1)) * (kWarp * kRmax) + lane * R;
@@ -779,6 +827,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
                                eP, pmax, fo, flag);
     }
     cp_async_wait<0>();
+    if (io.pub && lane == 31) publish_progress(io.pub, io.pub_tag | kStepsDone);
     // ---- flush this strip's entries into the pool (row-major, columns ascending)
     int tot = 0;
 #pragma unroll
@@ -848,6 +897,29 @@ __device__ __forceinline__ void fwd_dispatch(int Rs, const Problem& Pb, const fl
     }
 }
 
+// Control block of one group of warps working on one pair (shared memory).
+struct GroupCtl {
+    long long prog[4];          // progress word of each warp of the group
+    int q;                      // the group's current work item
+    int pad;
+    float Zh, Zp;               // pass-1 totals (from the warp of strip 0)
+    int eZh, eZp;
+    float fZh, fZp;             // pass-2 corner values (from the warp of the last strip)
+    int feh, fep, fA;
+    int flag[4];
+    float pmax[4];
+    long long tot[4];
+};
+
+// Barrier of one group.  Groups of 2 warps use named barriers 1 and 2, a group
+// of 4 barrier 1 (literal ids: a register id would reserve all 16 barriers of
+// the block and cost occupancy).
+__device__ __forceinline__ void group_sync(int gib, int W) {
+    if (W == 1) { __syncwarp(); return; }
+    if (gib == 0) asm volatile("bar.sync 1, %0;" ::"r"(32 * W) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"r"(32 * W) : "memory");
+}
+
 // CKPT = false (stored form): pass 1 stores (B_M, Zm_b) of every strip, pass 2
 // reads them back.  CKPT = true (checkpointed form, for long sequences): pass 1
 // keeps only the boundary row at the top of every strip; pass 2 recomputes the
@@ -856,13 +928,20 @@ __device__ __forceinline__ void fwd_dispatch(int Rs, const Problem& Pb, const fl
 // of the whole matrix, for one more backward sweep of work.  Both forms give
 // the same values: the recomputed strip starts from the same boundary row and
 // runs the same instructions.
-template <int MINB, bool CKPT>
+//
+// W warps (1 or 2; Pb.wpp) share a pair: warp w of the group takes every
+// W-th strip (pass 1 from the bottom, pass 2 from the top) and trails the warp
+// of the neighbouring strip through that strip's boundary row and its
+// progress word, so the strips of one pair run concurrently.
+template <int MINB, bool CKPT, int W>
 __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     float2* s_ow = (float2*)s_raw;
     for (int i = threadIdx.x; i < kTab * kTab; i += blockDim.x) s_ow[i] = Pb.cst->ow[i];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    const int nwb = blockDim.x >> 5;
+    const int gib = wib / W, wig = wib % W;
     WarpSmem ws;
     {
         unsigned char* p = s_raw + kOwBytes + (size_t)wib * warp_smem_bytes(Pb.max_len);
@@ -870,19 +949,29 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
         ws.ring_e = (float4*)(p + kD * kWarp * kRmax * 8);
         ws.sy = p + kD * kWarp * kRmax * 8 + kD * 32;
     }
+    GroupCtl* gc = (GroupCtl*)(s_raw + kOwBytes + (size_t)nwb * warp_smem_bytes(Pb.max_len)) + gib;
     __syncthreads();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t gg = gw / W;
     PairCtx c;
-    c.bst = Pb.bst + gw * Pb.bst_stride;
-    c.bex = Pb.bex + gw * Pb.bex_stride;
-    c.bnd = Pb.bnd + gw * Pb.bnd_stride;
-    c.bck = CKPT ? Pb.bck + gw * Pb.bck_stride : nullptr;
+    c.bst = Pb.bst + (CKPT ? gw : gg) * Pb.bst_stride;
+    c.bex = Pb.bex + (CKPT ? gw : gg) * Pb.bex_stride;
+    c.bnd = Pb.bnd + gg * Pb.bnd_stride;
+    c.bck = Pb.bck + gg * Pb.bck_stride;
     c.stg = Pb.stg + gw * Pb.stg_stride;
     c.st = Pb.status;
+    // boundary rows: one per strip when other warps or a later recompute read
+    // them, else one row reused in place (the writer trails the reader)
+    const bool bck_rows = CKPT || W > 1;
+    const bool bnd_rows = W > 1;
+    volatile long long* my_prog = W > 1 ? &gc->prog[wig] : nullptr;
     for (;;) {
-        int q = 0;
-        if (lane == 0) q = atomicAdd(&Pb.status->work_f32, 1);
-        q = __shfl_sync(FULL, q, 0);
+        if (lane == 0) {
+            if (my_prog) *my_prog = 0;
+            if (wig == 0) gc->q = atomicAdd(&Pb.status->work_f32, 1);
+        }
+        group_sync(gib, W);
+        const int q = *(volatile int*)&gc->q;
         if (q >= Pb.n_work) break;
         const int2 it = Pb.items[q];
         const FamDesc& fd = Pb.fams[it.x];
@@ -907,32 +996,44 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
         }
         __syncwarp();
         int flag = 0;
-        // ---- pass 1: backward, bottom strip first
+        // ---- pass 1: backward, bottom strip first (strip s: warp (ns-1-s) % W)
         float Zh = 0.f, Zp = 0.f;
         int eZh = 0, eZp = 0;
         const int64_t strip_vals = (int64_t)kStripRows * (n + 32), strip_exps = (int64_t)c.nch * 32;
         const int64_t row_len = 2 * (int64_t)(n + 1);
-        for (int s = nstrips - 1; s >= 0; --s) {
+        for (int s = nstrips - 1 - wig, seq = 0; s >= 0; s -= W, ++seq) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = rows_per_lane(rows_in);
             StripIO io;
+            io.bnd_in = (s == nstrips - 1) ? nullptr : c.bck + (bck_rows ? (s + 1) * row_len : 0);
+            io.bnd_out = (s == 0) ? nullptr : c.bck + (bck_rows ? s * row_len : 0);
+            io.wait = nullptr; io.pub = nullptr; io.wait_tag = io.pub_tag = 0;
+            if (W > 1) {
+                if (s < nstrips - 1) {
+                    const int ps = nstrips - 2 - s;          // order of strip s + 1 in pass 1
+                    io.wait = &gc->prog[ps % W];
+                    io.wait_tag = (long long)(ps / W + 1) << 32;
+                }
+                if (s > 0) { io.pub = my_prog; io.pub_tag = (long long)(seq + 1) << 32; }
+            }
             if (CKPT) {
-                io.bnd_in = (s == nstrips - 1) ? nullptr : c.bck + (s + 1) * row_len;
-                io.bnd_out = (s == 0) ? nullptr : c.bck + s * row_len;
                 io.bst = nullptr;
                 io.bex = nullptr;
                 bwd_dispatch<false>(Rs, Pb.cf, s_ow, c, ws, s, nstrips, io, Zh, Zp, eZh, eZp, flag);
             } else {
-                io.bnd_in = (s == nstrips - 1) ? nullptr : c.bnd;
-                io.bnd_out = (s == 0) ? nullptr : c.bnd;
                 io.bst = c.bst + s * strip_vals;
                 io.bex = c.bex + s * strip_exps;
                 bwd_dispatch<true>(Rs, Pb.cf, s_ow, c, ws, s, nstrips, io, Zh, Zp, eZh, eZp, flag);
             }
             __syncwarp();
         }
-        Zh = __shfl_sync(FULL, Zh, 0); Zp = __shfl_sync(FULL, Zp, 0);
-        eZh = __shfl_sync(FULL, eZh, 0); eZp = __shfl_sync(FULL, eZp, 0);
+        // the totals come from strip 0 (lane 0 of its warp)
+        if (wig == (nstrips - 1) % W && lane == 0) {
+            gc->Zh = Zh; gc->Zp = Zp; gc->eZh = eZh; gc->eZp = eZp;
+        }
+        group_sync(gib, W);
+        Zh = *(volatile float*)&gc->Zh; Zp = *(volatile float*)&gc->Zp;
+        eZh = *(volatile int*)&gc->eZh; eZp = *(volatile int*)&gc->eZp;
         // normalise the totals to [1, 2) * 2^e
         if (!(Zh > 0.f) || !(Zp > 0.f) || !(Zh < kBig) || !(Zp < kBig)) flag |= kGuardTotal;
         {
@@ -942,6 +1043,7 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
         }
         const float invZh = 1.f / Zh, invZp = 1.f / Zp;
         // ---- pass 2: forward + posterior + threshold + MEA, top strip first
+        // (strip s: warp s % W)
         const int mn = min(m, n);
         int sA = 30 - (32 - __clz(mn + 1));
         if (sA > 21) sA = 21;
@@ -949,12 +1051,20 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
         float pmax = 0.f;
         FwdOut fo{0.f, 0.f, 0, 0, 0};
         int64_t pair_tot = 0;
-        for (int s = 0; s < nstrips; ++s) {
+        for (int s = wig, seq = 0; s < nstrips; s += W, ++seq) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = rows_per_lane(rows_in);
             StripIO io;
-            io.bnd_in = (s == 0) ? nullptr : c.bnd;
-            io.bnd_out = (s == nstrips - 1) ? nullptr : c.bnd;
+            io.bnd_in = (s == 0) ? nullptr : c.bnd + (bnd_rows ? (s - 1) * row_len : 0);
+            io.bnd_out = (s == nstrips - 1) ? nullptr : c.bnd + (bnd_rows ? s * row_len : 0);
+            io.wait = nullptr; io.pub = nullptr; io.wait_tag = io.pub_tag = 0;
+            if (W > 1) {
+                if (s > 0) {
+                    io.wait = &gc->prog[(s - 1) % W];
+                    io.wait_tag = (kPass2Tag + (s - 1) / W + 1) << 32;
+                }
+                if (s < nstrips - 1) { io.pub = my_prog; io.pub_tag = (kPass2Tag + seq + 1) << 32; }
+            }
             if (CKPT) {
                 // the strip's backward values again, from its checkpoint row
                 StripIO bio;
@@ -962,6 +1072,7 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
                 bio.bnd_out = nullptr;
                 bio.bst = c.bst;
                 bio.bex = c.bex;
+                bio.wait = nullptr; bio.pub = nullptr; bio.wait_tag = bio.pub_tag = 0;
                 float dZh = 0.f, dZp = 0.f;
                 int deZh = 0, deZp = 0;
                 bwd_dispatch<true>(Rs, Pb.cf, s_ow, c, ws, s, nstrips, bio, dZh, dZp, deZh, deZp, flag);
@@ -976,26 +1087,44 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
                          pair_tot, flag);
             __syncwarp();
         }
-        // ---- pair results (held by the lane that owns row m)
-        const int lastRs = rows_per_lane(min(kStripRows, m + 1 - (nstrips - 1) * kStripRows));
-        const int Lend = (m - (nstrips - 1) * kStripRows) / lastRs;
-        const float fZh = __shfl_sync(FULL, fo.Zh, Lend), fZp = __shfl_sync(FULL, fo.Zp, Lend);
-        const int feh = __shfl_sync(FULL, fo.eZh, Lend), fep = __shfl_sync(FULL, fo.eZp, Lend);
-        const int Aend = __shfl_sync(FULL, fo.A, Lend);
-        if (pmax > 1.001f) flag |= kGuardPost;
+        // ---- pair results: partial values of every warp of the group
+        if (wig == (nstrips - 1) % W) {
+            // corner values, held by the lane that owns row m
+            const int lastRs = rows_per_lane(min(kStripRows, m + 1 - (nstrips - 1) * kStripRows));
+            const int Lend = (m - (nstrips - 1) * kStripRows) / lastRs;
+            const float fZh = __shfl_sync(FULL, fo.Zh, Lend), fZp = __shfl_sync(FULL, fo.Zp, Lend);
+            const int feh = __shfl_sync(FULL, fo.eZh, Lend), fep = __shfl_sync(FULL, fo.eZp, Lend);
+            const int Aend = __shfl_sync(FULL, fo.A, Lend);
+            if (lane == 0) { gc->fZh = fZh; gc->fZp = fZp; gc->feh = feh; gc->fep = fep; gc->fA = Aend; }
+        }
+        for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(FULL, pmax, o));
         flag = __reduce_or_sync(FULL, flag);
-        if (lane == 0) {
+        if (lane == 0) { gc->flag[wig] = flag; gc->pmax[wig] = pmax; gc->tot[wig] = pair_tot; }
+        group_sync(gib, W);
+        if (wig == 0 && lane == 0) {
+            int fl = 0;
+            float pm = 0.f;
+            int64_t tot = 0;
+            for (int w = 0; w < W; ++w) {
+                fl |= ((volatile int*)gc->flag)[w];
+                pm = fmaxf(pm, ((volatile float*)gc->pmax)[w]);
+                tot += ((volatile long long*)gc->tot)[w];
+            }
+            if (pm > 1.001f) fl |= kGuardPost;
+            const float fZh = *(volatile float*)&gc->fZh, fZp = *(volatile float*)&gc->fZp;
+            const int feh = *(volatile int*)&gc->feh, fep = *(volatile int*)&gc->fep;
+            const int Aend = *(volatile int*)&gc->fA;
             const double ln2 = 0.69314718055994530942;
             const double lzb_h = log((double)Zh) + (double)eZh * ln2;
             const double lzb_p = log((double)Zp) + (double)eZp * ln2;
             const double lzf_h = log((double)fZh) + (double)feh * ln2;
             const double lzf_p = log((double)fZp) + (double)fep * ln2;
-            if (!(fabs(lzb_h - lzf_h) <= 1e-3)) flag |= kGuardAgreeH;
-            if (!(fabs(lzb_p - lzf_p) <= 1e-3)) flag |= kGuardAgreeP;
+            if (!(fabs(lzb_h - lzf_h) <= 1e-3)) fl |= kGuardAgreeH;
+            if (!(fabs(lzb_p - lzf_p) <= 1e-3)) fl |= kGuardAgreeP;
             // a full entry pool is not a range problem: the pair keeps its FP32
             // results, its flag tells the host to grow the pool and run again
-            if (flag & ~kGuardPool) {
-                fd.pair_flags[p] = flag;
+            if (fl & ~kGuardPool) {
+                fd.pair_flags[p] = fl;
                 const int slot = atomicAdd(&Pb.status->n_fallback, 1);
                 Pb.fallback[slot] = it;
             } else {
@@ -1003,8 +1132,8 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
                 fd.mea[p] = A;
                 fd.logz_h[p] = lzb_h + fd.seq_logq[ab.x] + fd.seq_logq[ab.y];
                 fd.logz_p[p] = lzb_p;
-                fd.pair_nnz[p] = pair_tot;
-                fd.pair_flags[p] = flag;
+                fd.pair_nnz[p] = tot;
+                fd.pair_flags[p] = fl;
                 const double d = 1.0 - A / (double)mn;
                 const int64_t k = fd.k;
                 fd.dist[ab.x * k + ab.y] = (float)d;
@@ -1014,15 +1143,20 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
                 if (fd.n_done) { __threadfence(); atomicAdd(fd.n_done, 1); }
             }
         }
-        __syncwarp();
+        group_sync(gib, W);
     }
 }
 
 using F32Kernel = void (*)(Problem);
 
-static F32Kernel f32_kernel(int variant, bool ckpt) {
-    if (ckpt) return variant == 1 ? k_posterior_f32<3, true> : k_posterior_f32<4, true>;
-    return variant == 1 ? k_posterior_f32<3, false> : k_posterior_f32<4, false>;
+template <int W>
+static F32Kernel f32_kernel_w(int variant, bool ckpt) {
+    if (ckpt) return variant == 1 ? k_posterior_f32<3, true, W> : k_posterior_f32<4, true, W>;
+    return variant == 1 ? k_posterior_f32<3, false, W> : k_posterior_f32<4, false, W>;
+}
+
+static F32Kernel f32_kernel(int variant, bool ckpt, int wpp = 1) {
+    return wpp == 2 ? f32_kernel_w<2>(variant, ckpt) : f32_kernel_w<1>(variant, ckpt);
 }
 
 static cudaError_t set_smem(F32Kernel k, size_t smem) {
@@ -1037,12 +1171,14 @@ int posterior_f32_regs(int variant, bool ckpt) {
 }
 
 size_t posterior_f32_smem(int warps_per_block, int max_len) {
-    return (size_t)kOwBytes + (size_t)warps_per_block * warp_smem_bytes(max_len);
+    return (size_t)kOwBytes + (size_t)warps_per_block * warp_smem_bytes(max_len) +
+           (size_t)warps_per_block * sizeof(GroupCtl);
 }
 
-int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant, bool ckpt) {
+int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant, bool ckpt,
+                            int wpp) {
     const size_t smem = posterior_f32_smem(warps_per_block, max_len);
-    const F32Kernel k = f32_kernel(variant, ckpt);
+    const F32Kernel k = f32_kernel(variant, ckpt, wpp);
     set_smem(k, smem);
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, warps_per_block * 32, smem);
 }
@@ -1050,7 +1186,8 @@ int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block, cudaStream_t s,
                                  int variant) {
     const size_t smem = posterior_f32_smem(warps_per_block, P.max_len);
-    const F32Kernel k = f32_kernel(variant, P.ckpt != 0);
+    if (P.wpp != 1 && P.wpp != 2) return cudaErrorInvalidValue;
+    const F32Kernel k = f32_kernel(variant, P.ckpt != 0, P.wpp);
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, warps_per_block * 32, smem, s>>>(P);

@@ -129,6 +129,7 @@ struct Rec {
     std::vector<std::pair<int, int64_t>> per_fam, per_fam_f64;
     double work = 0, cells = 0;
     int variant = 0;
+    int cfg = 0;
     int64_t tkey = 0;
 };
 
@@ -201,7 +202,8 @@ size_t scratch_bytes_for(const qp_server* S, int L, int64_t* warps_out, int* bps
             bmax = std::max(bmax, bb);
         }
         warps = (int64_t)S->ctx->sm_count * bmax * kWpb;
-        b = (size_t)warps * qpk::F32Scratch(L, cap, ckpt).bytes();
+        // room for one or two warps per pair
+        b = std::max(qpk::F32Scratch(L, cap, ckpt, 1).bytes(warps), qpk::F32Scratch(L, cap, ckpt, 2).bytes(warps));
         if (ckpt || S->ctx->tune.ckpt == 0 || (S->ctx->tune.ckpt < 0 && b <= S->budget / 3)) break;
         ckpt = true;
     }
@@ -233,14 +235,16 @@ int set_scratch(qp_server* S, int L) {
     int cap = 0;
     bool ckpt = false;
     const size_t bytes = scratch_bytes_for(S, L, &warps, S->bps, &cap, &ckpt);
-    const qpk::F32Scratch sz(L, cap, ckpt);
+    // room for one warp per pair (a group is a warp) and for two
+    const qpk::F32Scratch s1(L, cap, ckpt, 1), s2(L, cap, ckpt, 2);
     const int64_t L1 = L + 1;
+    const int64_t u1 = warps, u2 = ckpt ? warps : warps / 2;
     struct A { void** p; size_t b; } al[] = {
-        {&S->bst, sizeof(float2) * (size_t)sz.bst * warps},
-        {&S->bex, sizeof(int2) * (size_t)sz.bex * warps},
-        {&S->bnd, sizeof(float4) * (size_t)sz.bnd * warps},
-        {&S->bck, sizeof(float4) * (size_t)sz.bck * warps},
-        {&S->stg, sizeof(int2) * (size_t)sz.stg * warps},
+        {&S->bst, sizeof(float2) * (size_t)std::max(s1.bst * u1, s2.bst * u2)},
+        {&S->bex, sizeof(int2) * (size_t)std::max(s1.bex * u1, s2.bex * u2)},
+        {&S->bnd, sizeof(float4) * (size_t)std::max(s1.bnd * warps, s2.bnd * (warps / 2))},
+        {&S->bck, sizeof(float4) * (size_t)std::max(s1.bck * warps, s2.bck * (warps / 2))},
+        {&S->stg, sizeof(int2) * (size_t)s1.stg * warps},
         {&S->d_b, sizeof(double2) * (size_t)(L1 * L1) * kF64Grid},
         {&S->d_diag, sizeof(double) * (size_t)(3 * qpk::kNS * L1) * kF64Grid},
         {&S->d_cnt, sizeof(int32_t) * (size_t)(5 * L1 + 8) * kF64Grid},
@@ -264,7 +268,7 @@ int set_scratch(qp_server* S, int L) {
     return QP_OK;
 }
 
-qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items) {
+qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items, int wpp = 1) {
     qpk::Problem Pb;
     memset(&Pb, 0, sizeof Pb);
     Pb.cf = S->cf;
@@ -279,12 +283,13 @@ qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items) {
     Pb.fallback = R.d_fallback;
     const int L = S->scratch_len;
     const int64_t L1 = L + 1;
-    const qpk::F32Scratch sz(L, S->cap, S->ckpt);
+    const qpk::F32Scratch sz(L, S->cap, S->ckpt, wpp);
     Pb.bst = (float2*)S->bst; Pb.bst_stride = sz.bst;
     Pb.bex = (int2*)S->bex;   Pb.bex_stride = sz.bex;
     Pb.bnd = (float4*)S->bnd; Pb.bnd_stride = sz.bnd;
     Pb.bck = (float4*)S->bck; Pb.bck_stride = sz.bck;
     Pb.ckpt = S->ckpt ? 1 : 0;
+    Pb.wpp = wpp;
     Pb.stg = (int2*)S->stg;   Pb.stg_stride = sz.stg;
     Pb.d_b = (double2*)S->d_b; Pb.d_b_stride = L1 * L1;
     Pb.d_diag = (double*)S->d_diag; Pb.d_diag_stride = 3 * qpk::kNS * L1;
@@ -569,12 +574,19 @@ bool issue(qp_server* S) {
         return false;
     }
     R.tkey = Context::tune_key(n_items, S->scratch_len, R.work) ^ ((int64_t)S->ckpt << 62);
-    R.variant = S->ctx->tune.variant >= 0 ? S->ctx->tune.variant : S->tuner[R.tkey].choose();
-    int64_t grid = (int64_t)S->ctx->sm_count * S->bps[R.variant];
-    grid = std::min<int64_t>(grid, (n_items + kWpb - 1) / kWpb);
+    const int max_strips = (S->scratch_len + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
+    const unsigned allowed = allowed_configs(n_items, max_strips, S->scratch_warps, kWpb, S->ctx->tune);
+    R.cfg = S->tuner[R.tkey].choose(allowed);
+    R.variant = config_variant(R.cfg);
+    const int W = config_wpp(R.cfg);
+    int bps = 0;
+    qpk::posterior_f32_occupancy(kWpb, S->scratch_len, &bps, R.variant, S->ckpt, W);
+    bps = std::max(1, std::min(bps, S->bps[R.variant]));
+    int64_t grid = (int64_t)S->ctx->sm_count * bps;
+    grid = std::min<int64_t>(grid, ((int64_t)n_items * W + kWpb - 1) / kWpb);
     grid = std::max<int64_t>(grid, 1);
     grid = std::min<int64_t>(grid, S->scratch_warps / kWpb);
-    const qpk::Problem Pb = base_problem(S, R, n_items);
+    const qpk::Problem Pb = base_problem(S, R, n_items, W);
     cudaEventRecord(R.ev0, S->cs);
     if ((e = qpk::launch_posterior_f32(Pb, (int)grid, kWpb, S->cs, R.variant)) != cudaSuccess) {
         fail_all(S, cuda_fail(e, "k_posterior_f32 launch"), last_error());
@@ -610,7 +622,7 @@ void retire(qp_server* S, int ri) {
     if (ms > 1.0f) S->rate = 0.7 * S->rate + 0.3 * (R.work / ms);
     if (S->ctx->tune.variant < 0) {
         TuneEntry& te = S->tuner[R.tkey];
-        te.ms[R.variant] = te.ms[R.variant] < 0 ? ms : std::min<double>(te.ms[R.variant], ms);
+        te.record(R.cfg, ms);
     }
     qpk::Status hs;
     cudaError_t e = cudaMemcpyAsync(S->h_status.ptr, R.d_status, sizeof hs, cudaMemcpyDeviceToHost, S->up);

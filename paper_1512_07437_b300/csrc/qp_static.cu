@@ -29,7 +29,8 @@ constexpr size_t oRowCnt = oCodes + al(2 * kSMaxLen);
 constexpr size_t oBst = oRowCnt + al(sizeof(int32_t) * (kSMaxLen + 1));
 constexpr size_t oBex = oBst + al(sizeof(float2) * (size_t)kSStrips * kStripRows * (kSMaxLen + 32));
 constexpr size_t oBnd = oBex + al(sizeof(int2) * (size_t)kSStrips * kSChunks * 32);
-constexpr size_t oStg = oBnd + al(sizeof(float4) * 2 * (size_t)(kSMaxLen + 1));
+constexpr size_t oBck = oBnd + al(sizeof(float4) * 2 * (size_t)(kSMaxLen + 1));
+constexpr size_t oStg = oBck + al(sizeof(float4) * 2 * (size_t)(kSMaxLen + 1));
 constexpr size_t oPool = oStg + al(sizeof(int2) * (size_t)kStripRows * kSCap);
 constexpr size_t kSBytes = oPool + al(sizeof(int2) * (size_t)kSMaxLen * kSCap);
 
@@ -171,6 +172,8 @@ extern "C" int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int
     Pb.bst = (float2*)(S + oBst); Pb.bst_stride = 0;
     Pb.bex = (int2*)(S + oBex); Pb.bex_stride = 0;
     Pb.bnd = (float4*)(S + oBnd); Pb.bnd_stride = 0;
+    Pb.bck = (float4*)(S + oBck); Pb.bck_stride = 0;
+    Pb.wpp = 1;
     Pb.stg = (int2*)(S + oStg); Pb.stg_stride = 0;
     Pb.f64_all = 0;
     Pb.max_len = m > n ? m : n;

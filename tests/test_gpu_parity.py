@@ -337,3 +337,27 @@ def test_large_family_sampled_pairs(qp):
     for q in sample[:4]:
         a, b = pl[q]
         compare_pair(res, fam, int(q), a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
+
+
+@pytest.mark.parametrize("wpp", [2])
+@pytest.mark.parametrize("ckpt", [0, 1])
+def test_warps_per_pair_equal_one(qp, wpp, ckpt):
+    """Several warps sharing a pair (each taking every wpp-th strip and
+    trailing its neighbour through the strip's boundary row) give the result
+    of one warp per pair, bit for bit, in both forms."""
+    fams = [synth.make_family("c2", 3), synth.star_family(46, 5, (560, 700), 0.3),
+            synth.family_from_strings(["ACDEFGHIKLMNPQRSTVWY" * 7, "ACDEF", "WYVTSRQPNMLKIHGFEDCA" * 9])]
+    prm = synth.default_params(threshold=0.01)
+    try:
+        qp.qp_set_option("ckpt", ckpt)
+        for fam in fams:
+            qp.qp_set_option("wpp", 1)
+            one = _run(qp, fam, prm)
+            qp.qp_set_option("wpp", wpp)
+            many = _run(qp, fam, prm)
+            _no_fallback(one)
+            _no_fallback(many)
+            _same_csr(one, many)
+    finally:
+        qp.qp_set_option("wpp", 0)
+        qp.qp_set_option("ckpt", -1)
