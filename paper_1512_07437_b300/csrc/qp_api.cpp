@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -298,6 +299,7 @@ Context* get_context(int device, int* status) {
     if (const char* v = getenv("QP_F32_CKPT")) c->tune.ckpt = atoi(v);
     if (const char* v = getenv("QP_F32_BLOCKS")) c->tune.blocks_per_sm = atoi(v);
     if (const char* v = getenv("QP_F32_WPP")) c->tune.wpp = atoi(v);
+    if (const char* v = getenv("QP_GRAPH")) c->tune.graph = atoi(v) != 0;
     if (const char* v = getenv("QP_SCRATCH_BYTES")) c->tune.scratch_bytes = atoll(v);
     Context* raw = c.get();
     g_ctx[device] = std::move(c);
@@ -371,10 +373,9 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     const int64_t total_res = f->offsets[k];
     const bool f64 = prm->precision == QP_F64_PLAIN;
     const int cap = row_capacity(prm, pl->max_len);
+    const int64_t budget = scratch_budget(C->tune);
 
-    e = cudaEventRecord(C->ev[0], st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    // ---- inputs
+    // ---- inputs and fixed workspace
     if ((e = C->codes.ensure(total_res)) != cudaSuccess ||
         (!f->residues_on_device && (e = C->ascii.ensure(total_res)) != cudaSuccess) ||
         (e = C->off.ensure(sizeof(int64_t) * (k + 1))) != cudaSuccess ||
@@ -382,28 +383,136 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         (e = C->cst.ensure(sizeof(qpk::Consts))) != cudaSuccess ||
         (e = C->status.ensure(sizeof(qpk::Status))) != cudaSuccess ||
         (e = C->fam.ensure(sizeof(qpk::FamDesc))) != cudaSuccess ||
-        (e = C->h_status.ensure(sizeof(qpk::Status))) != cudaSuccess ||
+        (e = C->h_status.ensure(sizeof(qpk::Status) + 64)) != cudaSuccess ||
         (e = C->h_fam.ensure(sizeof(qpk::FamDesc))) != cudaSuccess ||
-        (e = C->h_off.ensure(sizeof(int64_t) * (k + 1))) != cudaSuccess)
+        (e = C->h_off.ensure(sizeof(int64_t) * (k + 1))) != cudaSuccess ||
+        (e = C->row_cnt.ensure(sizeof(int32_t) * pl->n_rows)) != cudaSuccess ||
+        (e = C->chunk_off.ensure(sizeof(int64_t) * pl->n_strips)) != cudaSuccess ||
+        (e = C->pair_nnz.ensure(sizeof(int64_t) * P)) != cudaSuccess ||
+        (e = C->fallback.ensure(sizeof(int2) * P)) != cudaSuccess)
         return fail(QP_ENOMEM, "workspace allocation failed: %s", cudaGetErrorString(e));
     memcpy(C->h_off.ptr, f->offsets, sizeof(int64_t) * (k + 1));
-    cudaMemcpyAsync(C->off.ptr, C->h_off.ptr, sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, st);
     const uint8_t* d_ascii = f->residues;
     if (!f->residues_on_device) {
+        // pageable user memory: copied before (outside) the captured sequence
         e = cudaMemcpyAsync(C->ascii.ptr, f->residues, total_res, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "copy residues");
         d_ascii = (const uint8_t*)C->ascii.ptr;
     }
-    cudaMemsetAsync(C->status.ptr, 0, sizeof(qpk::Status), st);
+    // derived tables: recomputed only when the parameters change
     qpk::RawParams raw;
+    memset(&raw, 0, sizeof raw);
     make_raw(prm, &raw);
-    if ((e = qpk::launch_setup(&raw, (qpk::Consts*)C->cst.ptr, st)) != cudaSuccess) return cuda_fail(e, "k_setup");
-    if ((e = qpk::launch_encode(d_ascii, (uint8_t*)C->codes.ptr, total_res, (const int64_t*)C->off.ptr, k,
-                                (double*)C->seqlogq.ptr, (const qpk::Consts*)C->cst.ptr,
-                                (qpk::Status*)C->status.ptr, st)) != cudaSuccess)
-        return cuda_fail(e, "k_encode");
+    if (!C->raw_valid || memcmp(&raw, &C->last_raw, sizeof raw) != 0) {
+        if ((e = C->d_raw.ensure(sizeof(qpk::RawParams))) != cudaSuccess)
+            return fail(QP_ENOMEM, "workspace allocation failed");
+        if ((e = qpk::launch_setup(&raw, (qpk::RawParams*)C->d_raw.ptr, (qpk::Consts*)C->cst.ptr, st)) != cudaSuccess)
+            return cuda_fail(e, "k_setup");
+        C->last_raw = raw;
+        C->raw_valid = true;
+    }
 
-    // ---- result, fixed part
+    // ---- launch configuration of the FP32 kernel
+    const int wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 4;
+    int variant = 0, cfg = 0, W = 1;
+    bool ckpt = false;
+    int64_t grid = 1, tkey = 0;
+    qpk::Problem Pb;
+    memset(&Pb, 0, sizeof Pb);
+    make_coef(prm, &Pb.cf);
+    Pb.cst = (const qpk::Consts*)C->cst.ptr;
+    Pb.fams = (const qpk::FamDesc*)C->fam.ptr;
+    Pb.items = (const int2*)pl->d_items.ptr;
+    Pb.n_work = (int32_t)P;
+    Pb.cap = cap;
+    Pb.status = (qpk::Status*)C->status.ptr;
+    Pb.fallback = (int2*)C->fallback.ptr;
+    Pb.max_len = pl->max_len;
+    if (!f64) {
+        auto occupancy = [&](int v, bool ck, int w = 1) {
+            int b = C->tune.blocks_per_sm;
+            if (b <= 0) {
+                qpk::posterior_f32_occupancy(wpb, pl->max_len, &b, v, ck, w);
+                b = std::max(1, std::min(b, 8));
+            }
+            return b;
+        };
+        // bytes of a grid of `warps` warps, w warps per pair (the stored form
+        // keeps the plan's tighter per-pair sizes)
+        auto scratch_of = [&](bool ck, int w, int64_t warps) -> int64_t {
+            const qpk::F32Scratch sz(pl->max_len, cap, ck, w);
+            if (ck) return (int64_t)sz.bytes(warps);
+            const int64_t groups = warps / w;
+            return groups * (int64_t)(sizeof(float2) * pl->bst_stride + sizeof(int2) * pl->bex_stride +
+                                      sizeof(float4) * (sz.bnd + sz.bck)) +
+                   warps * (int64_t)(sizeof(int2) * sz.stg);
+        };
+        // stored form unless its scratch for a full grid exceeds the budget;
+        // then the checkpointed form, on a grid cut to the budget if need be
+        ckpt = C->tune.ckpt >= 0 ? C->tune.ckpt != 0 : false;
+        const int64_t warps_full = (int64_t)C->sm_count * occupancy(0, false) * wpb;
+        if (C->tune.ckpt < 0)
+            ckpt = scratch_of(false, 1, std::min<int64_t>(warps_full, ((P + wpb - 1) / wpb) * wpb)) > budget;
+        const int max_strips = (pl->max_len + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
+        const unsigned allowed = allowed_configs(P, max_strips, warps_full, wpb, C->tune);
+        tkey = Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)ckpt << 62);
+        cfg = C->tuner[tkey].choose(allowed);
+        variant = config_variant(cfg);
+        W = config_wpp(cfg);
+        grid = (int64_t)C->sm_count * occupancy(variant, ckpt, W);
+        grid = std::min<int64_t>(grid, (P * W + wpb - 1) / wpb);
+        grid = std::min<int64_t>(grid, std::max<int64_t>(1, budget / std::max<int64_t>(1, scratch_of(ckpt, W, wpb))));
+        grid = std::max<int64_t>(grid, 1);
+        const int64_t warps = grid * wpb, groups = warps / W;
+        const qpk::F32Scratch sz(pl->max_len, cap, ckpt, W);
+        const int64_t bst_stride = ckpt ? sz.bst : pl->bst_stride;
+        const int64_t bex_stride = ckpt ? sz.bex : pl->bex_stride;
+        const int64_t units = ckpt ? warps : groups;
+        if ((e = C->bst.ensure(sizeof(float2) * bst_stride * units)) != cudaSuccess ||
+            (e = C->bex.ensure(sizeof(int2) * bex_stride * units)) != cudaSuccess ||
+            (e = C->bnd.ensure(sizeof(float4) * sz.bnd * groups)) != cudaSuccess ||
+            (e = C->bck.ensure(sizeof(float4) * sz.bck * groups)) != cudaSuccess ||
+            (e = C->stg.ensure(sizeof(int2) * sz.stg * warps)) != cudaSuccess)
+            return fail(QP_ENOMEM, "FP32 scratch allocation failed");
+        Pb.bst = (float2*)C->bst.ptr; Pb.bst_stride = bst_stride;
+        Pb.bex = (int2*)C->bex.ptr; Pb.bex_stride = bex_stride;
+        Pb.bnd = (float4*)C->bnd.ptr; Pb.bnd_stride = sz.bnd;
+        Pb.bck = (float4*)C->bck.ptr; Pb.bck_stride = sz.bck;
+        Pb.ckpt = ckpt ? 1 : 0;
+        Pb.wpp = W;
+        Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = sz.stg;
+    }
+    // FP64 form: over every pair (plain form), or as the follow-up of the FP32
+    // kernel on a small fixed grid that finds its pairs in the fallback list
+    // (it ends at once when the list is empty, so no host decision is needed)
+    int f64_grid;
+    {
+        const int64_t L = pl->max_len + 1;
+        const int64_t db = L * L;
+        const int64_t per_cta = (int64_t)(sizeof(double2) * db + sizeof(double) * 3 * qpk::kNS * L +
+                                          sizeof(int32_t) * (5 * L + 8) +
+                                          (sizeof(int2) + sizeof(double)) * (int64_t)pl->max_len * cap);
+        // (the follow-up grid keeps at most ~1 GiB of FP64 scratch)
+        const int64_t want = f64 ? std::min<int64_t>(P, (int64_t)C->sm_count * C->f64_blocks_per_sm)
+                                 : std::min<int64_t>(std::min<int64_t>(P, kF64FollowGrid),
+                                                     std::max<int64_t>(2, ((int64_t)1 << 30) / per_cta));
+        f64_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, budget / per_cta));
+        if ((e = C->d_b.ensure(sizeof(double2) * db * f64_grid)) != cudaSuccess ||
+            (e = C->d_diag.ensure(sizeof(double) * 3 * qpk::kNS * L * f64_grid)) != cudaSuccess ||
+            (e = C->d_cnt.ensure(sizeof(int32_t) * (5 * L + 8) * f64_grid)) != cudaSuccess ||
+            (e = C->d_stg.ensure(sizeof(int2) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess ||
+            (e = C->d_stg64.ensure(sizeof(double) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess)
+            return fail(QP_ENOMEM, "FP64 scratch allocation failed");
+        Pb.d_b = (double2*)C->d_b.ptr; Pb.d_b_stride = db;
+        Pb.d_diag = (double*)C->d_diag.ptr; Pb.d_diag_stride = 3 * qpk::kNS * L;
+        Pb.d_cnt = (int32_t*)C->d_cnt.ptr; Pb.d_cnt_stride = 5 * L + 8;
+        Pb.d_stg = (int2*)C->d_stg.ptr; Pb.d_stg64 = (double*)C->d_stg64.ptr;
+        Pb.d_stg_stride = (int64_t)pl->max_len * cap;
+        Pb.f64_all = f64 ? 1 : 0;
+    }
+
+    // ---- result: fixed part, and col / val at the pool's capacity (the
+    // entry count is known only at the end; no host decision in between)
     ResultOwner* own = new ResultOwner();
     own->device = C->device;
     auto bail = [&](int code) {
@@ -414,34 +523,20 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         return code;
     };
     const ResultLayout lay(P, pl->n_rows, k);
-    const size_t sz = lay.bytes;
-    e = cudaMallocAsync(&own->dev_a, sz, st);
-    if (e != cudaSuccess) { own->dev_a = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation (%zu bytes) failed", sz)); }
+    e = cudaMallocAsync(&own->dev_a, lay.bytes, st);
+    if (e != cudaSuccess) { own->dev_a = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation (%zu bytes) failed", lay.bytes)); }
     char* A = (char*)own->dev_a;
-    cudaMemcpyAsync(A + lay.o_pro, pl->d_row_off.ptr, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToDevice, st);
-    cudaMemsetAsync(A + lay.o_dist, 0, sizeof(float) * (size_t)k * k, st);
-    cudaMemsetAsync(A + lay.o_d64, 0, sizeof(double) * (size_t)k * k, st);
-    cudaMemsetAsync(A + lay.o_fl, 0, sizeof(int32_t) * P, st);
-
-    // ---- workspace
-    if ((e = C->row_cnt.ensure(sizeof(int32_t) * pl->n_rows)) != cudaSuccess ||
-        (e = C->chunk_off.ensure(sizeof(int64_t) * pl->n_strips)) != cudaSuccess ||
-        (e = C->pair_nnz.ensure(sizeof(int64_t) * P)) != cudaSuccess ||
-        (e = C->fallback.ensure(sizeof(int2) * P)) != cudaSuccess)
-        return bail(fail(QP_ENOMEM, "workspace allocation failed: %s", cudaGetErrorString(e)));
     {
-        // pool estimate; grown and rerun on overflow
         const double per_row = std::min<double>(pl->max_len + 1.0, 4.0 + 0.04 / prm->threshold);
         int64_t est = (int64_t)(per_row * (double)pl->n_rows) + 4096;
         est = std::max<int64_t>(est, C->pool_hint);
-        if ((e = C->pool.ensure(sizeof(int2) * est)) != cudaSuccess)
+        if ((e = C->pool.ensure(sizeof(int2) * est)) != cudaSuccess ||
+            (f64 && (e = C->pool64.ensure(sizeof(double) * est)) != cudaSuccess))
             return bail(fail(QP_ENOMEM, "pool allocation failed"));
         C->pool_cap = (int64_t)(C->pool.bytes / sizeof(int2));
-        if (f64 && (e = C->pool64.ensure(sizeof(double) * C->pool_cap)) != cudaSuccess)
-            return bail(fail(QP_ENOMEM, "pool allocation failed"));
+        if (f64) C->pool_cap = std::min<int64_t>(C->pool_cap, (int64_t)(C->pool64.bytes / sizeof(double)));
     }
 
-    qpk::Status* d_status = (qpk::Status*)C->status.ptr;
     qpk::FamDesc fd;
     memset(&fd, 0, sizeof fd);
     fd.codes = (const uint8_t*)C->codes.ptr;
@@ -460,187 +555,97 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     fd.dist = (float*)(A + lay.o_dist);
     fd.dist64 = (double*)(A + lay.o_d64);
     fd.pair_flags = (int32_t*)(A + lay.o_fl);
+    qpk::Status* d_status = (qpk::Status*)C->status.ptr;
     fd.pool_used = &d_status->pool_used;
     fd.pool_base = 0;
-    fd.n_done = nullptr;
-
-    qpk::Problem Pb;
-    memset(&Pb, 0, sizeof Pb);
-    make_coef(prm, &Pb.cf);
-    Pb.cst = (const qpk::Consts*)C->cst.ptr;
-    Pb.fams = (const qpk::FamDesc*)C->fam.ptr;
-    Pb.items = (const int2*)pl->d_items.ptr;
-    Pb.n_work = (int32_t)P;
-    Pb.cap = cap;
-    Pb.status = d_status;
-    Pb.fallback = (int2*)C->fallback.ptr;
-    Pb.max_len = pl->max_len;
 
     qpk::Status hs;
     memset(&hs, 0, sizeof hs);
-    int variant = 0;
-    int last_cfg = 0;
-    bool last_ckpt = false;
+    int64_t nnz = 0;
     for (int attempt = 0;; ++attempt) {
+        if (own->dev_b) { cudaFreeAsync(own->dev_b, st); own->dev_b = nullptr; }
+        const int64_t nnz_cap = C->pool_cap;
+        e = cudaMallocAsync(&own->dev_b, std::max<size_t>(ResultLayout::entry_bytes(nnz_cap, f64), 256), st);
+        if (e != cudaSuccess) { own->dev_b = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation failed")); }
+        qp_result probe;
+        memset(&probe, 0, sizeof probe);
+        fill_result(&probe, own, lay, k, P, pl->n_rows, nnz_cap, f64, prm->precision, C->device);
         fd.pool_cap = C->pool_cap;
         memcpy(C->h_fam.ptr, &fd, sizeof fd);
-        cudaMemcpyAsync(C->fam.ptr, C->h_fam.ptr, sizeof fd, cudaMemcpyHostToDevice, st);
         Pb.pool = (int2*)C->pool.ptr;
         Pb.pool64 = f64 ? (double*)C->pool64.ptr : nullptr;
-        if (attempt > 0) {
-            // rerun after a pool overflow: clear the counters, keep the rest
-            cudaMemsetAsync(&d_status->pool_used, 0, sizeof(unsigned long long), st);
-            cudaMemsetAsync(&d_status->pool_overflow, 0, sizeof(int32_t) * 2, st);
-            cudaMemsetAsync(&d_status->work_f32, 0, sizeof(int32_t) * 2, st);
-            cudaMemsetAsync(A + lay.o_fl, 0, sizeof(int32_t) * P, st);
-        }
-        cudaEventRecord(C->ev[1], st);
-        int f64_grid = 0;
-        if (!f64) {
-            const int wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 4;
-            // stored form unless its scratch for a full grid exceeds the budget;
-            // then the checkpointed form, on a grid cut to the budget if need be
-            const int64_t budget = scratch_budget(C->tune);
-            auto occupancy = [&](int v, bool ck, int W = 1) {
-                int b = C->tune.blocks_per_sm;
-                if (b <= 0) {
-                    qpk::posterior_f32_occupancy(wpb, pl->max_len, &b, v, ck, W);
-                    b = std::max(1, std::min(b, 8));
-                }
-                return b;
-            };
-            // bytes of a grid of `warps` warps, W warps per pair (the stored form
-            // keeps the plan's tighter per-pair sizes)
-            auto scratch_of = [&](bool ck, int W, int64_t warps) -> int64_t {
-                const qpk::F32Scratch sz(pl->max_len, cap, ck, W);
-                if (ck) return (int64_t)sz.bytes(warps);
-                const int64_t groups = warps / W;
-                return groups * (int64_t)(sizeof(float2) * pl->bst_stride + sizeof(int2) * pl->bex_stride +
-                                          sizeof(float4) * (sz.bnd + sz.bck)) +
-                       warps * (int64_t)(sizeof(int2) * sz.stg);
-            };
-            bool ckpt = C->tune.ckpt >= 0 ? C->tune.ckpt != 0 : false;
-            const int64_t warps_full = (int64_t)C->sm_count * occupancy(0, false) * wpb;
-            if (C->tune.ckpt < 0)
-                ckpt = scratch_of(false, 1, std::min<int64_t>(warps_full, ((P + wpb - 1) / wpb) * wpb)) > budget;
-            const int max_strips = (pl->max_len + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
-            const unsigned allowed = allowed_configs(P, max_strips, warps_full, wpb, C->tune);
-            const int64_t tkey = Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)ckpt << 62);
-            last_cfg = C->tuner[tkey].choose(allowed);
-            variant = config_variant(last_cfg);
-            const int W = config_wpp(last_cfg);
-            const int bps = occupancy(variant, ckpt, W);
-            int64_t grid = (int64_t)C->sm_count * bps;
-            grid = std::min<int64_t>(grid, (P * W + wpb - 1) / wpb);
-            grid = std::min<int64_t>(grid, std::max<int64_t>(1, budget / std::max<int64_t>(1, scratch_of(ckpt, W, wpb))));
-            grid = std::max<int64_t>(grid, 1);
-            const int64_t warps = grid * wpb, groups = warps / W;
-            const qpk::F32Scratch sz(pl->max_len, cap, ckpt, W);
-            const int64_t bst_stride = ckpt ? sz.bst : pl->bst_stride;
-            const int64_t bex_stride = ckpt ? sz.bex : pl->bex_stride;
-            const int64_t units = ckpt ? warps : groups;
-            if ((e = C->bst.ensure(sizeof(float2) * bst_stride * units)) != cudaSuccess ||
-                (e = C->bex.ensure(sizeof(int2) * bex_stride * units)) != cudaSuccess ||
-                (e = C->bnd.ensure(sizeof(float4) * sz.bnd * groups)) != cudaSuccess ||
-                (e = C->bck.ensure(sizeof(float4) * sz.bck * groups)) != cudaSuccess ||
-                (e = C->stg.ensure(sizeof(int2) * sz.stg * warps)) != cudaSuccess)
-                return bail(fail(QP_ENOMEM, "FP32 scratch allocation failed"));
-            Pb.bst = (float2*)C->bst.ptr; Pb.bst_stride = bst_stride;
-            Pb.bex = (int2*)C->bex.ptr; Pb.bex_stride = bex_stride;
-            Pb.bnd = (float4*)C->bnd.ptr; Pb.bnd_stride = sz.bnd;
-            Pb.bck = (float4*)C->bck.ptr; Pb.bck_stride = sz.bck;
-            Pb.ckpt = ckpt ? 1 : 0;
-            Pb.wpp = W;
-            Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = sz.stg;
-            last_ckpt = ckpt;
-            if ((e = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st, variant)) != cudaSuccess)
-                return bail(cuda_fail(e, "k_posterior_f32 launch"));
-            cudaEventRecord(C->ev[2], st);
-            e = cudaMemcpyAsync(C->h_status.ptr, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return bail(cuda_fail(e, "k_posterior_f32"));
-            {
-                float kms = 0.f;
-                if (cudaEventElapsedTime(&kms, C->ev[1], C->ev[2]) == cudaSuccess) {
-                    C->tuner[Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)last_ckpt << 62)]
-                        .record(last_cfg, kms);
-                }
+        // the whole call, one host synchronisation at the end
+        auto enqueue = [&]() -> cudaError_t {
+            cudaError_t x;
+            if ((x = cudaEventRecord(C->ev[0], st)) != cudaSuccess) return x;
+            if ((x = cudaMemcpyAsync(C->off.ptr, C->h_off.ptr, sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (x = cudaMemcpyAsync(C->fam.ptr, C->h_fam.ptr, sizeof fd, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (x = cudaMemsetAsync(C->status.ptr, 0, sizeof(qpk::Status), st)) != cudaSuccess ||
+                (x = cudaMemcpyAsync(A + lay.o_pro, pl->d_row_off.ptr, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                (x = cudaMemsetAsync(A + lay.o_dist, 0, sizeof(float) * (size_t)k * k, st)) != cudaSuccess ||
+                (x = cudaMemsetAsync(A + lay.o_d64, 0, sizeof(double) * (size_t)k * k, st)) != cudaSuccess ||
+                (x = cudaMemsetAsync(A + lay.o_fl, 0, sizeof(int32_t) * P, st)) != cudaSuccess)
+                return x;
+            if ((x = qpk::launch_encode(d_ascii, (uint8_t*)C->codes.ptr, total_res, (const int64_t*)C->off.ptr, k,
+                                        (double*)C->seqlogq.ptr, (const qpk::Consts*)C->cst.ptr, d_status, st)) != cudaSuccess)
+                return x;
+            if ((x = cudaEventRecord(C->ev[1], st)) != cudaSuccess) return x;
+            if (!f64 && (x = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st, variant)) != cudaSuccess) return x;
+            if ((x = cudaEventRecord(C->ev[2], st)) != cudaSuccess) return x;
+            if ((x = qpk::launch_posterior_f64(Pb, f64_grid, st)) != cudaSuccess) return x;
+            if ((x = cudaEventRecord(C->ev[3], st)) != cudaSuccess) return x;
+            if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, probe.pair_nnz_off, st)) != cudaSuccess ||
+                (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
+                                         fd.chunk_off, Pb.pool, Pb.pool64, P, probe.pair_nnz_off, probe.row_ptr,
+                                         probe.col, probe.val, probe.val64, st)) != cudaSuccess)
+                return x;
+            if ((x = cudaEventRecord(C->ev[4], st)) != cudaSuccess) return x;
+            char* hs_p = (char*)C->h_status.ptr;
+            if ((x = cudaMemcpyAsync(hs_p, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (x = cudaMemcpyAsync(hs_p + sizeof(qpk::Status), probe.pair_nnz_off + P, sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return x;
+            return cudaSuccess;
+        };
+        if (C->tune.graph) {
+            e = launch_graph(C, st, enqueue);
+            if (e != cudaSuccess && cudaPeekAtLastError() == cudaSuccess) {
+                // the graph could not be built or launched (nothing ran): keep
+                // to plain launches on this device from now on
+                fprintf(stderr, "libqp: CUDA graph launch failed (%s); using plain launches\n",
+                        cudaGetErrorName(e));
+                C->tune.graph = false;
+                e = enqueue();
             }
-            memcpy(&hs, C->h_status.ptr, sizeof hs);
-            if (hs.bad_residue)
-                return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
-            f64_grid = hs.n_fallback > 0 ? std::min<int>(hs.n_fallback, C->sm_count * C->f64_blocks_per_sm) : 0;
-            Pb.f64_all = 0;
         } else {
-            cudaEventRecord(C->ev[2], st);
-            f64_grid = (int)std::min<int64_t>(P, (int64_t)C->sm_count * C->f64_blocks_per_sm);
-            Pb.f64_all = 1;
+            e = enqueue();
         }
-        if (f64_grid > 0) {
-            const int64_t L = pl->max_len + 1;
-            const int64_t db = L * L;
-            // per-CTA scratch of the FP64 form; the grid is cut to the budget
-            const int64_t per_cta = (int64_t)(sizeof(double2) * db + sizeof(double) * 3 * qpk::kNS * L +
-                                              sizeof(int32_t) * (5 * L + 8) +
-                                              (sizeof(int2) + sizeof(double)) * (int64_t)pl->max_len * cap);
-            f64_grid = (int)std::max<int64_t>(1, std::min<int64_t>(f64_grid, scratch_budget(C->tune) / per_cta));
-            if ((e = C->d_b.ensure(sizeof(double2) * db * f64_grid)) != cudaSuccess ||
-                (e = C->d_diag.ensure(sizeof(double) * 3 * qpk::kNS * L * f64_grid)) != cudaSuccess ||
-                (e = C->d_cnt.ensure(sizeof(int32_t) * (5 * L + 8) * f64_grid)) != cudaSuccess ||
-                (e = C->d_stg.ensure(sizeof(int2) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess ||
-                (e = C->d_stg64.ensure(sizeof(double) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess)
-                return bail(fail(QP_ENOMEM, "FP64 scratch allocation failed"));
-            Pb.d_b = (double2*)C->d_b.ptr; Pb.d_b_stride = db;
-            Pb.d_diag = (double*)C->d_diag.ptr; Pb.d_diag_stride = 3 * qpk::kNS * L;
-            Pb.d_cnt = (int32_t*)C->d_cnt.ptr; Pb.d_cnt_stride = 5 * L + 8;
-            Pb.d_stg = (int2*)C->d_stg.ptr; Pb.d_stg64 = (double*)C->d_stg64.ptr;
-            Pb.d_stg_stride = (int64_t)pl->max_len * cap;
-            if ((e = qpk::launch_posterior_f64(Pb, f64_grid, st)) != cudaSuccess)
-                return bail(cuda_fail(e, "k_posterior_f64 launch"));
-        }
-        cudaEventRecord(C->ev[3], st);
-        e = cudaMemcpyAsync(C->h_status.ptr, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "posterior kernels"));
+        if (e != cudaSuccess) return bail(cuda_fail(e, "posterior stage"));
         memcpy(&hs, C->h_status.ptr, sizeof hs);
+        memcpy(&nnz, (char*)C->h_status.ptr + sizeof(qpk::Status), sizeof nnz);
         if (hs.bad_residue)
             return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
         if (hs.stage_overflow) return bail(fail(QP_ECUDA, "internal: a row exceeded its entry capacity"));
+        if (!f64) {
+            float kms = 0.f;
+            if (cudaEventElapsedTime(&kms, C->ev[1], C->ev[2]) == cudaSuccess) C->tuner[tkey].record(cfg, kms);
+        }
         if (!hs.pool_overflow) break;
         if (attempt >= 2) return bail(fail(QP_ENOMEM, "the entry pool kept overflowing"));
-        // grow the pool to what was asked for, and run again
+        // grow the pool (and the result's entry part) to what was asked for, and run again
         const int64_t need = (int64_t)(hs.pool_used * 5 / 4) + 4096;
         C->pool_hint = need;
         if ((e = C->pool.ensure(sizeof(int2) * need)) != cudaSuccess ||
             (f64 && (e = C->pool64.ensure(sizeof(double) * need)) != cudaSuccess))
             return bail(fail(QP_ENOMEM, "pool allocation (%lld entries) failed", (long long)need));
         C->pool_cap = (int64_t)(C->pool.bytes / sizeof(int2));
+        if (f64) C->pool_cap = std::min<int64_t>(C->pool_cap, (int64_t)(C->pool64.bytes / sizeof(double)));
     }
-    const int64_t nnz_bound = (int64_t)hs.pool_used;
-    // ---- CSR assembly
-    const size_t szb = ResultLayout::entry_bytes(nnz_bound, f64);
-    e = cudaMallocAsync(&own->dev_b, std::max<size_t>(szb, 256), st);
-    if (e != cudaSuccess) { own->dev_b = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation failed")); }
+
     qp_result* r = (qp_result*)calloc(1, sizeof(qp_result));
     if (!r) return bail(fail(QP_ENOMEM, "host allocation failed"));
-    fill_result(r, own, lay, k, P, pl->n_rows, nnz_bound, f64, prm->precision, C->device);
-    int32_t* d_col = r->col;
-    float* d_val = r->val;
-    double* d_val64 = r->val64;
-    if ((e = qpk::launch_scan_nnz(fd.pair_nnz, P, (int64_t*)(A + lay.o_pno), st)) != cudaSuccess ||
-        (e = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
-                                 fd.chunk_off, (const int2*)C->pool.ptr, Pb.pool64, P, (int64_t*)(A + lay.o_pno),
-                                 (int32_t*)(A + lay.o_rp), d_col, d_val, d_val64, st)) != cudaSuccess) {
-        free(r);
-        return bail(cuda_fail(e, "CSR assembly"));
-    }
-    cudaEventRecord(C->ev[4], st);
-    int64_t nnz = 0;
-    e = cudaMemcpyAsync(C->h_status.ptr, A + lay.o_pno + sizeof(int64_t) * P, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { free(r); return bail(cuda_fail(e, "CSR assembly")); }
-    memcpy(&nnz, C->h_status.ptr, sizeof nnz);
-
+    fill_result(r, own, lay, k, P, pl->n_rows, C->pool_cap, f64, prm->precision, C->device);
     r->nnz = nnz;
     r->n_fallback = f64 ? 0 : hs.n_fallback;
     for (int i = 0; i < 10; ++i) r->guard_info[i] = hs.diag[i];
@@ -655,6 +660,46 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     }
     *out = r;
     return QP_OK;
+}
+
+// Runs the enqueue function as one CUDA graph on stream st: the sequence is
+// captured, the context's executable graph is updated in place when the
+// topology is unchanged (new pointers and sizes only), else instantiated anew,
+// and launched.  A stream that is already capturing gets the plain sequence.
+cudaError_t launch_graph(Context* C, cudaStream_t st, const std::function<cudaError_t()>& enqueue) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return enqueue();
+    }
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t ee = enqueue();
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (ee != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return ee != cudaSuccess ? ee : e;
+    }
+    if (C->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(C->gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(C->gexec);
+            C->gexec = nullptr;
+        }
+    }
+    if (!C->gexec) {
+        e = cudaGraphInstantiate(&C->gexec, g, 0);
+        if (e != cudaSuccess) {
+            C->gexec = nullptr;
+            cudaGraphDestroy(g);
+            return e;
+        }
+    }
+    cudaGraphDestroy(g);
+    return cudaGraphLaunch(C->gexec, st);
 }
 
 int to_host(qp_result* r, cudaStream_t st) {
@@ -768,6 +813,8 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
     } else if (n == "wpp") {
         if (value > 0 && value != 1 && value != 2) return fail(QP_EINVAL, "wpp must be 1 or 2");
         C->tune.wpp = value > 0 ? (int)value : 0;
+    } else if (n == "graph") {
+        C->tune.graph = value != 0;
     } else if (n == "blocks_per_sm") {
         C->tune.blocks_per_sm = value > 0 ? (int)std::min<int64_t>(value, 32) : 0;
     } else if (n == "warps_per_block") {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -59,6 +60,7 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int variant = -1;
     int ckpt = -1;                       // 0 stored form, 1 checkpointed form
     int wpp = 0;                         // warps per pair (1, 2)
+    bool graph = true;                   // run each call as one captured CUDA graph
     int64_t scratch_bytes = 0;           // budget of the FP32 / FP64 scratch
 };
 
@@ -111,10 +113,13 @@ struct Context {
     int f64_blocks_per_sm = 2;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[6] = {};
+    cudaGraphExec_t gexec = nullptr;     // the last captured call sequence
     std::mutex mu;
     std::vector<std::shared_ptr<Plan>> plans;
     // workspace (grow-only)
-    DevBuf ascii, codes, off, seqlogq, cst, status, fam;
+    DevBuf ascii, codes, off, seqlogq, cst, d_raw, status, fam;
+    qpk::RawParams last_raw;             // parameters the tables in cst were derived from
+    bool raw_valid = false;
     DevBuf row_cnt, chunk_off, pair_nnz, fallback, pool, pool64;
     DevBuf bst, bex, bnd, bck, stg;
     DevBuf d_b, d_diag, d_cnt, d_stg, d_stg64;
@@ -182,6 +187,8 @@ Context* get_context(int device, int* status);
 int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
                qp_result** out);
 int to_host(qp_result* r, cudaStream_t st);
+cudaError_t launch_graph(Context* C, cudaStream_t st, const std::function<cudaError_t()>& enqueue);
+constexpr int kF64FollowGrid = 16;      // CTAs of the FP64 follow-up of an FP32 call
 void free_result(qp_result* r);
 
 }  // namespace qph

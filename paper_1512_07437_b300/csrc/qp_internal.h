@@ -131,7 +131,8 @@ struct Problem {
 };
 
 // launch wrappers (qp_kernels.cu)
-cudaError_t launch_setup(const RawParams* host_raw, Consts* dev_cst, cudaStream_t s);
+// copies the parameters (host) into d_raw (device) and derives the tables
+cudaError_t launch_setup(const RawParams* host_raw, RawParams* d_raw, Consts* dev_cst, cudaStream_t s);
 cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
                           const int64_t* seq_off, int32_t k, double* seq_logq,
                           const Consts* cst, Status* status, cudaStream_t s);

@@ -22,6 +22,10 @@
 // (Zm, Ze, Zf) with Boltzmann weights.
 #include "qp_internal.h"
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include <cstdio>
 
 namespace qpk {
@@ -49,7 +53,8 @@ __device__ __forceinline__ int ilog2f(float v) {
 }
 
 // ---------------------------------------------------------------- set-up
-__global__ void k_setup(RawParams raw, Consts* c) {
+__global__ void k_setup(const RawParams* __restrict__ rp, Consts* c) {
+    const RawParams& raw = *rp;
     const int t = threadIdx.x;
     for (int idx = t; idx < kTab * kTab; idx += blockDim.x) {
         const int y = idx / kTab, x = idx % kTab;
@@ -77,8 +82,10 @@ __global__ void k_setup(RawParams raw, Consts* c) {
     }
 }
 
-cudaError_t launch_setup(const RawParams* raw, Consts* cst, cudaStream_t s) {
-    k_setup<<<1, 512, 0, s>>>(*raw, cst);
+cudaError_t launch_setup(const RawParams* raw, RawParams* d_raw, Consts* cst, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(d_raw, raw, sizeof(RawParams), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_setup<<<1, 512, 0, s>>>(d_raw, cst);
     return cudaGetLastError();
 }
 
@@ -1159,9 +1166,20 @@ static F32Kernel f32_kernel(int variant, bool ckpt, int wpp = 1) {
     return wpp == 2 ? f32_kernel_w<2>(variant, ckpt) : f32_kernel_w<1>(variant, ckpt);
 }
 
+// Raises a kernel's dynamic shared memory limit once per size (so that a
+// launch inside a stream capture makes no attribute call).
 static cudaError_t set_smem(F32Kernel k, size_t smem) {
     if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::mutex mu;
+    static std::map<std::pair<F32Kernel, int>, size_t> done;   // (kernel, device) -> limit set
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    size_t& cur = done[std::make_pair(k, dev)];
+    if (smem <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
 }
 
 int posterior_f32_regs(int variant, bool ckpt) {

@@ -146,6 +146,7 @@ struct qp_server {
     double target_ms = 30.0, aging_s = 5.0;
     // device state
     qpk::Consts* d_cst = nullptr;
+    qpk::RawParams* d_raw = nullptr;
     qpk::FamDesc* d_fams = nullptr;
     qpk::Status* d_enc_status = nullptr;
     void* d_rec_mem = nullptr;
@@ -928,6 +929,7 @@ int qp_server_create(const qp_params* params, size_t mem_budget, int32_t out_on_
         return cuda_fail(e, "cudaStreamCreate");
     const size_t rec_bytes = align256(sizeof(int2) * kMaxItems) * 2 + align256(sizeof(qpk::Status));
     if ((e = cudaMalloc((void**)&S->d_cst, sizeof(qpk::Consts))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&S->d_raw, sizeof(qpk::RawParams))) != cudaSuccess ||
         (e = cudaMalloc((void**)&S->d_fams, sizeof(qpk::FamDesc) * kSlots)) != cudaSuccess ||
         (e = cudaMalloc((void**)&S->d_enc_status, sizeof(qpk::Status))) != cudaSuccess ||
         (e = cudaMalloc(&S->d_rec_mem, rec_bytes * kRecs)) != cudaSuccess) {
@@ -949,7 +951,7 @@ int qp_server_create(const qp_params* params, size_t mem_budget, int32_t out_on_
     qpk::RawParams raw;
     make_raw(params, &raw);
     if ((e = cudaMemsetAsync(S->d_enc_status, 0, sizeof(qpk::Status), S->cs)) != cudaSuccess ||
-        (e = qpk::launch_setup(&raw, S->d_cst, S->cs)) != cudaSuccess ||
+        (e = qpk::launch_setup(&raw, S->d_raw, S->d_cst, S->cs)) != cudaSuccess ||
         (e = cudaStreamSynchronize(S->cs)) != cudaSuccess)
         return cuda_fail(e, "server set-up");
     qp_server* raw_s = S.release();
@@ -1069,6 +1071,7 @@ void qp_server_destroy(qp_server* S) {
         if (R.ev1) cudaEventDestroy(R.ev1);
     }
     cudaFree(S->d_cst);
+    cudaFree(S->d_raw);
     cudaFree(S->d_fams);
     cudaFree(S->d_enc_status);
     cudaFree(S->d_rec_mem);

@@ -21,7 +21,8 @@ constexpr size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // Fixed layout of the scratch array (worst-case sizes for m, n <= kSMaxLen).
 constexpr size_t oConsts = 0;
-constexpr size_t oStatus = oConsts + al(sizeof(Consts));
+constexpr size_t oRaw = oConsts + al(sizeof(Consts));
+constexpr size_t oStatus = oRaw + al(sizeof(RawParams));
 constexpr size_t oFam = oStatus + al(sizeof(Status));
 constexpr size_t oSmall = oFam + al(sizeof(FamDesc));
 constexpr size_t oCodes = oSmall + al(1024);
@@ -152,7 +153,7 @@ extern "C" int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int
 
     RawParams raw;
     make_raw(params, &raw);
-    if ((e = launch_setup(&raw, cst, st)) != cudaSuccess) return cuda_fail(e, "k_setup");
+    if ((e = launch_setup(&raw, (RawParams*)(S + oRaw), cst, st)) != cudaSuccess) return cuda_fail(e, "k_setup");
     if ((e = launch_encode(residues, codes, (int64_t)m + n, sm->seq_off, 2, sm->seq_logq, cst, status,
                            st)) != cudaSuccess)
         return cuda_fail(e, "k_encode");
