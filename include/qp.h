@@ -116,8 +116,13 @@ typedef struct qp_params {
  *   pair_flags   [n_pairs]   : bit 0 set when an FP32 range guard fired and
  *                              the pair was recomputed by the FP64 form; bits
  *                              2.. name the guard;
- *   kernel_ms[0..3]           : device time of the posterior kernel, the FP64
- *                              kernel, the CSR compaction and the whole call;
+ *   kernel_ms[0..3]           : device time of the FP32 posterior kernel and
+ *                              of the FP64 kernel (CUDA events around them
+ *                              with plain launches; with a CUDA graph, time
+ *                              stamps the kernels take themselves), of the
+ *                              rest of the call (input staging, CSR
+ *                              assembly), and of the whole call (CUDA events
+ *                              around it);
  *   n_fallback                : pairs recomputed by the FP64 form;
  *   guard_info[12]            : the first FP32 range-guard event of the call
  *                              (site, strip, step, lane, HMM exponent and its
@@ -156,7 +161,10 @@ typedef struct qp_result {
 int qp_posteriors(const qp_family* family, const qp_params* params,
                   int32_t out_on_device, qp_result** out);
 
-/* Releases a result and everything it points to.  NULL is ignored. */
+/* Releases a result and everything it points to.  NULL is ignored.  Device
+ * blocks of a result may be kept by the library for the next call of the same
+ * shape: call it after the caller's own work that reads the result (on any
+ * stream) has completed. */
 void qp_result_free(qp_result* result);
 
 /* Serving loop with continuous batching: many families in one run under a
@@ -240,6 +248,8 @@ void qp_server_destroy(qp_server* server);
  *                     second 128-row strip, trailing the other through the
  *                     boundary row between them); by default the autotuner
  *                     tries 2 when pairs are too few to fill the grid;
+ *   "graph"           1 (default): run each call as one captured CUDA graph;
+ *                     0: plain launches;
  *   "blocks_per_sm", "warps_per_block";
  *   "scratch_bytes"   device bytes the kernels' scratch may take (default:
  *                     45% of free memory, at most 48 GiB); the stored form is

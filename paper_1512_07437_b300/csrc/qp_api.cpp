@@ -255,6 +255,39 @@ int64_t scratch_budget(const LaunchOverride& t) {
     return std::max<int64_t>((int64_t)1 << 30, std::min<int64_t>(cap, (int64_t)(0.45 * (double)fr)));
 }
 
+// ------------------------------------------------------------------ result blocks
+constexpr size_t kSpareCap = (size_t)1 << 30;   // bytes of result blocks kept for reuse
+constexpr size_t kSpareCount = 16;
+
+cudaError_t Context::take_block(void** p, size_t bytes, cudaStream_t st) {
+    {
+        std::lock_guard<std::mutex> g(spare_mu);
+        auto it = spare.find(bytes);
+        if (it != spare.end()) {
+            *p = it->second;
+            spare.erase(it);
+            spare_bytes -= bytes;
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) { *p = nullptr; cudaGetLastError(); }
+    return e;
+}
+
+void Context::give_block(void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes > 0) {
+        std::lock_guard<std::mutex> g(spare_mu);
+        if (spare_bytes + bytes <= kSpareCap && spare.size() < kSpareCount) {
+            spare.emplace(bytes, p);
+            spare_bytes += bytes;
+            return;
+        }
+    }
+    cudaFreeAsync(p, stream);
+}
+
 // ------------------------------------------------------------------ autotuner key
 int64_t Context::tune_key(int64_t n_pairs, int max_len, double work) {
     // buckets: pair count (half powers of two), longest sequence (64s), mean
@@ -523,8 +556,9 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         return code;
     };
     const ResultLayout lay(P, pl->n_rows, k);
-    e = cudaMallocAsync(&own->dev_a, lay.bytes, st);
-    if (e != cudaSuccess) { own->dev_a = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation (%zu bytes) failed", lay.bytes)); }
+    e = C->take_block(&own->dev_a, lay.bytes, st);
+    if (e != cudaSuccess) return bail(fail(QP_ENOMEM, "result allocation (%zu bytes) failed", lay.bytes));
+    own->bytes_a = lay.bytes;
     char* A = (char*)own->dev_a;
     {
         const double per_row = std::min<double>(pl->max_len + 1.0, 4.0 + 0.04 / prm->threshold);
@@ -562,11 +596,13 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     qpk::Status hs;
     memset(&hs, 0, sizeof hs);
     int64_t nnz = 0;
+    bool timed_call = false;
     for (int attempt = 0;; ++attempt) {
-        if (own->dev_b) { cudaFreeAsync(own->dev_b, st); own->dev_b = nullptr; }
+        if (own->dev_b) { C->give_block(own->dev_b, own->bytes_b); own->dev_b = nullptr; }
         const int64_t nnz_cap = C->pool_cap;
-        e = cudaMallocAsync(&own->dev_b, std::max<size_t>(ResultLayout::entry_bytes(nnz_cap, f64), 256), st);
-        if (e != cudaSuccess) { own->dev_b = nullptr; cudaGetLastError(); return bail(fail(QP_ENOMEM, "result allocation failed")); }
+        own->bytes_b = std::max<size_t>(ResultLayout::entry_bytes(nnz_cap, f64), 256);
+        e = C->take_block(&own->dev_b, own->bytes_b, st);
+        if (e != cudaSuccess) return bail(fail(QP_ENOMEM, "result allocation failed"));
         qp_result probe;
         memset(&probe, 0, sizeof probe);
         fill_result(&probe, own, lay, k, P, pl->n_rows, nnz_cap, f64, prm->precision, C->device);
@@ -575,9 +611,11 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         Pb.pool = (int2*)C->pool.ptr;
         Pb.pool64 = f64 ? (double*)C->pool64.ptr : nullptr;
         // the whole call, one host synchronisation at the end
+        // timed: CUDA events around the posterior kernels (plain launches only:
+        // a captured sequence carries none)
+        bool timed = false;
         auto enqueue = [&]() -> cudaError_t {
             cudaError_t x;
-            if ((x = cudaEventRecord(C->ev[0], st)) != cudaSuccess) return x;
             if ((x = cudaMemcpyAsync(C->off.ptr, C->h_off.ptr, sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
                 (x = cudaMemcpyAsync(C->fam.ptr, C->h_fam.ptr, sizeof fd, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
                 (x = cudaMemsetAsync(C->status.ptr, 0, sizeof(qpk::Status), st)) != cudaSuccess ||
@@ -589,17 +627,16 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             if ((x = qpk::launch_encode(d_ascii, (uint8_t*)C->codes.ptr, total_res, (const int64_t*)C->off.ptr, k,
                                         (double*)C->seqlogq.ptr, (const qpk::Consts*)C->cst.ptr, d_status, st)) != cudaSuccess)
                 return x;
-            if ((x = cudaEventRecord(C->ev[1], st)) != cudaSuccess) return x;
+            if (timed) cudaEventRecord(C->ev[1], st);
             if (!f64 && (x = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st, variant)) != cudaSuccess) return x;
-            if ((x = cudaEventRecord(C->ev[2], st)) != cudaSuccess) return x;
+            if (timed) cudaEventRecord(C->ev[2], st);
             if ((x = qpk::launch_posterior_f64(Pb, f64_grid, st)) != cudaSuccess) return x;
-            if ((x = cudaEventRecord(C->ev[3], st)) != cudaSuccess) return x;
+            if (timed) cudaEventRecord(C->ev[3], st);
             if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, probe.pair_nnz_off, st)) != cudaSuccess ||
                 (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
                                          fd.chunk_off, Pb.pool, Pb.pool64, P, probe.pair_nnz_off, probe.row_ptr,
                                          probe.col, probe.val, probe.val64, st)) != cudaSuccess)
                 return x;
-            if ((x = cudaEventRecord(C->ev[4], st)) != cudaSuccess) return x;
             char* hs_p = (char*)C->h_status.ptr;
             if ((x = cudaMemcpyAsync(hs_p, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
                 (x = cudaMemcpyAsync(hs_p + sizeof(qpk::Status), probe.pair_nnz_off + P, sizeof(int64_t),
@@ -607,19 +644,38 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
                 return x;
             return cudaSuccess;
         };
+        // events only outside the captured sequence: the whole call; the
+        // kernels time themselves (Status time stamps)
+        cudaEventRecord(C->ev[0], st);
         if (C->tune.graph) {
-            e = launch_graph(C, st, enqueue);
+            // everything the sequence's nodes hold (pointers, sizes, launch
+            // shapes, kernel parameters): equal keys relaunch the cached graph
+            GraphKey key;
+            memset(&key, 0, sizeof key);
+            const void* ptrs[] = {C->off.ptr, C->h_off.ptr, C->fam.ptr, C->h_fam.ptr, C->status.ptr,
+                                  C->h_status.ptr, A, own->dev_b, pl->d_row_off.ptr, d_ascii, C->codes.ptr,
+                                  C->seqlogq.ptr, C->cst.ptr, (const void*)st};
+            static_assert(sizeof ptrs / sizeof ptrs[0] <= sizeof key.p / sizeof key.p[0], "graph key");
+            memcpy(key.p, ptrs, sizeof ptrs);
+            const int64_t vals[] = {k, P, pl->n_rows, total_res, nnz_cap, grid, wpb, variant, f64_grid, f64 ? 1 : 0};
+            memcpy(key.v, vals, sizeof vals);
+            key.pb = Pb;
+            e = launch_graph(C, st, key, enqueue);
             if (e != cudaSuccess && cudaPeekAtLastError() == cudaSuccess) {
                 // the graph could not be built or launched (nothing ran): keep
                 // to plain launches on this device from now on
                 fprintf(stderr, "libqp: CUDA graph launch failed (%s); using plain launches\n",
                         cudaGetErrorName(e));
                 C->tune.graph = false;
+                timed = true;
                 e = enqueue();
             }
         } else {
+            timed = true;
             e = enqueue();
         }
+        cudaEventRecord(C->ev[4], st);
+        timed_call = timed;
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return bail(cuda_fail(e, "posterior stage"));
         memcpy(&hs, C->h_status.ptr, sizeof hs);
@@ -627,10 +683,8 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         if (hs.bad_residue)
             return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
         if (hs.stage_overflow) return bail(fail(QP_ECUDA, "internal: a row exceeded its entry capacity"));
-        if (!f64) {
-            float kms = 0.f;
-            if (cudaEventElapsedTime(&kms, C->ev[1], C->ev[2]) == cudaSuccess) C->tuner[tkey].record(cfg, kms);
-        }
+        if (!f64 && hs.t_f32[1] > hs.t_f32[0] && hs.t_f32[0] > 0)
+            C->tuner[tkey].record(cfg, 1e-6 * (double)(hs.t_f32[1] - hs.t_f32[0]));
         if (!hs.pool_overflow) break;
         if (attempt >= 2) return bail(fail(QP_ENOMEM, "the entry pool kept overflowing"));
         // grow the pool (and the result's entry part) to what was asked for, and run again
@@ -649,11 +703,22 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     r->nnz = nnz;
     r->n_fallback = f64 ? 0 : hs.n_fallback;
     for (int i = 0; i < 10; ++i) r->guard_info[i] = hs.diag[i];
-    float ms = 0;
-    cudaEventElapsedTime(&ms, C->ev[1], C->ev[2]); r->kernel_ms[0] = ms;
-    cudaEventElapsedTime(&ms, C->ev[2], C->ev[3]); r->kernel_ms[1] = ms;
-    cudaEventElapsedTime(&ms, C->ev[3], C->ev[4]); r->kernel_ms[2] = ms;
-    cudaEventElapsedTime(&ms, C->ev[0], C->ev[4]); r->kernel_ms[3] = ms;
+    // device time of the FP32 and FP64 kernels (their own time stamps), of
+    // everything else, and of the whole call (events around it)
+    auto span = [](const unsigned long long* t) {
+        return (t[0] > 0 && t[1] > t[0]) ? 1e-6 * (double)(t[1] - t[0]) : 0.0;
+    };
+    float ms = 0, k32 = 0, k64 = 0;
+    cudaEventElapsedTime(&ms, C->ev[0], C->ev[4]);
+    r->kernel_ms[0] = span(hs.t_f32);
+    r->kernel_ms[1] = span(hs.t_f64);
+    if (timed_call && cudaEventElapsedTime(&k32, C->ev[1], C->ev[2]) == cudaSuccess &&
+        cudaEventElapsedTime(&k64, C->ev[2], C->ev[3]) == cudaSuccess) {
+        r->kernel_ms[0] = k32;
+        r->kernel_ms[1] = k64;
+    }
+    r->kernel_ms[3] = ms;
+    r->kernel_ms[2] = std::max(0.0, (double)ms - r->kernel_ms[0] - r->kernel_ms[1]);
     if (!out_on_device) {
         int rc = to_host(r, st);
         if (rc != QP_OK) { qp_result_free(r); return rc; }
@@ -662,16 +727,22 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     return QP_OK;
 }
 
-// Runs the enqueue function as one CUDA graph on stream st: the sequence is
-// captured, the context's executable graph is updated in place when the
-// topology is unchanged (new pointers and sizes only), else instantiated anew,
-// and launched.  A stream that is already capturing gets the plain sequence.
-cudaError_t launch_graph(Context* C, cudaStream_t st, const std::function<cudaError_t()>& enqueue) {
+// Runs the enqueue function as one CUDA graph on stream st.  When the key
+// (every pointer, size and launch shape the sequence uses) equals the one of
+// the context's executable graph, that graph is relaunched as it is.  Else the
+// sequence is captured, the executable graph is updated in place when the
+// topology is unchanged, or instantiated anew, and launched.  A stream that is
+// already capturing gets the plain sequence.
+cudaError_t launch_graph(Context* C, cudaStream_t st, const GraphKey& key,
+                         const std::function<cudaError_t()>& enqueue) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
         cudaGetLastError();
         return enqueue();
     }
+    if (C->gexec && C->gkey_valid && memcmp(&key, &C->gkey, sizeof key) == 0)
+        return cudaGraphLaunch(C->gexec, st);
+    C->gkey_valid = false;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t ee = enqueue();
@@ -699,6 +770,8 @@ cudaError_t launch_graph(Context* C, cudaStream_t st, const std::function<cudaEr
         }
     }
     cudaGraphDestroy(g);
+    C->gkey = key;
+    C->gkey_valid = true;
     return cudaGraphLaunch(C->gexec, st);
 }
 
@@ -739,8 +812,17 @@ int to_host(qp_result* r, cudaStream_t st) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { free(h); return cuda_fail(e, "copy result to host"); }
-    if (own->dev_a) cudaFreeAsync(own->dev_a, st);
-    if (own->dev_b) cudaFreeAsync(own->dev_b, st);
+    if (own->dev_a || own->dev_b) {
+        int rc = QP_OK;
+        Context* C = get_context(own->device, &rc);
+        if (C) {
+            C->give_block(own->dev_a, own->bytes_a);
+            C->give_block(own->dev_b, own->bytes_b);
+        } else {
+            if (own->dev_a) cudaFreeAsync(own->dev_a, st);
+            if (own->dev_b) cudaFreeAsync(own->dev_b, st);
+        }
+    }
     own->dev_a = own->dev_b = nullptr;
     own->host = h;
     own->on_device = false;
@@ -757,9 +839,13 @@ void free_result(qp_result* r) {
             cudaGetDevice(&cur);
             cudaSetDevice(own->device);
             Context* C = get_context(own->device, &rc);
-            cudaStream_t s = C ? C->stream : nullptr;
-            if (own->dev_a) cudaFreeAsync(own->dev_a, s);
-            if (own->dev_b) cudaFreeAsync(own->dev_b, s);
+            if (C) {
+                C->give_block(own->dev_a, own->bytes_a);
+                C->give_block(own->dev_b, own->bytes_b);
+            } else {
+                if (own->dev_a) cudaFreeAsync(own->dev_a, nullptr);
+                if (own->dev_b) cudaFreeAsync(own->dev_b, nullptr);
+            }
             cudaSetDevice(cur);
         }
         free(own->host);

@@ -105,6 +105,13 @@ struct TuneEntry {
 unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, int warps_per_block,
                          const LaunchOverride& t);
 
+// Identity of a captured call sequence (see launch_graph).
+struct GraphKey {
+    const void* p[16];
+    int64_t v[16];
+    qpk::Problem pb;
+};
+
 struct Context {
     int device = 0;
     int sm_count = 0;
@@ -114,6 +121,15 @@ struct Context {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[6] = {};
     cudaGraphExec_t gexec = nullptr;     // the last captured call sequence
+    GraphKey gkey;                       // what it was captured with
+    bool gkey_valid = false;
+    // result blocks freed by the caller, kept for the next call of the same
+    // shape (same addresses: the captured graph is relaunched as it is)
+    std::mutex spare_mu;
+    std::multimap<size_t, void*> spare;
+    size_t spare_bytes = 0;
+    cudaError_t take_block(void** p, size_t bytes, cudaStream_t st);
+    void give_block(void* p, size_t bytes);
     std::mutex mu;
     std::vector<std::shared_ptr<Plan>> plans;
     // workspace (grow-only)
@@ -166,6 +182,7 @@ struct ResultOwner {
     bool on_device = true;
     void* dev_a = nullptr;   // fixed-size part (ResultLayout)
     void* dev_b = nullptr;   // col / val part
+    size_t bytes_a = 0, bytes_b = 0;   // sizes when the blocks may be kept for reuse (else 0)
     void* host = nullptr;
 };
 
@@ -187,7 +204,8 @@ Context* get_context(int device, int* status);
 int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
                qp_result** out);
 int to_host(qp_result* r, cudaStream_t st);
-cudaError_t launch_graph(Context* C, cudaStream_t st, const std::function<cudaError_t()>& enqueue);
+cudaError_t launch_graph(Context* C, cudaStream_t st, const GraphKey& key,
+                         const std::function<cudaError_t()>& enqueue);
 constexpr int kF64FollowGrid = 16;      // CTAs of the FP64 follow-up of an FP32 call
 void free_result(qp_result* r);
 

@@ -51,6 +51,10 @@ struct Status {
     int32_t work_f64;
     int32_t pad[2];
     int32_t diag[16];               // first guard event: site, strip, step, lane, exponents, m, n
+    // device time stamps (ns, %globaltimer): first block start and last block
+    // end of the FP32 and of the FP64 kernel (0: did not run)
+    unsigned long long t_f32[2];
+    unsigned long long t_f64[2];
 };
 
 // Scalar coefficients passed by value (they live in the constant bank).

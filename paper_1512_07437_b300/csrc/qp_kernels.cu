@@ -228,6 +228,22 @@ __device__ __forceinline__ void publish_progress(volatile long long* w, long lon
     *w = v;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Kernel time stamps without events (they also work inside a CUDA graph):
+// the first block to start sets ts[0], every block raises ts[1] at its end.
+__device__ __forceinline__ void stamp_begin(unsigned long long* ts) {
+    if (threadIdx.x == 0) atomicCAS(&ts[0], 0ull, global_ns());
+}
+__device__ __forceinline__ void stamp_end(unsigned long long* ts) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&ts[1], global_ns());
+}
+
 constexpr float kBig = 1.2676506002282294e30f;   // 2^100
 constexpr int kNoExp = (int)0x80000000;           // "no exponent yet" in the fill scan
 
@@ -943,6 +959,7 @@ __device__ __forceinline__ void group_sync(int gib, int W) {
 template <int MINB, bool CKPT, int W>
 __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     extern __shared__ __align__(16) unsigned char s_raw[];
+    stamp_begin(Pb.status->t_f32);
     float2* s_ow = (float2*)s_raw;
     for (int i = threadIdx.x; i < kTab * kTab; i += blockDim.x) s_ow[i] = Pb.cst->ow[i];
     const int lane = threadIdx.x & 31;
@@ -1152,6 +1169,7 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
         }
         group_sync(gib, W);
     }
+    stamp_end(Pb.status->t_f32);
 }
 
 using F32Kernel = void (*)(Problem);
@@ -1247,6 +1265,7 @@ __device__ int block_sum(int v, int* red) {
 }
 
 __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
+    stamp_begin(Pb.status->t_f64);
     __shared__ double sred[2][kF64Threads / 32];
     __shared__ int ired[kF64Threads / 32];
     __shared__ int s_q;
@@ -1501,6 +1520,7 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
         }
         __syncthreads();
     }
+    stamp_end(Pb.status->t_f64);
 }
 
 int posterior_f64_occupancy(int* blocks_per_sm) {
