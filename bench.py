@@ -75,10 +75,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1512_07437_b300 import dist as qd
+    return qd.env()
 
 
 class ClockSampler:
@@ -224,10 +222,12 @@ def run_reference(args, fam, prm, rank):
 
 
 def run_serving(args, rank, world, local):
-    """--config c4: the serving loop under Poisson arrivals."""
+    """--config c4: the serving loop under Poisson arrivals (one trace per rank)."""
     import torch
     import paper_1512_07437_b300 as qp
+    from paper_1512_07437_b300 import dist as qd
     torch.cuda.set_device(local)
+    qd.init()
     dev = torch.device("cuda", local)
     prm = synth.default_params(threshold=0.01)
     trace = synth.make_serving_trace(seed=4 + 1000 * rank)
@@ -294,7 +294,10 @@ def run_serving(args, rank, world, local):
     wall = nonlocal_state["t_last"] - t0
     st = srv.stats()
     srv.destroy()
-    cells = nonlocal_state["cells"]
+    cells_rank = nonlocal_state["cells"]
+    # whole job: cells of all ranks over the slowest rank's wall time
+    cells = qd.sum_over_ranks(cells_rank)
+    wall = qd.max_over_ranks(wall)
     kernel_ms = st["kernel_ms"] - st0["kernel_ms"]
     n_f32 = st["launches_f32"] - st0["launches_f32"]
     n_f64 = st["launches_f64"] - st0["launches_f64"]
@@ -312,7 +315,7 @@ def run_serving(args, rank, world, local):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = float(clocks["sm_max_mhz"] or 2032.0)
     peak_tops = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
-    achieved = cells * ALU_OPS_PER_CELL / (kernel_ms * 1e-3) / 1e12
+    achieved = cells_rank * ALU_OPS_PER_CELL / (kernel_ms * 1e-3) / 1e12
     line = {
         "metric": "posterior-stage GCUPS and p50/p99 family latency (serving)",
         "value": value, "unit": "GCUPS", "n_gpus": world, "steps": 1, "warmup": len(warm),
@@ -327,7 +330,7 @@ def run_serving(args, rank, world, local):
                    "max_families_per_launch": st["max_families_per_launch"]},
         "latency_ms": {"p50": q(0.50), "p99": q(0.99), "max": lat_s[-1], "min": lat_s[0]},
         "latency_ms_by_k": by_k,
-        "busy_gcups": cells / (kernel_ms * 1e-3) / 1e9,
+        "busy_gcups": cells_rank / (kernel_ms * 1e-3) / 1e9,
         "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(sum(f.k * f.k * 4 for _, f in trace)),
                 "what": "families submitted from host memory at their arrival times; distance "
@@ -341,6 +344,7 @@ def run_serving(args, rank, world, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    qd.finalize()
 
 
 def f64_plain(qp, torch, fam, prm, local, stream, steps=3):
@@ -375,17 +379,17 @@ def main():
                           key=lambda f: f.cells())
             return run_reference(args, fams[len(fams) // 2], synth.default_params(), rank)
         return run_serving(args, rank, world, local)
-    fam = synth.make_family(args.config, args.seed)
+    from paper_1512_07437_b300 import dist as qd
+    # every rank works on its own family of the configuration (weak scaling)
+    fam = synth.make_family(args.config, qd.rank_seed(args.seed, rank))
     prm = synth.default_params(threshold=0.01, precision=args.precision)
     if args.impl == "reference":
         return run_reference(args, fam, prm, rank)
 
     import torch
     import paper_1512_07437_b300 as qp
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    qd.init()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     cells = fam.cells()
@@ -402,9 +406,7 @@ def main():
         step_dev().free()
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    barrier = qd.barrier
 
     # ---- device-resident timing
     times, kms, launches, fallbacks, nnz = [], [], 0, 0, 0
@@ -430,12 +432,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     ms = statistics.mean(times)
-    t_tot = sum(times) / 1e3
-    if world > 1:
-        t = torch.tensor([t_tot], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_tot = float(t.item())
-    value = cells * args.steps * world / t_tot / 1e9
+    # whole job: cells of all ranks over the slowest rank's timed region
+    value = qd.whole_job_rate(cells * args.steps, sum(times) / 1e3) / 1e9
 
     # ---- end to end through the public API: residues from pinned host memory,
     # the CSR stays on the device (the next stages consume it there), the MEA
@@ -453,7 +451,7 @@ def main():
         torch.cuda.current_stream(dev).synchronize()
         e2e_times.append(time.perf_counter() - t0)
         r.free()
-    e2e_val = cells * world / statistics.mean(e2e_times) / 1e9
+    e2e_val = qd.whole_job_rate(cells * len(e2e_times), sum(e2e_times)) / 1e9
     h2d = int(fam.residues.nbytes + fam.offsets.nbytes)
     d2h = int(h_dist.numel() * 4)
 
@@ -517,8 +515,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline(fam, prm, args.cpu_sample_s)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    qd.finalize()
 
 
 if __name__ == "__main__":
