@@ -409,6 +409,7 @@ def main():
     barrier = qd.barrier
 
     # ---- device-resident timing
+    cnt0 = {k: qp.qp_get_counter(k, device=local) for k in ("graph_captures", "graph_relaunches", "plain_calls")}
     times, kms, launches, fallbacks, nnz = [], [], 0, 0, 0
     barrier()
     torch.cuda.synchronize()
@@ -431,6 +432,7 @@ def main():
             r.free()
     torch.cuda.synchronize()
     barrier()
+    graph_calls = {k: qp.qp_get_counter(k, device=local) - v for k, v in cnt0.items()}
     ms = statistics.mean(times)
     # whole job: cells of all ranks over the slowest rank's timed region
     value = qd.whole_job_rate(cells * args.steps, sum(times) / 1e3) / 1e9
@@ -498,6 +500,7 @@ def main():
                 "d2h_bytes_per_step": d2h,
                 "what": "host residues -> device; CSR kept on device; distance matrix -> host"},
         "gpu_launches": launches,
+        "graph_calls_in_timed_region": graph_calls,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tissue/s",
                      "frac": achieved / peak_tops, "traffic": traffic,
                      "kernel": "k_posterior_f32" if args.precision == "f32" else "k_posterior_f64",

@@ -259,6 +259,13 @@ void qp_server_destroy(qp_server* server);
  * QP_EINVAL for an unknown name or device. */
 int qp_set_option(int32_t device, const char* name, int64_t value);
 
+/* Counters of qp_posteriors calls on one device (no counterpart in the
+ * paper): "graph_captures" (calls that captured their sequence as a new CUDA
+ * graph), "graph_relaunches" (calls that relaunched the cached graph as it
+ * was), "plain_calls" (calls with plain launches).  QP_EINVAL for an unknown
+ * name or device. */
+int qp_get_counter(int32_t device, const char* name, int64_t* value);
+
 /* Allocation-free variant for callers that cannot allocate device memory.
  * There is no counterpart in the paper: it exists for code that must not call
  * cudaMalloc / cudaFree while it runs -- for instance a host program whose

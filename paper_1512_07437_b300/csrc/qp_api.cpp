@@ -672,6 +672,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             }
         } else {
             timed = true;
+            ++C->plain_calls;
             e = enqueue();
         }
         cudaEventRecord(C->ev[4], st);
@@ -740,9 +741,12 @@ cudaError_t launch_graph(Context* C, cudaStream_t st, const GraphKey& key,
         cudaGetLastError();
         return enqueue();
     }
-    if (C->gexec && C->gkey_valid && memcmp(&key, &C->gkey, sizeof key) == 0)
+    if (C->gexec && C->gkey_valid && memcmp(&key, &C->gkey, sizeof key) == 0) {
+        ++C->graph_relaunches;
         return cudaGraphLaunch(C->gexec, st);
+    }
     C->gkey_valid = false;
+    ++C->graph_captures;
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t ee = enqueue();
@@ -877,6 +881,24 @@ int qp_posteriors(const qp_family* family, const qp_params* params, int32_t out_
 }
 
 void qp_result_free(qp_result* result) { qph::free_result(result); }
+
+int qp_get_counter(int32_t device, const char* name, int64_t* value) {
+    using namespace qph;
+    if (!name || !value) return fail(QP_EINVAL, "name or value is NULL");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return fail(QP_ECUDA, "no CUDA device"); }
+    if (device < 0 || device >= ndev) return fail(QP_EINVAL, "device %d does not exist", device);
+    int rc = QP_OK;
+    Context* C = get_context(device, &rc);
+    if (!C) return rc;
+    std::lock_guard<std::mutex> g(C->mu);
+    const std::string n(name);
+    if (n == "graph_captures") *value = C->graph_captures;
+    else if (n == "graph_relaunches") *value = C->graph_relaunches;
+    else if (n == "plain_calls") *value = C->plain_calls;
+    else return fail(QP_EINVAL, "unknown counter '%s'", name);
+    return QP_OK;
+}
 
 int qp_set_option(int32_t device, const char* name, int64_t value) {
     using namespace qph;

@@ -123,6 +123,7 @@ struct Context {
     cudaGraphExec_t gexec = nullptr;     // the last captured call sequence
     GraphKey gkey;                       // what it was captured with
     bool gkey_valid = false;
+    int64_t graph_captures = 0, graph_relaunches = 0, plain_calls = 0;
     // result blocks freed by the caller, kept for the next call of the same
     // shape (same addresses: the captured graph is relaunched as it is)
     std::mutex spare_mu;

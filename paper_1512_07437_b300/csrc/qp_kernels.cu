@@ -24,6 +24,7 @@
 
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 
 #include <cstdio>
@@ -309,6 +310,24 @@ __host__ __device__ constexpr int warp_smem_bytes(int max_len) {
     return kD * kWarp * kRmax * 8 + kD * 32 + ((max_len + 2 * kYPad + 15) / 16) * 16;
 }
 
+// Runs steps 0 .. nsteps-1 of a strip: the steps t_a and t_b (-1: none) with
+// the corner-cell copy of the step, all others with the plain copy, which is
+// the only one inside the hot loop.
+template <class Step>
+__device__ __forceinline__ void run_steps(int nsteps, int t_a, int t_b, Step& step) {
+    int t = 0;
+    while (t < nsteps) {
+        int stop = nsteps;
+        if (t_a >= t && t_a < stop) stop = t_a;
+        if (t_b >= t && t_b < stop) stop = t_b;
+        for (; t < stop; ++t) step(t, std::false_type{});
+        if (t < nsteps) {
+            step(t, std::true_type{});
+            ++t;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- pass 1
 template <int R, bool SPEC, bool STORE>
 __device__ __forceinline__ void bwd_step(
@@ -461,7 +480,10 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
     // column residue of the lane, one step ahead (padded: no range check)
     auto ycode = [&](int j) { return (int)ws.sy[j + kYPad - 1]; };
     int yc = ycode(n + 31 - lane);
-    for (int t = 0; t < nsteps; ++t) {
+    // one step; SPEC: the step holds a corner cell (its own copy of the step,
+    // kept out of the loop below)
+    auto step = [&](int t, auto spec) {
+        constexpr bool SPEC = decltype(spec)::value;
         const int ph = t & (kC - 1);
         if (ph == 0) {
             wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag);
@@ -529,15 +551,11 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, const float2* __restri
         }
         const int yc_now = yc;
         yc = ycode(j - 1);
-        if (t == t_end || t == t_start)
-            bwd_step<R, true, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, DD, tV, tX2,
-                                     HB, BY2o, xo, dDD, cv, bst_strip, ebnd, bnd_out, eH, eP, Zh, Zp, eZh,
-                                     eZp, flag);
-        else
-            bwd_step<R, false, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, DD, tV, tX2,
-                                      HB, BY2o, xo, dDD, cv, bst_strip, ebnd, bnd_out, eH, eP, Zh, Zp, eZh,
-                                      eZp, flag);
-    }
+        bwd_step<R, SPEC, STORE>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, DD, tV, tX2,
+                                 HB, BY2o, xo, dDD, cv, bst_strip, ebnd, bnd_out, eH, eP, Zh, Zp, eZh, eZp,
+                                 flag);
+    };
+    run_steps(nsteps, t_start, t_end, step);
     cp_async_wait<0>();
     if (io.pub && lane == 0) publish_progress(io.pub, io.pub_tag | kStepsDone);
 }
@@ -768,7 +786,10 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     for (int t = 0; t < kD - 1; ++t) fetch(t);
     auto ycode = [&](int j) { return (int)ws.sy[j + kYPad - 1]; };
     int yc = ycode(-lane);
-    for (int t = 0; t < nsteps; ++t) {
+    // one step; SPEC: the step holds a corner cell (its own copy of the step,
+    // kept out of the loop below)
+    auto step = [&](int t, auto spec) {
+        constexpr bool SPEC = decltype(spec)::value;
         // column T of the row above is written at the writer's step T + 31 and
         // fetched here kD - 1 steps ahead: stay 16 + kD + 32 steps behind it
         if ((t & (kC - 1)) == 0) {
@@ -840,15 +861,11 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
         }
         const int yc_now = yc;
         yc = ycode(j + 1);
-        if (t == t_end || t == t_start)
-            fwd_step<R, true>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, MZ, lV, lX2, HY,
-                              Y2i, Aa, cnt, xo, uMZ, uA, cv, ps, scaleA, bs, ebnd, bnd_out, stg, cap, eH,
-                              eP, pmax, fo, flag);
-        else
-            fwd_step<R, false>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, MZ, lV, lX2, HY,
-                               Y2i, Aa, cnt, xo, uMZ, uA, cv, ps, scaleA, bs, ebnd, bnd_out, stg, cap, eH,
-                               eP, pmax, fo, flag);
-    }
+        fwd_step<R, SPEC>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, MZ, lV, lX2, HY, Y2i,
+                          Aa, cnt, xo, uMZ, uA, cv, ps, scaleA, bs, ebnd, bnd_out, stg, cap, eH, eP, pmax,
+                          fo, flag);
+    };
+    run_steps(nsteps, t_start, t_end, step);
     cp_async_wait<0>();
     if (io.pub && lane == 31) publish_progress(io.pub, io.pub_tag | kStepsDone);
     // ---- flush this strip's entries into the pool (row-major, columns ascending)

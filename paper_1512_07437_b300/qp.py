@@ -109,6 +109,8 @@ def lib():
         L.qp_server_cancel.restype = ctypes.c_int
         L.qp_set_option.argtypes = [ctypes.c_int32, ctypes.c_char_p, ctypes.c_int64]
         L.qp_set_option.restype = ctypes.c_int
+        L.qp_get_counter.argtypes = [ctypes.c_int32, ctypes.c_char_p, P(ctypes.c_int64)]
+        L.qp_get_counter.restype = ctypes.c_int
         L.qp_server_get_stats.argtypes = [ctypes.c_void_p, P(qp_server_stats)]
         L.qp_server_get_stats.restype = ctypes.c_int
         L.qp_server_destroy.argtypes = [ctypes.c_void_p]
@@ -315,6 +317,13 @@ def qp_pair_posteriors_static(residues, m: int, n: int, params, row_ptr, col, va
 
 def qp_result_free(result: Result):
     result.free()
+
+
+def qp_get_counter(name: str, device: int = 0) -> int:
+    """Call counter of a device (qp_get_counter in qp.h)."""
+    v = ctypes.c_int64(0)
+    _check(lib().qp_get_counter(int(device), name.encode(), ctypes.byref(v)))
+    return int(v.value)
 
 
 def qp_set_option(name: str, value: int, device: int = 0):
