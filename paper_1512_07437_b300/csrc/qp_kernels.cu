@@ -310,6 +310,16 @@ __host__ __device__ constexpr int warp_smem_bytes(int max_len) {
     return kD * kWarp * kRmax * 8 + kD * 32 + ((max_len + 2 * kYPad + 15) / 16) * 16;
 }
 
+// Predicated stores without a branch: the address is only used when p holds.
+__device__ __forceinline__ void st_pred_v4(bool p, float4* a, float x, float y, float z, float w) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.global.v4.f32 [%1], {%2, %3, %4, %5};\n\t}"
+                 ::"r"((int)p), "l"(a), "f"(x), "f"(y), "f"(z), "f"(w));
+}
+__device__ __forceinline__ void st_pred_v2i(bool p, int2* a, int x, int y) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.global.v2.s32 [%1], {%2, %3};\n\t}"
+                 ::"r"((int)p), "l"(a), "r"(x), "r"(y));
+}
+
 // Runs steps 0 .. nsteps-1 of a strip: the steps t_a and t_b (-1: none) with
 // the corner-cell copy of the step, all others with the plain copy, which is
 // the only one inside the hot loop.
@@ -396,9 +406,11 @@ __device__ __forceinline__ void bwd_step(
         HB[r] = nH; BY2o[r] = BY2;
         if (r == 0) { tV = nV; tX2 = BX2; }
     }
-    if (lane == 0 && act && bnd_out) {
-        bnd_out[2 * j] = make_float4(DD[0].x, DD[0].y, tV.x, tV.y);
-        bnd_out[2 * j + 1] = make_float4(tX2, 0.f, __int_as_float(eH), __int_as_float(eP));
+    {
+        const bool wr = (lane == 0) && act && (bnd_out != nullptr);
+        float4* q = bnd_out + 2 * j;
+        st_pred_v4(wr, q, DD[0].x, DD[0].y, tV.x, tV.y);
+        st_pred_v4(wr, q + 1, tX2, 0.f, __int_as_float(eH), __int_as_float(eP));
     }
 }
 
@@ -654,19 +666,22 @@ __device__ __forceinline__ void fwd_step(
         MZ[r] = nMZ; HY[r] = nH; Y2i[r] = nY2; Aa[r] = nA;
         if (r == R - 1) { lV = nV; lX2 = nX2; }
     }
-    // entries at or above the threshold are rare: one vote per step
+    // entries at or above the threshold: one vote per step (long rows have
+    // few), then a predicated store per row without a branch
     if (__any_sync(FULL, any)) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (Pv[r] >= cf.theta) {
-                const int q = cnt[r]++;
-                if (q < cap) stg[(lane * R + r) * cap + q] = make_int2(j - 1, __float_as_int(Pv[r]));
-            }
+            const bool keep = Pv[r] >= cf.theta;
+            const int q = cnt[r];
+            st_pred_v2i(keep && q < cap, stg + ((lane * R + r) * cap + q), j - 1, __float_as_int(Pv[r]));
+            cnt[r] = q + (keep ? 1 : 0);
         }
     }
-    if (lane == 31 && act && bnd_out) {
-        bnd_out[2 * j] = make_float4(MZ[R - 1].x, MZ[R - 1].y, lV.x, lV.y);
-        bnd_out[2 * j + 1] = make_float4(lX2, __int_as_float(Aa[R - 1]), __int_as_float(eH), __int_as_float(eP));
+    {
+        const bool wr = (lane == 31) && act && (bnd_out != nullptr);
+        float4* q = bnd_out + 2 * j;
+        st_pred_v4(wr, q, MZ[R - 1].x, MZ[R - 1].y, lV.x, lV.y);
+        st_pred_v4(wr, q + 1, lX2, __int_as_float(Aa[R - 1]), __int_as_float(eH), __int_as_float(eP));
     }
 }
 
