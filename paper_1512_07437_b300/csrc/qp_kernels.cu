@@ -630,7 +630,7 @@ __device__ __forceinline__ void fwd_step(
         float2 nMZ = __ffma2_rn(cf.k_close, __fadd2_rn(V, H), __fmul2_rn(cf.k_mm, F));
         nMZ.x = fmaf(cf.c2, FX2 + FY2, nMZ.x);
         // posteriors of the cell and their combination
-        const float2 Pq2 = __fmul2_rn(__fmul2_rn(F, ps), bs[r]);
+        const float2 Pq2 = __fmul2_rn(__fmul2_rn(F, ps), bs[(r >> 1) * 2 * kWarp + (r & 1)]);
         float P;
         if (cf.combine == 0) {
             const float2 sq = __fmul2_rn(Pq2, Pq2);
@@ -765,23 +765,20 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
     // boundary row column T
     const bool streams = (lane == 0) && (bnd_in != nullptr);
     const float2* bst_lane = bst_strip + lane * R;
-    float2* ring_lane = ws.ring_b + lane * R;
+    // ring slot layout: the lane's values of rows 2h, 2h+1 (16 bytes) at
+    // h * 64 + lane * 2 (float2 units), so that the 16-byte reads of
+    // consecutive lanes hit consecutive banks; one row: lane * 1
+    float2* ring_lane = ws.ring_b + (R == 1 ? lane : lane * 2);
     auto fetch = [&](int T) {
         // the block of step T exists for this lane when 0 <= T - lane <= n
         const bool ok = (unsigned)(T - lane) <= (unsigned)n;
         const float2* src = ok ? bst_lane + T * (kWarp * R) : bst_lane;
         float2* dst = ring_lane + (T & (kD - 1)) * (kWarp * kRmax);
-        if (R == 8) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cp_async16(dst + 2 * q, src + 2 * q, ok ? 16 : 0);
-        } else if (R == 4) {
-            cp_async16(dst, src, ok ? 16 : 0);
-            cp_async16(dst + 2, src + 2, ok ? 16 : 0);
-        } else if (R == 2) {
-            cp_async16(dst, src, ok ? 16 : 0);
+        if (R == 1) {
+            cp_async8(dst, src, ok ? 8 : 0);
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) cp_async8(dst + r, src + r, ok ? 8 : 0);
+            for (int h = 0; h < R / 2; ++h) cp_async16(dst + h * 2 * kWarp, src + 2 * h, ok ? 16 : 0);
         }
         if (streams) {
             const bool okb = (T < nsteps) && T <= n;
@@ -813,7 +810,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
         }
         fetch(t + kD - 1);
         cp_async_wait<kD - 1>();
-        const float2* bs = ws.ring_b + (t & (kD - 1)) * (kWarp * kRmax) + lane * R;
+        const float2* bs = ws.ring_b + (t & (kD - 1)) * (kWarp * kRmax) + (R == 1 ? lane : lane * 2);
         const float4* ebnd = ws.ring_e + 2 * (streams ? (t & (kD - 1)) : 0);
         const int j = t - lane;
         const bool act = (j >= 0) && (j <= n);
