@@ -529,12 +529,17 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         const int64_t want = f64 ? std::min<int64_t>(P, (int64_t)C->sm_count * C->f64_blocks_per_sm)
                                  : std::min<int64_t>(std::min<int64_t>(P, kF64FollowGrid),
                                                      std::max<int64_t>(2, ((int64_t)1 << 30) / per_cta));
-        f64_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, budget / per_cta));
-        if ((e = C->d_b.ensure(sizeof(double2) * db * f64_grid)) != cudaSuccess ||
+        // sequences so long that one CTA's FP64 scratch exceeds the budget get
+        // no follow-up (a pair that would need it makes the call fail below)
+        f64_grid = (int)std::min<int64_t>(want, budget / per_cta);
+        if (f64 && f64_grid < 1)
+            return fail(QP_ENOMEM, "the FP64 form needs %lld bytes per pair at length %d, more than the scratch "
+                        "budget %lld", (long long)per_cta, pl->max_len, (long long)budget);
+        if (f64_grid > 0 && ((e = C->d_b.ensure(sizeof(double2) * db * f64_grid)) != cudaSuccess ||
             (e = C->d_diag.ensure(sizeof(double) * 3 * qpk::kNS * L * f64_grid)) != cudaSuccess ||
             (e = C->d_cnt.ensure(sizeof(int32_t) * (5 * L + 8) * f64_grid)) != cudaSuccess ||
             (e = C->d_stg.ensure(sizeof(int2) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess ||
-            (e = C->d_stg64.ensure(sizeof(double) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess)
+            (e = C->d_stg64.ensure(sizeof(double) * (int64_t)pl->max_len * cap * f64_grid)) != cudaSuccess))
             return fail(QP_ENOMEM, "FP64 scratch allocation failed");
         Pb.d_b = (double2*)C->d_b.ptr; Pb.d_b_stride = db;
         Pb.d_diag = (double*)C->d_diag.ptr; Pb.d_diag_stride = 3 * qpk::kNS * L;
@@ -630,7 +635,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             if (timed) cudaEventRecord(C->ev[1], st);
             if (!f64 && (x = qpk::launch_posterior_f32(Pb, (int)grid, wpb, st, variant)) != cudaSuccess) return x;
             if (timed) cudaEventRecord(C->ev[2], st);
-            if ((x = qpk::launch_posterior_f64(Pb, f64_grid, st)) != cudaSuccess) return x;
+            if (f64_grid > 0 && (x = qpk::launch_posterior_f64(Pb, f64_grid, st)) != cudaSuccess) return x;
             if (timed) cudaEventRecord(C->ev[3], st);
             if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, probe.pair_nnz_off, st)) != cudaSuccess ||
                 (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
@@ -684,6 +689,9 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         if (hs.bad_residue)
             return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
         if (hs.stage_overflow) return bail(fail(QP_ECUDA, "internal: a row exceeded its entry capacity"));
+        if (!f64 && f64_grid == 0 && hs.n_fallback > 0)
+            return bail(fail(QP_ENOMEM, "%d pair(s) tripped an FP32 range guard and need the FP64 form, whose "
+                             "scratch at length %d exceeds the budget", hs.n_fallback, pl->max_len));
         if (!f64 && hs.t_f32[1] > hs.t_f32[0] && hs.t_f32[0] > 0)
             C->tuner[tkey].record(cfg, 1e-6 * (double)(hs.t_f32[1] - hs.t_f32[0]));
         if (!hs.pool_overflow) break;

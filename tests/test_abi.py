@@ -52,6 +52,8 @@ def test_struct_layout_matches_header(libqp):
     # pi..score: 5+4+400+20+5+400 doubles, 3 doubles, 2 ints, 1 double, 2 ints, 1 pointer
     assert ctypes.sizeof(q.qp_params) == 8 * (5 + 4 + 400 + 20 + 5 + 400 + 3) + 8 + 8 + 8 + 8
     assert ctypes.sizeof(q.qp_result) == 4 * 4 + 8 * 3 + 8 * 12 + 8 * 4 + 8 + 4 * 12 + 8
+    # 4 counters, pairs, cells, 2 launch counts, kernel ms, 4 int32, 2 byte counts
+    assert ctypes.sizeof(q.qp_server_stats) == 8 * 4 + 8 + 8 + 8 * 2 + 8 + 4 * 4 + 8 * 2
 
 
 def test_no_device_fails_loudly(libqp):
@@ -85,6 +87,10 @@ def test_invalid_inputs_rejected_on_host(libqp):
         with pytest.raises(qp.QpError) as e:
             qp.qp_posteriors(fam.residues, fam.offsets, bad)
         assert e.value.code == 1, field
+    long_res = np.full((1 << 20) + 11, ord("A"), dtype=np.uint8)     # one sequence over 2^20
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_posteriors(long_res, np.array([0, 10, long_res.size]), prm)
+    assert e.value.code == 1
     bad = prm.replace(pi=np.array([0.5, 0.1, 0.1, 0.1, 0.1]))
     with pytest.raises(qp.QpError) as e:
         qp.qp_posteriors(fam.residues, fam.offsets, bad)

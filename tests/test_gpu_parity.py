@@ -361,3 +361,20 @@ def test_warps_per_pair_equal_one(qp, wpp, ckpt):
     finally:
         qp.qp_set_option("wpp", 0)
         qp.qp_set_option("ckpt", -1)
+
+
+def test_long_pair_without_fp64_scratch(qp):
+    """A scratch budget below one FP64 CTA's need (here 32 MiB against 36 MiB
+    for length 1500) leaves the FP64 follow-up out; pairs that stay in FP32
+    give the same result as with it."""
+    fam = synth.star_family(47, 2, (1450, 1500), 0.3)
+    prm = synth.default_params(threshold=0.01)
+    ref = _run(qp, fam, prm)
+    try:
+        qp.qp_set_option("scratch_bytes", 32 << 20)
+        small = _run(qp, fam, prm)
+    finally:
+        qp.qp_set_option("scratch_bytes", 0)
+    _no_fallback(ref)
+    _no_fallback(small)
+    _same_csr(ref, small)
