@@ -105,6 +105,10 @@ struct TuneEntry {
 unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, int warps_per_block,
                          const LaunchOverride& t);
 
+// Grid of the persistent FP32 kernel for blocks_needed blocks of work: at most
+// blocks_per_sm per SM, and a multiple of the SM count once it exceeds it.
+int64_t balanced_grid(int sm_count, int blocks_per_sm, int64_t blocks_needed);
+
 // Identity of a captured call sequence (see launch_graph).
 struct GraphKey {
     const void* p[16];

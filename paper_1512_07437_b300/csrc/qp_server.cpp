@@ -583,9 +583,7 @@ bool issue(qp_server* S) {
     int bps = 0;
     qpk::posterior_f32_occupancy(kWpb, S->scratch_len, &bps, R.variant, S->ckpt, W);
     bps = std::max(1, std::min(bps, S->bps[R.variant]));
-    int64_t grid = (int64_t)S->ctx->sm_count * bps;
-    grid = std::min<int64_t>(grid, ((int64_t)n_items * W + kWpb - 1) / kWpb);
-    grid = std::max<int64_t>(grid, 1);
+    int64_t grid = balanced_grid(S->ctx->sm_count, bps, ((int64_t)n_items * W + kWpb - 1) / kWpb);
     grid = std::min<int64_t>(grid, S->scratch_warps / kWpb);
     const qpk::Problem Pb = base_problem(S, R, n_items, W);
     cudaEventRecord(R.ev0, S->cs);
