@@ -238,8 +238,8 @@ void qp_server_destroy(qp_server* server);
 /* Launch knobs of the FP32 kernel on one device, for benchmarks and tests
  * (no counterpart in the paper).  value -1 (or 0 for the sizes) restores the
  * automatic choice.  Names:
- *   "variant"         0: 4 blocks of 4 warps per SM (at most 128 registers),
- *                     1: 3 blocks of 4 warps per SM;
+ *   "variant"         0: at most 128 registers a thread (16 warps per SM),
+ *                     1: at most 168 registers (12 warps per SM);
  *   "ckpt"            0: stored form (pass 1 keeps the backward values of the
  *                     whole matrix), 1: checkpointed form (pass 1 keeps one
  *                     boundary row per 128-row strip; pass 2 recomputes each
@@ -250,7 +250,8 @@ void qp_server_destroy(qp_server* server);
  *                     tries 2 when pairs are too few to fill the grid;
  *   "graph"           1 (default): run each call as one captured CUDA graph;
  *                     0: plain launches;
- *   "blocks_per_sm", "warps_per_block";
+ *   "blocks_per_sm", "warps_per_block" (default 2 for qp_posteriors, 4 in
+ *                     a server);
  *   "scratch_bytes"   device bytes the kernels' scratch may take (default:
  *                     45% of free memory, at most 48 GiB); the stored form is
  *                     chosen while it fits a full grid, else the checkpointed

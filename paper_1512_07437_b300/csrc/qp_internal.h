@@ -140,8 +140,8 @@ cudaError_t launch_setup(const RawParams* host_raw, RawParams* d_raw, Consts* de
 cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
                           const int64_t* seq_off, int32_t k, double* seq_logq,
                           const Consts* cst, Status* status, cudaStream_t s);
-// variant: 0 = 4 blocks of 4 warps per SM (<= 128 registers),
-//          1 = 3 blocks of 4 warps per SM (no register cap below 168);
+// variant: 0 = at most 128 registers a thread (16 warps per SM),
+//          1 = at most 168 registers a thread (12 warps per SM);
 // P.ckpt picks the stored or the checkpointed form.
 constexpr int kF32Variants = 2;
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block,
