@@ -184,3 +184,46 @@ def pairs(family, pair_list, prm, threads: int | None = None, theta: float | Non
         raise MemoryError("oracle: out of memory")
     return dict(logz_hmm=logz[0::2].copy(), logz_pf=logz[1::2].copy(), mea=mea,
                 dist=dist, nnz=nnz, threads=threads)
+
+
+def guide_tree(dist) -> dict:
+    """Guide tree by weighted UPGMA (paper, Methods, stage II: the pairwise
+    distances of stage I feed weighted UPGMA, after Sneath and Sokal).
+
+    Weighted UPGMA (WPGMA): repeatedly join the two clusters at the smallest
+    distance; the distance from the joined cluster to any other cluster is
+    the mean of the distances from its two parts, whatever their sizes.
+    Clusters live in slots 0..k-1 (slot i starts as leaf i); joining the
+    clusters in slots i < j puts the new cluster in slot i and empties slot j.
+    Ties: the smallest distance, then the smallest i, then the smallest j.
+    Leaves have ids 0..k-1, the cluster formed at step s has id k + s.
+
+    Returns merges (k-1, 2) int32 (ids joined at each step) and heights
+    (k-1,) float64 (half the joining distance).  Plain O(k^3) (a full
+    search of the live pairs at every step), FP64.
+    """
+    D = np.array(dist, dtype=np.float64)
+    k = D.shape[0]
+    if D.shape != (k, k) or k < 2:
+        raise ValueError("dist must be a k x k matrix with k >= 2")
+    alive = np.ones(k, dtype=bool)
+    cid = np.arange(k)
+    merges = np.zeros((k - 1, 2), dtype=np.int32)
+    heights = np.zeros(k - 1)
+    upper = np.triu(np.ones((k, k), dtype=bool), 1)
+    for s in range(k - 1):
+        # candidate pairs i < j among live slots; the first minimum in
+        # row-major order is the tie rule (smallest i, then smallest j)
+        cand = np.where(upper & alive[:, None] & alive[None, :], D, np.inf)
+        bi, bj = divmod(int(np.argmin(cand)), k)
+        best = cand[bi, bj]
+        merges[s] = (cid[bi], cid[bj])
+        heights[s] = best / 2.0
+        others = alive.copy()
+        others[bi] = others[bj] = False
+        v = (D[bi, others] + D[bj, others]) / 2.0
+        D[bi, others] = v
+        D[others, bi] = v
+        alive[bj] = False
+        cid[bi] = k + s
+    return dict(merges=merges, heights=heights)
