@@ -464,6 +464,22 @@ def main():
     h2d = int(fam.residues.nbytes + fam.offsets.nbytes)
     d2h = int(h_dist.numel() * 4)
 
+    # ---- guide tree (weighted UPGMA) on the stage's FP64 distance matrix,
+    # device to device, the step that consumes this stage's output
+    r = step_dev()
+    d64 = r.dist64.clone()
+    r.free()
+    tree_ms = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree = qp.qp_guide_tree(d64, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        tree_ms.append(e0.elapsed_time(e1))
+    tree_host = (tree[0].cpu().numpy(), tree[1].cpu().numpy())
+
     # ---- kernel time of k_posterior_f32 for the roofline: CUDA events around
     # the kernel on its stream, in a pass with plain launches (a captured graph
     # carries no events; the kernels' own time stamps from the timed region are
@@ -519,10 +535,20 @@ def main():
                      "ops_per_cell": ALU_OPS_PER_CELL},
         "clocks": clocks,
     }
+    line["guide_tree"] = {"k": fam.k, "ms": statistics.median(tree_ms[1:]),
+                          "kernels": "k_tree_mirror, k_tree_rows, k_tree_join",
+                          "what": "weighted UPGMA on the FP64 distance matrix, device in and out"}
     if args.precision == "f32" and args.config in ("c1", "c2"):
         line["f64_plain"] = f64_plain(qp, torch, fam, prm, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(fam, prm, args.cpu_sample_s)
+        import oracle
+        t0 = time.perf_counter()
+        ref_tree = oracle.guide_tree(d64.cpu().numpy())
+        line["cpu_baseline"]["guide_tree"] = {
+            "s": time.perf_counter() - t0, "kind": "oracle", "k": fam.k,
+            "identical": bool(np.array_equal(ref_tree["merges"], tree_host[0])
+                              and np.array_equal(ref_tree["heights"], tree_host[1]))}
     if rank == 0:
         print(json.dumps(line), flush=True)
     qd.finalize()

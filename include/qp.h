@@ -30,7 +30,9 @@
  *   Errors: every entry point returns a qp_status; qp_last_error() gives a
  *   thread-local message for the last failure on the calling thread.
  *   Streams: work is issued on params->stream (a cudaStream_t), or on a
- *   library-owned stream of params->device when it is NULL.  qp_posteriors
+ *   library-owned stream of params->device when it is NULL; that stream
+ *   first waits for all work issued so far to the legacy default stream,
+ *   so inputs written there are complete.  qp_posteriors
  *   returns after the results are complete on the device.
  */
 #ifndef QP_H
@@ -305,6 +307,37 @@ int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int32_t n,
                               const qp_params* params, int32_t* row_ptr, int32_t* col,
                               float* val, int64_t nnz_capacity, double* pair_out,
                               int64_t* nnz_out);
+
+/* Guide tree by weighted UPGMA (paper, Methods, stage II: the distances of
+ * stage I feed weighted UPGMA, after Sneath and Sokal).  Repeatedly joins the
+ * two clusters at the smallest distance; the distance from the joined cluster
+ * to any other is the mean of the distances from its two parts, whatever
+ * their sizes.  Clusters live in slots 0..k-1 (slot i starts as leaf i);
+ * joining slots i < j puts the new cluster in slot i and empties slot j.
+ * Ties: the smallest distance, then the smallest i, then the smallest j.
+ * Arithmetic is FP64; the result is bit-identical to any FP64 implementation
+ * of the same rule.
+ *   dist      : k x k row-major FP64 distances (for instance
+ *               qp_result.dist64); only the upper triangle (i < j) is read, so
+ *               the matrix is taken as symmetric.  HOST memory, or DEVICE
+ *               memory of `device` when on_device != 0.  Entries should be
+ *               finite (NaN gives a valid tree of unspecified shape).  Not
+ *               modified;
+ *   k         : 2 <= k <= 46340, else QP_EINVAL;
+ *   merges    : int32[(k - 1) * 2], the ids joined at step s; leaves are
+ *               0..k-1 and the cluster formed at step s has id k + s;
+ *   heights   : double[k - 1], half the joining distance of step s
+ *               (non-decreasing: weighted UPGMA has no inversions);
+ *   merges and heights are in the same memory as dist (host or device).
+ *   stream    : cudaStream_t to run on, or NULL for the library's stream
+ *               (ordered after the legacy default stream, as for
+ *               qp_posteriors).
+ * Device working memory: 8 k^2 bytes (plus 8 k^2 more for a host matrix),
+ * taken and released within the call.  Returns after the outputs are
+ * written.  QP_EINVAL for a bad k, NULL pointer or device; QP_ENOMEM when the
+ * working memory cannot be allocated; QP_ECUDA otherwise. */
+int qp_guide_tree(const double* dist, int32_t k, int32_t on_device, int32_t device, void* stream,
+                  int32_t* merges, double* heights);
 
 /* Thread-local message of the last failure on the calling thread. */
 const char* qp_last_error(void);

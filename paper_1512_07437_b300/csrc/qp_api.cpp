@@ -335,6 +335,8 @@ Context* get_context(int device, int* status) {
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) { *status = cuda_fail(e, "cudaEventCreate"); return nullptr; }
     }
+    e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) { *status = cuda_fail(e, "cudaEventCreate"); return nullptr; }
     int bps64 = 0;
     qpk::posterior_f64_occupancy(&bps64);
     c->f64_blocks_per_sm = std::max(1, std::min(bps64, 2));
@@ -347,6 +349,17 @@ Context* get_context(int device, int* status) {
     Context* raw = c.get();
     g_ctx[device] = std::move(c);
     return raw;
+}
+
+cudaError_t call_stream(Context* C, void* user, cudaStream_t* st) {
+    if (user) {
+        *st = (cudaStream_t)user;
+        return cudaSuccess;
+    }
+    *st = C->stream;
+    cudaError_t e = cudaEventRecord(C->ev_join, cudaStreamLegacy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(C->stream, C->ev_join, 0);
+    return e;
 }
 
 std::shared_ptr<Plan> Context::plan_for(int k, const int64_t* off, int* status) {
@@ -408,7 +421,8 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
                qp_result** out) {
     cudaError_t e;
     const int k = f->k;
-    cudaStream_t st = prm->stream ? (cudaStream_t)prm->stream : C->stream;
+    cudaStream_t st;
+    if ((e = call_stream(C, prm->stream, &st)) != cudaSuccess) return cuda_fail(e, "stream order");
     int status = QP_OK;
     auto pl = C->plan_for(k, f->offsets, &status);
     if (!pl) return status;
@@ -950,6 +964,8 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
         C->tune.warps_per_block = value > 0 ? (int)value : 0;
     } else if (n == "scratch_bytes") {
         C->tune.scratch_bytes = value > 0 ? value : 0;
+    } else if (n == "tree_smem") {
+        C->tune.tree_smem = value < 0 ? -1 : (value ? 1 : 0);
     } else {
         return fail(QP_EINVAL, "unknown option '%s'", name);
     }

@@ -62,6 +62,7 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int wpp = 0;                         // warps per pair (1, 2)
     bool graph = true;                   // run each call as one captured CUDA graph
     int64_t scratch_bytes = 0;           // budget of the FP32 / FP64 scratch
+    int tree_smem = -1;                  // guide tree slot state: 0 global memory, else shared when it fits
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the
@@ -123,6 +124,7 @@ struct Context {
     int f32_blocks_per_sm = 3;
     int f64_blocks_per_sm = 2;
     cudaStream_t stream = nullptr;
+    cudaEvent_t ev_join = nullptr;       // orders the library stream after the legacy default stream
     cudaEvent_t ev[6] = {};
     cudaGraphExec_t gexec = nullptr;     // the last captured call sequence
     GraphKey gkey;                       // what it was captured with
@@ -206,6 +208,10 @@ void make_coef(const qp_params* p, qpk::Coef* c);
 int row_capacity(const qp_params* p, int max_len);
 std::shared_ptr<Plan> build_plan(int k, const int64_t* off);
 Context* get_context(int device, int* status);
+// The stream a call runs on: the caller's, or when it is NULL the library's
+// stream, made to wait first for all work issued so far to the legacy
+// default stream (so inputs written there are complete).
+cudaError_t call_stream(Context* C, void* user, cudaStream_t* st);
 int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
                qp_result** out);
 int to_host(qp_result* r, cudaStream_t st);

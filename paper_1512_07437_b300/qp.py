@@ -120,6 +120,9 @@ def lib():
                                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                                 P(ctypes.c_int64)]
         L.qp_pair_posteriors_static.restype = ctypes.c_int
+        L.qp_guide_tree.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.qp_guide_tree.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -313,6 +316,44 @@ def qp_pair_posteriors_static(residues, m: int, n: int, params, row_ptr, col, va
         int(pair_out.data_ptr()), ctypes.byref(nnz))
     _check(rc)
     return int(nnz.value)
+
+
+def qp_guide_tree(dist, device: Optional[int] = None, stream=None):
+    """Weighted UPGMA guide tree (qp_guide_tree in qp.h).
+
+    ``dist`` is a k x k distance matrix (only i < j is read): a numpy array
+    (host; the outputs are numpy) or a CUDA tensor (device; the outputs are
+    CUDA tensors on its device, and the call runs on torch's current stream
+    unless ``stream`` is given).  Returns (merges int32 (k-1, 2), heights
+    float64 (k-1,)): the ids joined at step s (leaves 0..k-1, the cluster of
+    step s is k + s) and half the joining distance."""
+    if hasattr(dist, "is_cuda") and dist.is_cuda:
+        import torch
+        d = dist.to(torch.float64).contiguous()
+        if d.dim() != 2 or d.shape[0] != d.shape[1]:
+            raise ValueError("dist must be a square matrix")
+        k = int(d.shape[0])
+        dev = d.device.index if device is None else int(device)
+        merges = torch.empty((max(k - 1, 0), 2), dtype=torch.int32, device=d.device)
+        heights = torch.empty(max(k - 1, 0), dtype=torch.float64, device=d.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(d.device).cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        _check(lib().qp_guide_tree(int(d.data_ptr()), k, 1, dev, stream or None,
+                                   int(merges.data_ptr()), int(heights.data_ptr())))
+        return merges, heights
+    d = np.ascontiguousarray(dist, dtype=np.float64)
+    if d.ndim != 2 or d.shape[0] != d.shape[1]:
+        raise ValueError("dist must be a square matrix")
+    k = int(d.shape[0])
+    merges = np.zeros((max(k - 1, 0), 2), dtype=np.int32)
+    heights = np.zeros(max(k - 1, 0), dtype=np.float64)
+    if hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(lib().qp_guide_tree(d.ctypes.data, k, 0, 0 if device is None else int(device), stream or None,
+                               merges.ctypes.data, heights.ctypes.data))
+    return merges, heights
 
 
 def qp_result_free(result: Result):

@@ -97,6 +97,26 @@ def test_invalid_inputs_rejected_on_host(libqp):
     assert e.value.code == 1
 
 
+def test_guide_tree_rejects_bad_input_on_host(libqp):
+    """qp_guide_tree checks k and its pointers before touching a device, and
+    without a device it fails rather than computing on the CPU."""
+    import paper_1512_07437_b300 as qp
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_guide_tree(np.zeros((1, 1)))
+    assert e.value.code == 1
+    L = qp.lib()
+    m = np.zeros(4, dtype=np.int32)
+    h = np.zeros(2)
+    assert L.qp_guide_tree(None, 3, 0, 0, None, m.ctypes.data, h.ctypes.data) == 1
+    assert L.qp_guide_tree(np.zeros(9).ctypes.data, 46341, 0, 0, None, m.ctypes.data, h.ctypes.data) == 1
+    with pytest.raises(ValueError):
+        qp.qp_guide_tree(np.zeros((2, 3)))
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(qp.QpError):
+            qp.qp_guide_tree(np.ones((3, 3)))
+
+
 def test_server_without_device_fails_loudly(libqp):
     import torch
     if torch.cuda.is_available():

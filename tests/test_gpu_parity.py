@@ -378,3 +378,21 @@ def test_long_pair_without_fp64_scratch(qp):
     _no_fallback(ref)
     _no_fallback(small)
     _same_csr(ref, small)
+
+
+def test_null_stream_waits_for_the_default_stream(qp):
+    """With params.stream NULL the call runs on the library's stream, which
+    must first wait for the work queued on the legacy default stream: here
+    the device residues are written there behind a 0.1 s spin."""
+    import torch
+    fam = synth.star_family(5, 8, (100, 150), 0.3)
+    prm = synth.default_params()
+    ref = _run(qp, fam, prm)
+    src = torch.from_numpy(fam.residues).cuda()
+    dst = torch.zeros_like(src)
+    torch.cuda.synchronize()
+    torch.cuda._sleep(200_000_000)
+    dst.copy_(src)
+    got = qp.qp_posteriors(dst, fam.offsets, qp.make_params(prm, device=0))
+    assert np.array_equal(got.dist64, ref.dist64)
+    assert np.array_equal(got.mea, ref.mea)
