@@ -536,7 +536,8 @@ def main():
         "clocks": clocks,
     }
     line["guide_tree"] = {"k": fam.k, "ms": statistics.median(tree_ms[1:]),
-                          "kernels": "k_tree_mirror, k_tree_rows, k_tree_join",
+                          "kernels": "k_tree_cluster (k up to about 660), else k_tree_mirror, "
+                                     "k_tree_rows, k_tree_join",
                           "what": "weighted UPGMA on the FP64 distance matrix, device in and out"}
     if args.precision == "f32" and args.config in ("c1", "c2"):
         line["f64_plain"] = f64_plain(qp, torch, fam, prm, local, stream)

@@ -257,7 +257,15 @@ void qp_server_destroy(qp_server* server);
  *   "scratch_bytes"   device bytes the kernels' scratch may take (default:
  *                     45% of free memory, at most 48 GiB); the stored form is
  *                     chosen while it fits a full grid, else the checkpointed
- *                     form, on a grid cut to the budget if need be.
+ *                     form, on a grid cut to the budget if need be;
+ *   "tree_form"       qp_guide_tree: 2 the cluster form (matrix in the
+ *                     shared memory of a thread-block cluster; QP_EINVAL from
+ *                     qp_guide_tree when it does not fit), 1 one CTA with
+ *                     per-slot state in shared memory (k <= 8192), 0 one CTA
+ *                     with the state in global memory; automatic: the first
+ *                     that fits, in that order;
+ *   "tree_ctas"       qp_guide_tree cluster form: CTAs of the cluster (1, 2,
+ *                     4, 8 or 16; automatic: the fewest that fit).
  * Applies to later qp_posteriors calls and servers created afterwards.
  * QP_EINVAL for an unknown name or device. */
 int qp_set_option(int32_t device, const char* name, int64_t value);

@@ -964,8 +964,13 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
         C->tune.warps_per_block = value > 0 ? (int)value : 0;
     } else if (n == "scratch_bytes") {
         C->tune.scratch_bytes = value > 0 ? value : 0;
-    } else if (n == "tree_smem") {
-        C->tune.tree_smem = value < 0 ? -1 : (value ? 1 : 0);
+    } else if (n == "tree_form") {
+        if (value > 2) return fail(QP_EINVAL, "tree_form must be 0, 1, 2 or -1");
+        C->tune.tree_form = value < 0 ? -1 : (int)value;
+    } else if (n == "tree_ctas") {
+        if (value > 0 && (value > 16 || (value & (value - 1))))
+            return fail(QP_EINVAL, "tree_ctas must be 1, 2, 4, 8 or 16");
+        C->tune.tree_ctas = value > 0 ? (int)value : 0;
     } else {
         return fail(QP_EINVAL, "unknown option '%s'", name);
     }

@@ -62,7 +62,9 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int wpp = 0;                         // warps per pair (1, 2)
     bool graph = true;                   // run each call as one captured CUDA graph
     int64_t scratch_bytes = 0;           // budget of the FP32 / FP64 scratch
-    int tree_smem = -1;                  // guide tree slot state: 0 global memory, else shared when it fits
+    int tree_form = -1;                  // guide tree: 0 one CTA, state in global memory; 1 one CTA,
+                                         // state in shared memory; 2 cluster form; -1 automatic
+    int tree_ctas = 0;                   // guide tree cluster form: CTAs (1, 2, 4, 8, 16; 0 automatic)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the
@@ -144,6 +146,11 @@ struct Context {
     qpk::RawParams last_raw;             // parameters the tables in cst were derived from
     bool raw_valid = false;
     DevBuf row_cnt, chunk_off, pair_nnz, fallback, pool, pool64;
+    // guide tree: working memory kept between calls, pinned staging
+    std::mutex tree_mu;
+    DevBuf tree_ws;
+    HostBuf tree_h;
+    int tree_optin = 0;                  // shared memory a CTA may opt in to
     DevBuf bst, bex, bnd, bck, stg;
     DevBuf d_b, d_diag, d_cnt, d_stg, d_stg64;
     HostBuf h_status, h_off, h_fam;

@@ -26,14 +26,28 @@ def qp():
     return qp
 
 
-@pytest.fixture(params=["smem", "global"])
-def state(qp, request):
-    """Where k_tree_join keeps its per-slot state: shared memory (the default
-    up to k = 8192) or global memory (the form above that), forced here at
-    sizes the oracle finishes."""
-    qp.qp_set_option("tree_smem", 1 if request.param == "smem" else 0)
+FORMS = {"auto": (-1, 0), "cluster16": (2, 16), "cluster4": (2, 4), "smem": (1, 0), "global": (0, 0)}
+
+
+@pytest.fixture(params=list(FORMS))
+def form(qp, request):
+    """The form of the kernel: automatic (the cluster form up to k of about
+    660), the cluster form forced onto 16 or 4 CTAs, or one CTA with its
+    per-slot state in shared or global memory -- each forced here at sizes
+    the oracle finishes."""
+    f, ctas = FORMS[request.param]
+    qp.qp_set_option("tree_form", f)
+    qp.qp_set_option("tree_ctas", ctas)
     yield request.param
-    qp.qp_set_option("tree_smem", -1)
+    qp.qp_set_option("tree_form", -1)
+    qp.qp_set_option("tree_ctas", 0)
+
+
+def _fits_cluster(form, k):
+    """Whether a forced cluster form holds k slots (rows of a slab x k x 8
+    bytes within one CTA's shared memory)."""
+    n = {"cluster16": 16, "cluster4": 4}.get(form)
+    return n is None or -(-k // n) * (k + (k & 1)) * 8 + 16 * k < 220 * 1024
 
 
 def _sym(rng, k, levels=None):
@@ -58,14 +72,18 @@ def test_hand_example_and_tie_rule(qp):
 
 
 @pytest.mark.parametrize("k", [2, 3, 31, 33, 64, 257, 700])
-def test_random_matrix_bit_exact(qp, state, k):
+def test_random_matrix_bit_exact(qp, form, k):
+    if not _fits_cluster(form, k):
+        pytest.skip("the forced cluster form does not hold this k")
     D = _sym(np.random.default_rng(100 + k), k)
     _same(qp.qp_guide_tree(D), oracle.guide_tree(D))
 
 
 @pytest.mark.parametrize("k,levels", [(300, 3), (129, 1), (500, 8)])
-def test_ties_bit_exact(qp, state, k, levels):
+def test_ties_bit_exact(qp, form, k, levels):
     """Few distinct values: most steps choose among equal distances."""
+    if not _fits_cluster(form, k):
+        pytest.skip("the forced cluster form does not hold this k")
     D = _sym(np.random.default_rng(k * levels), k, levels)
     _same(qp.qp_guide_tree(D), oracle.guide_tree(D))
 
@@ -93,7 +111,7 @@ def test_device_input_equals_host_input(qp):
     assert np.array_equal(ms.cpu().numpy(), mh) and np.array_equal(hs.cpu().numpy(), hh)
 
 
-def test_distances_of_the_posterior_stage(qp, state):
+def test_distances_of_the_posterior_stage(qp, form):
     """The matrix the posterior stage produces (dist64 of a 64-sequence
     family of 200-400 residues) in device memory, as the pipeline passes it."""
     fam = synth.star_family(41, 64, (200, 400), 0.4)
@@ -175,13 +193,15 @@ def _device_line_ultrametric(k, seed):
 
 
 @pytest.mark.parametrize("k", [1100, 9000, 46340])
-def test_line_ultrametric_any_size(qp, state, k):
+def test_line_ultrametric_any_size(qp, form, k):
     """Sizes the oracle cannot finish, up to the k limit (a 17 GB matrix):
     the closed-form tree of a line ultrametric, exactly.  k = 1100 is also
     checked against the oracle to tie the closed form to it."""
     import torch
-    if state == "smem" and k > 8192:
+    if form == "smem" and k > 8192:
         pytest.skip("above 8192 slots the state is always in global memory")
+    if not _fits_cluster(form, k):
+        pytest.skip("the forced cluster form does not hold this k")
     D, pos, gap_pos = _device_line_ultrametric(k, seed=k)
     m, h = qp.qp_guide_tree(D)
     m, h = m.cpu().numpy(), h.cpu().numpy()
