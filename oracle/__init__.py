@@ -158,6 +158,27 @@ def sparsify(P: np.ndarray, theta: float):
     return row_ptr, cols.astype(np.int64), P[rows, cols]
 
 
+def budget_threshold(values, theta: float, n_keep: int, dtype=np.float32):
+    """Threshold of the entry budget (paper, Methods, "Other algorithmic
+    improvements": the posterior matrices are fitted into a user-given amount
+    of memory by lowering the sparsity coefficient, i.e. keeping fewer
+    entries).
+
+    ``values``: every entry kept at threshold ``theta`` (all >= theta), taken
+    in the precision the entries are compared in (``dtype``).  ``n_keep``: the
+    entries the budget holds.  Returns the smallest threshold t >= theta in
+    that precision with count(values >= t) <= n_keep: theta itself when the
+    entries already fit, else the next representable value above the
+    (n_keep + 1)-th largest value (all entries equal to it are dropped).
+    """
+    v = np.asarray(values, dtype=dtype).ravel()
+    t0 = dtype(theta)
+    if v.size <= n_keep:
+        return t0
+    largest_first = np.sort(v)[::-1]
+    return np.nextafter(largest_first[n_keep], dtype(np.inf))
+
+
 def pairs(family, pair_list, prm, threads: int | None = None, theta: float | None = None) -> dict:
     """Per-pair log Z (HMM, PF), MEA score, distance and nnz for the listed
     pairs of ``family``, on a thread pool of ``threads`` host cores."""
