@@ -82,7 +82,18 @@ typedef struct qp_family {
  *   combine: QP_COMBINE_*.  threshold: keep P >= threshold, 0 < threshold <= 1.
  *   precision: QP_F32_SCALED (FP32 recurrences with power-of-two rescaling,
  *   FP64 totals) or QP_F64_PLAIN (FP64 recurrences, one CTA per pair).
- *   device: CUDA ordinal.  stream: cudaStream_t or NULL. */
+ *   device: CUDA ordinal.  stream: cudaStream_t or NULL.
+ *   entry_budget: bytes the sparse entries of all pairs may take (col + val,
+ *   plus val64 for QP_F64_PLAIN: 8 or 16 bytes an entry); 0 = no budget.  When
+ *   the entries at `threshold` exceed it, the threshold is raised to the
+ *   smallest value whose entries fit (paper, Methods, "Other algorithmic
+ *   improvements": the posterior matrices are fitted into a given amount of
+ *   memory by lowering the sparsity coefficient).  That value, one unit in the
+ *   last place above the (N+1)-th largest entry (N = entry_budget / bytes an
+ *   entry), in the precision the entries are compared in, is reported as
+ *   qp_result.threshold_used; entries equal to the (N+1)-th are all dropped.
+ *   Must be >= 0.  Servers reject it (QP_EINVAL) and
+ *   qp_pair_posteriors_static ignores it. */
 typedef struct qp_params {
     double pi[5];
     double delta1, eps1, delta2, eps2;
@@ -97,6 +108,7 @@ typedef struct qp_params {
     int32_t precision;
     int32_t device;
     void* stream;
+    int64_t entry_budget;
 } qp_params;
 
 /* Results.  When on_device, every pointer is device memory of the call's
@@ -129,7 +141,11 @@ typedef struct qp_params {
  *   guard_info[12]            : the first FP32 range-guard event of the call
  *                              (site, strip, step, lane, HMM exponent and its
  *                              neighbour's, PF exponent and its neighbour's,
- *                              m, n), all zero when no guard fired. */
+ *                              m, n), all zero when no guard fired;
+ *   threshold_used            : the threshold the entries were kept at, in
+ *                              the precision they were compared in (float
+ *                              for QP_F32_SCALED): params.threshold, or the
+ *                              raised one when params.entry_budget applied. */
 typedef struct qp_result {
     int32_t k;
     int32_t on_device;
@@ -153,6 +169,7 @@ typedef struct qp_result {
     double kernel_ms[4];
     int64_t n_fallback;
     int32_t guard_info[12];
+    double threshold_used;
     void* owner_;            /* library bookkeeping; do not touch */
 } qp_result;
 

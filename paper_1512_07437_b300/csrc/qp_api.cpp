@@ -125,6 +125,7 @@ int validate_params(const qp_params* p) {
     if (!(p->threshold > 0.0 && p->threshold <= 1.0)) return fail(QP_EINVAL, "threshold must be in (0, 1]");
     if (p->precision != QP_F32_SCALED && p->precision != QP_F64_PLAIN)
         return fail(QP_EINVAL, "precision must be QP_F32_SCALED or QP_F64_PLAIN");
+    if (p->entry_budget < 0) return fail(QP_EINVAL, "entry_budget must be >= 0");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "cudaGetDeviceCount"); }
@@ -628,9 +629,26 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     memset(&hs, 0, sizeof hs);
     int64_t nnz = 0;
     bool timed_call = false;
+    // entry budget: the full CSR goes to scratch, a select finds the raised
+    // threshold and a filter writes the result (at most n_keep entries)
+    const bool ebudget = prm->entry_budget > 0;
+    const int64_t n_keep = ebudget ? prm->entry_budget / (f64 ? 16 : 8) : 0;
+    auto nnz_cap_of = [&]() { return ebudget ? std::min<int64_t>(C->pool_cap, n_keep) : C->pool_cap; };
+    if (ebudget &&
+        ((e = C->bud_rp.ensure(sizeof(int32_t) * pl->n_rows)) != cudaSuccess ||
+         (e = C->bud_off.ensure(sizeof(int64_t) * (P + 1))) != cudaSuccess ||
+         (e = C->bud_nnz.ensure(sizeof(int64_t) * P)) != cudaSuccess ||
+         (e = C->bud_state.ensure(sizeof(qpk::SelectState))) != cudaSuccess ||
+         (e = C->bud_hist.ensure(sizeof(unsigned) * qpk::kBudgetBins)) != cudaSuccess))
+        return bail(fail(QP_ENOMEM, "entry budget scratch allocation failed"));
     for (int attempt = 0;; ++attempt) {
         if (own->dev_b) { C->give_block(own->dev_b, own->bytes_b); own->dev_b = nullptr; }
-        const int64_t nnz_cap = C->pool_cap;
+        if (ebudget &&
+            ((e = C->bud_col.ensure(sizeof(int32_t) * C->pool_cap)) != cudaSuccess ||
+             (e = C->bud_val.ensure(sizeof(float) * C->pool_cap)) != cudaSuccess ||
+             (f64 && (e = C->bud_val64.ensure(sizeof(double) * C->pool_cap)) != cudaSuccess)))
+            return bail(fail(QP_ENOMEM, "entry budget scratch allocation failed"));
+        const int64_t nnz_cap = nnz_cap_of();
         own->bytes_b = std::max<size_t>(ResultLayout::entry_bytes(nnz_cap, f64), 256);
         e = C->take_block(&own->dev_b, own->bytes_b, st);
         if (e != cudaSuccess) return bail(fail(QP_ENOMEM, "result allocation failed"));
@@ -663,11 +681,36 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             if (timed) cudaEventRecord(C->ev[2], st);
             if (f64_grid > 0 && (x = qpk::launch_posterior_f64(Pb, f64_grid, st)) != cudaSuccess) return x;
             if (timed) cudaEventRecord(C->ev[3], st);
-            if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, probe.pair_nnz_off, st)) != cudaSuccess ||
-                (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
-                                         fd.chunk_off, Pb.pool, Pb.pool64, P, probe.pair_nnz_off, probe.row_ptr,
-                                         probe.col, probe.val, probe.val64, st)) != cudaSuccess)
-                return x;
+            if (!ebudget) {
+                if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, probe.pair_nnz_off, st)) != cudaSuccess ||
+                    (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
+                                             fd.chunk_off, Pb.pool, Pb.pool64, P, probe.pair_nnz_off, probe.row_ptr,
+                                             probe.col, probe.val, probe.val64, st)) != cudaSuccess)
+                    return x;
+            } else {
+                int64_t* b_off = (int64_t*)C->bud_off.ptr;
+                int32_t* b_rp = (int32_t*)C->bud_rp.ptr;
+                int32_t* b_col = (int32_t*)C->bud_col.ptr;
+                float* b_val = (float*)C->bud_val.ptr;
+                double* b_val64 = f64 ? (double*)C->bud_val64.ptr : nullptr;
+                qpk::SelectState* sel = (qpk::SelectState*)C->bud_state.ptr;
+                if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, b_off, st)) != cudaSuccess ||
+                    (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
+                                             fd.chunk_off, Pb.pool, Pb.pool64, P, b_off, b_rp, b_col, b_val,
+                                             b_val64, st)) != cudaSuccess ||
+                    (x = qpk::launch_budget_select(b_off + P, n_keep, prm->threshold, f64, b_val, b_val64, sel,
+                                                   (unsigned*)C->bud_hist.ptr, d_status, 4 * C->sm_count, st)) !=
+                        cudaSuccess ||
+                    (x = qpk::launch_budget_count(fd.pairs, fd.seq_off, fd.pair_row_off, b_off, b_rp, b_val,
+                                                  b_val64, sel, P, probe.row_ptr, (int64_t*)C->bud_nnz.ptr, st)) !=
+                        cudaSuccess ||
+                    (x = qpk::launch_scan_nnz((const int64_t*)C->bud_nnz.ptr, P, probe.pair_nnz_off, st)) !=
+                        cudaSuccess ||
+                    (x = qpk::launch_budget_copy(fd.pairs, fd.seq_off, fd.pair_row_off, b_off, b_rp, b_col, b_val,
+                                                 b_val64, sel, P, probe.pair_nnz_off, probe.row_ptr, probe.col,
+                                                 probe.val, probe.val64, nnz_cap, st)) != cudaSuccess)
+                    return x;
+            }
             char* hs_p = (char*)C->h_status.ptr;
             if ((x = cudaMemcpyAsync(hs_p, C->status.ptr, sizeof(qpk::Status), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
                 (x = cudaMemcpyAsync(hs_p + sizeof(qpk::Status), probe.pair_nnz_off + P, sizeof(int64_t),
@@ -685,10 +728,13 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             memset(&key, 0, sizeof key);
             const void* ptrs[] = {C->off.ptr, C->h_off.ptr, C->fam.ptr, C->h_fam.ptr, C->status.ptr,
                                   C->h_status.ptr, A, own->dev_b, pl->d_row_off.ptr, d_ascii, C->codes.ptr,
-                                  C->seqlogq.ptr, C->cst.ptr, (const void*)st};
+                                  C->seqlogq.ptr, C->cst.ptr, (const void*)st, C->bud_rp.ptr, C->bud_off.ptr,
+                                  C->bud_col.ptr, C->bud_val.ptr, C->bud_val64.ptr, C->bud_nnz.ptr,
+                                  C->bud_state.ptr, C->bud_hist.ptr};
             static_assert(sizeof ptrs / sizeof ptrs[0] <= sizeof key.p / sizeof key.p[0], "graph key");
             memcpy(key.p, ptrs, sizeof ptrs);
-            const int64_t vals[] = {k, P, pl->n_rows, total_res, nnz_cap, grid, wpb, variant, f64_grid, f64 ? 1 : 0};
+            const int64_t vals[] = {k, P, pl->n_rows, total_res, nnz_cap, grid, wpb, variant, f64_grid, f64 ? 1 : 0,
+                                    ebudget ? n_keep : -1};
             memcpy(key.v, vals, sizeof vals);
             key.pb = Pb;
             e = launch_graph(C, st, key, enqueue);
@@ -715,6 +761,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         if (hs.bad_residue)
             return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
         if (hs.stage_overflow) return bail(fail(QP_ECUDA, "internal: a row exceeded its entry capacity"));
+        if (hs.select_error) return bail(fail(QP_ECUDA, "internal: the entry budget's selection failed"));
         if (!f64 && f64_grid == 0 && hs.n_fallback > 0)
             return bail(fail(QP_ENOMEM, "%d pair(s) tripped an FP32 range guard and need the FP64 form, whose "
                              "scratch at length %d exceeds the budget", hs.n_fallback, pl->max_len));
@@ -734,8 +781,9 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
 
     qp_result* r = (qp_result*)calloc(1, sizeof(qp_result));
     if (!r) return bail(fail(QP_ENOMEM, "host allocation failed"));
-    fill_result(r, own, lay, k, P, pl->n_rows, C->pool_cap, f64, prm->precision, C->device);
+    fill_result(r, own, lay, k, P, pl->n_rows, nnz_cap_of(), f64, prm->precision, C->device);
     r->nnz = nnz;
+    r->threshold_used = ebudget ? hs.theta_used : (f64 ? prm->threshold : (double)(float)prm->threshold);
     r->n_fallback = f64 ? 0 : hs.n_fallback;
     for (int i = 0; i < 10; ++i) r->guard_info[i] = hs.diag[i];
     // device time of the FP32 and FP64 kernels (their own time stamps), of

@@ -114,7 +114,7 @@ int64_t balanced_grid(int sm_count, int blocks_per_sm, int64_t blocks_needed);
 
 // Identity of a captured call sequence (see launch_graph).
 struct GraphKey {
-    const void* p[16];
+    const void* p[24];
     int64_t v[16];
     qpk::Problem pb;
 };
@@ -153,6 +153,9 @@ struct Context {
     int tree_optin = 0;                  // shared memory a CTA may opt in to
     DevBuf bst, bex, bnd, bck, stg;
     DevBuf d_b, d_diag, d_cnt, d_stg, d_stg64;
+    // entry budget: the full CSR before the filter, per-pair counts after it,
+    // the select's state and histogram
+    DevBuf bud_rp, bud_off, bud_col, bud_val, bud_val64, bud_nnz, bud_state, bud_hist;
     HostBuf h_status, h_off, h_fam;
     int64_t pool_cap = 0;
     int64_t pool_hint = 0;

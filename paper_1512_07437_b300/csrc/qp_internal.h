@@ -55,6 +55,21 @@ struct Status {
     // end of the FP32 and of the FP64 kernel (0: did not run)
     unsigned long long t_f32[2];
     unsigned long long t_f64[2];
+    double theta_used;              // threshold the result was filtered at (entry budget)
+    int32_t select_error;           // the budget's radix select lost its rank (logic error)
+    int32_t pad2;
+};
+
+// State of the entry-budget selection (device memory; qp_budget.cu).
+struct SelectState {
+    unsigned long long prefix;      // high bits of the wanted key found so far
+    long long rank;                 // rank from the top (0-based) among keys with that prefix
+    long long total;                // entries at the call's threshold
+    double theta_d;                 // threshold applied by the filter (FP64 form)
+    float theta_f;                  // threshold applied by the filter (FP32 form)
+    int bits_done;
+    int active;                     // 1 while the entries exceed the budget
+    int f64;
 };
 
 // Scalar coefficients passed by value (they live in the constant bank).
@@ -178,6 +193,23 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const double* pool64, int64_t n_pairs, const int64_t* pair_nnz_off,
                            int32_t* row_ptr, int32_t* col, float* val, double* val64,
                            cudaStream_t s);
+// Entry budget (qp_budget.cu): the threshold that fits n_keep entries, from
+// the full CSR's values (total at *total); then the filtered row pointers and
+// counts, and the filtered entries.
+cudaError_t launch_budget_select(const int64_t* total, int64_t n_keep, double theta, bool f64, const float* val,
+                                 const double* val64, SelectState* s, unsigned* hist, Status* st, int grid,
+                                 cudaStream_t str);
+cudaError_t launch_budget_count(const int2* pairs, const int64_t* seq_off, const int64_t* pair_row_off,
+                                const int64_t* in_off, const int32_t* in_rowptr, const float* in_val,
+                                const double* in_val64, const SelectState* s, int64_t n_pairs, int32_t* out_rowptr,
+                                int64_t* out_nnz, cudaStream_t str);
+cudaError_t launch_budget_copy(const int2* pairs, const int64_t* seq_off, const int64_t* pair_row_off,
+                               const int64_t* in_off, const int32_t* in_rowptr, const int32_t* in_col,
+                               const float* in_val, const double* in_val64, const SelectState* s, int64_t n_pairs,
+                               const int64_t* out_off, const int32_t* out_rowptr, int32_t* out_col, float* out_val,
+                               double* out_val64, int64_t out_cap, cudaStream_t str);
+constexpr int kBudgetBins = 2048;            // histogram bins of the select (11-bit digits)
+
 cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,
                             cudaStream_t s);
 int posterior_f32_regs(int variant = 0, bool ckpt = false);

@@ -896,6 +896,8 @@ int qp_server_create(const qp_params* params, size_t mem_budget, int32_t out_on_
     if (!out) return fail(QP_EINVAL, "out is NULL");
     *out = nullptr;
     int rc = validate_params(params);
+    if (rc == QP_OK && params->entry_budget != 0)
+        rc = fail(QP_EINVAL, "entry_budget is not supported by a server (its memory budget admits families)");
     if (rc != QP_OK) return rc;
     if (params->precision != QP_F32_SCALED) return fail(QP_EINVAL, "the server runs the FP32 form only");
     if (mem_budget == 0) return fail(QP_EINVAL, "mem_budget must be > 0");

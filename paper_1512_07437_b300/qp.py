@@ -48,7 +48,7 @@ class qp_params(ctypes.Structure):
         ("end_gap_mode", ctypes.c_int32), ("combine", ctypes.c_int32),
         ("threshold", ctypes.c_double),
         ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-        ("stream", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p), ("entry_budget", ctypes.c_int64),
     ]
 
 
@@ -64,7 +64,8 @@ class qp_result(ctypes.Structure):
         ("mea", ctypes.c_void_p), ("log_z_hmm", ctypes.c_void_p),
         ("log_z_pf", ctypes.c_void_p), ("pair_flags", ctypes.c_void_p),
         ("kernel_ms", ctypes.c_double * 4), ("n_fallback", ctypes.c_int64),
-        ("guard_info", ctypes.c_int32 * 12), ("owner_", ctypes.c_void_p),
+        ("guard_info", ctypes.c_int32 * 12), ("threshold_used", ctypes.c_double),
+        ("owner_", ctypes.c_void_p),
     ]
 
 
@@ -141,8 +142,10 @@ def _check(rc: int):
 
 
 def make_params(prm, device: int = 0, stream=None, threshold: Optional[float] = None,
-                combine: Optional[str] = None, precision: Optional[str] = None) -> qp_params:
-    """qp_params from any object with the model fields (pi, delta1, ...)."""
+                combine: Optional[str] = None, precision: Optional[str] = None,
+                entry_budget: Optional[int] = None) -> qp_params:
+    """qp_params from any object with the model fields (pi, delta1, ...).
+    ``entry_budget``: bytes the sparse entries may take (0: no budget)."""
     p = qp_params()
     p.pi[:] = [float(v) for v in prm.pi]
     p.delta1, p.eps1 = float(prm.delta1), float(prm.eps1)
@@ -160,6 +163,7 @@ def make_params(prm, device: int = 0, stream=None, threshold: Optional[float] = 
     pr = precision if precision is not None else prm.precision
     p.precision = QP_PRECISION[pr] if isinstance(pr, str) else int(pr)
     p.device = int(device)
+    p.entry_budget = int(entry_budget if entry_budget is not None else getattr(prm, "entry_budget", 0))
     if stream is None:
         p.stream = None
     elif isinstance(stream, int):
@@ -227,6 +231,7 @@ class Result:
         self.kernel_ms = list(r.kernel_ms)
         self.n_fallback = r.n_fallback
         self.guard_info = list(r.guard_info)
+        self.threshold_used = r.threshold_used
         self.precision = r.precision
 
     def array(self, name):

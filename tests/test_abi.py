@@ -45,15 +45,33 @@ def test_build_targets_sm_103a_only():
     assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
-def test_struct_layout_matches_header(libqp):
-    """ctypes mirrors must match the C structs."""
+def test_struct_layout_matches_header(libqp, tmp_path):
+    """ctypes mirrors must match the C structs: every field offset and every
+    struct size as the C compiler lays out include/qp.h."""
+    import shutil
+    import subprocess
     import paper_1512_07437_b300.qp as q
-    assert ctypes.sizeof(q.qp_family) == 24
-    # pi..score: 5+4+400+20+5+400 doubles, 3 doubles, 2 ints, 1 double, 2 ints, 1 pointer
-    assert ctypes.sizeof(q.qp_params) == 8 * (5 + 4 + 400 + 20 + 5 + 400 + 3) + 8 + 8 + 8 + 8
-    assert ctypes.sizeof(q.qp_result) == 4 * 4 + 8 * 3 + 8 * 12 + 8 * 4 + 8 + 4 * 12 + 8
-    # 4 counters, pairs, cells, 2 launch counts, kernel ms, 4 int32, 2 byte counts
-    assert ctypes.sizeof(q.qp_server_stats) == 8 * 4 + 8 + 8 + 8 * 2 + 8 + 4 * 4 + 8 * 2
+    structs = [q.qp_family, q.qp_params, q.qp_result, q.qp_server_stats]
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qp.h"', 'int main(void) {']
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in st._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                              check=True).stdout.splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(out[name]) == ctypes.sizeof(st), name
+        for fname, _ in st._fields_:
+            assert int(out[f"{name}.{fname}"]) == getattr(st, fname).offset, f"{name}.{fname}"
 
 
 def test_no_device_fails_loudly(libqp):
