@@ -464,6 +464,40 @@ def main():
     h2d = int(fam.residues.nbytes + fam.offsets.nbytes)
     d2h = int(h_dist.numel() * 4)
 
+    # ---- entry budget: the same call with room for half of its entries (the
+    # threshold is raised until they fit); extra passes over the entries at
+    # the threshold T: the select reads the values twice (FP32 keys, 4 B; the
+    # bits all keys share are known from the compaction), the filter reads the
+    # values, then columns + values, and writes the kept N entries: about
+    # 20 B x T + 8 B x N
+    bpe = 8 if args.precision == "f32" else 16
+    budget_bytes = max(bpe, (int(nnz) * bpe) // 2)
+    params_b = qp.make_params(prm, device=local, stream=stream, entry_budget=budget_bytes)
+    for _ in range(3):
+        qp.qp_posteriors(d_res, fam.offsets, params_b, out_on_device=True).free()
+    b_times = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rb = qp.qp_posteriors(d_res, fam.offsets, params_b, out_on_device=True)
+        e1.record(stream)
+        e1.synchronize()
+        b_times.append(e0.elapsed_time(e1))
+        b_nnz, b_theta = int(rb.nnz), rb.threshold_used
+        rb.free()
+    b_ms = statistics.median(b_times)
+    extra_ms = b_ms - statistics.median(times)
+    extra_bytes = 20 * int(nnz) + 8 * b_nnz
+    entry_budget = {"budget_bytes": budget_bytes, "threshold": prm.threshold, "threshold_used": b_theta,
+                    "nnz": b_nnz, "nnz_unbudgeted": int(nnz), "ms_per_step": b_ms,
+                    "ms_per_step_unbudgeted": statistics.median(times), "extra_ms": extra_ms,
+                    "extra_bytes": extra_bytes,
+                    "extra_gbs": extra_bytes / (extra_ms * 1e-3) / 1e9 if extra_ms > 0 else None,
+                    "kernels": "k_sel_init, k_sel_hist (2 of 3 passes active), k_sel_pick, k_budget_count, "
+                               "k_scan_nnz, k_budget_copy (plus the compaction into scratch)"}
+
     # ---- guide tree (weighted UPGMA) on the stage's FP64 distance matrix,
     # device to device, the step that consumes this stage's output
     r = step_dev()
@@ -535,6 +569,7 @@ def main():
                      "ops_per_cell": ALU_OPS_PER_CELL},
         "clocks": clocks,
     }
+    line["entry_budget"] = entry_budget
     line["guide_tree"] = {"k": fam.k, "ms": statistics.median(tree_ms[1:]),
                           "kernels": "k_tree_cluster (k up to about 660), else k_tree_mirror, "
                                      "k_tree_rows, k_tree_join",

@@ -639,7 +639,8 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
          (e = C->bud_off.ensure(sizeof(int64_t) * (P + 1))) != cudaSuccess ||
          (e = C->bud_nnz.ensure(sizeof(int64_t) * P)) != cudaSuccess ||
          (e = C->bud_state.ensure(sizeof(qpk::SelectState))) != cudaSuccess ||
-         (e = C->bud_hist.ensure(sizeof(unsigned) * qpk::kBudgetBins)) != cudaSuccess))
+         (e = C->bud_hist.ensure(sizeof(unsigned) * qpk::kBudgetBins + 16)) != cudaSuccess ||
+         (e = qpk::prepare_budget_kernels()) != cudaSuccess))
         return bail(fail(QP_ENOMEM, "entry budget scratch allocation failed"));
     for (int attempt = 0;; ++attempt) {
         if (own->dev_b) { C->give_block(own->dev_b, own->bytes_b); own->dev_b = nullptr; }
@@ -694,13 +695,17 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
                 float* b_val = (float*)C->bud_val.ptr;
                 double* b_val64 = f64 ? (double*)C->bud_val64.ptr : nullptr;
                 qpk::SelectState* sel = (qpk::SelectState*)C->bud_state.ptr;
-                if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, b_off, st)) != cudaSuccess ||
+                unsigned* hist = (unsigned*)C->bud_hist.ptr;
+                // smallest and largest key, after the histogram
+                unsigned long long* minmax = (unsigned long long*)(hist + qpk::kBudgetBins);
+                if ((x = cudaMemsetAsync(minmax, 0xff, sizeof(unsigned long long), st)) != cudaSuccess ||
+                    (x = cudaMemsetAsync(minmax + 1, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+                    (x = qpk::launch_scan_nnz(fd.pair_nnz, P, b_off, st)) != cudaSuccess ||
                     (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
                                              fd.chunk_off, Pb.pool, Pb.pool64, P, b_off, b_rp, b_col, b_val,
-                                             b_val64, st)) != cudaSuccess ||
-                    (x = qpk::launch_budget_select(b_off + P, n_keep, prm->threshold, f64, b_val, b_val64, sel,
-                                                   (unsigned*)C->bud_hist.ptr, d_status, 4 * C->sm_count, st)) !=
-                        cudaSuccess ||
+                                             b_val64, st, minmax)) != cudaSuccess ||
+                    (x = qpk::launch_budget_select(b_off + P, n_keep, prm->threshold, f64, b_val, b_val64, minmax,
+                                                   sel, hist, d_status, 4 * C->sm_count, st)) != cudaSuccess ||
                     (x = qpk::launch_budget_count(fd.pairs, fd.seq_off, fd.pair_row_off, b_off, b_rp, b_val,
                                                   b_val64, sel, P, probe.row_ptr, (int64_t*)C->bud_nnz.ptr, st)) !=
                         cudaSuccess ||

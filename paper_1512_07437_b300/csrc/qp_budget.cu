@@ -10,9 +10,12 @@
 // are all dropped, so fewer than N may remain.
 //
 // The values are positive, so their bit patterns order like the values; the
-// (N+1)-th largest is found by a radix select on the bit patterns, 11 bits a
-// pass (3 passes for float, 6 for double), each pass a histogram of the keys
-// that share the bits found so far.  Every kernel reads its counts from
+// (N+1)-th largest is found by a radix select on the bit patterns.  The
+// compaction records the smallest and largest key; their common leading bits
+// are known before the first pass (for values in [theta, 1] that is the sign
+// and most of the exponent), and each pass resolves 14 more bits with a
+// histogram of the keys that share the bits found so far (2 passes for float
+// entries in practice, at most 3; at most 5 for double).  Every kernel reads its counts from
 // device memory, so the sequence needs no host decision (it runs inside the
 // captured call).  The filtered CSR is then written from the full one.
 #include "qp_internal.h"
@@ -22,8 +25,9 @@ namespace qpk {
 namespace {
 
 constexpr unsigned FULLM = 0xffffffffu;
-constexpr int kDigitBits = 11;
+constexpr int kDigitBits = 14;
 constexpr int kBins = 1 << kDigitBits;
+static_assert(kBins == kBudgetBins, "histogram size");
 
 template <typename K>
 __device__ __forceinline__ K key_at(const void* vals, int64_t i);
@@ -36,13 +40,18 @@ __device__ __forceinline__ unsigned long long key_at<unsigned long long>(const v
     return (unsigned long long)__double_as_longlong(((const double*)vals)[i]);
 }
 
-__global__ void k_sel_init(const int64_t* total, int64_t n_keep, double theta, int f64, SelectState* s,
-                           unsigned* hist, Status* st) {
+__global__ void k_sel_init(const int64_t* total, int64_t n_keep, double theta, int f64,
+                           const unsigned long long* minmax, SelectState* s, unsigned* hist, Status* st) {
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) hist[i] = 0;
     if (threadIdx.x == 0) {
         s->total = *total;
-        s->prefix = 0;
-        s->bits_done = 0;
+        // bits shared by every key: the smallest and the largest agree on them
+        const int KB = f64 ? 64 : 32;
+        const unsigned long long lo = minmax[0], hi = minmax[1];
+        int common = KB;
+        if (s->total > 0 && lo != hi) common = __clzll((long long)(lo ^ hi)) - (64 - KB);
+        s->prefix = (s->total > 0 && common > 0) ? (lo >> (KB - common)) : 0ull;
+        s->bits_done = s->total > 0 ? common : 0;
         s->rank = n_keep;                 // 0-based rank, from the top, of the (N+1)-th largest
         s->active = s->total > n_keep ? 1 : 0;
         s->theta_f = (float)theta;
@@ -55,9 +64,9 @@ __global__ void k_sel_init(const int64_t* total, int64_t n_keep, double theta, i
 // histogram of the next digit of the keys that carry the prefix found so far
 template <typename K>
 __global__ void k_sel_hist(const void* vals, const SelectState* s, unsigned* hist) {
-    __shared__ unsigned h[kBins];
-    if (!s->active) return;               // the same for every thread of the grid
+    extern __shared__ unsigned h[];                   // kBins counters (dynamic: 64 KB)
     constexpr int KB = (int)sizeof(K) * 8;
+    if (!s->active || s->bits_done >= KB) return;   // the same for every thread of the grid
     const int done = s->bits_done;
     const int dig = min(kDigitBits, KB - done);
     const int shift = KB - done - dig;
@@ -76,20 +85,45 @@ __global__ void k_sel_hist(const void* vals, const SelectState* s, unsigned* his
         if (h[b]) atomicAdd(&hist[b], h[b]);
 }
 
-// the digit whose bucket holds the wanted rank; after the last digit, the
+// writes the cut one unit above the found key
+template <typename K>
+__device__ __forceinline__ void write_cut(SelectState* s, Status* st, unsigned long long key) {
+    if (sizeof(K) == 4) {
+        const float t = __uint_as_float((uint32_t)key + 1u);
+        s->theta_f = t;
+        st->theta_used = (double)t;
+    } else {
+        const double t = __longlong_as_double((long long)(key + 1ull));
+        s->theta_d = t;
+        st->theta_used = t;
+    }
+}
+
+// the digit whose bucket holds the wanted rank (one block of 1024 threads,
+// 16 bins each, counted from the top bin); after the last digit, the
 // threshold one unit above the found key
 template <typename K>
-__global__ void k_sel_pick(SelectState* s, unsigned* hist, Status* st) {
-    if (!s->active || threadIdx.x >= 32) return;
+__global__ void __launch_bounds__(1024) k_sel_pick(SelectState* s, unsigned* hist, Status* st) {
     constexpr int KB = (int)sizeof(K) * 8;
-    const int lane = threadIdx.x;
+    __shared__ unsigned long long wsum[32];
+    __shared__ int found;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (!s->active) return;                       // the same for every thread
     const int done = s->bits_done;
+    if (done >= KB) {
+        // every bit is known (all keys of the bucket are equal): the cut, once
+        if (done == KB && tid == 0) {
+            s->bits_done = KB + 1;
+            write_cut<K>(s, st, s->prefix);
+        }
+        return;
+    }
     const int dig = min(kDigitBits, KB - done);
     const int nb = 1 << dig;
-    const int per = (nb + 31) / 32;       // bins a lane sums, counted from the top bin
+    const int per = (nb + 1023) / 1024;
     unsigned long long sum = 0;
     for (int q = 0; q < per; ++q) {
-        const int j = lane * per + q;
+        const int j = tid * per + q;
         if (j < nb) sum += hist[nb - 1 - j];
     }
     unsigned long long incl = sum;
@@ -98,52 +132,62 @@ __global__ void k_sel_pick(SelectState* s, unsigned* hist, Status* st) {
         const unsigned long long u = __shfl_up_sync(FULLM, incl, o);
         if (lane >= o) incl += u;
     }
-    const unsigned long long excl = incl - sum;
-    const unsigned long long rank = (unsigned long long)s->rank;
-    const unsigned who = __ballot_sync(FULLM, excl <= rank && rank < incl);
-    if (who == 0) {
-        // the counts do not hold the rank: a logic error, reported to the host
-        if (lane == 0) { st->select_error = 1; s->active = 0; }
-        return;
+    if (lane == 31) wsum[wid] = incl;
+    if (tid == 0) found = 0;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = wsum[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(FULLM, wi, o);
+            if (lane >= o) wi += u;
+        }
+        wsum[lane] = wi - w;                     // exclusive prefix of each warp
     }
-    const int l = __ffs(who) - 1;
-    int digit = -1;
-    unsigned long long left = 0;
-    if (lane == l) {
+    __syncthreads();
+    const unsigned long long excl = wsum[wid] + incl - sum;
+    const unsigned long long rank = (unsigned long long)s->rank;
+    if (excl <= rank && rank < excl + sum) {
+        // this thread's bins hold the rank (exactly one thread: the ranges tile)
         unsigned long long acc = excl;
         for (int q = 0; q < per; ++q) {
-            const int j = lane * per + q;
-            if (j >= nb) break;
+            const int j = tid * per + q;
             const unsigned c = hist[nb - 1 - j];
-            if (rank < acc + c) { digit = nb - 1 - j; left = rank - acc; break; }
+            if (rank < acc + c) {
+                const unsigned long long prefix = (s->prefix << dig) | (unsigned long long)(nb - 1 - j);
+                s->prefix = prefix;
+                s->rank = (long long)(rank - acc);
+                if (done + dig == KB) {
+                    // prefix is the (N+1)-th largest key: keep entries strictly above it
+                    s->bits_done = KB + 1;
+                    write_cut<K>(s, st, prefix);
+                } else {
+                    s->bits_done = done + dig;
+                }
+                found = 1;
+                break;
+            }
             acc += c;
         }
     }
-    __syncwarp();
-    for (int b = lane; b < kBins; b += 32) hist[b] = 0;   // ready for the next pass
-    if (lane == l) {
-        if (digit < 0) { st->select_error = 1; s->active = 0; return; }
-        const unsigned long long prefix = (s->prefix << dig) | (unsigned long long)digit;
-        s->prefix = prefix;
-        s->rank = (long long)left;
-        s->bits_done = done + dig;
-        if (done + dig == KB) {
-            // prefix is the (N+1)-th largest key: keep entries strictly above it
-            if (KB == 32) {
-                const float t = __uint_as_float((uint32_t)prefix + 1u);
-                s->theta_f = t;
-                st->theta_used = (double)t;
-            } else {
-                const double t = __longlong_as_double((long long)(prefix + 1ull));
-                s->theta_d = t;
-                st->theta_used = t;
-            }
-        }
+    __syncthreads();
+    for (int b = tid; b < kBins; b += 1024) hist[b] = 0;   // ready for the next pass
+    if (tid == 0 && !found) {
+        // the counts do not hold the rank: a logic error, reported to the host
+        st->select_error = 1;
+        s->active = 0;
     }
 }
 
-__device__ __forceinline__ bool kept(const float* val, const double* val64, int64_t i, const SelectState* s) {
-    return val64 ? val64[i] >= s->theta_d : val[i] >= s->theta_f;
+// thresholds read once per thread (the output stores could alias the state)
+struct Cut {
+    float f;
+    double d;
+    __device__ explicit Cut(const SelectState* s) : f(s->theta_f), d(s->theta_d) {}
+};
+
+__device__ __forceinline__ bool kept(const float* val, const double* val64, int64_t i, const Cut& t) {
+    return val64 ? val64[i] >= t.d : val[i] >= t.f;
 }
 
 // row pointers and entry count of every pair after the filter (warp per pair)
@@ -158,13 +202,15 @@ __global__ void k_budget_count(const int2* __restrict__ pairs, const int64_t* __
     const int2 ab = pairs[p];
     const int m = (int)(seq_off[ab.x + 1] - seq_off[ab.x]);
     const int64_t ro = pair_row_off[p], base = in_off[p];
+    const Cut cut(s);
+    // a lane per row (32 rows in flight), then a scan of the counts
     int carry = 0;
     for (int r0 = 0; r0 <= m; r0 += 32) {
         const int r = r0 + lane;
         int cnt = 0;
         if (r < m) {
             const int beg = in_rowptr[ro + r], end = in_rowptr[ro + r + 1];
-            for (int e = beg; e < end; ++e) cnt += kept(in_val, in_val64, base + e, s) ? 1 : 0;
+            for (int e = beg; e < end; ++e) cnt += kept(in_val, in_val64, base + e, cut) ? 1 : 0;
         }
         int incl = cnt;
 #pragma unroll
@@ -192,42 +238,49 @@ __global__ void k_budget_copy(const int2* __restrict__ pairs, const int64_t* __r
     const int2 ab = pairs[p];
     const int m = (int)(seq_off[ab.x + 1] - seq_off[ab.x]);
     const int64_t ro = pair_row_off[p], bin = in_off[p], bout = out_off[p];
-    const unsigned below = (1u << lane) - 1u;
-    for (int r = 0; r < m; ++r) {
+    const Cut cut(s);
+    // a lane per row (32 rows in flight), each writing its kept entries in order
+    for (int r = lane; r < m; r += 32) {
         const int beg = in_rowptr[ro + r], end = in_rowptr[ro + r + 1];
-        int64_t dst = bout + out_rowptr[ro + r];
-        for (int e0 = beg; e0 < end; e0 += 32) {
-            const int e = e0 + lane;
-            const bool keep = e < end && kept(in_val, in_val64, bin + e, s);
-            const unsigned mk = __ballot_sync(FULLM, keep);
-            const int64_t o = dst + __popc(mk & below);
-            if (keep && o < out_cap) {          // always, unless the select failed (reported)
+        int64_t o = bout + out_rowptr[ro + r];
+        for (int e = beg; e < end; ++e) {
+            if (!kept(in_val, in_val64, bin + e, cut)) continue;
+            if (o < out_cap) {                   // always, unless the select failed (reported)
                 out_col[o] = in_col[bin + e];
                 out_val[o] = in_val[bin + e];
                 if (out_val64) out_val64[o] = in_val64[bin + e];
             }
-            dst += __popc(mk);
+            ++o;
         }
     }
 }
 
 }  // namespace
 
+cudaError_t prepare_budget_kernels() {
+    const int hbytes = (int)(sizeof(unsigned) * kBins);
+    cudaError_t e = cudaFuncSetAttribute(k_sel_hist<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, hbytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sel_hist<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, hbytes);
+    return e;
+}
+
 cudaError_t launch_budget_select(const int64_t* total, int64_t n_keep, double theta, bool f64, const float* val,
-                                 const double* val64, SelectState* s, unsigned* hist, Status* st, int grid,
-                                 cudaStream_t str) {
-    k_sel_init<<<1, 256, 0, str>>>(total, n_keep, theta, f64 ? 1 : 0, s, hist, st);
-    if (f64) {
-        for (int pass = 0; pass < (64 + kDigitBits - 1) / kDigitBits; ++pass) {
-            k_sel_hist<unsigned long long><<<grid, 256, 0, str>>>(val64, s, hist);
-            k_sel_pick<unsigned long long><<<1, 32, 0, str>>>(s, hist, st);
-        }
-    } else {
-        for (int pass = 0; pass < (32 + kDigitBits - 1) / kDigitBits; ++pass) {
-            k_sel_hist<uint32_t><<<grid, 256, 0, str>>>(val, s, hist);
-            k_sel_pick<uint32_t><<<1, 32, 0, str>>>(s, hist, st);
-        }
+                                 const double* val64, const unsigned long long* minmax, SelectState* s,
+                                 unsigned* hist, Status* st, int grid, cudaStream_t str) {
+    // passes for the worst case (only the sign bit shared); a pass with
+    // nothing left to find returns at once, and one more pick writes the cut
+    k_sel_init<<<1, 256, 0, str>>>(total, n_keep, theta, f64 ? 1 : 0, minmax, s, hist, st);
+    const int passes = ((f64 ? 63 : 31) + kDigitBits - 1) / kDigitBits;
+    const size_t hbytes = sizeof(unsigned) * kBins;
+    for (int pass = 0; pass < passes; ++pass) {
+        if (f64) k_sel_hist<unsigned long long><<<grid, 256, hbytes, str>>>(val64, s, hist);
+        else k_sel_hist<uint32_t><<<grid, 256, hbytes, str>>>(val, s, hist);
+        if (f64) k_sel_pick<unsigned long long><<<1, 1024, 0, str>>>(s, hist, st);
+        else k_sel_pick<uint32_t><<<1, 1024, 0, str>>>(s, hist, st);
     }
+    if (f64) k_sel_pick<unsigned long long><<<1, 1024, 0, str>>>(s, hist, st);
+    else k_sel_pick<uint32_t><<<1, 1024, 0, str>>>(s, hist, st);
     return cudaGetLastError();
 }
 

@@ -192,13 +192,14 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const int32_t* row_cnt, const int64_t* chunk_off, const int2* pool,
                            const double* pool64, int64_t n_pairs, const int64_t* pair_nnz_off,
                            int32_t* row_ptr, int32_t* col, float* val, double* val64,
-                           cudaStream_t s);
+                           cudaStream_t s, unsigned long long* minmax = nullptr);
 // Entry budget (qp_budget.cu): the threshold that fits n_keep entries, from
 // the full CSR's values (total at *total); then the filtered row pointers and
 // counts, and the filtered entries.
+cudaError_t prepare_budget_kernels();       // before the first launch (not inside a capture)
 cudaError_t launch_budget_select(const int64_t* total, int64_t n_keep, double theta, bool f64, const float* val,
-                                 const double* val64, SelectState* s, unsigned* hist, Status* st, int grid,
-                                 cudaStream_t str);
+                                 const double* val64, const unsigned long long* minmax, SelectState* s,
+                                 unsigned* hist, Status* st, int grid, cudaStream_t str);
 cudaError_t launch_budget_count(const int2* pairs, const int64_t* seq_off, const int64_t* pair_row_off,
                                 const int64_t* in_off, const int32_t* in_rowptr, const float* in_val,
                                 const double* in_val64, const SelectState* s, int64_t n_pairs, int32_t* out_rowptr,
@@ -208,7 +209,7 @@ cudaError_t launch_budget_copy(const int2* pairs, const int64_t* seq_off, const 
                                const float* in_val, const double* in_val64, const SelectState* s, int64_t n_pairs,
                                const int64_t* out_off, const int32_t* out_rowptr, int32_t* out_col, float* out_val,
                                double* out_val64, int64_t out_cap, cudaStream_t str);
-constexpr int kBudgetBins = 2048;            // histogram bins of the select (11-bit digits)
+constexpr int kBudgetBins = 16384;           // histogram bins of the select (14-bit digits)
 
 cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,
                             cudaStream_t s);

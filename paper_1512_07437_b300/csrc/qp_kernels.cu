@@ -1589,7 +1589,8 @@ __global__ void k_compact(const int2* __restrict__ pairs, const int64_t* __restr
                           const int32_t* __restrict__ row_cnt, const int64_t* __restrict__ chunk_off,
                           const int2* __restrict__ pool, const double* __restrict__ pool64, int64_t n_pairs,
                           const int64_t* __restrict__ pair_nnz_off, int32_t* __restrict__ row_ptr,
-                          int32_t* __restrict__ col, float* __restrict__ val, double* __restrict__ val64) {
+                          int32_t* __restrict__ col, float* __restrict__ val, double* __restrict__ val64,
+                          unsigned long long* __restrict__ minmax) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= n_pairs) return;
@@ -1612,6 +1613,9 @@ __global__ void k_compact(const int2* __restrict__ pairs, const int64_t* __restr
     __syncwarp();
     const int64_t base = pair_nnz_off[p];
     const int nstrips = (m + 1 + kStripRows - 1) / kStripRows;
+    // smallest and largest key (bit pattern of the compared value), for the
+    // entry budget's select
+    unsigned long long kmin = ~0ull, kmax = 0ull;
     for (int s = 0; s < nstrips; ++s) {
         const int r0 = max(1, s * kStripRows) - 1;
         const int r1 = min(m + 1, s * kStripRows + kStripRows) - 1;
@@ -1621,7 +1625,26 @@ __global__ void k_compact(const int2* __restrict__ pairs, const int64_t* __restr
             const int2 v = pool[src + e];
             col[base + beg + e] = v.x;
             val[base + beg + e] = __int_as_float(v.y);
-            if (val64) val64[base + beg + e] = pool64[src + e];
+            unsigned long long key = (unsigned)v.y;
+            if (val64) {
+                const double d = pool64[src + e];
+                val64[base + beg + e] = d;
+                key = (unsigned long long)__double_as_longlong(d);
+            }
+            kmin = key < kmin ? key : kmin;
+            kmax = key > kmax ? key : kmax;
+        }
+    }
+    if (minmax) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(FULL, kmin, o), b = __shfl_xor_sync(FULL, kmax, o);
+            kmin = a < kmin ? a : kmin;
+            kmax = b > kmax ? b : kmax;
+        }
+        if (lane == 0 && kmax >= kmin) {
+            atomicMin(&minmax[0], kmin);
+            atomicMax(&minmax[1], kmax);
         }
     }
 }
@@ -1637,12 +1660,12 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const int32_t* row_cnt, const int64_t* chunk_off, const int2* pool,
                            const double* pool64, int64_t n_pairs, const int64_t* pair_nnz_off,
                            int32_t* row_ptr, int32_t* col, float* val, double* val64,
-                           cudaStream_t s) {
+                           cudaStream_t s, unsigned long long* minmax) {
     const int64_t threads = n_pairs * 32;
     const int blocks = (int)((threads + 255) / 256);
     if (blocks > 0)
         k_compact<<<blocks, 256, 0, s>>>(pairs, seq_off, pair_row_off, pair_strip_off, row_cnt, chunk_off,
-                                         pool, pool64, n_pairs, pair_nnz_off, row_ptr, col, val, val64);
+                                         pool, pool64, n_pairs, pair_nnz_off, row_ptr, col, val, val64, minmax);
     return cudaGetLastError();
 }
 
