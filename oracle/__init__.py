@@ -27,10 +27,18 @@ _lock = threading.Lock()
 _lib = None
 
 COMBINE = {"rms": 0, "mean": 1, "hmm": 2, "pf": 3}
-_LUT = np.full(256, 255, dtype=np.uint8)
-for _i, _c in enumerate("ACDEFGHIKLMNPQRSTVWY"):
-    _LUT[ord(_c)] = _i
-    _LUT[ord(_c.lower())] = _i
+# residue letters -> codes: the 20 amino acids, or the nucleotide mode's
+# A, C, G, T with U read as T (paper, Methods, "Other algorithmic
+# improvements": nucleotide mode)
+_LUTS = {}
+for _name, _letters in (("protein", "ACDEFGHIKLMNPQRSTVWY"), ("nucleotide", "ACGT")):
+    _t = np.full(256, 255, dtype=np.uint8)
+    for _i, _c in enumerate(_letters):
+        _t[ord(_c)] = _i
+        _t[ord(_c.lower())] = _i
+    _LUTS[_name] = _t
+_LUTS["nucleotide"][[ord("U"), ord("u")]] = 3
+_LUT = _LUTS["protein"]
 
 
 class OrParams(ctypes.Structure):
@@ -97,13 +105,14 @@ def to_struct(prm) -> OrParams:
     return s
 
 
-def encode(seq) -> np.ndarray:
-    """Residue letters (str or uint8 ASCII array) -> codes 0..19."""
+def encode(seq, alphabet: str = "protein") -> np.ndarray:
+    """Residue letters (str or uint8 ASCII array) -> codes: 0..19 for
+    proteins, 0..3 (A, C, G, T; U as T) for nucleotides."""
     if isinstance(seq, str):
         seq = np.frombuffer(seq.encode("ascii"), dtype=np.uint8)
-    c = _LUT[np.asarray(seq, dtype=np.uint8)]
+    c = _LUTS[alphabet][np.asarray(seq, dtype=np.uint8)]
     if (c == 255).any():
-        raise ValueError("residue outside the 20-letter alphabet")
+        raise ValueError(f"residue outside the {alphabet} alphabet")
     return c
 
 
@@ -184,7 +193,7 @@ def pairs(family, pair_list, prm, threads: int | None = None, theta: float | Non
     pairs of ``family``, on a thread pool of ``threads`` host cores."""
     lib = _load()
     threads = os.cpu_count() if threads is None else threads
-    codes = encode(family.residues)
+    codes = encode(family.residues, getattr(family, "alphabet", "protein"))
     off = np.ascontiguousarray(family.offsets, dtype=np.int64)
     pl = np.asarray(list(pair_list), dtype=np.int32).reshape(-1, 2)
     pa = np.ascontiguousarray(pl[:, 0])

@@ -1,16 +1,17 @@
-"""Seeded synthetic protein families and model parameters.
+"""Seeded synthetic protein and nucleotide families and model parameters.
 
 This module is the only code shared by the CUDA path's tests/benchmarks and the
 oracle's tests.  It produces *inputs*: residue strings, family layouts, arrival
 schedules and the numeric model parameters.  It contains none of the posterior
 method's arithmetic (no DP, no posterior, no MEA, no distance).
 """
-from .families import (ALPHABET, Family, background, evolve, make_family, star_family, tree_family, domain_family, pair_index,
-                       make_serving_trace, family_from_strings, CONFIGS)
-from .params import ModelParams, default_params
+from .families import (ALPHABET, NUCLEOTIDES, Family, background, nucleotide_background, evolve, make_family,
+                       star_family, tree_family, domain_family, pair_index, make_serving_trace,
+                       family_from_strings, CONFIGS)
+from .params import ModelParams, default_params, gtr_joint, nucleotide_params
 
 __all__ = [
-    "ALPHABET", "Family", "background", "evolve", "make_family", "star_family", "tree_family", "domain_family", "pair_index",
+    "ALPHABET", "NUCLEOTIDES", "Family", "background", "nucleotide_background", "evolve", "make_family", "star_family", "tree_family", "domain_family", "pair_index",
     "make_serving_trace", "family_from_strings", "CONFIGS",
-    "ModelParams", "default_params",
+    "ModelParams", "default_params", "gtr_joint", "nucleotide_params",
 ]

@@ -1,4 +1,4 @@
-"""Seeded synthetic protein families.
+"""Seeded synthetic protein and nucleotide families.
 
 The paper evaluates on curated benchmark families (BAliBASE, PREFAB, OXBench,
 SABmark, BaliFam with ~934 sequences per set, HomFam^1K with ~1093 per family;
@@ -15,6 +15,9 @@ Evolution model (the same for every configuration):
     half are insertions, half deletions; event lengths are geometric on
     {1, 2, ...} with mean 3; inserted residues are drawn from ``q``.
 
+Nucleotide families (alphabet ACGT) use the same model over a 4-letter
+background (``nucleotide_background``); protein families are unchanged by it.
+
 Randomness comes from ``numpy.random.Generator(PCG64(seed))`` only.
 """
 from __future__ import annotations
@@ -26,7 +29,10 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 ALPHABET = "ACDEFGHIKLMNPQRSTVWY"
+NUCLEOTIDES = "ACGT"
 _ALPHA_BYTES = np.frombuffer(ALPHABET.encode("ascii"), dtype=np.uint8)
+_NUC_BYTES = np.frombuffer(NUCLEOTIDES.encode("ascii"), dtype=np.uint8)
+LETTERS = {"protein": _ALPHA_BYTES, "nucleotide": _NUC_BYTES}
 
 # Per-configuration defaults.  The sizes follow the five workload
 # configurations of the posterior stage (8 / 64 / 500 / serving / 100
@@ -54,6 +60,7 @@ class Family:
     offsets: np.ndarray           # int64, k+1
     name: str = ""
     meta: dict = field(default_factory=dict)
+    alphabet: str = "protein"     # "protein" (20 letters) or "nucleotide" (ACGT)
 
     @property
     def k(self) -> int:
@@ -67,9 +74,13 @@ class Family:
         return self.residues[self.offsets[a]:self.offsets[a + 1]].tobytes().decode("ascii")
 
     def codes(self, a: int) -> np.ndarray:
-        """Residue codes 0..19 of sequence ``a`` (index into ``ALPHABET``)."""
+        """Residue codes of sequence ``a``: 0..19 (index into ``ALPHABET``),
+        or 0..3 (index into ``NUCLEOTIDES``, U read as T)."""
+        letters = LETTERS[self.alphabet]
         lut = np.full(256, 255, dtype=np.uint8)
-        lut[_ALPHA_BYTES] = np.arange(20, dtype=np.uint8)
+        lut[letters] = np.arange(letters.size, dtype=np.uint8)
+        if self.alphabet == "nucleotide":
+            lut[ord("U")] = 3
         return lut[self.residues[self.offsets[a]:self.offsets[a + 1]]]
 
     def pairs(self):
@@ -101,8 +112,19 @@ def background(seed: int = 20151223) -> np.ndarray:
     return q / q.sum()
 
 
+def nucleotide_background(seed: int = 20151224) -> np.ndarray:
+    """Background nucleotide frequencies (A, C, G, T): one seeded Dirichlet(20) draw."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    q = rng.dirichlet(np.full(4, 20.0))
+    return q / q.sum()
+
+
+def _background(alphabet: str) -> np.ndarray:
+    return background() if alphabet == "protein" else nucleotide_background()
+
+
 def _draw_residues(rng, q, n):
-    return rng.choice(20, size=n, p=q).astype(np.uint8)
+    return rng.choice(len(q), size=n, p=q).astype(np.uint8)
 
 
 def evolve(rng, seq: np.ndarray, s: float, q: np.ndarray) -> np.ndarray:
@@ -143,26 +165,26 @@ def evolve(rng, seq: np.ndarray, s: float, q: np.ndarray) -> np.ndarray:
     return np.concatenate(pieces).astype(np.uint8)
 
 
-def _pack(seqs: Sequence[np.ndarray], name: str, meta: dict) -> Family:
+def _pack(seqs: Sequence[np.ndarray], name: str, meta: dict, alphabet: str = "protein") -> Family:
     offs = np.zeros(len(seqs) + 1, dtype=np.int64)
     offs[1:] = np.cumsum([len(x) for x in seqs])
     codes = np.concatenate(list(seqs)).astype(np.uint8)
-    return Family(residues=_ALPHA_BYTES[codes].copy(), offsets=offs,
-                  name=name, meta=meta)
+    return Family(residues=LETTERS[alphabet][codes].copy(), offsets=offs,
+                  name=name, meta=meta, alphabet=alphabet)
 
 
-def family_from_strings(seqs: Sequence[str], name: str = "custom") -> Family:
+def family_from_strings(seqs: Sequence[str], name: str = "custom", alphabet: str = "protein") -> Family:
     """Family from Python strings (letters are not validated here)."""
     offs = np.zeros(len(seqs) + 1, dtype=np.int64)
     offs[1:] = np.cumsum([len(x) for x in seqs])
     buf = np.frombuffer("".join(seqs).encode("ascii"), dtype=np.uint8).copy()
-    return Family(residues=buf, offsets=offs, name=name, meta={})
+    return Family(residues=buf, offsets=offs, name=name, meta={}, alphabet=alphabet)
 
 
 def star_family(seed: int, k: int, root_len: tuple, s: float,
-                keep: Optional[tuple] = None, q=None, name="star") -> Family:
+                keep: Optional[tuple] = None, q=None, name="star", alphabet: str = "protein") -> Family:
     """k leaves evolved independently from one root (a star tree)."""
-    q = background() if q is None else q
+    q = _background(alphabet) if q is None else q
     rng = np.random.Generator(np.random.PCG64(seed))
     L0 = int(rng.integers(root_len[0], root_len[1] + 1))
     root = _draw_residues(rng, q, L0)
@@ -175,7 +197,7 @@ def star_family(seed: int, k: int, root_len: tuple, s: float,
         else:
             raise RuntimeError("could not draw a leaf inside the length window")
         seqs.append(leaf)
-    return _pack(seqs, name, dict(seed=seed, k=k, root_len=L0, s=s))
+    return _pack(seqs, name, dict(seed=seed, k=k, root_len=L0, s=s), alphabet)
 
 
 def _random_tree(rng, n_leaves: int):
@@ -200,7 +222,7 @@ def _random_tree(rng, n_leaves: int):
 
 def tree_family(seed: int, k: int, root_len: tuple, s_range: tuple,
                 trim: Optional[tuple] = None, keep: Optional[tuple] = None,
-                q=None, name="tree") -> Family:
+                q=None, name="tree", alphabet: str = "protein") -> Family:
     """k leaves evolved down a seeded random binary tree.
 
     Every branch draws its own substitution rate from U[s_range].  With
@@ -208,7 +230,7 @@ def tree_family(seed: int, k: int, root_len: tuple, s_range: tuple,
     longer).  With ``keep`` a leaf shorter than keep[0] is re-evolved from its
     parent (bounded tries) and a longer one is cut to a random window.
     """
-    q = background() if q is None else q
+    q = _background(alphabet) if q is None else q
     rng = np.random.Generator(np.random.PCG64(seed))
     parent, n_nodes = _random_tree(rng, k)
     L0 = int(rng.integers(root_len[0], root_len[1] + 1))
@@ -252,7 +274,7 @@ def tree_family(seed: int, k: int, root_len: tuple, s_range: tuple,
         if x.size < 1:
             x = _draw_residues(rng, q, 1)
         leaves.append(x)
-    return _pack(leaves, name, dict(seed=seed, k=k, root_len=L0))
+    return _pack(leaves, name, dict(seed=seed, k=k, root_len=L0), alphabet)
 
 
 def domain_family(seed: int, k: int, n_domains: int, domain_len: tuple,

@@ -27,8 +27,10 @@ def _rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def _rand_seq(rng, n):
-    return rng.integers(0, 20, size=n).astype(np.uint8)
+def _rand_seq(rng, n, prm=None):
+    """n random residue codes of the parameters' alphabet (20 or 4 letters)."""
+    a = 4 if prm is not None and prm.alphabet == "nucleotide" else 20
+    return rng.integers(0, a, size=n).astype(np.uint8)
 
 
 def _odd_params():
@@ -40,7 +42,17 @@ def _odd_params():
     return p.replace(pi=pi, end_w=np.array([1.0, 0.7, 0.4, 0.9, 0.2]))
 
 
-PARAMS = {"default": synth.default_params(), "odd": _odd_params()}
+def _odd_nucleotide_params():
+    """Nucleotide mode (GTR-derived tables, 4 letters) with the same odd
+    start, end and gap constants."""
+    p = synth.nucleotide_params(delta1=0.07, eps1=0.55, delta2=0.03, eps2=0.85,
+                                gap_open=-5.0, gap_ext=-2.0, temperature=2.0)
+    pi = np.array([0.6, 0.1, 0.15, 0.05, 0.1])
+    return p.replace(pi=pi, end_w=np.array([1.0, 0.7, 0.4, 0.9, 0.2]))
+
+
+PARAMS = {"default": synth.default_params(), "odd": _odd_params(),
+          "nucleotide": _odd_nucleotide_params()}
 SHAPES = [(1, 1), (1, 3), (3, 1), (2, 2), (2, 4), (4, 3), (3, 5), (5, 5)]
 
 
@@ -50,7 +62,7 @@ def test_hmm_equals_bruteforce(pname, shape):
     prm = PARAMS[pname]
     rng = _rng(zlib.crc32(repr((pname, shape)).encode()))
     for _ in range(3):
-        x, y = _rand_seq(rng, shape[0]), _rand_seq(rng, shape[1])
+        x, y = _rand_seq(rng, shape[0], prm), _rand_seq(rng, shape[1], prm)
         Z, PM, GX, GY = hmm_brute(x, y, prm)
         r = oracle.pair(x, y, prm)
         assert abs(r["logz_hmm"] - math.log(Z)) < 1e-11 * max(1.0, abs(math.log(Z)))
@@ -65,7 +77,7 @@ def test_pf_equals_bruteforce(pname, shape):
     prm = PARAMS[pname]
     rng = _rng(1000 + zlib.crc32(repr((pname, shape)).encode()))
     for _ in range(3):
-        x, y = _rand_seq(rng, shape[0]), _rand_seq(rng, shape[1])
+        x, y = _rand_seq(rng, shape[0], prm), _rand_seq(rng, shape[1], prm)
         Z, PP, GX, GY = pf_brute(x, y, prm)
         r = oracle.pair(x, y, prm)
         assert abs(r["logz_pf"] - math.log(Z)) < 1e-11 * max(1.0, abs(math.log(Z)))
@@ -91,7 +103,7 @@ def test_mea_equals_bruteforce(combine, shape):
     prm = PARAMS["odd"].replace(combine=combine)
     rng = _rng(7 + shape[0] * 10 + shape[1])
     for _ in range(3):
-        x, y = _rand_seq(rng, shape[0]), _rand_seq(rng, shape[1])
+        x, y = _rand_seq(rng, shape[0], prm), _rand_seq(rng, shape[1], prm)
         r = oracle.pair(x, y, prm)
         best = mea_brute(r["P"])
         assert abs(r["mea"] - best) < 1e-12
@@ -123,7 +135,7 @@ def test_combination_modes():
 def test_forward_equals_backward(pname, shape):
     prm = PARAMS[pname]
     rng = _rng(shape[0] * 1000 + shape[1])
-    x, y = _rand_seq(rng, shape[0]), _rand_seq(rng, shape[1])
+    x, y = _rand_seq(rng, shape[0], prm), _rand_seq(rng, shape[1], prm)
     r = oracle.pair(x, y, prm)
     assert abs(r["logz_hmm"] - r["logz_hmm_bwd"]) < 1e-10 * abs(r["logz_hmm"])
     assert abs(r["logz_pf"] - r["logz_pf_bwd"]) < 1e-10 * max(1.0, abs(r["logz_pf"]))
@@ -135,7 +147,7 @@ def test_posterior_identities(pname):
     by a gap state; so the row sum of P_M plus the row's gap posterior is 1,
     and likewise for columns, for both models."""
     prm = PARAMS[pname]
-    fam = synth.star_family(3, 2, (60, 80), 0.3)
+    fam = synth.star_family(3, 2, (60, 80), 0.3, alphabet=prm.alphabet)
     x, y = fam.codes(0), fam.codes(1)
     r = oracle.pair(x, y, prm)
     np.testing.assert_allclose(r["P_hmm"].sum(1) + r["gx_hmm"], 1.0, atol=1e-11)
@@ -152,8 +164,9 @@ def test_posterior_identities(pname):
 def test_closed_form_one_by_one(pname):
     """m = n = 1: no X->Y move exists, so the only path is one match."""
     prm = PARAMS[pname]
-    for a in range(0, 20, 7):
-        for b in range(0, 20, 5):
+    n_alpha = 4 if prm.alphabet == "nucleotide" else 20
+    for a in range(0, n_alpha, 7 if n_alpha == 20 else 1):
+        for b in range(0, n_alpha, 5 if n_alpha == 20 else 1):
             r = oracle.pair(np.array([a], np.uint8), np.array([b], np.uint8), prm)
             z = prm.pi[0] * prm.emit_pair[a, b] * prm.end_w[0]
             assert abs(r["logz_hmm"] - math.log(z)) < 1e-13
@@ -170,8 +183,8 @@ def test_closed_form_one_by_n(pname, n):
     kind per run) before and after; sum the n placements in closed form."""
     prm = PARAMS[pname]
     rng = _rng(n)
-    x = _rand_seq(rng, 1)
-    y = _rand_seq(rng, n)
+    x = _rand_seq(rng, 1, prm)
+    y = _rand_seq(rng, n, prm)
     q, p = prm.emit_bg, prm.emit_pair
     d1, e1, d2, e2 = prm.delta1, prm.eps1, prm.delta2, prm.eps2
     pi, tau = prm.pi, prm.end_w
@@ -272,7 +285,7 @@ def test_swap_transposes(pname):
     # the swap symmetry needs symmetric parameters (start and end too)
     prm = prm.replace(pi=np.array([prm.pi[0], prm.pi[1], prm.pi[1], prm.pi[3], prm.pi[3]]),
                       end_w=np.array([1.0, 0.5, 0.5, 0.25, 0.25]))
-    fam = synth.star_family(5, 2, (40, 60), 0.35)
+    fam = synth.star_family(5, 2, (40, 60), 0.35, alphabet=prm.alphabet)
     x, y = fam.codes(0), fam.codes(1)
     r1 = oracle.pair(x, y, prm)
     r2 = oracle.pair(y, x, prm)
@@ -301,3 +314,20 @@ def test_sparsify_is_threshold():
     assert rp.tolist() == [0, 2, 4]
     assert col.tolist() == [0, 1, 1, 2]
     assert val.tolist() == [0.5, 0.01, 1.0, 0.2]
+
+
+def test_nucleotide_encoding_and_tables():
+    """Nucleotide mode: A, C, G, T map to 0..3 (U read as T, either case),
+    protein letters are rejected; the GTR-derived emission table is a
+    symmetric joint distribution whose marginals are the base frequencies."""
+    assert oracle.encode("ACGTUacgtu", "nucleotide").tolist() == [0, 1, 2, 3, 3, 0, 1, 2, 3, 3]
+    with pytest.raises(ValueError):
+        oracle.encode("ACGTE", "nucleotide")
+    prm = synth.nucleotide_params()
+    J = prm.emit_pair[:4, :4]
+    assert abs(J.sum() - 1.0) < 1e-14 and np.allclose(J, J.T, atol=1e-15)
+    np.testing.assert_allclose(J.sum(axis=1), prm.emit_bg[:4], atol=1e-14)
+    assert (prm.emit_pair[4:, :] == 0).all() and (prm.emit_pair[:, 4:] == 0).all()
+    # transitions (A<->G, C<->T) score above transversions
+    s = prm.score
+    assert s[0, 2] > s[0, 1] and s[1, 3] > s[1, 2] and (np.diag(s)[:4] > 0).all()
