@@ -23,8 +23,9 @@
  *   Pairs: a < b, linear index p = a*k - a(a+1)/2 + (b - a - 1).  Rows of
  *   pair p index sequence a (row i-1 <-> residue x_i), columns index
  *   sequence b.  The pair (b, a) is the transpose.
- *   Residues: ASCII letters of the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY
- *   (lower case accepted).  Any other byte -> QP_EINVAL.
+ *   Residues: ASCII letters of the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY,
+ *   or in nucleotide mode (params->alphabet = QP_NUCLEOTIDE) of A, C, G, T
+ *   with U read as T (lower case accepted).  Any other byte -> QP_EINVAL.
  *   Ownership: inputs are borrowed for the duration of the call.  A
  *   qp_result is owned by the library and released with qp_result_free.
  *   Errors: every entry point returns a qp_status; qp_last_error() gives a
@@ -57,6 +58,7 @@ typedef enum {
 
 enum { QP_COMBINE_RMS = 0, QP_COMBINE_MEAN = 1, QP_COMBINE_HMM = 2, QP_COMBINE_PF = 3 };
 enum { QP_F32_SCALED = 0, QP_F64_PLAIN = 1 };
+enum { QP_PROTEIN = 0, QP_NUCLEOTIDE = 1 };
 
 /* A family of k sequences laid out as one buffer.
  *   residues : concatenated ASCII residues, offsets[k] bytes; host memory,
@@ -93,7 +95,13 @@ typedef struct qp_family {
  *   entry), in the precision the entries are compared in, is reported as
  *   qp_result.threshold_used; entries equal to the (N+1)-th are all dropped.
  *   Must be >= 0.  Servers reject it (QP_EINVAL) and
- *   qp_pair_posteriors_static ignores it. */
+ *   qp_pair_posteriors_static ignores it.
+ *   alphabet: QP_PROTEIN (20 letters, codes in the order ACDEFGHIKLMNPQRSTVWY)
+ *   or QP_NUCLEOTIDE (paper, Methods, "Other algorithmic improvements":
+ *   nucleotide mode; letters A, C, G, T = codes 0..3, U read as T).  The
+ *   tables keep their layout, [a*20+b] and [a]; in nucleotide mode only
+ *   entries with a, b < 4 are read, emit_pair over that block and
+ *   emit_bg[0..3] sum to 1, and the rest is ignored.  reserved_ must be 0. */
 typedef struct qp_params {
     double pi[5];
     double delta1, eps1, delta2, eps2;
@@ -109,6 +117,8 @@ typedef struct qp_params {
     int32_t device;
     void* stream;
     int64_t entry_budget;
+    int32_t alphabet;
+    int32_t reserved_;
 } qp_params;
 
 /* Results.  When on_device, every pointer is device memory of the call's
@@ -282,7 +292,10 @@ void qp_server_destroy(qp_server* server);
  *                     with the state in global memory; automatic: the first
  *                     that fits, in that order;
  *   "tree_ctas"       qp_guide_tree cluster form: CTAs of the cluster (1, 2,
- *                     4, 8 or 16; automatic: the fewest that fit).
+ *                     4, 8 or 16; automatic: about 8 rows per CTA);
+ *   "pool_entries"    releases the entry pool and starts later calls from a
+ *                     pool of at most this many entries (a call whose entries
+ *                     overflow it grows it and runs again; 0: estimated).
  * Applies to later qp_posteriors calls and servers created afterwards.
  * QP_EINVAL for an unknown name or device. */
 int qp_set_option(int32_t device, const char* name, int64_t value);
@@ -290,7 +303,8 @@ int qp_set_option(int32_t device, const char* name, int64_t value);
 /* Counters of qp_posteriors calls on one device (no counterpart in the
  * paper): "graph_captures" (calls that captured their sequence as a new CUDA
  * graph), "graph_relaunches" (calls that relaunched the cached graph as it
- * was), "plain_calls" (calls with plain launches).  QP_EINVAL for an unknown
+ * was), "plain_calls" (calls with plain launches), "pool_retries" (calls run again because their entries
+ * overflowed the entry pool).  QP_EINVAL for an unknown
  * name or device. */
 int qp_get_counter(int32_t device, const char* name, int64_t* value);
 

@@ -97,18 +97,24 @@ int validate_params(const qp_params* p) {
         return fail(QP_EINVAL, "need delta1, delta2 >= 0 and 2 delta1 + 2 delta2 <= 1");
     if (!(p->eps1 >= 0 && p->eps1 < 1 && p->eps2 >= 0 && p->eps2 < 1))
         return fail(QP_EINVAL, "eps1, eps2 must be in [0, 1)");
+    if (p->alphabet != QP_PROTEIN && p->alphabet != QP_NUCLEOTIDE)
+        return fail(QP_EINVAL, "alphabet must be QP_PROTEIN or QP_NUCLEOTIDE");
+    if (p->reserved_ != 0) return fail(QP_EINVAL, "reserved_ must be 0");
+    const int na = alphabet_size(p->alphabet);
     s = 0;
-    for (int i = 0; i < 400; ++i) {
-        if (!(p->emit_pair[i] >= 0.0)) return fail(QP_EINVAL, "emit_pair[%d] must be >= 0", i);
-        s += p->emit_pair[i];
-    }
-    if (!near1(s)) return fail(QP_EINVAL, "emit_pair must sum to 1 (sum %.12g)", s);
+    for (int a = 0; a < na; ++a)
+        for (int b = 0; b < na; ++b) {
+            const int i = a * 20 + b;
+            if (!(p->emit_pair[i] >= 0.0)) return fail(QP_EINVAL, "emit_pair[%d] must be >= 0", i);
+            s += p->emit_pair[i];
+        }
+    if (!near1(s)) return fail(QP_EINVAL, "emit_pair must sum to 1 over the alphabet (sum %.12g)", s);
     s = 0;
-    for (int i = 0; i < 20; ++i) {
+    for (int i = 0; i < na; ++i) {
         if (!(p->emit_bg[i] > 0.0)) return fail(QP_EINVAL, "emit_bg[%d] must be > 0", i);
         s += p->emit_bg[i];
     }
-    if (!near1(s)) return fail(QP_EINVAL, "emit_bg must sum to 1 (sum %.12g)", s);
+    if (!near1(s)) return fail(QP_EINVAL, "emit_bg must sum to 1 over the alphabet (sum %.12g)", s);
     double te = 0;
     for (int i = 0; i < 5; ++i) {
         if (!(p->end_w[i] >= 0.0 && std::isfinite(p->end_w[i])))
@@ -116,8 +122,9 @@ int validate_params(const qp_params* p) {
         te += p->end_w[i];
     }
     if (!(te > 0)) return fail(QP_EINVAL, "end_w must not be all zero");
-    for (int i = 0; i < 400; ++i)
-        if (!std::isfinite(p->score[i])) return fail(QP_EINVAL, "score[%d] is not finite", i);
+    for (int a = 0; a < na; ++a)
+        for (int b = 0; b < na; ++b)
+            if (!std::isfinite(p->score[a * 20 + b])) return fail(QP_EINVAL, "score[%d] is not finite", a * 20 + b);
     if (!(p->temperature > 0 && std::isfinite(p->temperature))) return fail(QP_EINVAL, "temperature must be > 0");
     if (!std::isfinite(p->gap_open) || !std::isfinite(p->gap_ext)) return fail(QP_EINVAL, "gap penalties must be finite");
     if (p->end_gap_mode != 0) return fail(QP_EINVAL, "only end_gap_mode 0 is supported");
@@ -144,6 +151,7 @@ void make_raw(const qp_params* p, qpk::RawParams* r) {
     r->gap_open = p->gap_open; r->gap_ext = p->gap_ext; r->temperature = p->temperature;
     r->threshold = p->threshold;
     r->combine = p->combine;
+    r->n_alpha = alphabet_size(p->alphabet);
 }
 
 void make_coef(const qp_params* p, qpk::Coef* c) {
@@ -596,6 +604,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         const double per_row = std::min<double>(pl->max_len + 1.0, 4.0 + 0.04 / prm->threshold);
         int64_t est = (int64_t)(per_row * (double)pl->n_rows) + 4096;
         est = std::max<int64_t>(est, C->pool_hint);
+        if (C->tune.pool_entries > 0) est = std::min<int64_t>(est, C->tune.pool_entries);
         if ((e = C->pool.ensure(sizeof(int2) * est)) != cudaSuccess ||
             (f64 && (e = C->pool64.ensure(sizeof(double) * est)) != cudaSuccess))
             return bail(fail(QP_ENOMEM, "pool allocation failed"));
@@ -686,7 +695,8 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
                 if ((x = qpk::launch_scan_nnz(fd.pair_nnz, P, probe.pair_nnz_off, st)) != cudaSuccess ||
                     (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
                                              fd.chunk_off, Pb.pool, Pb.pool64, P, probe.pair_nnz_off, probe.row_ptr,
-                                             probe.col, probe.val, probe.val64, st)) != cudaSuccess)
+                                             probe.col, probe.val, probe.val64, st, nullptr,
+                                             &d_status->pool_overflow)) != cudaSuccess)
                     return x;
             } else {
                 int64_t* b_off = (int64_t*)C->bud_off.ptr;
@@ -703,17 +713,17 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
                     (x = qpk::launch_scan_nnz(fd.pair_nnz, P, b_off, st)) != cudaSuccess ||
                     (x = qpk::launch_compact(fd.pairs, fd.seq_off, fd.pair_row_off, fd.pair_strip_off, fd.row_cnt,
                                              fd.chunk_off, Pb.pool, Pb.pool64, P, b_off, b_rp, b_col, b_val,
-                                             b_val64, st, minmax)) != cudaSuccess ||
+                                             b_val64, st, minmax, &d_status->pool_overflow)) != cudaSuccess ||
                     (x = qpk::launch_budget_select(b_off + P, n_keep, prm->threshold, f64, b_val, b_val64, minmax,
                                                    sel, hist, d_status, 4 * C->sm_count, st)) != cudaSuccess ||
                     (x = qpk::launch_budget_count(fd.pairs, fd.seq_off, fd.pair_row_off, b_off, b_rp, b_val,
-                                                  b_val64, sel, P, probe.row_ptr, (int64_t*)C->bud_nnz.ptr, st)) !=
-                        cudaSuccess ||
+                                                  b_val64, sel, P, probe.row_ptr, (int64_t*)C->bud_nnz.ptr,
+                                                  d_status, st)) != cudaSuccess ||
                     (x = qpk::launch_scan_nnz((const int64_t*)C->bud_nnz.ptr, P, probe.pair_nnz_off, st)) !=
                         cudaSuccess ||
                     (x = qpk::launch_budget_copy(fd.pairs, fd.seq_off, fd.pair_row_off, b_off, b_rp, b_col, b_val,
                                                  b_val64, sel, P, probe.pair_nnz_off, probe.row_ptr, probe.col,
-                                                 probe.val, probe.val64, nnz_cap, st)) != cudaSuccess)
+                                                 probe.val, probe.val64, nnz_cap, d_status, st)) != cudaSuccess)
                     return x;
             }
             char* hs_p = (char*)C->h_status.ptr;
@@ -764,7 +774,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         memcpy(&hs, C->h_status.ptr, sizeof hs);
         memcpy(&nnz, (char*)C->h_status.ptr + sizeof(qpk::Status), sizeof nnz);
         if (hs.bad_residue)
-            return bail(fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY"));
+            return bail(fail(QP_EINVAL, "%s", alphabet_error(prm->alphabet)));
         if (hs.stage_overflow) return bail(fail(QP_ECUDA, "internal: a row exceeded its entry capacity"));
         if (hs.select_error) return bail(fail(QP_ECUDA, "internal: the entry budget's selection failed"));
         if (!f64 && f64_grid == 0 && hs.n_fallback > 0)
@@ -775,6 +785,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         if (!hs.pool_overflow) break;
         if (attempt >= 2) return bail(fail(QP_ENOMEM, "the entry pool kept overflowing"));
         // grow the pool (and the result's entry part) to what was asked for, and run again
+        ++C->pool_retries;
         const int64_t need = (int64_t)(hs.pool_used * 5 / 4) + 4096;
         C->pool_hint = need;
         if ((e = C->pool.ensure(sizeof(int2) * need)) != cudaSuccess ||
@@ -983,6 +994,7 @@ int qp_get_counter(int32_t device, const char* name, int64_t* value) {
     if (n == "graph_captures") *value = C->graph_captures;
     else if (n == "graph_relaunches") *value = C->graph_relaunches;
     else if (n == "plain_calls") *value = C->plain_calls;
+    else if (n == "pool_retries") *value = C->pool_retries;
     else return fail(QP_EINVAL, "unknown counter '%s'", name);
     return QP_OK;
 }
@@ -1017,6 +1029,14 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
         C->tune.warps_per_block = value > 0 ? (int)value : 0;
     } else if (n == "scratch_bytes") {
         C->tune.scratch_bytes = value > 0 ? value : 0;
+    } else if (n == "pool_entries") {
+        // start the next calls from a pool of at most this many entries (the
+        // pool grows when a call overflows it); 0 / -1: estimated
+        C->tune.pool_entries = value > 0 ? value : 0;
+        C->pool.release();
+        C->pool64.release();
+        C->pool_cap = 0;
+        C->pool_hint = 0;
     } else if (n == "tree_form") {
         if (value > 2) return fail(QP_EINVAL, "tree_form must be 0, 1, 2 or -1");
         C->tune.tree_form = value < 0 ? -1 : (int)value;

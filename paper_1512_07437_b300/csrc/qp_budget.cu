@@ -53,7 +53,8 @@ __global__ void k_sel_init(const int64_t* total, int64_t n_keep, double theta, i
         s->prefix = (s->total > 0 && common > 0) ? (lo >> (KB - common)) : 0ull;
         s->bits_done = s->total > 0 ? common : 0;
         s->rank = n_keep;                 // 0-based rank, from the top, of the (N+1)-th largest
-        s->active = s->total > n_keep ? 1 : 0;
+        // nothing to select when the pool overflowed (the call runs again)
+        s->active = (s->total > n_keep && !st->pool_overflow) ? 1 : 0;
         s->theta_f = (float)theta;
         s->theta_d = theta;
         s->f64 = f64;
@@ -195,10 +196,10 @@ __global__ void k_budget_count(const int2* __restrict__ pairs, const int64_t* __
                                const int64_t* __restrict__ pair_row_off, const int64_t* __restrict__ in_off,
                                const int32_t* __restrict__ in_rowptr, const float* in_val, const double* in_val64,
                                const SelectState* s, int64_t n_pairs, int32_t* __restrict__ out_rowptr,
-                               int64_t* __restrict__ out_nnz) {
+                               int64_t* __restrict__ out_nnz, const Status* st) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (p >= n_pairs) return;
+    if (p >= n_pairs || st->pool_overflow) return;   // the call runs again
     const int2 ab = pairs[p];
     const int m = (int)(seq_off[ab.x + 1] - seq_off[ab.x]);
     const int64_t ro = pair_row_off[p], base = in_off[p];
@@ -231,10 +232,10 @@ __global__ void k_budget_copy(const int2* __restrict__ pairs, const int64_t* __r
                               const float* in_val, const double* in_val64, const SelectState* s, int64_t n_pairs,
                               const int64_t* __restrict__ out_off, const int32_t* __restrict__ out_rowptr,
                               int32_t* __restrict__ out_col, float* __restrict__ out_val,
-                              double* __restrict__ out_val64, int64_t out_cap) {
+                              double* __restrict__ out_val64, int64_t out_cap, const Status* st) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (p >= n_pairs) return;
+    if (p >= n_pairs || st->pool_overflow) return;   // the call runs again
     const int2 ab = pairs[p];
     const int m = (int)(seq_off[ab.x + 1] - seq_off[ab.x]);
     const int64_t ro = pair_row_off[p], bin = in_off[p], bout = out_off[p];
@@ -287,11 +288,11 @@ cudaError_t launch_budget_select(const int64_t* total, int64_t n_keep, double th
 cudaError_t launch_budget_count(const int2* pairs, const int64_t* seq_off, const int64_t* pair_row_off,
                                 const int64_t* in_off, const int32_t* in_rowptr, const float* in_val,
                                 const double* in_val64, const SelectState* s, int64_t n_pairs, int32_t* out_rowptr,
-                                int64_t* out_nnz, cudaStream_t str) {
+                                int64_t* out_nnz, const Status* st, cudaStream_t str) {
     const int blocks = (int)((n_pairs * 32 + 255) / 256);
     if (blocks > 0)
         k_budget_count<<<blocks, 256, 0, str>>>(pairs, seq_off, pair_row_off, in_off, in_rowptr, in_val, in_val64,
-                                                 s, n_pairs, out_rowptr, out_nnz);
+                                                 s, n_pairs, out_rowptr, out_nnz, st);
     return cudaGetLastError();
 }
 
@@ -299,12 +300,12 @@ cudaError_t launch_budget_copy(const int2* pairs, const int64_t* seq_off, const 
                                const int64_t* in_off, const int32_t* in_rowptr, const int32_t* in_col,
                                const float* in_val, const double* in_val64, const SelectState* s, int64_t n_pairs,
                                const int64_t* out_off, const int32_t* out_rowptr, int32_t* out_col, float* out_val,
-                               double* out_val64, int64_t out_cap, cudaStream_t str) {
+                               double* out_val64, int64_t out_cap, const Status* st, cudaStream_t str) {
     const int blocks = (int)((n_pairs * 32 + 255) / 256);
     if (blocks > 0)
         k_budget_copy<<<blocks, 256, 0, str>>>(pairs, seq_off, pair_row_off, in_off, in_rowptr, in_col, in_val,
                                                 in_val64, s, n_pairs, out_off, out_rowptr, out_col, out_val,
-                                                out_val64, out_cap);
+                                                out_val64, out_cap, st);
     return cudaGetLastError();
 }
 

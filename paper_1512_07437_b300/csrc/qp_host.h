@@ -65,6 +65,7 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int tree_form = -1;                  // guide tree: 0 one CTA, state in global memory; 1 one CTA,
                                          // state in shared memory; 2 cluster form; -1 automatic
     int tree_ctas = 0;                   // guide tree cluster form: CTAs (1, 2, 4, 8, 16; 0 automatic)
+    int64_t pool_entries = 0;            // initial entry pool of a call (0: estimated)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the
@@ -131,7 +132,7 @@ struct Context {
     cudaGraphExec_t gexec = nullptr;     // the last captured call sequence
     GraphKey gkey;                       // what it was captured with
     bool gkey_valid = false;
-    int64_t graph_captures = 0, graph_relaunches = 0, plain_calls = 0;
+    int64_t graph_captures = 0, graph_relaunches = 0, plain_calls = 0, pool_retries = 0;
     // result blocks freed by the caller, kept for the next call of the same
     // shape (same addresses: the captured graph is relaunched as it is)
     std::mutex spare_mu;
@@ -207,6 +208,21 @@ struct ResultOwner {
 // is known in advance).  The caller sets nnz, n_fallback, guard_info, kernel_ms.
 void fill_result(qp_result* r, ResultOwner* own, const ResultLayout& L, int k, int64_t n_pairs,
                  int64_t n_rows, int64_t nnz_bound, bool f64, int precision, int device);
+
+// Letters of an alphabet (QP_PROTEIN: 20, QP_NUCLEOTIDE: 4) and the error
+// message for a residue outside it.
+inline int alphabet_size(int alphabet) { return alphabet == QP_NUCLEOTIDE ? 4 : 20; }
+inline const char* alphabet_error(int alphabet) {
+    return alphabet == QP_NUCLEOTIDE ? "a residue is outside the nucleotide alphabet ACGT (U read as T)"
+                                     : "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY";
+}
+// Host check of one residue byte (the encode kernel checks again on the device).
+inline bool valid_residue(uint8_t c, int alphabet) {
+    const char* letters = alphabet == QP_NUCLEOTIDE ? "ACGTUacgtu" : "ACDEFGHIKLMNPQRSTVWYacdefghiklmnpqrstvwy";
+    for (const char* l = letters; *l; ++l)
+        if ((uint8_t)*l == c) return true;
+    return false;
+}
 
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);

@@ -30,6 +30,7 @@ struct Consts {
     double logq[20];
     int32_t combine;
     int32_t err;
+    int32_t n_alpha;             // letters of the alphabet (20 or 4)
 };
 
 // Host-side copy of the parameters the setup kernel needs (plain doubles).
@@ -38,6 +39,7 @@ struct RawParams {
     double emit_pair[400], emit_bg[20], end_w[5], score[400];
     double gap_open, gap_ext, temperature, threshold;
     int32_t combine;
+    int32_t n_alpha;             // letters of the alphabet (20 or 4)
 };
 
 // Status words written by the kernels (device memory, zeroed per call).
@@ -192,7 +194,8 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const int32_t* row_cnt, const int64_t* chunk_off, const int2* pool,
                            const double* pool64, int64_t n_pairs, const int64_t* pair_nnz_off,
                            int32_t* row_ptr, int32_t* col, float* val, double* val64,
-                           cudaStream_t s, unsigned long long* minmax = nullptr);
+                           cudaStream_t s, unsigned long long* minmax = nullptr,
+                           const int32_t* overflow = nullptr);   // skip everything when *overflow
 // Entry budget (qp_budget.cu): the threshold that fits n_keep entries, from
 // the full CSR's values (total at *total); then the filtered row pointers and
 // counts, and the filtered entries.
@@ -203,12 +206,12 @@ cudaError_t launch_budget_select(const int64_t* total, int64_t n_keep, double th
 cudaError_t launch_budget_count(const int2* pairs, const int64_t* seq_off, const int64_t* pair_row_off,
                                 const int64_t* in_off, const int32_t* in_rowptr, const float* in_val,
                                 const double* in_val64, const SelectState* s, int64_t n_pairs, int32_t* out_rowptr,
-                                int64_t* out_nnz, cudaStream_t str);
+                                int64_t* out_nnz, const Status* st, cudaStream_t str);
 cudaError_t launch_budget_copy(const int2* pairs, const int64_t* seq_off, const int64_t* pair_row_off,
                                const int64_t* in_off, const int32_t* in_rowptr, const int32_t* in_col,
                                const float* in_val, const double* in_val64, const SelectState* s, int64_t n_pairs,
                                const int64_t* out_off, const int32_t* out_rowptr, int32_t* out_col, float* out_val,
-                               double* out_val64, int64_t out_cap, cudaStream_t str);
+                               double* out_val64, int64_t out_cap, const Status* st, cudaStream_t str);
 constexpr int kBudgetBins = 16384;           // histogram bins of the select (14-bit digits)
 
 cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* pair_nnz_off,

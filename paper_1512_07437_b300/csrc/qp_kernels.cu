@@ -60,7 +60,7 @@ __global__ void k_setup(const RawParams* __restrict__ rp, Consts* c) {
     for (int idx = t; idx < kTab * kTab; idx += blockDim.x) {
         const int y = idx / kTab, x = idx % kTab;
         double o = 0.0, w = 0.0;
-        if (x < 20 && y < 20) {
+        if (x < raw.n_alpha && y < raw.n_alpha) {
             o = raw.emit_pair[x * 20 + y] / (raw.emit_bg[x] * raw.emit_bg[y]);
             w = exp(raw.score[x * 20 + y] / raw.temperature);
         }
@@ -68,7 +68,7 @@ __global__ void k_setup(const RawParams* __restrict__ rp, Consts* c) {
         c->oddsd[idx] = o;
         c->wd[idx] = w;
     }
-    if (t < 20) c->logq[t] = log(raw.emit_bg[t]);
+    if (t < 20) c->logq[t] = t < raw.n_alpha ? log(raw.emit_bg[t]) : 0.0;
     if (t == 0) {
         c->tMMd = 1.0 - 2.0 * raw.delta1 - 2.0 * raw.delta2;
         c->d1d = raw.delta1; c->d2d = raw.delta2;
@@ -80,6 +80,7 @@ __global__ void k_setup(const RawParams* __restrict__ rp, Consts* c) {
         c->thetad = raw.threshold;
         c->combine = raw.combine;
         c->err = 0;
+        c->n_alpha = raw.n_alpha;
     }
 }
 
@@ -91,16 +92,20 @@ cudaError_t launch_setup(const RawParams* raw, RawParams* d_raw, Consts* cst, cu
 }
 
 // ---------------------------------------------------------------- encode
+// letters -> codes: the 20 amino acids, or in nucleotide mode A, C, G, T
+// (U read as T); the alphabet comes from the call's constants
 __global__ void k_encode(const uint8_t* __restrict__ ascii, uint8_t* __restrict__ codes,
-                         int64_t n, Status* st) {
+                         int64_t n, const Consts* __restrict__ cst, Status* st) {
     __shared__ uint8_t lut[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = 255;
     __syncthreads();
-    if (threadIdx.x < 20) {
-        const char* A = "ACDEFGHIKLMNPQRSTVWY";
+    const bool nuc = cst->n_alpha == 4;
+    if (threadIdx.x < (nuc ? 5 : 20)) {
+        const char* A = nuc ? "ACGTU" : "ACDEFGHIKLMNPQRSTVWY";
         const int c = A[threadIdx.x];
-        lut[c] = (uint8_t)threadIdx.x;
-        lut[c + 32] = (uint8_t)threadIdx.x;   // lower case
+        const uint8_t code = (uint8_t)(nuc && threadIdx.x == 4 ? 3 : threadIdx.x);
+        lut[c] = code;
+        lut[c + 32] = code;                    // lower case
     }
     __syncthreads();
     int bad = 0;
@@ -130,7 +135,7 @@ cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_encode<<<blocks, 256, 0, s>>>(ascii, codes, n, status);
+    k_encode<<<blocks, 256, 0, s>>>(ascii, codes, n, cst, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_seqlogq<<<(k * 32 + 255) / 256, 256, 0, s>>>(codes, seq_off, k, cst, seq_logq);
@@ -1590,10 +1595,12 @@ __global__ void k_compact(const int2* __restrict__ pairs, const int64_t* __restr
                           const int2* __restrict__ pool, const double* __restrict__ pool64, int64_t n_pairs,
                           const int64_t* __restrict__ pair_nnz_off, int32_t* __restrict__ row_ptr,
                           int32_t* __restrict__ col, float* __restrict__ val, double* __restrict__ val64,
-                          unsigned long long* __restrict__ minmax) {
+                          unsigned long long* __restrict__ minmax, const int32_t* __restrict__ overflow) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (p >= n_pairs) return;
+    // a pool that overflowed holds chunks beyond its end: nothing to assemble
+    // (the call runs again with a larger pool)
+    if (p >= n_pairs || (overflow && *overflow)) return;
     const int2 ab = pairs[p];
     const int m = (int)(seq_off[ab.x + 1] - seq_off[ab.x]);
     const int64_t ro = pair_row_off[p];
@@ -1660,12 +1667,13 @@ cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const int32_t* row_cnt, const int64_t* chunk_off, const int2* pool,
                            const double* pool64, int64_t n_pairs, const int64_t* pair_nnz_off,
                            int32_t* row_ptr, int32_t* col, float* val, double* val64,
-                           cudaStream_t s, unsigned long long* minmax) {
+                           cudaStream_t s, unsigned long long* minmax, const int32_t* overflow) {
     const int64_t threads = n_pairs * 32;
     const int blocks = (int)((threads + 255) / 256);
     if (blocks > 0)
         k_compact<<<blocks, 256, 0, s>>>(pairs, seq_off, pair_row_off, pair_strip_off, row_cnt, chunk_off,
-                                         pool, pool64, n_pairs, pair_nnz_off, row_ptr, col, val, val64, minmax);
+                                         pool, pool64, n_pairs, pair_nnz_off, row_ptr, col, val, val64, minmax,
+                                         overflow);
     return cudaGetLastError();
 }
 

@@ -53,12 +53,6 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-// Host check of the alphabet (the encode kernel checks again on the device).
-bool valid_residue(uint8_t c) {
-    static const char* kAlpha = "ACDEFGHIKLMNPQRSTVWYacdefghiklmnpqrstvwy";
-    return c != 0 && std::strchr(kAlpha, (int)c) != nullptr;
-}
-
 struct Job {
     uint64_t ticket = 0;
     std::vector<uint8_t> residues;
@@ -971,8 +965,8 @@ int qp_server_submit(qp_server* S, const qp_family* family, uint64_t* ticket) {
     const int k = family->k;
     const int64_t total = family->offsets[k];
     for (int64_t i = 0; i < total; ++i)
-        if (!valid_residue(family->residues[i]))
-            return fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY");
+        if (!valid_residue(family->residues[i], S->params.alphabet))
+            return fail(QP_EINVAL, "%s", alphabet_error(S->params.alphabet));
     auto J = std::make_shared<Job>();
     J->residues.assign(family->residues, family->residues + total);
     J->offsets.assign(family->offsets, family->offsets + k + 1);

@@ -185,7 +185,7 @@ extern "C" int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(e, "k_posterior_f32");
     if (hs.bad_residue)
-        return fail(QP_EINVAL, "a residue is outside the 20-letter alphabet ACDEFGHIKLMNPQRSTVWY");
+        return fail(QP_EINVAL, "%s", qph::alphabet_error(params->alphabet));
     if (hs.stage_overflow || hs.pool_overflow)
         return fail(QP_ECUDA, "internal: static scratch entry capacity exceeded");
     if (hs.n_fallback > 0)

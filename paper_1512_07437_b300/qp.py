@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libqp.so")
 QP_OK, QP_EINVAL, QP_ENOMEM, QP_ECUDA, QP_ETIMEOUT, QP_ECANCELLED, QP_ENOTREADY = range(7)
 QP_COMBINE = {"rms": 0, "mean": 1, "hmm": 2, "pf": 3}
 QP_PRECISION = {"f32": 0, "f64": 1}
+QP_ALPHABET = {"protein": 0, "nucleotide": 1}
 QP_F32_SCALED, QP_F64_PLAIN = 0, 1
 _STATUS_NAMES = {0: "QP_OK", 1: "QP_EINVAL", 2: "QP_ENOMEM", 3: "QP_ECUDA",
                  4: "QP_ETIMEOUT", 5: "QP_ECANCELLED", 6: "QP_ENOTREADY"}
@@ -49,6 +50,7 @@ class qp_params(ctypes.Structure):
         ("threshold", ctypes.c_double),
         ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
         ("stream", ctypes.c_void_p), ("entry_budget", ctypes.c_int64),
+        ("alphabet", ctypes.c_int32), ("reserved_", ctypes.c_int32),
     ]
 
 
@@ -164,6 +166,8 @@ def make_params(prm, device: int = 0, stream=None, threshold: Optional[float] = 
     p.precision = QP_PRECISION[pr] if isinstance(pr, str) else int(pr)
     p.device = int(device)
     p.entry_budget = int(entry_budget if entry_budget is not None else getattr(prm, "entry_budget", 0))
+    al = getattr(prm, "alphabet", "protein")
+    p.alphabet = QP_ALPHABET[al] if isinstance(al, str) else int(al)
     if stream is None:
         p.stream = None
     elif isinstance(stream, int):

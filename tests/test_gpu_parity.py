@@ -396,3 +396,29 @@ def test_null_stream_waits_for_the_default_stream(qp):
     got = qp.qp_posteriors(dst, fam.offsets, qp.make_params(prm, device=0))
     assert np.array_equal(got.dist64, ref.dist64)
     assert np.array_equal(got.mea, ref.mea)
+
+
+def test_entry_pool_overflow_reruns_the_call(qp):
+    """A call whose entries overflow the entry pool must run again with a
+    larger pool and give the result of a call that fitted: nothing after the
+    posterior kernels may read the overflowed pool (with or without an entry
+    budget)."""
+    fam = synth.make_family("c1", 4)
+    prm = synth.default_params(threshold=0.001)
+    ref = _run(qp, fam, prm)
+    ref_b = _run(qp, fam, prm, entry_budget=(ref.nnz // 3) * 8)
+    try:
+        for budget in (0, (ref.nnz // 3) * 8):
+            base = ref if budget == 0 else ref_b
+            qp.qp_set_option("pool_entries", 1000)
+            before = qp.qp_get_counter("pool_retries")
+            r = _run(qp, fam, prm, entry_budget=budget)
+            assert qp.qp_get_counter("pool_retries") > before, "the pool did not overflow"
+            assert r.nnz == base.nnz and r.threshold_used == base.threshold_used
+            for name in ("row_ptr", "pair_nnz_off", "col", "val"):
+                assert np.array_equal(host(r.array(name)), host(base.array(name))), name
+            r.free()
+    finally:
+        qp.qp_set_option("pool_entries", 0)
+    ref.free()
+    ref_b.free()
