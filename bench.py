@@ -498,6 +498,35 @@ def main():
                     "kernels": "k_sel_init, k_sel_hist (2 of 3 passes active), k_sel_pick, k_budget_count, "
                                "k_scan_nnz, k_budget_copy (plus the compaction into scratch)"}
 
+    # ---- nucleotide mode: a family of the c2 shape over ACGT (64 sequences,
+    # 200-400 nt, star tree, the same divergence) with GTR-derived tables,
+    # timed the same way (device residues, L2 flushed, CUDA events)
+    nfam = synth.star_family(qd.rank_seed(args.seed, rank), 64, (200, 400), 0.40, keep=(200, 400),
+                             alphabet="nucleotide", name="c2-nucleotide")
+    nprm = qp.make_params(synth.nucleotide_params(threshold=0.01, precision=args.precision), device=local,
+                          stream=stream)
+    d_nres = torch.from_numpy(nfam.residues).to(dev)
+    for _ in range(3):
+        qp.qp_posteriors(d_nres, nfam.offsets, nprm, out_on_device=True).free()
+    n_times = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rn = qp.qp_posteriors(d_nres, nfam.offsets, nprm, out_on_device=True)
+        e1.record(stream)
+        e1.synchronize()
+        n_times.append(e0.elapsed_time(e1))
+        n_nnz, n_fb = int(rn.nnz), int(rn.n_fallback)
+        n_kms = rn.kernel_ms[ki]
+        rn.free()
+    n_ms = statistics.median(n_times)
+    nucleotide = {"workload": "64 sequences over ACGT, 200-400 nt, star tree s=0.40, GTR-derived tables",
+                  "value": nfam.cells() / (n_ms * 1e-3) / 1e9, "unit": "GCUPS", "ms_per_step": n_ms,
+                  "pairs": nfam.n_pairs, "cells_per_step": nfam.cells(), "nnz": n_nnz,
+                  "fp64_fallback_pairs": n_fb, "kernel_ms_timed_region": n_kms}
+
     # ---- guide tree (weighted UPGMA) on the stage's FP64 distance matrix,
     # device to device, the step that consumes this stage's output
     r = step_dev()
@@ -570,6 +599,11 @@ def main():
         "clocks": clocks,
     }
     line["entry_budget"] = entry_budget
+    if nucleotide["kernel_ms_timed_region"] > 0:
+        n_ach = nfam.cells() * ALU_OPS_PER_CELL / (nucleotide["kernel_ms_timed_region"] * 1e-3) / 1e12
+        nucleotide["roofline"] = {"bound": "alu", "achieved": n_ach, "peak": peak_tops, "unit": "Tissue/s",
+                                  "frac": n_ach / peak_tops, "kernel": "k_posterior_f32"}
+    line["nucleotide"] = nucleotide
     line["guide_tree"] = {"k": fam.k, "ms": statistics.median(tree_ms[1:]),
                           "kernels": "k_tree_cluster (k up to about 660), else k_tree_mirror, "
                                      "k_tree_rows, k_tree_join",
