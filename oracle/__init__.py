@@ -188,6 +188,62 @@ def budget_threshold(values, theta: float, n_keep: int, dtype=np.float32):
     return np.nextafter(largest_first[n_keep], dtype(np.inf))
 
 
+def tree_distances(merges, k: int) -> np.ndarray:
+    """Tree-guided distance of selective consistency (paper, Methods,
+    "Selective consistency", variant (b)): d[x, y] = the number of sequences
+    (leaves) in the smallest subtree of the guide tree that contains both x
+    and y, i.e. the subtree at their lowest common ancestor.  ``merges`` are
+    the joins of the guide tree (leaves 0..k-1, the node of step s is k + s).
+    d[x, x] = 1."""
+    members = {i: [i] for i in range(k)}
+    d = np.ones((k, k), dtype=np.int64)
+    for s, (a, b) in enumerate(np.asarray(merges, dtype=np.int64).reshape(-1, 2)):
+        A, B = members.pop(int(a)), members.pop(int(b))
+        size = len(A) + len(B)
+        for x in A:
+            for y in B:
+                d[x, y] = d[y, x] = size
+        members[k + s] = A + B
+    return d
+
+
+def consistency(S: dict, lens, merges, T: int = 200, h: float = 3.0, n_max: int = 200,
+                theta: float = 0.01) -> dict:
+    """Selective consistency (paper, Methods, stage III and "Selective
+    consistency"): every posterior matrix S_xy is relaxed through the third
+    sequences z whose tree distances to x and y both stay within T, and its
+    own signal is amplified by h_xy.
+
+    ``S``: {(x, y): dense (len x, len y) matrix} for every pair x < y (the
+    sparse posteriors, zeros where absent); S_yx is S_xy transposed.
+    For each pair, with Z = {z not in {x, y} : max(d_xz, d_zy) <= T} and
+    h_xy = 1 + (h - 1) min(|Z|, n_max) / n_max:
+        S'_xy = (2 h_xy S_xy + sum_{z in Z} S_xz S_zy) / (2 + |Z|),
+    the relaxation of ProbCons (a sum over all sequences, x and y included
+    with S_xx = I, divided by their number) restricted to Z; then entries
+    below ``theta`` are dropped.  Returns {(x, y): dense S'_xy} and
+    {(x, y): |Z|}."""
+    k = len(lens)
+    d = tree_distances(merges, k)
+
+    def mat(a, b):
+        return S[(a, b)] if a < b else S[(b, a)].T
+
+    out, nz = {}, {}
+    for x in range(k):
+        for y in range(x + 1, k):
+            Z = [z for z in range(k) if z != x and z != y and max(d[x, z], d[z, y]) <= T]
+            hxy = 1.0 + (h - 1.0) * min(len(Z), n_max) / n_max
+            acc = 2.0 * hxy * S[(x, y)]
+            for z in Z:
+                acc = acc + mat(x, z) @ mat(z, y)
+            R = acc / (2.0 + len(Z))
+            R[R < theta] = 0.0
+            out[(x, y)] = R
+            nz[(x, y)] = len(Z)
+    return out, nz
+
+
 def pairs(family, pair_list, prm, threads: int | None = None, theta: float | None = None) -> dict:
     """Per-pair log Z (HMM, PF), MEA score, distance and nnz for the listed
     pairs of ``family``, on a thread pool of ``threads`` host cores."""
