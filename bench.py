@@ -543,6 +543,34 @@ def main():
         tree_ms.append(e0.elapsed_time(e1))
     tree_host = (tree[0].cpu().numpy(), tree[1].cpu().numpy())
 
+    # ---- selective consistency (stage III) on the stage's posteriors over
+    # that guide tree, the paper's settings (T = 200, h = 3): device in and out
+    post = step_dev()
+    for _ in range(2):
+        qp.qp_consistency(post, fam.offsets, tree[0], T=200, h=3.0, threshold=prm.threshold,
+                          out_on_device=True).free()
+    c_ms, c_dev_ms = [], []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc_ = qp.qp_consistency(post, fam.offsets, tree[0], T=200, h=3.0, threshold=prm.threshold,
+                                out_on_device=True)
+        e1.record(stream)
+        e1.synchronize()
+        c_ms.append(e0.elapsed_time(e1))
+        c_dev_ms.append(rc_.kernel_ms[0])
+        c_nnz = int(rc_.nnz)
+        rc_.free()
+    c_fma = qp.qp_get_counter("consistency_fma", device=local)
+    post.free()
+    cms = statistics.median(c_ms)
+    consistency = {"T": 200, "h": 3.0, "threshold": prm.threshold, "ms": cms,
+                   "device_ms": statistics.median(c_dev_ms), "nnz_in": int(nnz), "nnz_out": c_nnz,
+                   "fma": c_fma, "gflops": 2.0 * c_fma / (statistics.median(c_dev_ms) * 1e-3) / 1e9,
+                   "kernels": "k_cons_tree, k_cons_ranges, k_cons_tcount/tscan/tfill, k_cons_relax, "
+                              "k_cons_pair_nnz, k_scan_nnz, k_cons_compact"}
+
     # ---- kernel time of k_posterior_f32 for the roofline: CUDA events around
     # the kernel on its stream, in a pass with plain launches (a captured graph
     # carries no events; the kernels' own time stamps from the timed region are
@@ -598,6 +626,7 @@ def main():
                      "ops_per_cell": ALU_OPS_PER_CELL},
         "clocks": clocks,
     }
+    line["consistency"] = consistency
     line["entry_budget"] = entry_budget
     if nucleotide["kernel_ms_timed_region"] > 0:
         n_ach = nfam.cells() * ALU_OPS_PER_CELL / (nucleotide["kernel_ms_timed_region"] * 1e-3) / 1e12

@@ -304,7 +304,8 @@ int qp_set_option(int32_t device, const char* name, int64_t value);
  * paper): "graph_captures" (calls that captured their sequence as a new CUDA
  * graph), "graph_relaunches" (calls that relaunched the cached graph as it
  * was), "plain_calls" (calls with plain launches), "pool_retries" (calls run again because their entries
- * overflowed the entry pool).  QP_EINVAL for an unknown
+ * overflowed the entry pool), "consistency_fma" (multiply-adds of the last
+ * qp_consistency relaxation).  QP_EINVAL for an unknown
  * name or device. */
 int qp_get_counter(int32_t device, const char* name, int64_t* value);
 
@@ -377,6 +378,47 @@ int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int32_t n,
  * working memory cannot be allocated; QP_ECUDA otherwise. */
 int qp_guide_tree(const double* dist, int32_t k, int32_t on_device, int32_t device, void* stream,
                   int32_t* merges, double* heights);
+
+/* Selective consistency (paper, Methods, stage III and "Selective
+ * consistency").  Every posterior matrix S_xy is relaxed through the third
+ * sequences z whose tree distances to x and y both stay within T, and its own
+ * signal is amplified:
+ *   S'_xy = (2 h_xy S_xy + sum_{z in Z_xy} S_xz S_zy) / (2 + |Z_xy|),
+ *   Z_xy  = {z not in {x, y} : max(d_xz, d_zy) <= T},
+ *   h_xy  = 1 + (h - 1) min(|Z_xy|, n_max) / n_max,
+ * where d_xy is the number of sequences in the smallest subtree of the guide
+ * tree holding x and y, S_yx is S_xy transposed, and the 2 counts x and y
+ * themselves (S_xx = I: the ProbCons relaxation restricted to Z).  Entries
+ * below `threshold` are dropped.  FP32 arithmetic; the sum over z runs in
+ * the guide tree's leaf order.
+ *   T         : tree-distance threshold (the paper: about 200);
+ *   n_max     : relaxations at which the amplification reaches h (200);
+ *   h         : amplification, >= 1 (the paper: 3);
+ *   threshold : entries kept, 0 < threshold <= 1. */
+typedef struct qp_consistency_params {
+    int32_t T;
+    int32_t n_max;
+    double h;
+    double threshold;
+} qp_consistency_params;
+
+/*   posteriors : a qp_posteriors result (host or device, either precision; its
+ *                float values are used);
+ *   offsets    : HOST int64[k + 1], the family's sequence offsets (lengths
+ *                1 .. 51200);
+ *   merges     : int32[(k - 1) * 2], a guide tree's joins as qp_guide_tree
+ *                writes them (leaves 0..k-1, node of step s = k + s); HOST,
+ *                or DEVICE memory of the result's device when
+ *                merges_on_device;
+ *   out        : a new result in the layout of the posteriors (the relaxed
+ *                matrices; dist, dist64, mea, log totals and flags copied
+ *                from the input; kernel_ms[0] the device time of the stage).
+ * k <= 16384.  QP_EINVAL for bad arguments or merges that are not a join
+ * sequence of k leaves, QP_ENOMEM, QP_ECUDA.  Runs on the library's stream
+ * and returns after the result is complete. */
+int qp_consistency(const qp_result* posteriors, const int64_t* offsets, const int32_t* merges,
+                   int32_t merges_on_device, const qp_consistency_params* params, int32_t out_on_device,
+                   qp_result** out);
 
 /* Thread-local message of the last failure on the calling thread. */
 const char* qp_last_error(void);

@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libqp.so")
-SOURCES = ["qp_kernels.cu", "qp_api.cpp", "qp_server.cpp", "qp_static.cu", "qp_tree.cu", "qp_budget.cu"]
+SOURCES = ["qp_kernels.cu", "qp_api.cpp", "qp_server.cpp", "qp_static.cu", "qp_tree.cu", "qp_budget.cu", "qp_consistency.cu"]
 HEADERS = ["qp_internal.h", "qp_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

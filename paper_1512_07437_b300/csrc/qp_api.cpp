@@ -995,6 +995,7 @@ int qp_get_counter(int32_t device, const char* name, int64_t* value) {
     else if (n == "graph_relaunches") *value = C->graph_relaunches;
     else if (n == "plain_calls") *value = C->plain_calls;
     else if (n == "pool_retries") *value = C->pool_retries;
+    else if (n == "consistency_fma") *value = C->cons_fma;
     else return fail(QP_EINVAL, "unknown counter '%s'", name);
     return QP_OK;
 }

@@ -147,6 +147,13 @@ struct Context {
     qpk::RawParams last_raw;             // parameters the tables in cst were derived from
     bool raw_valid = false;
     DevBuf row_cnt, chunk_off, pair_nnz, fallback, pool, pool64;
+    // selective consistency: workspace, entry pool, pinned status, events
+    std::mutex cons_mu;
+    DevBuf cons_ws, cons_pool;
+    HostBuf cons_h;
+    int64_t cons_pool_hint = 0;
+    int64_t cons_fma = 0;                // multiply-adds of the last relaxation
+    cudaEvent_t cons_ev[2] = {};
     // guide tree: working memory kept between calls, pinned staging
     std::mutex tree_mu;
     DevBuf tree_ws;

@@ -71,6 +71,11 @@ class qp_result(ctypes.Structure):
     ]
 
 
+class qp_consistency_params(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("n_max", ctypes.c_int32), ("h", ctypes.c_double),
+                ("threshold", ctypes.c_double)]
+
+
 class qp_server_stats(ctypes.Structure):
     _fields_ = [
         ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
@@ -126,6 +131,9 @@ def lib():
         L.qp_guide_tree.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.qp_guide_tree.restype = ctypes.c_int
+        L.qp_consistency.argtypes = [P(qp_result), P(ctypes.c_int64), ctypes.c_void_p, ctypes.c_int32,
+                                     P(qp_consistency_params), ctypes.c_int32, P(P(qp_result))]
+        L.qp_consistency.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -363,6 +371,28 @@ def qp_guide_tree(dist, device: Optional[int] = None, stream=None):
     _check(lib().qp_guide_tree(d.ctypes.data, k, 0, 0 if device is None else int(device), stream or None,
                                merges.ctypes.data, heights.ctypes.data))
     return merges, heights
+
+
+def qp_consistency(posteriors: Result, offsets, merges, T: int = 200, n_max: int = 200, h: float = 3.0,
+                   threshold: float = 0.01, out_on_device: bool = False) -> Result:
+    """Selective consistency (qp_consistency in qp.h): the relaxed posterior
+    matrices of ``posteriors`` over the guide tree ``merges`` (an int32 (k-1, 2)
+    numpy array, or a CUDA tensor on the result's device)."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    cp = qp_consistency_params(int(T), int(n_max), float(h), float(threshold))
+    if hasattr(merges, "is_cuda") and merges.is_cuda:
+        import torch
+        mg = merges.to(torch.int32).contiguous()
+        addr, on_dev = int(mg.data_ptr()), 1
+    else:
+        mg = np.ascontiguousarray(np.asarray(merges, dtype=np.int32))
+        addr, on_dev = mg.ctypes.data, 0
+    out = ctypes.POINTER(qp_result)()
+    rc = lib().qp_consistency(posteriors._ptr, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), addr, on_dev,
+                              ctypes.byref(cp), int(bool(out_on_device)), ctypes.byref(out))
+    del mg
+    _check(rc)
+    return Result(out)
 
 
 def qp_result_free(result: Result):

@@ -220,6 +220,21 @@ def _random_tree(rng, n_leaves: int):
     return parent, nxt
 
 
+def random_guide_tree(seed: int, k: int) -> np.ndarray:
+    """A seeded random join sequence over k leaves, in the guide-tree layout
+    (row s joins two ids; leaves 0..k-1, the node of step s is k + s): an
+    input for stages that consume a guide tree."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    slots = list(range(k))
+    merges = np.zeros((max(k - 1, 0), 2), dtype=np.int32)
+    for s in range(k - 1):
+        i, j = sorted(rng.choice(len(slots), size=2, replace=False).tolist())
+        merges[s] = (slots[i], slots[j])
+        slots.pop(j)
+        slots[i] = k + s
+    return merges
+
+
 def tree_family(seed: int, k: int, root_len: tuple, s_range: tuple,
                 trim: Optional[tuple] = None, keep: Optional[tuple] = None,
                 q=None, name="tree", alphabet: str = "protein") -> Family:

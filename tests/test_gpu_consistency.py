@@ -1,0 +1,153 @@
+"""Selective consistency (paper, Methods, stage III and "Selective
+consistency") on the GPU against the oracle.
+
+Parity: both sides relax their own dense posteriors (threshold 1e-30, so no
+entry is near a threshold) over the same seeded guide tree.  The posteriors
+differ by at most 1e-5 (FP32 form); a product term of row sums at most
+sqrt(2) then moves by at most 2 sqrt(2) 1e-5, and so does the average of
+terms: the relaxed values must agree within 4e-5, and the kept pattern
+outside that band around the output threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import host
+
+pytestmark = pytest.mark.gpu
+
+DENSE = 1e-30
+TOL = 4e-5
+
+
+@pytest.fixture(scope="module")
+def qp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1512_07437_b300 as qp
+    qp.lib()
+    return qp
+
+
+@pytest.fixture(scope="module")
+def small(qp):
+    """7 sequences of 30-70 residues, their dense posteriors on the GPU and
+    in the oracle, and a seeded guide tree."""
+    fam = synth.star_family(71, 7, (30, 70), 0.3)
+    prm = synth.default_params(threshold=DENSE)
+    res = qp.qp_posteriors(fam.residues, fam.offsets, prm, device=0)
+    S = {}
+    for a, b in fam.pairs():
+        S[(a, b)] = oracle.pair(fam.codes(a), fam.codes(b), prm)["P"]
+    merges = synth.random_guide_tree(5, fam.k)
+    return fam, res, S, merges
+
+
+def _dense(res, k, lens):
+    out = {}
+    pro = host(res.array("pair_row_off"))
+    pno = host(res.array("pair_nnz_off"))
+    rp_all = host(res.array("row_ptr"))
+    col = host(res.array("col"))
+    val = host(res.array("val")).astype(np.float64)
+    p = 0
+    for a in range(k):
+        for b in range(a + 1, k):
+            rp = rp_all[pro[p]:pro[p + 1]]
+            D = np.zeros((lens[a], lens[b]))
+            base = int(pno[p])
+            for i in range(lens[a]):
+                c = col[base + rp[i]:base + rp[i + 1]]
+                assert (np.diff(c) > 0).all(), "columns must ascend within a row"
+                D[i, c] = val[base + rp[i]:base + rp[i + 1]]
+            out[(a, b)] = D
+            p += 1
+    return out
+
+
+@pytest.mark.parametrize("T,h,n_max", [(200, 3.0, 200), (3, 3.0, 200), (5, 1.0, 200), (4, 3.0, 2), (1, 3.0, 200)])
+def test_relaxation_matches_oracle(qp, small, T, h, n_max):
+    fam, res, S, merges = small
+    lens = [int(v) for v in fam.lengths]
+    theta = 0.01
+    got = qp.qp_consistency(res, fam.offsets, merges, T=T, n_max=n_max, h=h, threshold=theta)
+    exp, nz = oracle.consistency(S, lens, merges, T=T, h=h, n_max=n_max, theta=theta)
+    # the oracle's threshold applied to its unthresholded relaxation, for the band
+    raw, _ = oracle.consistency(S, lens, merges, T=T, h=h, n_max=n_max, theta=-1.0)
+    G = _dense(got, fam.k, lens)
+    worst = 0.0
+    for key in exp:
+        kept_ref = raw[key] >= theta
+        kept_gpu = G[key] > 0
+        band = np.abs(raw[key] - theta) <= TOL
+        assert not ((kept_ref != kept_gpu) & ~band).any(), f"pair {key}: pattern differs outside the band"
+        both = kept_ref & kept_gpu
+        if both.any():
+            worst = max(worst, float(np.abs(G[key][both] - raw[key][both]).max()))
+    assert worst <= TOL, worst
+    assert got.threshold_used == float(np.float32(theta))
+    # distances and MEA scores are those of the posteriors
+    assert np.array_equal(host(got.dist64), host(res.dist64))
+    got.free()
+
+
+def test_no_relaxation_keeps_the_posteriors(qp, small):
+    """T = 0 selects no third sequence: S'_xy = (2 S_xy) / 2 = S_xy exactly,
+    filtered at the threshold."""
+    fam, res, S, merges = small
+    lens = [int(v) for v in fam.lengths]
+    got = qp.qp_consistency(res, fam.offsets, merges, T=0, threshold=0.02)
+    G = _dense(got, fam.k, lens)
+    R = _dense(res, fam.k, lens)
+    for key in G:
+        exp = np.where(R[key] >= np.float32(0.02), R[key], 0.0)
+        assert np.array_equal(G[key], exp), key
+    got.free()
+
+
+def test_host_device_paths_and_determinism(qp):
+    """Host and device posteriors, host and device merges, host and device
+    output: bit-identical results; two runs are identical; merges produced by
+    qp_guide_tree on the device chain straight in."""
+    import torch
+    fam = synth.star_family(72, 12, (60, 140), 0.35)
+    prm = synth.default_params(threshold=0.01)
+    d_res = torch.from_numpy(fam.residues).cuda()
+    post_h = qp.qp_posteriors(fam.residues, fam.offsets, prm, device=0)
+    post_d = qp.qp_posteriors(d_res, fam.offsets, prm, device=0, out_on_device=True)
+    merges_d, _ = qp.qp_guide_tree(post_d.dist64)
+    merges_h = merges_d.cpu().numpy()
+    runs = [
+        qp.qp_consistency(post_h, fam.offsets, merges_h, T=6),
+        qp.qp_consistency(post_d, fam.offsets, merges_d, T=6),
+        qp.qp_consistency(post_d, fam.offsets, merges_h, T=6, out_on_device=True),
+        qp.qp_consistency(post_h, fam.offsets, merges_h, T=6),
+    ]
+    ref = runs[0]
+    n = int(ref.nnz)
+    assert n > 0
+    for r in runs[1:]:
+        assert int(r.nnz) == n
+        for name in ("pair_row_off", "row_ptr", "pair_nnz_off", "col", "val"):
+            assert np.array_equal(host(r.array(name)), host(ref.array(name))), name
+    for r in runs + [post_h, post_d]:
+        r.free()
+
+
+def test_rejects_bad_input(qp, small):
+    fam, res, S, merges = small
+    bad = merges.copy()
+    bad[1] = bad[0]                                   # a node joined twice
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_consistency(res, fam.offsets, bad)
+    assert e.value.code == 1
+    off = fam.offsets.copy()
+    off[2] += 1                                       # lengths that do not match the posteriors
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_consistency(res, off, merges)
+    assert e.value.code == 1
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_consistency(res, fam.offsets, merges, h=0.5)
+    assert e.value.code == 1
