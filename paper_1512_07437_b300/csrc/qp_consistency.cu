@@ -26,12 +26,14 @@
 //                     accumulator row in shared memory, a Gustavson product
 //                     per z with lanes over (outer entry, inner entry) pairs,
 //                     then the amplified S_xy row, the scale, the threshold,
-//                     and the kept entries into a pool chunk per row.  The
-//                     products are added as 64-bit fixed point (units of
-//                     2^-40): integer addition is associative, so the sum
-//                     does not depend on the order the lanes' atomics land
-//                     in (bit-reproducible results) and is exact apart from
-//                     one rounding per product;
+//                     and the kept entries into a pool chunk per row.  Each
+//                     product (at most 1) is rounded to 32-bit fixed point
+//                     (units of 2^-30) and added into a 64-bit accumulator:
+//                     integer addition is associative, so the sum does not
+//                     depend on the order the lanes' atomics land in
+//                     (bit-reproducible results) and is exact apart from one
+//                     rounding per product.  No 64-bit conversion per
+//                     product: those run on B300's narrow FP64 pipe;
 //   k_cons_compact    CSR of every pair from the row chunks.
 #include "../../include/qp.h"
 #include "qp_host.h"
@@ -45,8 +47,15 @@ namespace {
 constexpr unsigned FULLM = 0xffffffffu;
 constexpr int kConsWarps = 8;                 // warps per CTA (fewer for very long sequences)
 constexpr int kConsMaxLen = 25600;            // accumulator row of one warp: 200 KB of shared memory
-constexpr float kFix = 1099511627776.0f;      // 2^40: fixed-point unit of the accumulator
-constexpr float kUnfix = 1.0f / 1099511627776.0f;
+constexpr float kFix = 1073741824.0f;         // 2^30: fixed-point unit of a product (products are <= 1)
+constexpr float kUnfix = 1.0f / 1073741824.0f;
+
+// 64-bit fixed-point sum (>= 0) to float: two 32-bit conversions in a fixed
+// order (deterministic), then the unit
+__device__ __forceinline__ float unfix(unsigned long long a) {
+    if (a == 0ull) return 0.0f;
+    return (__uint2float_rn((unsigned)(a >> 32)) * 4294967296.0f + __uint2float_rn((unsigned)a)) * kUnfix;
+}
 constexpr size_t kConsSmem = 200 * 1024;
 
 struct ConsIn {
@@ -59,8 +68,10 @@ struct ConsIn {
     // transposed CSR (rows of b for pair (a, b)), same entry offsets pno
     const int64_t* tpro;    // [P + 1]
     const int32_t* trp;     // [n_rows_t]
-    const int32_t* tcol;
-    const float* tval;
+    // (column, value bits) of every entry, interleaved for single 8-byte
+    // loads: the posteriors (fcv) and their transposes (tcv)
+    const int2* fcv;
+    const int2* tcv;
     const int32_t* len;     // [k]
     const int32_t* leaf_at; // [k] leaf at each DFS position
     const int32_t* pos;     // [k] DFS position of each leaf
@@ -196,7 +207,7 @@ __global__ void k_cons_tscan(ConsIn in, int32_t* tcnt, int32_t* trp) {
 
 // entries in transposed order: rows of a visited in order, so each
 // transposed row lists its entries by ascending row of a
-__global__ void k_cons_tfill(ConsIn in, int32_t* cursor, int32_t* tcol, float* tval) {
+__global__ void k_cons_tfill(ConsIn in, int32_t* cursor, int2* tcv) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
@@ -209,11 +220,16 @@ __global__ void k_cons_tfill(ConsIn in, int32_t* cursor, int32_t* tcol, float* t
         for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
             const int j = in.col[base + e];
             const int q = cur[j]++;
-            tcol[base + q] = i;
-            tval[base + q] = in.val[base + e];
+            tcv[base + q] = make_int2(i, __float_as_int(in.val[base + e]));
         }
         __syncwarp();
     }
+}
+
+// the posteriors' (column, value) pairs interleaved
+__global__ void k_cons_interleave(const int32_t* col, const float* val, int64_t nnz, int2* cv) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        cv[e] = make_int2(col[e], __float_as_int(val[e]));
 }
 
 // ---------------------------------------------------------------- relaxation
@@ -221,8 +237,7 @@ __global__ void k_cons_tfill(ConsIn in, int32_t* cursor, int32_t* tcol, float* t
 // rows of S_ab (a != b): the stored pair when a < b, else the transposed one
 struct MatRef {
     const int32_t* rp;
-    const int32_t* c;
-    const float* v;
+    const int2* cv;     // (column, value bits)
 };
 
 __device__ __forceinline__ MatRef mat_of(const ConsIn& in, int a, int b) {
@@ -230,15 +245,30 @@ __device__ __forceinline__ MatRef mat_of(const ConsIn& in, int a, int b) {
     if (a < b) {
         const int64_t p = pidx(a, b, in.k);
         M.rp = in.rp + in.pro[p];
-        M.c = in.col + in.pno[p];
-        M.v = in.val + in.pno[p];
+        M.cv = in.fcv + in.pno[p];
     } else {
         const int64_t p = pidx(b, a, in.k);
         M.rp = in.trp + in.tpro[p];
-        M.c = in.tcol + in.pno[p];
-        M.v = in.tval + in.pno[p];
+        M.cv = in.tcv + in.pno[p];
     }
     return M;
+}
+
+// the products of one outer entry (t, vk) with row t of B added into acc:
+// the row's entries are loaded eight at a time before their atomics
+__device__ __forceinline__ unsigned long long add_products(unsigned long long* acc, const MatRef& B, int t,
+                                                           float vk) {
+    const int b0 = B.rp[t], nb = B.rp[t + 1] - b0;
+    for (int f0 = 0; f0 < nb; f0 += 8) {
+        int2 cv[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) cv[f] = f0 + f < nb ? B.cv[b0 + f0 + f] : make_int2(-1, 0);
+#pragma unroll
+        for (int f = 0; f < 8; ++f)
+            if (cv[f].x >= 0)
+                atomicAdd(&acc[cv[f].x], (unsigned long long)(unsigned)__float2int_rn(vk * __int_as_float(cv[f].y)));
+    }
+    return (unsigned long long)nb;
 }
 
 // the selected z of a pair and the bases of its two matrices (S_xz rows of
@@ -249,7 +279,7 @@ struct ZRef {
 };
 constexpr int kZTab = 256;                  // table entries (T = 200 selects at most 198 z)
 
-__global__ void __launch_bounds__(kConsWarps * 32, 2) k_cons_relax(ConsIn in, ConsOut out, int nwarps, int acc_len,
+__global__ void __launch_bounds__(kConsWarps * 32, 4) k_cons_relax(ConsIn in, ConsOut out, int nwarps, int acc_len,
                                                                     float h, int n_max, float theta,
                                                                     const int32_t* tree_status) {
     extern __shared__ unsigned long long acc_all[];
@@ -296,16 +326,11 @@ __global__ void __launch_bounds__(kConsWarps * 32, 2) k_cons_relax(ConsIn in, Co
             for (int z0 = 0; z0 < nz; z0 += 8) {
                 const int zi = z0 + g;
                 if (zi < nz) {
-                    const ZRef& Z = ztab[zi];
+                    const ZRef Z = ztab[zi];
                     const int a0 = Z.A.rp[i], na = Z.A.rp[i + 1] - a0;
                     for (int e = q; e < na; e += 4) {
-                        const int t = Z.A.c[a0 + e];
-                        const float v = Z.A.v[a0 + e];
-                        const int b0 = Z.B.rp[t], nb = Z.B.rp[t + 1] - b0;
-                        for (int f = 0; f < nb; ++f)
-                            atomicAdd(&acc[Z.B.c[b0 + f]],
-                                      (unsigned long long)__float2ll_rn(v * Z.B.v[b0 + f] * kFix));
-                        fmas += (unsigned long long)nb;
+                        const int2 tv = Z.A.cv[a0 + e];
+                        fmas += add_products(acc, Z.B, tv.x, __int_as_float(tv.y) * kFix);
                     }
                 }
             }
@@ -320,12 +345,8 @@ __global__ void __launch_bounds__(kConsWarps * 32, 2) k_cons_relax(ConsIn in, Co
                         const MatRef B = mat_of(in, z, y);
                         const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
                         for (int e = q; e < na; e += 4) {
-                            const int t = A.c[a0 + e];
-                            const float v = A.v[a0 + e];
-                            const int b0 = B.rp[t], nb = B.rp[t + 1] - b0;
-                            for (int f = 0; f < nb; ++f)
-                                atomicAdd(&acc[B.c[b0 + f]], (unsigned long long)__float2ll_rn(v * B.v[b0 + f] * kFix));
-                            fmas += (unsigned long long)nb;
+                            const int2 tv = A.cv[a0 + e];
+                            fmas += add_products(acc, B, tv.x, __int_as_float(tv.y) * kFix);
                         }
                     }
                 }
@@ -334,13 +355,13 @@ __global__ void __launch_bounds__(kConsWarps * 32, 2) k_cons_relax(ConsIn in, Co
         __syncwarp();
         // every lane turns its own slots into float bits (in place), then the
         // amplified own signal, then the scale and the threshold
-        for (int j = lane; j < n; j += 32)
-            acc[j] = (unsigned long long)__float_as_uint(__ll2float_rn((long long)acc[j]) * kUnfix);
+        for (int j = lane; j < n; j += 32) acc[j] = (unsigned long long)__float_as_uint(unfix(acc[j]));
         __syncwarp();
         const int s0 = own.rp[i], sn = own.rp[i + 1] - s0;
         for (int f = lane; f < sn; f += 32) {       // the own row's columns are distinct
-            const int j = own.c[s0 + f];
-            acc[j] = (unsigned long long)__float_as_uint(__uint_as_float((unsigned)acc[j]) + self * own.v[s0 + f]);
+            const int2 cv = own.cv[s0 + f];
+            acc[cv.x] = (unsigned long long)__float_as_uint(__uint_as_float((unsigned)acc[cv.x]) +
+                                                             self * __int_as_float(cv.y));
         }
         __syncwarp();
         int kept = 0;
@@ -489,8 +510,8 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     const size_t o_tpro = take(sizeof(int64_t) * (P + 1));
     const size_t o_trp = take(sizeof(int32_t) * rows_t);
     const size_t o_tcur = take(sizeof(int32_t) * rows_t);
-    const size_t o_tcol = take(sizeof(int32_t) * nnz_in);
-    const size_t o_tval = take(sizeof(float) * nnz_in);
+    const size_t o_tcv = take(sizeof(int2) * nnz_in);
+    const size_t o_fcv = take(sizeof(int2) * nnz_in);
     const size_t o_len = take(sizeof(int32_t) * k);
     const size_t o_mg = take(sizeof(int32_t) * 2 * (k - 1));
     const size_t o_tree = take(sizeof(int32_t) * (size_t)(2 * k - 1) * 6 + sizeof(int32_t) * k * 4);
@@ -511,8 +532,8 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     in.val = host_in ? (const float*)(W + o_val) : post->val;
     in.tpro = (const int64_t*)(W + o_tpro);
     in.trp = (const int32_t*)(W + o_trp);
-    in.tcol = (const int32_t*)(W + o_tcol);
-    in.tval = (const float*)(W + o_tval);
+    in.tcv = (const int2*)(W + o_tcv);
+    in.fcv = (const int2*)(W + o_fcv);
     in.len = (const int32_t*)(W + o_len);
     int32_t* tr = (int32_t*)(W + o_tree);
     const int nn = 2 * k - 1;
@@ -555,8 +576,9 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     k_cons_ranges<<<(k + 127) / 128, 128, 0, st>>>(k, cp->T, parent, size, first, rlo, rhi, d_status);
     k_cons_tcount<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_tcur));
     k_cons_tscan<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_tcur), (int32_t*)(W + o_trp));
-    k_cons_tfill<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_tcur), (int32_t*)(W + o_tcol),
-                                              (float*)(W + o_tval));
+    k_cons_tfill<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_tcur), (int2*)(W + o_tcv));
+    k_cons_interleave<<<(int)std::min<int64_t>(8 * C->sm_count, (nnz_in + 255) / 256 + 1), 256, 0, st>>>(
+        in.col, in.val, nnz_in, (int2*)(W + o_fcv));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "consistency: set-up kernels");
 
     // ---- relaxation into the pool (grown and run again when it overflows)
