@@ -563,13 +563,16 @@ def main():
         c_nnz = int(rc_.nnz)
         rc_.free()
     c_fma = qp.qp_get_counter("consistency_fma", device=local)
+    c_form = qp.qp_get_counter("consistency_form", device=local)
     post.free()
     cms = statistics.median(c_ms)
     consistency = {"T": 200, "h": 3.0, "threshold": prm.threshold, "ms": cms,
                    "device_ms": statistics.median(c_dev_ms), "nnz_in": int(nnz), "nnz_out": c_nnz,
                    "fma": c_fma, "gflops": 2.0 * c_fma / (statistics.median(c_dev_ms) * 1e-3) / 1e9,
-                   "kernels": "k_cons_tree, k_cons_ranges, k_cons_tcount/tscan/tfill, k_cons_relax, "
-                              "k_cons_pair_nnz, k_scan_nnz, k_cons_compact"}
+                   "form": "staged" if c_form == 1 else "row",
+                   "kernels": "k_cons_tree, k_cons_ranges, k_cons_tcount/tscan/tfill, k_cons_interleave, "
+                              + ("k_cons_stats, k_cons_relax_staged, " if c_form == 1 else "k_cons_relax, ")
+                              + "k_cons_pair_nnz, k_scan_nnz, k_cons_compact"}
 
     # ---- kernel time of k_posterior_f32 for the roofline: CUDA events around
     # the kernel on its stream, in a pass with plain launches (a captured graph

@@ -296,6 +296,17 @@ void qp_server_destroy(qp_server* server);
  *   "pool_entries"    releases the entry pool and starts later calls from a
  *                     pool of at most this many entries (a call whose entries
  *                     overflow it grows it and runs again; 0: estimated).
+ *   "cons_form"       qp_consistency: 1 the staged form (a CTA per row chunk
+ *                     of a pair, each third sequence's matrices copied into
+ *                     shared memory, 32-bit fixed-point sums), 0 the row form
+ *                     (a CTA per pair, matrices read from global memory,
+ *                     64-bit fixed-point sums); automatic: the staged form
+ *                     when T <= 256 and the sums' bound allows its unit;
+ *   "cons_chunk_rows" qp_consistency staged form: at most this many rows of
+ *                     x per CTA (0: as many as the shared memory holds);
+ *   "cons_min_unit"   qp_consistency staged form: the coarsest fixed-point
+ *                     unit 2^-u it accepts (default 21); a call whose bound
+ *                     on the sums needs a coarser unit runs the row form;
  * Applies to later qp_posteriors calls and servers created afterwards.
  * QP_EINVAL for an unknown name or device. */
 int qp_set_option(int32_t device, const char* name, int64_t value);
@@ -305,7 +316,8 @@ int qp_set_option(int32_t device, const char* name, int64_t value);
  * graph), "graph_relaunches" (calls that relaunched the cached graph as it
  * was), "plain_calls" (calls with plain launches), "pool_retries" (calls run again because their entries
  * overflowed the entry pool), "consistency_fma" (multiply-adds of the last
- * qp_consistency relaxation).  QP_EINVAL for an unknown
+ * qp_consistency relaxation), "consistency_form" (form of the last
+ * qp_consistency relaxation: 1 staged, 0 row form).  QP_EINVAL for an unknown
  * name or device. */
 int qp_get_counter(int32_t device, const char* name, int64_t* value);
 

@@ -334,6 +334,7 @@ Context* get_context(int device, int* status) {
     if (e != cudaSuccess) { *status = cuda_fail(e, "cudaGetDeviceProperties"); return nullptr; }
     c->sm_count = prop.multiProcessorCount;
     c->cc_major = prop.major; c->cc_minor = prop.minor;
+    c->smem_optin = (int)prop.sharedMemPerBlockOptin;
     if (prop.major < 10) {
         *status = fail(QP_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a", device, prop.major, prop.minor);
         return nullptr;
@@ -996,6 +997,7 @@ int qp_get_counter(int32_t device, const char* name, int64_t* value) {
     else if (n == "plain_calls") *value = C->plain_calls;
     else if (n == "pool_retries") *value = C->pool_retries;
     else if (n == "consistency_fma") *value = C->cons_fma;
+    else if (n == "consistency_form") *value = C->cons_last_form;
     else return fail(QP_EINVAL, "unknown counter '%s'", name);
     return QP_OK;
 }
@@ -1045,6 +1047,14 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
         if (value > 0 && (value > 16 || (value & (value - 1))))
             return fail(QP_EINVAL, "tree_ctas must be 1, 2, 4, 8 or 16");
         C->tune.tree_ctas = value > 0 ? (int)value : 0;
+    } else if (n == "cons_form") {
+        if (value > 1) return fail(QP_EINVAL, "cons_form must be 0, 1 or -1");
+        C->tune.cons_form = value < 0 ? -1 : (int)value;
+    } else if (n == "cons_min_unit") {
+        if (value > 31) return fail(QP_EINVAL, "cons_min_unit must be <= 31");
+        C->tune.cons_min_unit = value > 0 ? (int)value : 0;
+    } else if (n == "cons_chunk_rows") {
+        C->tune.cons_chunk_rows = value > 0 ? (int)std::min<int64_t>(value, 1 << 20) : 0;
     } else {
         return fail(QP_EINVAL, "unknown option '%s'", name);
     }

@@ -68,8 +68,8 @@ struct ConsIn {
     // transposed CSR (rows of b for pair (a, b)), same entry offsets pno
     const int64_t* tpro;    // [P + 1]
     const int32_t* trp;     // [n_rows_t]
-    // (column, value bits) of every entry, interleaved for single 8-byte
-    // loads: the posteriors (fcv) and their transposes (tcv)
+    // (row << 16 | column, value bits) of every entry, interleaved for single
+    // 8-byte loads: the posteriors (fcv) and their transposes (tcv)
     const int2* fcv;
     const int2* tcv;
     const int32_t* len;     // [k]
@@ -107,6 +107,11 @@ __device__ __forceinline__ int2 pair_of(int64_t p, int k) {
     const int b = (int)(p - pidx(a, a + 1, k)) + a + 1;
     return make_int2(a, b);
 }
+
+// an entry's row and column in one word (both below 2^16)
+__device__ __forceinline__ int pack_key(int row, int col) { return (row << 16) | col; }
+__device__ __forceinline__ int key_col(int key) { return key & 0xffff; }
+__device__ __forceinline__ int key_row(int key) { return (int)((unsigned)key >> 16); }
 
 // ---------------------------------------------------------------- guide tree ranges
 
@@ -220,16 +225,26 @@ __global__ void k_cons_tfill(ConsIn in, int32_t* cursor, int2* tcv) {
         for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
             const int j = in.col[base + e];
             const int q = cur[j]++;
-            tcv[base + q] = make_int2(i, __float_as_int(in.val[base + e]));
+            tcv[base + q] = make_int2(pack_key(j, i), __float_as_int(in.val[base + e]));
         }
         __syncwarp();
     }
 }
 
-// the posteriors' (column, value) pairs interleaved
-__global__ void k_cons_interleave(const int32_t* col, const float* val, int64_t nnz, int2* cv) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
-        cv[e] = make_int2(col[e], __float_as_int(val[e]));
+// the posteriors' entries as (key, value bits) pairs, key = row << 16 |
+// column (lengths are below 2^16), for single 8-byte loads that carry
+// both indices (warp per pair, rows in order)
+__global__ void k_cons_interleave(ConsIn in, int2* cv) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= in.P) return;
+    const int2 ab = pair_of(p, in.k);
+    const int m = in.len[ab.x];
+    const int32_t* rp = in.rp + in.pro[p];
+    const int64_t base = in.pno[p];
+    for (int i = 0; i < m; ++i)
+        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32)
+            cv[base + e] = make_int2(pack_key(i, in.col[base + e]), __float_as_int(in.val[base + e]));
 }
 
 // ---------------------------------------------------------------- relaxation
@@ -237,7 +252,7 @@ __global__ void k_cons_interleave(const int32_t* col, const float* val, int64_t 
 // rows of S_ab (a != b): the stored pair when a < b, else the transposed one
 struct MatRef {
     const int32_t* rp;
-    const int2* cv;     // (column, value bits)
+    const int2* cv;     // (row << 16 | column, value bits)
 };
 
 __device__ __forceinline__ MatRef mat_of(const ConsIn& in, int a, int b) {
@@ -266,7 +281,8 @@ __device__ __forceinline__ unsigned long long add_products(unsigned long long* a
 #pragma unroll
         for (int f = 0; f < 8; ++f)
             if (cv[f].x >= 0)
-                atomicAdd(&acc[cv[f].x], (unsigned long long)(unsigned)__float2int_rn(vk * __int_as_float(cv[f].y)));
+                atomicAdd(&acc[key_col(cv[f].x)],
+                          (unsigned long long)(unsigned)__float2int_rn(vk * __int_as_float(cv[f].y)));
     }
     return (unsigned long long)nb;
 }
@@ -330,7 +346,7 @@ __global__ void __launch_bounds__(kConsWarps * 32, 4) k_cons_relax(ConsIn in, Co
                     const int a0 = Z.A.rp[i], na = Z.A.rp[i + 1] - a0;
                     for (int e = q; e < na; e += 4) {
                         const int2 tv = Z.A.cv[a0 + e];
-                        fmas += add_products(acc, Z.B, tv.x, __int_as_float(tv.y) * kFix);
+                        fmas += add_products(acc, Z.B, key_col(tv.x), __int_as_float(tv.y) * kFix);
                     }
                 }
             }
@@ -346,7 +362,7 @@ __global__ void __launch_bounds__(kConsWarps * 32, 4) k_cons_relax(ConsIn in, Co
                         const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
                         for (int e = q; e < na; e += 4) {
                             const int2 tv = A.cv[a0 + e];
-                            fmas += add_products(acc, B, tv.x, __int_as_float(tv.y) * kFix);
+                            fmas += add_products(acc, B, key_col(tv.x), __int_as_float(tv.y) * kFix);
                         }
                     }
                 }
@@ -360,7 +376,7 @@ __global__ void __launch_bounds__(kConsWarps * 32, 4) k_cons_relax(ConsIn in, Co
         const int s0 = own.rp[i], sn = own.rp[i + 1] - s0;
         for (int f = lane; f < sn; f += 32) {       // the own row's columns are distinct
             const int2 cv = own.cv[s0 + f];
-            acc[cv.x] = (unsigned long long)__float_as_uint(__uint_as_float((unsigned)acc[cv.x]) +
+            acc[key_col(cv.x)] = (unsigned long long)__float_as_uint(__uint_as_float((unsigned)acc[key_col(cv.x)]) +
                                                              self * __int_as_float(cv.y));
         }
         __syncwarp();
@@ -395,6 +411,375 @@ __global__ void __launch_bounds__(kConsWarps * 32, 4) k_cons_relax(ConsIn in, Co
     }
     for (int d = 16; d > 0; d >>= 1) fmas += __shfl_xor_sync(FULLM, fmas, d);
     if (lane == 0 && fmas) atomicAdd(out.fma, fmas);
+}
+
+// ---------------------------------------------------------------- staged form
+
+// largest value and largest row sum of every matrix and of its transpose
+// (lane per row, entries summed in order: deterministic), for the staged
+// form's fixed-point unit; stats[0] / stats[1] hold float bits (values >= 0)
+__global__ void k_cons_stats(ConsIn in, unsigned* stats) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= in.P) return;
+    const int2 ab = pair_of(p, in.k);
+    float vmax = 0.f, smax = 0.f;
+    for (int side = 0; side < 2; ++side) {
+        const int rows = in.len[side ? ab.y : ab.x];
+        const int32_t* rp = side ? in.trp + in.tpro[p] : in.rp + in.pro[p];
+        const int2* cv = (side ? in.tcv : in.fcv) + in.pno[p];
+        for (int r = lane; r < rows; r += 32) {
+            float s = 0.f;
+            for (int f = rp[r]; f < rp[r + 1]; ++f) {
+                const float v = __int_as_float(cv[f].y);
+                s += v;
+                vmax = fmaxf(vmax, v);
+            }
+            smax = fmaxf(smax, s);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        vmax = fmaxf(vmax, __shfl_xor_sync(FULLM, vmax, d));
+        smax = fmaxf(smax, __shfl_xor_sync(FULLM, smax, d));
+    }
+    if (lane == 0) {
+        atomicMax(&stats[0], __float_as_uint(vmax));
+        atomicMax(&stats[1], __float_as_uint(smax));
+    }
+}
+
+// one selected z of a (pair, row chunk): A = S_xz (rows i0 .. i1 - 1 of x),
+// B = S_zy (all rows of z), in global memory
+struct ZEnt {
+    const int2* acv;        // A's entries of the chunk (keys carry their rows)
+    const int32_t* brp;     // B's row pointers
+    const int2* bcv;        // B's entries
+    int na;                 // A's entries of the chunk
+    int nb;                 // B's entries
+    int lz;                 // B's rows
+};
+
+// where the products read one z from: its staged copy in shared memory, or
+// global memory for a z larger than a stage buffer
+struct SView {
+    const int2* acv;
+    const int32_t* brp;
+    const int2* bcv;
+};
+
+struct StageCfg {
+    int slot_bytes;         // one of the two stage buffers (a multiple of 16)
+    int acc_cells;          // accumulator cells (rows of the chunk x n)
+};
+
+constexpr int kStThreads = 512;             // 16 warps: one CTA per SM (its shared memory)
+constexpr int kStBatch = 32;                // z per stage buffer at most (a lane of the producer warp each)
+constexpr int kMinUnit = 21;                // coarsest fixed-point unit (2^-21) the staged form accepts by default
+constexpr int kStGroup = 1;                 // threads per A entry along a row of B
+constexpr int kStSlotBytes = 56 * 1024;     // one stage buffer
+constexpr int kStMaxRows = 1024;            // rows of a chunk at most
+constexpr int kStSpin = 1 << 22;            // polls of a stage buffer's barrier before the call is failed
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// TMA bulk copy global -> shared (16-byte aligned addresses, a multiple of
+// 16 bytes), completing on the barrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__host__ __device__ constexpr int r16(int b) { return (b + 15) & ~15; }
+
+// the bulk copy of [g, g + bytes): from the 16-byte boundary at or below g
+// (those bytes share g's 16-byte block, so they lie in the same allocation)
+// to the next one at or above g + bytes (every array read here ends at least
+// 16 bytes before the end of its allocation: allocations are padded to 256
+// bytes); returns the copy's size, *head = the offset of g in it
+__device__ __forceinline__ int bulk_span(const void* g, int bytes, int* head) {
+    const uintptr_t a = (uintptr_t)g;
+    *head = (int)(a & 15);
+    return bytes > 0 ? r16(*head + bytes) : 0;
+}
+
+// Relaxation of rows i0 .. i1 - 1 of one pair (a work item) with the
+// selected z staged in shared memory.  Warp 0 produces: its lanes take one
+// z each of the next batch, a warp scan packs as many as fit into a stage
+// buffer, and each lane issues the TMA bulk copies of its z (A's entries of
+// the chunk, B's row pointers and entries), completing on the buffer's
+// barrier; a z larger than a buffer is read from global memory.  Two
+// buffers: the next batch lands while this one is multiplied.  The batch's
+// A entries (t, v) are numbered through, G threads per entry (the key of an
+// entry holds its row, so no search is needed); the threads of an entry run
+// along row t of B and add v * S_zy(t, j) into the chunk's dense
+// accumulator as 32-bit fixed point in units of 2^-u: u is the largest unit
+// with (selected z bound) x (largest value) x (largest row sum) x 2^u <=
+// 2^31, so no sum can overflow, and integer atomics keep the result
+// independent of their order (bit-reproducible).  Then, per row, the
+// amplified own signal, the scale and the threshold; one pool reservation
+// for the chunk's kept entries.
+template <int G>
+__global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, ConsOut out, const int4* __restrict__ work,
+                                                                    StageCfg sc, float h, int n_max, float theta, int nzb,
+                                                                    const unsigned* __restrict__ stats, int min_unit,
+                                                                    int32_t* wide, int32_t* stage_err,
+                                                                    const int32_t* tree_status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned long long red[kStThreads / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ __align__(8) unsigned long long bars[2];
+    __shared__ int bcount[2];
+    __shared__ int bps[2][kStBatch + 1];            // first A entry of each z of a batch
+    if (*tree_status) return;
+    if (smem_u32(smem) & 15) {                       // bulk copies need 16-byte aligned buffers
+        if (threadIdx.x == 0) atomicExch(stage_err, 1);
+        return;
+    }
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
+    // the fixed-point unit (the same in every CTA)
+    const float bound = (float)nzb * __uint_as_float(stats[0]) * __uint_as_float(stats[1]);
+    int u = 30;
+    if (bound > 0.f) {
+        if (!(bound <= 1e30f)) u = -1;
+        else { int ex; frexpf(bound, &ex); u = min(30, 31 - ex); }
+    }
+    if (u < min_unit) {
+        if (tid == 0) atomicExch(wide, 1);
+        return;
+    }
+    const float unit = ldexpf(1.f, u), inv_unit = ldexpf(1.f, -u);
+
+    const int4 w = work[blockIdx.x];
+    const int p = w.x, i0 = w.y, i1 = w.z, rc = i1 - i0;
+    const int2 xy = pair_of(p, in.k);
+    const int x = xy.x, y = xy.y;
+    const int n = in.len[y];
+    const int lo = max(in.rlo[x], in.rlo[y]), hi = min(in.rhi[x], in.rhi[y]);
+    int nz = max(0, hi - lo);
+    const int px = in.pos[x], py = in.pos[y];
+    if (nz > 0 && px >= lo && px < hi) --nz;
+    if (nz > 0 && py >= lo && py < hi) --nz;
+    const float hxy = 1.0f + (h - 1.0f) * (float)min(nz, n_max) / (float)n_max;
+    const float self = 2.0f * hxy;
+    const float scale = 1.0f / (2.0f + (float)nz);
+    if (tid == 0 && i0 == 0) out.nz[p] = nz;
+
+    ZEnt* zt = (ZEnt*)smem;
+    SView* views = (SView*)(smem + sizeof(ZEnt) * kZTab);
+    unsigned char* slots = (unsigned char*)(views + 2 * kStBatch);
+    unsigned* acc = (unsigned*)(slots + 2 * sc.slot_bytes);
+    int* rcnt = (int*)(acc + sc.acc_cells);
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    for (int v = lo + tid; v < hi; v += nthr) {
+        const int z = in.leaf_at[v];
+        if (z == x || z == y) continue;
+        const int slot = v - lo - (px >= lo && px < v ? 1 : 0) - (py >= lo && py < v ? 1 : 0);
+        const MatRef A = mat_of(in, x, z), B = mat_of(in, z, y);
+        const int lz = in.len[z];
+        const int a0 = A.rp[i0];
+        ZEnt e;
+        e.acv = A.cv + a0; e.brp = B.rp; e.bcv = B.cv;
+        e.na = A.rp[i1] - a0; e.nb = B.rp[lz]; e.lz = lz;
+        zt[slot] = e;
+    }
+    __syncthreads();
+
+    // producer (warp 0): the batch of z starting at zs into buffer s;
+    // returns its size (the same in every lane)
+    auto issue = [&](int zs, int s) {
+        const int zi = zs + lane;
+        int need = 0, na = 0, h2 = 0, h3 = 0, h4 = 0, c2 = 0, c3 = 0, c4 = 0;
+        bool glob = false;
+        ZEnt Z = {};
+        if (zi < nz) {
+            Z = zt[zi];
+            na = Z.na;
+            c2 = bulk_span(Z.acv, Z.na * 8, &h2);
+            c3 = bulk_span(Z.brp, (Z.lz + 1) * 4, &h3);
+            c4 = bulk_span(Z.bcv, Z.nb * 8, &h4);
+            need = c2 + c3 + c4;
+            if (need > sc.slot_bytes) { need = 0; glob = true; }
+        }
+        int incl = need, nincl = na;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(FULLM, incl, d), tn = __shfl_up_sync(FULLM, nincl, d);
+            if (lane >= d) { incl += t; nincl += tn; }
+        }
+        const bool fits = zi < nz && incl <= sc.slot_bytes;
+        const unsigned stop = __ballot_sync(FULLM, !fits);
+        const int cnt = stop ? __ffs(stop) - 1 : 32;        // lanes [0, cnt) form the batch (cnt >= 1)
+        const int total = __shfl_sync(FULLM, incl, cnt - 1);
+        unsigned char* b = slots + s * sc.slot_bytes + (incl - need);
+        if (lane < cnt) {
+            SView v;
+            if (glob) {
+                v.acv = Z.acv; v.brp = Z.brp; v.bcv = Z.bcv;
+            } else {
+                v.acv = (const int2*)(b + h2);
+                v.brp = (const int32_t*)(b + c2 + h3);
+                v.bcv = (const int2*)(b + c2 + c3 + h4);
+            }
+            views[s * kStBatch + lane] = v;
+            bps[s][lane] = nincl - na;
+            if (lane == cnt - 1) bps[s][cnt] = nincl;
+        }
+        if (lane == 0) bcount[s] = cnt;
+        __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(&bars[s], (unsigned)total);
+        __syncwarp();
+        if (lane < cnt && !glob) {
+            if (c2) bulk_g2s(b, (const unsigned char*)Z.acv - h2, c2, &bars[s]);
+            if (c3) bulk_g2s(b + c2, (const unsigned char*)Z.brp - h3, c3, &bars[s]);
+            if (c4) bulk_g2s(b + c2 + c3, (const unsigned char*)Z.bcv - h4, c4, &bars[s]);
+        }
+        return cnt;
+    };
+
+    int zq = 0;                                      // producer: first z not yet issued
+    if (wid == 0 && nz > 0) {
+        zq = issue(0, 0);
+        if (zq < nz) zq += issue(zq, 1);
+    }
+    for (int c = tid; c < rc * n; c += nthr) acc[c] = 0u;
+    __syncthreads();
+
+    unsigned long long fmas = 0;
+    const int qs = nthr / G, q0 = tid / G, lg = tid % G;
+    for (int zs = 0, b = 0; zs < nz; ++b) {
+        const int s = b & 1;
+        bool ok = false;
+        for (int it = 0; it < kStSpin && !ok; ++it) ok = mbar_try_wait(&bars[s], (unsigned)((b >> 1) & 1));
+        if (!ok) atomicExch(stage_err, 1);
+        const int cnt = bcount[s];
+        const int* ps = bps[s];
+        const int na_all = ok ? ps[cnt] : 0;
+        // the batch's A entries, numbered through its z
+        int k = 0;
+        SView v = views[s * kStBatch];
+        for (int q = q0; q < na_all; q += qs) {
+            if (q >= ps[k + 1]) {
+                do { ++k; } while (q >= ps[k + 1]);
+                v = views[s * kStBatch + k];
+            }
+            const int2 tv = v.acv[q - ps[k]];
+            const int t = key_col(tv.x);
+            unsigned* accr = acc + (key_row(tv.x) - i0) * n;
+            const int b0 = v.brp[t], b1 = v.brp[t + 1];
+            const float vs = __int_as_float(tv.y) * unit;
+            if (lg == 0) fmas += (unsigned long long)(b1 - b0);
+            for (int f = b0 + lg; f < b1; f += G) {
+                const int2 jw = v.bcv[f];
+                atomicAdd(accr + key_col(jw.x), __float2uint_rn(vs * __int_as_float(jw.y)));
+            }
+        }
+        zs += cnt;
+        __syncthreads();                             // buffer s is free again
+        if (wid == 0 && zq < nz) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            zq += issue(zq, s);
+        }
+    }
+
+    // rows of the chunk (a warp per row): the sums as floats, the amplified
+    // own signal, the kept entries counted
+    const int64_t row_base = in.pro[p];
+    const MatRef own = mat_of(in, x, y);
+    for (int r = wid; r < rc; r += nwarps) {
+        const int i = i0 + r;
+        unsigned* ar = acc + r * n;
+        for (int j = lane; j < n; j += 32) ar[j] = __float_as_uint(__uint2float_rn(ar[j]) * inv_unit);
+        __syncwarp();
+        const int s0 = own.rp[i], sn = own.rp[i + 1] - s0;
+        for (int f = lane; f < sn; f += 32) {       // the own row's columns are distinct
+            const int2 cv = own.cv[s0 + f];
+            ar[key_col(cv.x)] = __float_as_uint(__uint_as_float(ar[key_col(cv.x)]) + self * __int_as_float(cv.y));
+        }
+        __syncwarp();
+        int kept = 0;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int j = j0 + lane;
+            const bool keep = j < n && __uint_as_float(ar[j]) * scale >= theta;
+            kept += __popc(__ballot_sync(FULLM, keep));
+        }
+        if (lane == 0) rcnt[r] = kept;
+    }
+    __syncthreads();
+    // one reservation in the pool for the chunk: row offsets by a scan (warp 0)
+    if (wid == 0) {
+        int carry = 0;
+        for (int r0 = 0; r0 < rc; r0 += 32) {
+            const int r = r0 + lane;
+            const int c = r < rc ? rcnt[r] : 0;
+            int incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(FULLM, incl, d);
+                if (lane >= d) incl += t;
+            }
+            if (r < rc) rcnt[r] = carry + incl - c;
+            carry += __shfl_sync(FULLM, incl, 31);
+        }
+        if (lane == 0) {
+            const unsigned long long off = carry > 0 ? atomicAdd(out.pool_used, (unsigned long long)carry) : 0ull;
+            const bool fits = (int64_t)off + carry <= out.pool_cap;
+            if (!fits) atomicExch(out.overflow, 1);
+            s_base = fits ? off : ~0ull;
+        }
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+    for (int r = wid; r < rc; r += nwarps) {
+        const int i = i0 + r;
+        const unsigned* ar = acc + r * n;
+        const int64_t off = (int64_t)base + rcnt[r];
+        int wpos = 0;
+        const unsigned below = (1u << lane) - 1u;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int j = j0 + lane;
+            const float v = j < n ? __uint_as_float(ar[j]) * scale : 0.0f;
+            const bool keep = j < n && v >= theta;
+            const unsigned mk = __ballot_sync(FULLM, keep);
+            if (keep && base != ~0ull) out.pool[off + wpos + __popc(mk & below)] = make_int2(j, __float_as_int(v));
+            wpos += __popc(mk);
+        }
+        if (lane == 0) {
+            out.row_cnt[row_base + i] = wpos;
+            out.row_off[row_base + i] = off;
+        }
+    }
+    // multiply-adds: one global atomic per CTA
+    for (int d = 16; d > 0; d >>= 1) fmas += __shfl_xor_sync(FULLM, fmas, d);
+    if (lane == 0) red[wid] = fmas;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long sum = 0;
+        for (int q = 0; q < nwarps; ++q) sum += red[q];
+        if (sum) atomicAdd(out.fma, sum);
+    }
 }
 
 // CSR of every pair from the row chunks (warp per pair): row pointers from
@@ -503,7 +888,9 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     auto take = [&](size_t bytes) { const size_t o = sz; sz += align256(std::max<size_t>(bytes, 16)); return o; };
     const bool host_in = !post->on_device;
     const size_t o_pro = host_in ? take(sizeof(int64_t) * (P + 1)) : 0;
-    const size_t o_rp = host_in ? take(sizeof(int32_t) * rows) : 0;
+    // row pointers: always a padded copy in the workspace (the staged form's
+    // bulk copies read up to 15 bytes past an array's end)
+    const size_t o_rp = take(sizeof(int32_t) * rows);
     const size_t o_pno = host_in ? take(sizeof(int64_t) * (P + 1)) : 0;
     const size_t o_col = host_in ? take(sizeof(int32_t) * nnz_in) : 0;
     const size_t o_val = host_in ? take(sizeof(float) * nnz_in) : 0;
@@ -520,13 +907,42 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     const size_t o_nz = take(sizeof(int32_t) * P);
     const size_t o_pn = take(sizeof(int64_t) * P);
     const size_t o_st = take(64);
+    // ---- the staged form: stage buffers, accumulator rows, work items
+    // (row chunks of every pair, in pair order)
+    StageCfg sc{};
+    int max_rc = 0;
+    std::vector<int4> work;
+    bool staged = C->tune.cons_form != 0 && cp->T <= kZTab;
+    if (staged) {
+        // shared memory: z table, views, two stage buffers, accumulator rows,
+        // row counts (at most kStMaxRows rows per chunk)
+        const int smem_total = std::min(C->smem_optin, 232448) - 1024;   // static shared memory and a margin
+        sc.slot_bytes = kStSlotBytes;
+        const int fixed = (int)(sizeof(ZEnt) * kZTab + sizeof(SView) * 2 * kStBatch) + 2 * sc.slot_bytes +
+                          4 * kStMaxRows;
+        sc.acc_cells = (smem_total - fixed) / 4;
+        if (sc.acc_cells < maxlen) staged = false;
+    }
+    if (staged) {
+        for (int a = 0, p = 0; a < k && staged; ++a)
+            for (int b = a + 1; b < k; ++b, ++p) {
+                int rcn = std::min(std::min(lens[a], sc.acc_cells / lens[b]), kStMaxRows);
+                if (C->tune.cons_chunk_rows > 0) rcn = std::min(rcn, C->tune.cons_chunk_rows);
+                rcn = std::max(rcn, 1);
+                max_rc = std::max(max_rc, rcn);
+                for (int i0 = 0; i0 < lens[a]; i0 += rcn) work.push_back(make_int4(p, i0, std::min(lens[a], i0 + rcn), 0));
+                if (work.size() > ((size_t)1 << 26)) { staged = false; break; }
+            }
+        if (!staged) std::vector<int4>().swap(work);
+    }
+    const size_t o_work = take(sizeof(int4) * std::max<size_t>(work.size(), 1));
     if ((e = C->cons_ws.ensure(sz)) != cudaSuccess) return fail(QP_ENOMEM, "consistency: %zu bytes of workspace", sz);
     char* W = (char*)C->cons_ws.ptr;
     ConsIn in;
     in.k = k;
     in.P = P;
     in.pro = host_in ? (const int64_t*)(W + o_pro) : post->pair_row_off;
-    in.rp = host_in ? (const int32_t*)(W + o_rp) : post->row_ptr;
+    in.rp = (const int32_t*)(W + o_rp);
     in.pno = host_in ? (const int64_t*)(W + o_pno) : post->pair_nnz_off;
     in.col = host_in ? (const int32_t*)(W + o_col) : post->col;
     in.val = host_in ? (const float*)(W + o_val) : post->val;
@@ -557,9 +973,13 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
                              merges_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
         return cuda_fail(e, "consistency: inputs");
+    if ((e = cudaMemcpyAsync(W + o_rp, post->row_ptr, sizeof(int32_t) * rows,
+                             host_in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "consistency: row pointers");
+    if (!work.empty() && (e = up(o_work, work.data(), sizeof(int4) * work.size())) != cudaSuccess)
+        return cuda_fail(e, "consistency: work items");
     if (host_in &&
         ((e = up(o_pro, post->pair_row_off, sizeof(int64_t) * (P + 1))) != cudaSuccess ||
-         (e = up(o_rp, post->row_ptr, sizeof(int32_t) * rows)) != cudaSuccess ||
          (e = up(o_pno, post->pair_nnz_off, sizeof(int64_t) * (P + 1))) != cudaSuccess ||
          (e = up(o_col, post->col, sizeof(int32_t) * nnz_in)) != cudaSuccess ||
          (e = up(o_val, post->val, sizeof(float) * nnz_in)) != cudaSuccess))
@@ -577,8 +997,10 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     k_cons_tcount<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_tcur));
     k_cons_tscan<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_tcur), (int32_t*)(W + o_trp));
     k_cons_tfill<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_tcur), (int2*)(W + o_tcv));
-    k_cons_interleave<<<(int)std::min<int64_t>(8 * C->sm_count, (nnz_in + 255) / 256 + 1), 256, 0, st>>>(
-        in.col, in.val, nnz_in, (int2*)(W + o_fcv));
+    k_cons_interleave<<<warp_blocks, 256, 0, st>>>(in, (int2*)(W + o_fcv));
+    unsigned* d_stats = (unsigned*)(d_status + 6);     // largest value, largest row sum (float bits)
+    int32_t* d_wide = d_status + 8;                    // the staged form's unit would be too coarse
+    if (staged) k_cons_stats<<<warp_blocks, 256, 0, st>>>(in, d_stats);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "consistency: set-up kernels");
 
     // ---- relaxation into the pool (grown and run again when it overflows)
@@ -603,14 +1025,39 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
             return fail(QP_ENOMEM, "consistency: entry pool of %lld entries", (long long)cap);
         o.pool = (int2*)C->cons_pool.ptr;
         o.pool_cap = (int64_t)(C->cons_pool.bytes / sizeof(int2));
-        if ((e = cudaMemsetAsync(d_status + 1, 0, 20, st)) != cudaSuccess) return cuda_fail(e, "consistency");
-        k_cons_relax<<<(unsigned)P, nwarps * 32, smem, st>>>(in, o, nwarps, acc_len, (float)cp->h, cp->n_max,
-                                                             (float)cp->threshold, d_status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "consistency: k_cons_relax");
-        if ((e = cudaMemcpyAsync(h_status, d_status, 24, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        if ((e = cudaMemsetAsync(d_status + 1, 0, 20, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d_wide, 0, 4, st)) != cudaSuccess)
+            return cuda_fail(e, "consistency");
+        if (staged) {
+            const int nzb = std::max(1, std::min(cp->T, k - 2));
+            const size_t dyn = sizeof(ZEnt) * kZTab + sizeof(SView) * 2 * kStBatch + 2 * (size_t)sc.slot_bytes +
+                               4 * (size_t)sc.acc_cells + 4 * (size_t)kStMaxRows;
+            if ((e = cudaFuncSetAttribute(k_cons_relax_staged<kStGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)dyn)) != cudaSuccess)
+                return cuda_fail(e, "consistency: shared memory size");
+            k_cons_relax_staged<kStGroup><<<(unsigned)work.size(), kStThreads, dyn, st>>>(
+                in, o, (const int4*)(W + o_work), sc, (float)cp->h, cp->n_max, (float)cp->threshold, nzb, d_stats,
+                C->tune.cons_min_unit > 0 ? C->tune.cons_min_unit : kMinUnit, d_wide, d_status + 9, d_status);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "consistency: k_cons_relax_staged");
+        } else {
+            k_cons_relax<<<(unsigned)P, nwarps * 32, smem, st>>>(in, o, nwarps, acc_len, (float)cp->h, cp->n_max,
+                                                                 (float)cp->threshold, d_status);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "consistency: k_cons_relax");
+        }
+        if ((e = cudaMemcpyAsync(h_status, d_status, 40, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_fail(e, "consistency");
         if (h_status[0]) return fail(QP_EINVAL, "consistency: merges are not a valid join sequence of k leaves");
+        if (h_status[9]) return fail(QP_ECUDA, "consistency: a stage buffer's copies did not complete in time");
+        if (staged && h_status[8]) {
+            // values or row sums too large for a fine enough 32-bit unit: the
+            // row form (64-bit sums) from the start
+            staged = false;
+            C->cons_last_form = 0;
+            --attempt;
+            continue;
+        }
+        C->cons_last_form = staged ? 1 : 0;
         memcpy(&used, h_status + 2, sizeof used);
         if (!h_status[1]) {
             unsigned long long f = 0;

@@ -66,6 +66,9 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
                                          // state in shared memory; 2 cluster form; -1 automatic
     int tree_ctas = 0;                   // guide tree cluster form: CTAs (1, 2, 4, 8, 16; 0 automatic)
     int64_t pool_entries = 0;            // initial entry pool of a call (0: estimated)
+    int cons_form = -1;                  // consistency: 0 row form, 1 staged form, -1 automatic
+    int cons_chunk_rows = 0;             // consistency staged form: at most this many rows per CTA (0: by shared memory)
+    int cons_min_unit = 0;               // consistency staged form: coarsest unit 2^-u accepted (0: 21)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the
@@ -124,6 +127,7 @@ struct Context {
     int device = 0;
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
+    int smem_optin = 0;                  // shared memory a block may opt in to (bytes)
     int f32_blocks_per_sm = 3;
     int f64_blocks_per_sm = 2;
     cudaStream_t stream = nullptr;
@@ -153,6 +157,7 @@ struct Context {
     HostBuf cons_h;
     int64_t cons_pool_hint = 0;
     int64_t cons_fma = 0;                // multiply-adds of the last relaxation
+    int cons_last_form = -1;             // form of the last relaxation (0 row form, 1 staged form)
     cudaEvent_t cons_ev[2] = {};
     // guide tree: working memory kept between calls, pinned staging
     std::mutex tree_mu;

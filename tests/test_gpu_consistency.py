@@ -67,8 +67,32 @@ def _dense(res, k, lens):
     return out
 
 
+@pytest.fixture
+def forms(qp):
+    """Restores the automatic choice of the relaxation's form after a test
+    that forces one."""
+    yield
+    for name in ("cons_form", "cons_chunk_rows", "cons_min_unit"):
+        qp.qp_set_option(name, -1 if name == "cons_form" else 0, device=0)
+
+
 @pytest.mark.parametrize("T,h,n_max", [(200, 3.0, 200), (3, 3.0, 200), (5, 1.0, 200), (4, 3.0, 2), (1, 3.0, 200)])
 def test_relaxation_matches_oracle(qp, small, T, h, n_max):
+    _check_against_oracle(qp, small, T, h, n_max)
+
+
+@pytest.mark.parametrize("form,chunk_rows", [(1, 0), (1, 7), (1, 1), (0, 0)])
+def test_each_form_matches_oracle(qp, small, forms, form, chunk_rows):
+    """The staged form (whole pairs, chunks of 7 rows, single rows) and the
+    row form, each against the oracle."""
+    qp.qp_set_option("cons_form", form)
+    qp.qp_set_option("cons_chunk_rows", chunk_rows)
+    for T, h, n_max in ((200, 3.0, 200), (4, 3.0, 2)):
+        _check_against_oracle(qp, small, T, h, n_max)
+        assert qp.qp_get_counter("consistency_form") == form
+
+
+def _check_against_oracle(qp, small, T, h, n_max):
     fam, res, S, merges = small
     lens = [int(v) for v in fam.lengths]
     theta = 0.01
@@ -151,3 +175,84 @@ def test_rejects_bad_input(qp, small):
     with pytest.raises(qp.QpError) as e:
         qp.qp_consistency(res, fam.offsets, merges, h=0.5)
     assert e.value.code == 1
+
+
+def _entries(res, k, lens):
+    """{(a, b): (row * n + column keys, values)} of a result, ascending keys."""
+    pro = host(res.array("pair_row_off"))
+    pno = host(res.array("pair_nnz_off"))
+    rp_all = host(res.array("row_ptr"))
+    col = host(res.array("col")).astype(np.int64)
+    val = host(res.array("val")).astype(np.float64)
+    out, p = {}, 0
+    for a in range(k):
+        for b in range(a + 1, k):
+            rp = rp_all[pro[p]:pro[p + 1]].astype(np.int64)
+            rows = np.repeat(np.arange(lens[a], dtype=np.int64), np.diff(rp))
+            sl = slice(int(pno[p]), int(pno[p]) + int(rp[-1]))
+            out[(a, b)] = (rows * lens[b] + col[sl], val[sl])
+            p += 1
+    return out
+
+
+def _compare_entries(A, B, theta, tol):
+    worst = 0.0
+    for key in A:
+        ka, va = A[key]
+        kb, vb = B[key]
+        both, ia, ib = np.intersect1d(ka, kb, assume_unique=True, return_indices=True)
+        if both.size:
+            worst = max(worst, float(np.abs(va[ia] - vb[ib]).max()))
+        only_a = np.setdiff1d(np.arange(ka.size), ia)
+        only_b = np.setdiff1d(np.arange(kb.size), ib)
+        assert (np.abs(va[only_a] - theta) <= tol).all(), f"pair {key}: pattern differs outside the band"
+        assert (np.abs(vb[only_b] - theta) <= tol).all(), f"pair {key}: pattern differs outside the band"
+    return worst
+
+
+def test_forms_agree_beyond_the_stage_buffers(qp, forms):
+    """Sequences of 700-1000 residues with posteriors kept down to 1e-3: some
+    matrices hold more entries than a stage buffer, so the staged form reads
+    those from global memory.  Staged (whole pairs and 50-row chunks) and row
+    forms agree within 1e-6: both sum the same products in fixed point (units
+    2^-30 and at most 2^-21), which differ by rounding alone; the multiply-add
+    counts are equal."""
+    import torch
+    fam = synth.star_family(73, 9, (700, 1000), 0.35)
+    prm = synth.default_params(threshold=1e-3)
+    post = qp.qp_posteriors(torch.from_numpy(fam.residues).cuda(), fam.offsets, prm, device=0, out_on_device=True)
+    pno = host(post.array("pair_nnz_off"))
+    assert int(np.diff(pno).max()) > 4096 + 1536, "no matrix beyond the stage buffers"
+    merges = synth.random_guide_tree(6, fam.k)
+    lens = [int(v) for v in fam.lengths]
+    got, fma = {}, {}
+    for name, form, chunk in (("row", 0, 0), ("staged", 1, 0), ("chunked", 1, 50)):
+        qp.qp_set_option("cons_form", form)
+        qp.qp_set_option("cons_chunk_rows", chunk)
+        r = qp.qp_consistency(post, fam.offsets, merges, T=200, threshold=2e-3, out_on_device=True)
+        assert qp.qp_get_counter("consistency_form") == form
+        fma[name] = qp.qp_get_counter("consistency_fma")
+        got[name] = _entries(r, fam.k, lens)
+        r.free()
+    post.free()
+    assert fma["row"] == fma["staged"] == fma["chunked"] > 0
+    for name in ("staged", "chunked"):
+        assert _compare_entries(got["row"], got[name], 2e-3, 1e-6) <= 1e-6, name
+
+
+def test_staged_form_hands_a_coarse_unit_to_the_row_form(qp, small, forms):
+    """When the bound on the sums would need a unit coarser than allowed, the
+    call runs the row form: asking for 2^-31 forces that here, and the result
+    is the row form's, bit for bit."""
+    fam, res, S, merges = small
+    lens = [int(v) for v in fam.lengths]
+    qp.qp_set_option("cons_form", 0)
+    ref = qp.qp_consistency(res, fam.offsets, merges, T=200)
+    qp.qp_set_option("cons_form", 1)
+    qp.qp_set_option("cons_min_unit", 31)
+    got = qp.qp_consistency(res, fam.offsets, merges, T=200)
+    assert qp.qp_get_counter("consistency_form") == 0
+    for name in ("pair_row_off", "row_ptr", "pair_nnz_off", "col", "val"):
+        assert np.array_equal(host(got.array(name)), host(ref.array(name))), name
+    got.free()
+    ref.free()
