@@ -335,6 +335,7 @@ Context* get_context(int device, int* status) {
     c->sm_count = prop.multiProcessorCount;
     c->cc_major = prop.major; c->cc_minor = prop.minor;
     c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    c->smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
     if (prop.major < 10) {
         *status = fail(QP_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a", device, prop.major, prop.minor);
         return nullptr;
@@ -1050,6 +1051,9 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
     } else if (n == "cons_form") {
         if (value > 1) return fail(QP_EINVAL, "cons_form must be 0, 1 or -1");
         C->tune.cons_form = value < 0 ? -1 : (int)value;
+    } else if (n == "cons_ctas_per_sm") {
+        if (value > 2) return fail(QP_EINVAL, "cons_ctas_per_sm must be 1, 2 or 0");
+        C->tune.cons_ctas_per_sm = value > 0 ? (int)value : 0;
     } else if (n == "cons_min_unit") {
         if (value > 31) return fail(QP_EINVAL, "cons_min_unit must be <= 31");
         C->tune.cons_min_unit = value > 0 ? (int)value : 0;

@@ -72,6 +72,11 @@ struct ConsIn {
     // 8-byte loads: the posteriors (fcv) and their transposes (tcv)
     const int2* fcv;
     const int2* tcv;
+    // column bands of the rows (staged form): for row r of a matrix,
+    // (largest column of rows 0..r) << 16 | (smallest column of rows r..end),
+    // indexed like rp / trp
+    const int32_t* fband;
+    const int32_t* tband;
     const int32_t* len;     // [k]
     const int32_t* leaf_at; // [k] leaf at each DFS position
     const int32_t* pos;     // [k] DFS position of each leaf
@@ -253,6 +258,7 @@ __global__ void k_cons_interleave(ConsIn in, int2* cv) {
 struct MatRef {
     const int32_t* rp;
     const int2* cv;     // (row << 16 | column, value bits)
+    const int32_t* band;
 };
 
 __device__ __forceinline__ MatRef mat_of(const ConsIn& in, int a, int b) {
@@ -261,10 +267,12 @@ __device__ __forceinline__ MatRef mat_of(const ConsIn& in, int a, int b) {
         const int64_t p = pidx(a, b, in.k);
         M.rp = in.rp + in.pro[p];
         M.cv = in.fcv + in.pno[p];
+        M.band = in.fband ? in.fband + in.pro[p] : nullptr;
     } else {
         const int64_t p = pidx(b, a, in.k);
         M.rp = in.trp + in.tpro[p];
         M.cv = in.tcv + in.pno[p];
+        M.band = in.tband ? in.tband + in.tpro[p] : nullptr;
     }
     return M;
 }
@@ -449,26 +457,30 @@ __global__ void k_cons_stats(ConsIn in, unsigned* stats) {
     }
 }
 
-// one selected z of a (pair, row chunk): A = S_xz (rows i0 .. i1 - 1 of x),
-// B = S_zy (all rows of z), in global memory
+// one selected z of a (pair, row chunk): A = S_xz (rows i0 .. i1 - 1 of x)
+// and the band of rows of B = S_zy those entries reach (rows bt0 .. bt1 - 1
+// of z), in global memory
 struct ZEnt {
     const int2* acv;        // A's entries of the chunk (keys carry their rows)
-    const int32_t* brp;     // B's row pointers
-    const int2* bcv;        // B's entries
+    const int32_t* brp;     // B's row pointers from row bt0
+    const int2* bcv;        // B's entries from entry b0
     int na;                 // A's entries of the chunk
-    int nb;                 // B's entries
-    int lz;                 // B's rows
+    int bt0, nbr;           // first row of the band, rows in it
+    int b0, nb;             // first entry of the band, entries in it
 };
 
 // where the products read one z from: its staged copy in shared memory, or
-// global memory for a z larger than a stage buffer
+// global memory for a z larger than a stage buffer; B's row pointers are
+// indexed by t - bt0 and give entry numbers, its entries by number - b0
 struct SView {
     const int2* acv;
     const int32_t* brp;
     const int2* bcv;
+    int bt0, b0;
 };
 
 struct StageCfg {
+    int ztab;               // z table entries (>= the selected z of any pair)
     int slot_bytes;         // one of the two stage buffers (a multiple of 16)
     int acc_cells;          // accumulator cells (rows of the chunk x n)
 };
@@ -477,9 +489,63 @@ constexpr int kStThreads = 512;             // 16 warps: one CTA per SM (its sha
 constexpr int kStBatch = 32;                // z per stage buffer at most (a lane of the producer warp each)
 constexpr int kMinUnit = 21;                // coarsest fixed-point unit (2^-21) the staged form accepts by default
 constexpr int kStGroup = 1;                 // threads per A entry along a row of B
-constexpr int kStSlotBytes = 56 * 1024;     // one stage buffer
 constexpr int kStMaxRows = 1024;            // rows of a chunk at most
 constexpr int kStSpin = 1 << 22;            // polls of a stage buffer's barrier before the call is failed
+
+// column bands of every matrix and of its transpose (warp per pair, 32
+// rows at a time): band[r] = (max over rows 0..r of the last column) << 16 |
+// (min over rows r..end of the first column); empty rows count as 0 / 0xffff.
+// The entries of rows i0 .. i1 - 1 then lie in columns
+// [band[i0] & 0xffff, band[i1 - 1] >> 16].
+__global__ void k_cons_bands(ConsIn in, int32_t* fband, int32_t* tband) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= in.P) return;
+    const int2 ab = pair_of(p, in.k);
+    for (int side = 0; side < 2; ++side) {
+        const int rows = in.len[side ? ab.y : ab.x];
+        const int32_t* rp = side ? in.trp + in.tpro[p] : in.rp + in.pro[p];
+        const int2* cv = (side ? in.tcv : in.fcv) + in.pno[p];
+        int32_t* band = side ? tband + in.tpro[p] : fband + in.pro[p];
+        // prefix maxima of the last columns, forward
+        int carry = 0;
+        for (int r0 = 0; r0 < rows; r0 += 32) {
+            const int r = r0 + lane;
+            int v = 0;
+            if (r < rows) {
+                const int e0 = rp[r], e1 = rp[r + 1];
+                if (e1 > e0) v = key_col(cv[e1 - 1].x);
+            }
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(FULLM, v, d);
+                if (lane >= d) v = max(v, t);
+            }
+            v = max(v, carry);
+            if (r < rows) band[r] = v << 16;
+            carry = __shfl_sync(FULLM, v, 31);
+        }
+        __syncwarp();
+        // suffix minima of the first columns, backward
+        carry = 0xffff;
+        for (int r1 = rows; r1 > 0; r1 -= 32) {
+            const int r = r1 - 1 - lane;
+            int v = 0xffff;
+            if (r >= 0) {
+                const int e0 = rp[r], e1 = rp[r + 1];
+                if (e1 > e0) v = key_col(cv[e0].x);
+            }
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(FULLM, v, d);
+                if (lane >= d) v = min(v, t);
+            }
+            v = min(v, carry);
+            if (r >= 0) band[r] |= v;
+            carry = __shfl_sync(FULLM, v, 31);
+        }
+    }
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
@@ -536,8 +602,8 @@ __device__ __forceinline__ int bulk_span(const void* g, int bytes, int* head) {
 // independent of their order (bit-reproducible).  Then, per row, the
 // amplified own signal, the scale and the threshold; one pool reservation
 // for the chunk's kept entries.
-template <int G>
-__global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, ConsOut out, const int4* __restrict__ work,
+template <int G, int MINB>
+__global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn in, ConsOut out, const int4* __restrict__ work,
                                                                     StageCfg sc, float h, int n_max, float theta, int nzb,
                                                                     const unsigned* __restrict__ stats, int min_unit,
                                                                     int32_t* wide, int32_t* stage_err,
@@ -556,7 +622,10 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
     // the fixed-point unit (the same in every CTA)
-    const float bound = (float)nzb * __uint_as_float(stats[0]) * __uint_as_float(stats[1]);
+    // a cell's sum: at most nzb selected z, each adding at most (largest
+    // value) x (largest row sum), plus the amplified own value (<= 2 h V)
+    const float V = __uint_as_float(stats[0]);
+    const float bound = (float)nzb * V * __uint_as_float(stats[1]) + 2.0f * h * V;
     int u = 30;
     if (bound > 0.f) {
         if (!(bound <= 1e30f)) u = -1;
@@ -584,7 +653,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
     if (tid == 0 && i0 == 0) out.nz[p] = nz;
 
     ZEnt* zt = (ZEnt*)smem;
-    SView* views = (SView*)(smem + sizeof(ZEnt) * kZTab);
+    SView* views = (SView*)(smem + sizeof(ZEnt) * sc.ztab);
     unsigned char* slots = (unsigned char*)(views + 2 * kStBatch);
     unsigned* acc = (unsigned*)(slots + 2 * sc.slot_bytes);
     int* rcnt = (int*)(acc + sc.acc_cells);
@@ -598,11 +667,18 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
         if (z == x || z == y) continue;
         const int slot = v - lo - (px >= lo && px < v ? 1 : 0) - (py >= lo && py < v ? 1 : 0);
         const MatRef A = mat_of(in, x, z), B = mat_of(in, z, y);
-        const int lz = in.len[z];
-        const int a0 = A.rp[i0];
+        const int a0 = A.rp[i0], na = A.rp[i1] - a0;
         ZEnt e;
-        e.acv = A.cv + a0; e.brp = B.rp; e.bcv = B.cv;
-        e.na = A.rp[i1] - a0; e.nb = B.rp[lz]; e.lz = lz;
+        e.acv = A.cv + a0;
+        e.na = na;
+        e.bt0 = 0; e.nbr = 0; e.b0 = 0; e.nb = 0;
+        if (na > 0) {
+            const int t0 = A.band[i0] & 0xffff, t1 = (A.band[i1 - 1] >> 16) + 1;
+            e.bt0 = t0; e.nbr = t1 - t0;
+            e.b0 = B.rp[t0]; e.nb = B.rp[t1] - e.b0;
+        }
+        e.brp = B.rp + e.bt0;
+        e.bcv = B.cv + e.b0;
         zt[slot] = e;
     }
     __syncthreads();
@@ -618,7 +694,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
             Z = zt[zi];
             na = Z.na;
             c2 = bulk_span(Z.acv, Z.na * 8, &h2);
-            c3 = bulk_span(Z.brp, (Z.lz + 1) * 4, &h3);
+            c3 = bulk_span(Z.brp, Z.nbr > 0 ? (Z.nbr + 1) * 4 : 0, &h3);
             c4 = bulk_span(Z.bcv, Z.nb * 8, &h4);
             need = c2 + c3 + c4;
             if (need > sc.slot_bytes) { need = 0; glob = true; }
@@ -636,6 +712,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
         unsigned char* b = slots + s * sc.slot_bytes + (incl - need);
         if (lane < cnt) {
             SView v;
+            v.bt0 = Z.bt0;
+            v.b0 = Z.b0;
             if (glob) {
                 v.acv = Z.acv; v.brp = Z.brp; v.bcv = Z.bcv;
             } else {
@@ -686,9 +764,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
                 v = views[s * kStBatch + k];
             }
             const int2 tv = v.acv[q - ps[k]];
-            const int t = key_col(tv.x);
+            const int t = key_col(tv.x) - v.bt0;
             unsigned* accr = acc + (key_row(tv.x) - i0) * n;
-            const int b0 = v.brp[t], b1 = v.brp[t + 1];
+            const int b0 = v.brp[t] - v.b0, b1 = v.brp[t + 1] - v.b0;
             const float vs = __int_as_float(tv.y) * unit;
             if (lg == 0) fmas += (unsigned long long)(b1 - b0);
             for (int f = b0 + lg; f < b1; f += G) {
@@ -704,25 +782,25 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
         }
     }
 
-    // rows of the chunk (a warp per row): the sums as floats, the amplified
-    // own signal, the kept entries counted
+    // the amplified own signal, in the same units
     const int64_t row_base = in.pro[p];
-    const MatRef own = mat_of(in, x, y);
-    for (int r = wid; r < rc; r += nwarps) {
-        const int i = i0 + r;
-        unsigned* ar = acc + r * n;
-        for (int j = lane; j < n; j += 32) ar[j] = __float_as_uint(__uint2float_rn(ar[j]) * inv_unit);
-        __syncwarp();
-        const int s0 = own.rp[i], sn = own.rp[i + 1] - s0;
-        for (int f = lane; f < sn; f += 32) {       // the own row's columns are distinct
-            const int2 cv = own.cv[s0 + f];
-            ar[key_col(cv.x)] = __float_as_uint(__uint_as_float(ar[key_col(cv.x)]) + self * __int_as_float(cv.y));
+    {
+        const MatRef own = mat_of(in, x, y);
+        const int oa0 = own.rp[i0], ona = own.rp[i1] - oa0;
+        const float su = self * unit;
+        for (int q = tid; q < ona; q += nthr) {
+            const int2 tv = own.cv[oa0 + q];
+            atomicAdd(acc + (key_row(tv.x) - i0) * n + key_col(tv.x), __float2uint_rn(su * __int_as_float(tv.y)));
         }
-        __syncwarp();
+    }
+    __syncthreads();
+    // rows of the chunk (a warp per row): the kept entries counted
+    for (int r = wid; r < rc; r += nwarps) {
+        const unsigned* ar = acc + r * n;
         int kept = 0;
         for (int j0 = 0; j0 < n; j0 += 32) {
             const int j = j0 + lane;
-            const bool keep = j < n && __uint_as_float(ar[j]) * scale >= theta;
+            const bool keep = j < n && (__uint2float_rn(ar[j]) * inv_unit) * scale >= theta;
             kept += __popc(__ballot_sync(FULLM, keep));
         }
         if (lane == 0) rcnt[r] = kept;
@@ -760,7 +838,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_cons_relax_staged(ConsIn in, 
         const unsigned below = (1u << lane) - 1u;
         for (int j0 = 0; j0 < n; j0 += 32) {
             const int j = j0 + lane;
-            const float v = j < n ? __uint_as_float(ar[j]) * scale : 0.0f;
+            const float v = j < n ? (__uint2float_rn(ar[j]) * inv_unit) * scale : 0.0f;
             const bool keep = j < n && v >= theta;
             const unsigned mk = __ballot_sync(FULLM, keep);
             if (keep && base != ~0ull) out.pool[off + wpos + __popc(mk & below)] = make_int2(j, __float_as_int(v));
@@ -913,14 +991,17 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     int max_rc = 0;
     std::vector<int4> work;
     bool staged = C->tune.cons_form != 0 && cp->T <= kZTab;
+    const int st_ctas = C->tune.cons_ctas_per_sm == 1 ? 1 : 2;      // CTAs of the staged form per SM
     if (staged) {
-        // shared memory: z table, views, two stage buffers, accumulator rows,
-        // row counts (at most kStMaxRows rows per chunk)
-        const int smem_total = std::min(C->smem_optin, 232448) - 1024;   // static shared memory and a margin
-        sc.slot_bytes = kStSlotBytes;
-        const int fixed = (int)(sizeof(ZEnt) * kZTab + sizeof(SView) * 2 * kStBatch) + 2 * sc.slot_bytes +
+        // shared memory of a CTA: z table, views, two stage buffers,
+        // accumulator rows, row counts (at most kStMaxRows rows per chunk);
+        // less the static shared memory and a margin
+        const int per_cta = std::min(C->smem_optin, C->smem_per_sm / st_ctas - 1024) - 1024;
+        sc.ztab = std::max(1, std::min(cp->T, k));
+        sc.slot_bytes = (per_cta / 5) & ~15;
+        const int fixed = (int)(sizeof(ZEnt) * sc.ztab + sizeof(SView) * 2 * kStBatch) + 2 * sc.slot_bytes +
                           4 * kStMaxRows;
-        sc.acc_cells = (smem_total - fixed) / 4;
+        sc.acc_cells = (per_cta - fixed) / 4;
         if (sc.acc_cells < maxlen) staged = false;
     }
     if (staged) {
@@ -936,6 +1017,8 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
         if (!staged) std::vector<int4>().swap(work);
     }
     const size_t o_work = take(sizeof(int4) * std::max<size_t>(work.size(), 1));
+    const size_t o_fband = staged ? take(sizeof(int32_t) * rows) : 0;
+    const size_t o_tband = staged ? take(sizeof(int32_t) * rows_t) : 0;
     if ((e = C->cons_ws.ensure(sz)) != cudaSuccess) return fail(QP_ENOMEM, "consistency: %zu bytes of workspace", sz);
     char* W = (char*)C->cons_ws.ptr;
     ConsIn in;
@@ -950,6 +1033,8 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     in.trp = (const int32_t*)(W + o_trp);
     in.tcv = (const int2*)(W + o_tcv);
     in.fcv = (const int2*)(W + o_fcv);
+    in.fband = staged ? (const int32_t*)(W + o_fband) : nullptr;
+    in.tband = staged ? (const int32_t*)(W + o_tband) : nullptr;
     in.len = (const int32_t*)(W + o_len);
     int32_t* tr = (int32_t*)(W + o_tree);
     const int nn = 2 * k - 1;
@@ -1000,7 +1085,10 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     k_cons_interleave<<<warp_blocks, 256, 0, st>>>(in, (int2*)(W + o_fcv));
     unsigned* d_stats = (unsigned*)(d_status + 6);     // largest value, largest row sum (float bits)
     int32_t* d_wide = d_status + 8;                    // the staged form's unit would be too coarse
-    if (staged) k_cons_stats<<<warp_blocks, 256, 0, st>>>(in, d_stats);
+    if (staged) {
+        k_cons_stats<<<warp_blocks, 256, 0, st>>>(in, d_stats);
+        k_cons_bands<<<warp_blocks, 256, 0, st>>>(in, (int32_t*)(W + o_fband), (int32_t*)(W + o_tband));
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "consistency: set-up kernels");
 
     // ---- relaxation into the pool (grown and run again when it overflows)
@@ -1030,12 +1118,12 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
             return cuda_fail(e, "consistency");
         if (staged) {
             const int nzb = std::max(1, std::min(cp->T, k - 2));
-            const size_t dyn = sizeof(ZEnt) * kZTab + sizeof(SView) * 2 * kStBatch + 2 * (size_t)sc.slot_bytes +
+            const size_t dyn = sizeof(ZEnt) * sc.ztab + sizeof(SView) * 2 * kStBatch + 2 * (size_t)sc.slot_bytes +
                                4 * (size_t)sc.acc_cells + 4 * (size_t)kStMaxRows;
-            if ((e = cudaFuncSetAttribute(k_cons_relax_staged<kStGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)dyn)) != cudaSuccess)
+            auto kern = st_ctas == 1 ? k_cons_relax_staged<kStGroup, 1> : k_cons_relax_staged<kStGroup, 2>;
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) != cudaSuccess)
                 return cuda_fail(e, "consistency: shared memory size");
-            k_cons_relax_staged<kStGroup><<<(unsigned)work.size(), kStThreads, dyn, st>>>(
+            kern<<<(unsigned)work.size(), kStThreads, dyn, st>>>(
                 in, o, (const int4*)(W + o_work), sc, (float)cp->h, cp->n_max, (float)cp->threshold, nzb, d_stats,
                 C->tune.cons_min_unit > 0 ? C->tune.cons_min_unit : kMinUnit, d_wide, d_status + 9, d_status);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "consistency: k_cons_relax_staged");

@@ -69,6 +69,7 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int cons_form = -1;                  // consistency: 0 row form, 1 staged form, -1 automatic
     int cons_chunk_rows = 0;             // consistency staged form: at most this many rows per CTA (0: by shared memory)
     int cons_min_unit = 0;               // consistency staged form: coarsest unit 2^-u accepted (0: 21)
+    int cons_ctas_per_sm = 0;            // consistency staged form: CTAs per SM (1 or 2; 0: 2)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the
@@ -128,6 +129,7 @@ struct Context {
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
     int smem_optin = 0;                  // shared memory a block may opt in to (bytes)
+    int smem_per_sm = 0;                 // shared memory of an SM (bytes)
     int f32_blocks_per_sm = 3;
     int f64_blocks_per_sm = 2;
     cudaStream_t stream = nullptr;
