@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--config", default="c2", choices=sorted(CONFIG_DESC))
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -145,36 +145,77 @@ def measured_peaks():
 
 
 def cpu_baseline(fam, prm, budget_s: float, seed: int = 0):
-    """The FP64 oracle on the host cores, on a bounded seeded sample of pairs."""
+    """The FP64 oracle on the host cores, on a bounded seeded sample of pairs:
+    batches of seeded random pairs until about ``budget_s`` seconds of work."""
     import oracle
     pl = list(fam.pairs())
     rng = np.random.Generator(np.random.PCG64(seed))
     order = rng.permutation(len(pl))
     threads = os.cpu_count() or 1
     L = fam.lengths.astype(np.int64)
-    # load the library, calibrate on a few pairs, then size the sample to the budget
-    oracle.pairs(fam, [pl[order[-1]]], prm, threads=1)
-    probe = [pl[i] for i in order[:threads]]
-    t0 = time.perf_counter()
-    oracle.pairs(fam, probe, prm, threads=threads)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    cells_probe = float(sum(L[a] * L[b] for a, b in probe))
-    want_cells = cells_probe / dt * budget_s
-    sample, cells = [], 0.0
-    for i in order[len(probe):]:
-        if cells >= want_cells:
-            break
-        a, b = pl[i]
-        sample.append((a, b))
-        cells += float(L[a] * L[b])
-    if not sample:
-        sample, cells = probe, cells_probe
-    t0 = time.perf_counter()
-    oracle.pairs(fam, sample, prm, threads=threads)
-    dt = time.perf_counter() - t0
+    oracle.pairs(fam, [pl[order[-1]]], prm, threads=1)      # load the library
+    batch = 4 * threads
+    done, cells, dt = 0, 0.0, 0.0
+    while dt < budget_s and done < len(order):
+        sample = [pl[i] for i in order[done:done + batch]]
+        t0 = time.perf_counter()
+        oracle.pairs(fam, sample, prm, threads=threads)
+        dt += time.perf_counter() - t0
+        cells += float(sum(L[a] * L[b] for a, b in sample))
+        done += len(sample)
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
-            "sample": f"{len(sample)} seeded random pairs of the family ({cells:.3g} cells), "
+            "sample": f"{done} seeded random pairs of the family ({cells:.3g} cells), "
                       f"FP64 log-space, {threads} threads, {dt:.1f} s"}
+
+
+def cpu_consistency(fam, prm, merges, seed: int, n_pairs: int = 3, T: int = 200, h: float = 3.0):
+    """The oracle's relaxation (dense FP64 products, numpy) on a few seeded
+    pairs of the family that have selected third sequences, over the seeded
+    guide tree ``merges``; its inputs are the oracle's own posteriors at the
+    threshold, computed beforehand on a thread pool and not timed.  The
+    family's time is extrapolated by the dense work, sum over pairs and
+    selected z of m l n."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    k = fam.k
+    L = fam.lengths.astype(np.float64)
+    d = oracle.tree_distances(merges, k)
+    # dense work of every pair: m n sum_{z in Z} l_z
+    work = np.zeros((k, k))
+    for x in range(k):
+        sel = (np.maximum(d[x][None, :], d) <= T)          # [y, z]: max(d_xz, d_zy) <= T
+        sel[:, x] = False
+        np.fill_diagonal(sel, False)
+        work[x] = L[x] * L * (sel @ L)
+    rng = np.random.Generator(np.random.PCG64(seed + 11))
+    cand = [(x, y) for x, y in fam.pairs() if work[x, y] > 0]
+    if not cand:
+        return {"kind": "oracle", "sample": "no pair has a selected third sequence"}
+    sample = [cand[i] for i in rng.permutation(len(cand))[:n_pairs]]
+    need = set()
+    for x, y in sample:
+        need.add((x, y))
+        for z in range(k):
+            if z != x and z != y and max(d[x, z], d[z, y]) <= T:
+                need.add((min(x, z), max(x, z)))
+                need.add((min(z, y), max(z, y)))
+    need = sorted(need)
+
+    def dense(ab):
+        P = oracle.pair(fam.codes(ab[0]), fam.codes(ab[1]), prm)["P"]
+        return np.where(P >= prm.threshold, P, 0.0)
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        S = dict(zip(need, ex.map(dense, need)))
+    t0 = time.perf_counter()
+    _, nz = oracle.consistency(S, [int(v) for v in fam.lengths], merges, T=T, h=h, theta=prm.threshold,
+                               pairs=sample)
+    dt = time.perf_counter() - t0
+    w_sample = float(sum(work[x, y] for x, y in sample))
+    w_all = float(sum(work[x, y] for x, y in fam.pairs()))
+    return {"s_sample": dt, "family_s": dt * w_all / w_sample, "kind": "oracle", "cores": os.cpu_count() or 1,
+            "sample": f"{len(sample)} seeded pairs with selected z ({sum(nz.values())} relaxations), dense "
+                      f"FP64 products (numpy), seeded random guide tree, T={T}, h={h}; family time "
+                      f"extrapolated by dense work (sum of m l n)"}
 
 
 def run_reference(args, fam, prm, rank):
@@ -564,12 +605,24 @@ def main():
         rc_.free()
     c_fma = qp.qp_get_counter("consistency_fma", device=local)
     c_form = qp.qp_get_counter("consistency_form", device=local)
+    # the same stage over a seeded random guide tree (the tree the oracle's
+    # timed sample uses below)
+    syn_tree = synth.random_guide_tree(args.seed + 7, fam.k)
+    s_ms = []
+    for _ in range(3):
+        rs_ = qp.qp_consistency(post, fam.offsets, syn_tree, T=200, h=3.0, threshold=prm.threshold,
+                                out_on_device=True)
+        s_ms.append(rs_.kernel_ms[0])
+        rs_.free()
+    s_fma = qp.qp_get_counter("consistency_fma", device=local)
     post.free()
     cms = statistics.median(c_ms)
     consistency = {"T": 200, "h": 3.0, "threshold": prm.threshold, "ms": cms,
                    "device_ms": statistics.median(c_dev_ms), "nnz_in": int(nnz), "nnz_out": c_nnz,
                    "fma": c_fma, "gflops": 2.0 * c_fma / (statistics.median(c_dev_ms) * 1e-3) / 1e9,
                    "form": "staged" if c_form == 1 else "row",
+                   "synthetic_tree": {"device_ms": statistics.median(s_ms), "fma": s_fma,
+                                      "what": "the same posteriors over a seeded random guide tree"},
                    "kernels": "k_cons_tree, k_cons_ranges, k_cons_tcount/tscan/tfill, k_cons_interleave, "
                               + ("k_cons_stats, k_cons_relax_staged, " if c_form == 1 else "k_cons_relax, ")
                               + "k_cons_pair_nnz, k_scan_nnz, k_cons_compact"}
@@ -629,6 +682,13 @@ def main():
                      "ops_per_cell": ALU_OPS_PER_CELL},
         "clocks": clocks,
     }
+    # relaxation: one multiply and one add per product (algorithmic issue
+    # slots) against the FP32 lanes' issue rate
+    c_ach = 2.0 * consistency["fma"] / (consistency["device_ms"] * 1e-3) / 1e12
+    consistency["roofline"] = {"bound": "alu", "achieved": c_ach, "peak": peak_tops, "unit": "Tissue/s",
+                               "frac": c_ach / peak_tops, "ops_per_product": 2,
+                               "kernel": "k_cons_relax_staged" if consistency["form"] == "staged" else "k_cons_relax",
+                               "note": "scatter-bound: every product is a shared-memory atomic add"}
     line["consistency"] = consistency
     line["entry_budget"] = entry_budget
     if nucleotide["kernel_ms_timed_region"] > 0:
@@ -647,6 +707,7 @@ def main():
         import oracle
         t0 = time.perf_counter()
         ref_tree = oracle.guide_tree(d64.cpu().numpy())
+        line["cpu_baseline"]["consistency"] = cpu_consistency(fam, prm, syn_tree, args.seed)
         line["cpu_baseline"]["guide_tree"] = {
             "s": time.perf_counter() - t0, "kind": "oracle", "k": fam.k,
             "identical": bool(np.array_equal(ref_tree["merges"], tree_host[0])

@@ -208,7 +208,7 @@ def tree_distances(merges, k: int) -> np.ndarray:
 
 
 def consistency(S: dict, lens, merges, T: int = 200, h: float = 3.0, n_max: int = 200,
-                theta: float = 0.01) -> dict:
+                theta: float = 0.01, pairs=None) -> dict:
     """Selective consistency (paper, Methods, stage III and "Selective
     consistency"): every posterior matrix S_xy is relaxed through the third
     sequences z whose tree distances to x and y both stay within T, and its
@@ -222,25 +222,27 @@ def consistency(S: dict, lens, merges, T: int = 200, h: float = 3.0, n_max: int 
     the relaxation of ProbCons (a sum over all sequences, x and y included
     with S_xx = I, divided by their number) restricted to Z; then entries
     below ``theta`` are dropped.  Returns {(x, y): dense S'_xy} and
-    {(x, y): |Z|}."""
+    {(x, y): |Z|}.  ``pairs``: relax only these (x, y), x < y (``S`` then
+    needs only the matrices they use)."""
     k = len(lens)
     d = tree_distances(merges, k)
 
     def mat(a, b):
         return S[(a, b)] if a < b else S[(b, a)].T
 
+    if pairs is None:
+        pairs = [(x, y) for x in range(k) for y in range(x + 1, k)]
     out, nz = {}, {}
-    for x in range(k):
-        for y in range(x + 1, k):
-            Z = [z for z in range(k) if z != x and z != y and max(d[x, z], d[z, y]) <= T]
-            hxy = 1.0 + (h - 1.0) * min(len(Z), n_max) / n_max
-            acc = 2.0 * hxy * S[(x, y)]
-            for z in Z:
-                acc = acc + mat(x, z) @ mat(z, y)
-            R = acc / (2.0 + len(Z))
-            R[R < theta] = 0.0
-            out[(x, y)] = R
-            nz[(x, y)] = len(Z)
+    for x, y in pairs:
+        Z = [z for z in range(k) if z != x and z != y and max(d[x, z], d[z, y]) <= T]
+        hxy = 1.0 + (h - 1.0) * min(len(Z), n_max) / n_max
+        acc = 2.0 * hxy * S[(x, y)]
+        for z in Z:
+            acc = acc + mat(x, z) @ mat(z, y)
+        R = acc / (2.0 + len(Z))
+        R[R < theta] = 0.0
+        out[(x, y)] = R
+        nz[(x, y)] = len(Z)
     return out, nz
 
 
