@@ -168,13 +168,15 @@ def cpu_baseline(fam, prm, budget_s: float, seed: int = 0):
                       f"FP64 log-space, {threads} threads, {dt:.1f} s"}
 
 
-def cpu_consistency(fam, prm, merges, seed: int, n_pairs: int = 3, T: int = 200, h: float = 3.0):
+def cpu_consistency(fam, prm, merges, seed: int, n_pairs: int = 3, T: int = 200, h: float = 3.0,
+                    mem_bytes: float = 2.0 * 2**30):
     """The oracle's relaxation (dense FP64 products, numpy) on a few seeded
     pairs of the family that have selected third sequences, over the seeded
     guide tree ``merges``; its inputs are the oracle's own posteriors at the
-    threshold, computed beforehand on a thread pool and not timed.  The
-    family's time is extrapolated by the dense work, sum over pairs and
-    selected z of m l n."""
+    threshold, computed beforehand on a thread pool and not timed, and held
+    in host memory: pairs whose inputs would take more than ``mem_bytes`` are
+    not sampled.  The family's time is extrapolated by the dense work, sum
+    over pairs and selected z of m l n."""
     from concurrent.futures import ThreadPoolExecutor
     import oracle
     k = fam.k
@@ -191,14 +193,25 @@ def cpu_consistency(fam, prm, merges, seed: int, n_pairs: int = 3, T: int = 200,
     cand = [(x, y) for x, y in fam.pairs() if work[x, y] > 0]
     if not cand:
         return {"kind": "oracle", "sample": "no pair has a selected third sequence"}
-    sample = [cand[i] for i in rng.permutation(len(cand))[:n_pairs]]
-    need = set()
-    for x, y in sample:
-        need.add((x, y))
+    # the dense FP64 inputs are held in host memory: at most mem_bytes of them
+    sample, need = [], set()
+    for i in rng.permutation(len(cand)):
+        if len(sample) == n_pairs:
+            break
+        x, y = cand[i]
+        more = {(x, y)}
         for z in range(k):
             if z != x and z != y and max(d[x, z], d[z, y]) <= T:
-                need.add((min(x, z), max(x, z)))
-                need.add((min(z, y), max(z, y)))
+                more.add((min(x, z), max(x, z)))
+                more.add((min(z, y), max(z, y)))
+        grown = need | more
+        if 8.0 * sum(L[a] * L[b] for a, b in grown) > mem_bytes:
+            continue
+        sample.append((x, y))
+        need = grown
+    if not sample:
+        return {"kind": "oracle", "sample": f"skipped: the oracle's dense inputs for one pair exceed "
+                                            f"{mem_bytes / 2**30:.0f} GiB of host memory"}
     need = sorted(need)
 
     def dense(ab):
