@@ -584,7 +584,7 @@ struct FwdOut {      // per-lane results captured at the end corner
     int A;
 };
 
-template <int R, bool SPEC>
+template <int R, bool SPEC, bool LIN>
 __device__ __forceinline__ void fwd_step(
     const Coef& cf, const float2* __restrict__ s_ow, const PairCtx& c, int j, bool act, int lane,
     int Lend, int rend, bool first_strip, int yc,
@@ -637,10 +637,10 @@ __device__ __forceinline__ void fwd_step(
         // posteriors of the cell and their combination
         const float2 Pq2 = __fmul2_rn(__fmul2_rn(F, ps), bs[(r >> 1) * 2 * kWarp + (r & 1)]);
         float P;
-        if (cf.combine == 0) {
+        if (!LIN) {         // the root-mean-square family (the default)
             const float2 sq = __fmul2_rn(Pq2, Pq2);
             P = sqrt_approx(fmaf(cf.wh, sq.x, cf.wp * sq.y));
-        } else {
+        } else {            // linear combinations (mean, one model alone)
             P = fmaf(cf.wh, Pq2.x, cf.wp * Pq2.y);
         }
         pmax = fmaxf(pmax, P);
@@ -690,7 +690,7 @@ __device__ __forceinline__ void fwd_step(
     }
 }
 
-template <int R>
+template <int R, bool LIN>
 __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __restrict__ s_ow, const PairCtx& c,
                           const WarpSmem& ws, int s, int nstrips, const StripIO& io, float invZh,
                           float invZp, int eZh, int eZp, float scaleA, float& pmax, FwdOut& fo,
@@ -878,7 +878,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, const float2* __res
         }
         const int yc_now = yc;
         yc = ycode(j + 1);
-        fwd_step<R, SPEC>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, MZ, lV, lX2, HY, Y2i,
+        fwd_step<R, SPEC, LIN>(cf, s_ow, c, j, act, lane, Lend, rend, first_strip, yc_now, MZ, lV, lX2, HY, Y2i,
                           Aa, cnt, xo, uMZ, uA, cv, ps, scaleA, bs, ebnd, bnd_out, stg, cap, eH, eP, pmax,
                           fo, flag);
     };
@@ -942,15 +942,16 @@ __device__ __forceinline__ void bwd_dispatch(int Rs, const Coef& cf, const float
     }
 }
 
+template <bool LIN>
 __device__ __forceinline__ void fwd_dispatch(int Rs, const Problem& Pb, const float2* s_ow, const PairCtx& c,
                                              const WarpSmem& ws, int s, int ns, const StripIO& io,
                                              float invZh, float invZp, int eZh, int eZp, float scaleA,
                                              float& pmax, FwdOut& fo, int64_t& pair_tot, int& flag) {
     switch (Rs) {
-        case 1: fwd_strip<1>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-        case 2: fwd_strip<2>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-        case 4: fwd_strip<4>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
-        default: fwd_strip<kRmax>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+        case 1: fwd_strip<1, LIN>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+        case 2: fwd_strip<2, LIN>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+        case 4: fwd_strip<4, LIN>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
+        default: fwd_strip<kRmax, LIN>(Pb, s_ow, c, ws, s, ns, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo, pair_tot, flag); break;
     }
 }
 
@@ -990,7 +991,7 @@ __device__ __forceinline__ void group_sync(int gib, int W) {
 // W-th strip (pass 1 from the bottom, pass 2 from the top) and trails the warp
 // of the neighbouring strip through that strip's boundary row and its
 // progress word, so the strips of one pair run concurrently.
-template <int MINB, bool CKPT, int W>
+template <int MINB, bool CKPT, int W, bool LIN>
 __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     stamp_begin(Pb.status->t_f32);
@@ -1141,7 +1142,7 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
                 io.bst = c.bst + s * strip_vals;
                 io.bex = c.bex + s * strip_exps;
             }
-            fwd_dispatch(Rs, Pb, s_ow, c, ws, s, nstrips, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo,
+            fwd_dispatch<LIN>(Rs, Pb, s_ow, c, ws, s, nstrips, io, invZh, invZp, eZh, eZp, scaleA, pmax, fo,
                          pair_tot, flag);
             __syncwarp();
         }
@@ -1208,14 +1209,18 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
 
 using F32Kernel = void (*)(Problem);
 
-template <int W>
-static F32Kernel f32_kernel_w(int variant, bool ckpt) {
-    if (ckpt) return variant == 1 ? k_posterior_f32<3, true, W> : k_posterior_f32<4, true, W>;
-    return variant == 1 ? k_posterior_f32<3, false, W> : k_posterior_f32<4, false, W>;
+template <int W, bool LIN>
+static F32Kernel f32_kernel_wl(int variant, bool ckpt) {
+    if (ckpt) return variant == 1 ? k_posterior_f32<3, true, W, LIN> : k_posterior_f32<4, true, W, LIN>;
+    return variant == 1 ? k_posterior_f32<3, false, W, LIN> : k_posterior_f32<4, false, W, LIN>;
 }
 
-static F32Kernel f32_kernel(int variant, bool ckpt, int wpp = 1) {
-    return wpp == 2 ? f32_kernel_w<2>(variant, ckpt) : f32_kernel_w<1>(variant, ckpt);
+// lin: a linear combination of the two posteriors (combine modes other than
+// the root mean square), compiled as its own kernel so the default keeps no
+// per-cell test of the mode
+static F32Kernel f32_kernel(int variant, bool ckpt, int wpp = 1, bool lin = false) {
+    if (lin) return wpp == 2 ? f32_kernel_wl<2, true>(variant, ckpt) : f32_kernel_wl<1, true>(variant, ckpt);
+    return wpp == 2 ? f32_kernel_wl<2, false>(variant, ckpt) : f32_kernel_wl<1, false>(variant, ckpt);
 }
 
 // Raises a kernel's dynamic shared memory limit once per size (so that a
@@ -1250,6 +1255,8 @@ int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm
     const size_t smem = posterior_f32_smem(warps_per_block, max_len);
     const F32Kernel k = f32_kernel(variant, ckpt, wpp);
     set_smem(k, smem);
+    set_smem(f32_kernel(variant, ckpt, wpp, true), smem);    // the linear-combination kernel too (no attribute
+                                                             // call inside a later stream capture)
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, warps_per_block * 32, smem);
 }
 
@@ -1257,7 +1264,7 @@ cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block
                                  int variant) {
     const size_t smem = posterior_f32_smem(warps_per_block, P.max_len);
     if (P.wpp != 1 && P.wpp != 2) return cudaErrorInvalidValue;
-    const F32Kernel k = f32_kernel(variant, P.ckpt != 0, P.wpp);
+    const F32Kernel k = f32_kernel(variant, P.ckpt != 0, P.wpp, P.cf.combine != 0);
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, warps_per_block * 32, smem, s>>>(P);
