@@ -473,9 +473,10 @@ struct ZEnt {
 // global memory for a z larger than a stage buffer; B's row pointers are
 // indexed by t - bt0 and give entry numbers, its entries by number - b0
 struct SView {
-    const int2* acv;
+    const int2* acv;        // global memory (a batch of one z larger than a buffer)
     const int32_t* brp;
     const int2* bcv;
+    int aoff, broff, bvoff; // byte offsets in the stage buffer (a staged batch)
     int bt0, b0;
 };
 
@@ -613,6 +614,8 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     __shared__ unsigned long long s_base;
     __shared__ __align__(8) unsigned long long bars[2];
     __shared__ int bcount[2];
+    __shared__ int bglob[2];                        // the batch is one z read from global memory
+    __shared__ int bnext[2];                        // next A entry of the batch a warp takes
     __shared__ int bps[2][kStBatch + 1];            // first A entry of each z of a batch
     if (*tree_status) return;
     if (smem_u32(smem) & 15) {                       // bulk copies need 16-byte aligned buffers
@@ -661,6 +664,7 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        bnext[0] = bnext[1] = 0;
     }
     for (int v = lo + tid; v < hi; v += nthr) {
         const int z = in.leaf_at[v];
@@ -684,11 +688,11 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     __syncthreads();
 
     // producer (warp 0): the batch of z starting at zs into buffer s;
-    // returns its size (the same in every lane)
+    // returns its size (the same in every lane).  A z larger than a buffer
+    // forms a batch of its own, read from global memory.
     auto issue = [&](int zs, int s) {
         const int zi = zs + lane;
         int need = 0, na = 0, h2 = 0, h3 = 0, h4 = 0, c2 = 0, c3 = 0, c4 = 0;
-        bool glob = false;
         ZEnt Z = {};
         if (zi < nz) {
             Z = zt[zi];
@@ -697,8 +701,8 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
             c3 = bulk_span(Z.brp, Z.nbr > 0 ? (Z.nbr + 1) * 4 : 0, &h3);
             c4 = bulk_span(Z.bcv, Z.nb * 8, &h4);
             need = c2 + c3 + c4;
-            if (need > sc.slot_bytes) { need = 0; glob = true; }
         }
+        const bool glob0 = __shfl_sync(FULLM, need, 0) > sc.slot_bytes;
         int incl = need, nincl = na;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -707,29 +711,27 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         }
         const bool fits = zi < nz && incl <= sc.slot_bytes;
         const unsigned stop = __ballot_sync(FULLM, !fits);
-        const int cnt = stop ? __ffs(stop) - 1 : 32;        // lanes [0, cnt) form the batch (cnt >= 1)
-        const int total = __shfl_sync(FULLM, incl, cnt - 1);
-        unsigned char* b = slots + s * sc.slot_bytes + (incl - need);
+        const int cnt = glob0 ? 1 : (stop ? __ffs(stop) - 1 : 32);   // lanes [0, cnt) form the batch
+        const int total = glob0 ? 0 : __shfl_sync(FULLM, incl, cnt - 1);
+        const int off = s * sc.slot_bytes + (incl - need);
         if (lane < cnt) {
             SView v;
             v.bt0 = Z.bt0;
             v.b0 = Z.b0;
-            if (glob) {
-                v.acv = Z.acv; v.brp = Z.brp; v.bcv = Z.bcv;
-            } else {
-                v.acv = (const int2*)(b + h2);
-                v.brp = (const int32_t*)(b + c2 + h3);
-                v.bcv = (const int2*)(b + c2 + c3 + h4);
-            }
+            v.acv = Z.acv; v.brp = Z.brp; v.bcv = Z.bcv;
+            v.aoff = off + h2;
+            v.broff = off + c2 + h3;
+            v.bvoff = off + c2 + c3 + h4;
             views[s * kStBatch + lane] = v;
             bps[s][lane] = nincl - na;
             if (lane == cnt - 1) bps[s][cnt] = nincl;
         }
-        if (lane == 0) bcount[s] = cnt;
+        if (lane == 0) { bcount[s] = cnt; bglob[s] = glob0 ? 1 : 0; }
         __syncwarp();
         if (lane == 0) mbar_arrive_expect_tx(&bars[s], (unsigned)total);
         __syncwarp();
-        if (lane < cnt && !glob) {
+        if (lane < cnt && !glob0) {
+            unsigned char* b = slots + off;
             if (c2) bulk_g2s(b, (const unsigned char*)Z.acv - h2, c2, &bars[s]);
             if (c3) bulk_g2s(b + c2, (const unsigned char*)Z.brp - h3, c3, &bars[s]);
             if (c4) bulk_g2s(b + c2 + c3, (const unsigned char*)Z.bcv - h4, c4, &bars[s]);
@@ -746,36 +748,67 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     __syncthreads();
 
     unsigned long long fmas = 0;
-    const int qs = nthr / G, q0 = tid / G, lg = tid % G;
+    const int lg = lane % G;
+    constexpr int kGrab = 32 / G;                    // A entries a warp takes at a time
     for (int zs = 0, b = 0; zs < nz; ++b) {
         const int s = b & 1;
         bool ok = false;
         for (int it = 0; it < kStSpin && !ok; ++it) ok = mbar_try_wait(&bars[s], (unsigned)((b >> 1) & 1));
         if (!ok) atomicExch(stage_err, 1);
         const int cnt = bcount[s];
+        const bool glob = bglob[s] != 0;
         const int* ps = bps[s];
+        const SView* vt = views + s * kStBatch;
         const int na_all = ok ? ps[cnt] : 0;
-        // the batch's A entries, numbered through its z
-        int k = 0;
-        SView v = views[s * kStBatch];
-        for (int q = q0; q < na_all; q += qs) {
-            if (q >= ps[k + 1]) {
-                do { ++k; } while (q >= ps[k + 1]);
-                v = views[s * kStBatch + k];
+        // the batch's A entries, numbered through its z, taken kGrab at a
+        // time by whichever warp is free
+        for (;;) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&bnext[s], kGrab);
+            base = __shfl_sync(FULLM, base, 0);
+            if (base >= na_all) break;
+            // the z holding entry `base` (ps ascending, ps[0] = 0), then this lane's
+            int k = 0, hi = cnt;
+            while (hi - k > 1) {
+                const int mid = (k + hi) >> 1;
+                if (ps[mid] <= base) k = mid; else hi = mid;
             }
-            const int2 tv = v.acv[q - ps[k]];
-            const int t = key_col(tv.x) - v.bt0;
-            unsigned* accr = acc + (key_row(tv.x) - i0) * n;
-            const int b0 = v.brp[t] - v.b0, b1 = v.brp[t + 1] - v.b0;
-            const float vs = __int_as_float(tv.y) * unit;
-            if (lg == 0) fmas += (unsigned long long)(b1 - b0);
-            for (int f = b0 + lg; f < b1; f += G) {
-                const int2 jw = v.bcv[f];
-                atomicAdd(accr + key_col(jw.x), __float2uint_rn(vs * __int_as_float(jw.y)));
+            const int q = base + lane / G;
+            if (q < na_all) {
+                while (q >= ps[k + 1]) ++k;
+                const SView v = vt[k];
+                const int e = q - ps[k];
+                if (glob) {
+                    const int2 tv = v.acv[e];
+                    const int t = key_col(tv.x) - v.bt0;
+                    unsigned* accr = acc + (key_row(tv.x) - i0) * n;
+                    const int b0 = v.brp[t] - v.b0, b1 = v.brp[t + 1] - v.b0;
+                    const float vs = __int_as_float(tv.y) * unit;
+                    if (lg == 0) fmas += (unsigned long long)(b1 - b0);
+                    for (int f = b0 + lg; f < b1; f += G) {
+                        const int2 jw = v.bcv[f];
+                        atomicAdd(accr + key_col(jw.x), __float2uint_rn(vs * __int_as_float(jw.y)));
+                    }
+                } else {
+                    // shared-memory loads from the stage buffer
+                    const int2 tv = *(const int2*)(slots + v.aoff + 8 * e);
+                    const int t = key_col(tv.x) - v.bt0;
+                    unsigned* accr = acc + (key_row(tv.x) - i0) * n;
+                    const int32_t* brp = (const int32_t*)(slots + v.broff);
+                    const int b0 = brp[t] - v.b0, b1 = brp[t + 1] - v.b0;
+                    const int2* bcv = (const int2*)(slots + v.bvoff);
+                    const float vs = __int_as_float(tv.y) * unit;
+                    if (lg == 0) fmas += (unsigned long long)(b1 - b0);
+                    for (int f = b0 + lg; f < b1; f += G) {
+                        const int2 jw = bcv[f];
+                        atomicAdd(accr + key_col(jw.x), __float2uint_rn(vs * __int_as_float(jw.y)));
+                    }
+                }
             }
         }
         zs += cnt;
         __syncthreads();                             // buffer s is free again
+        if (tid == 0) bnext[s] = 0;                  // (its next batch starts after another barrier)
         if (wid == 0 && zq < nz) {
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             zq += issue(zq, s);
