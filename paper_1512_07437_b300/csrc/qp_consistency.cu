@@ -799,7 +799,13 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
                     const int2* bcv = (const int2*)(slots + v.bvoff);
                     const float vs = __int_as_float(tv.y) * unit;
                     if (lg == 0) fmas += (unsigned long long)(b1 - b0);
-                    for (int f = b0 + lg; f < b1; f += G) {
+                    int f = b0 + lg;
+                    for (; f + G < b1; f += 2 * G) {        // two loads in flight
+                        const int2 jw0 = bcv[f], jw1 = bcv[f + G];
+                        atomicAdd(accr + key_col(jw0.x), __float2uint_rn(vs * __int_as_float(jw0.y)));
+                        atomicAdd(accr + key_col(jw1.x), __float2uint_rn(vs * __int_as_float(jw1.y)));
+                    }
+                    if (f < b1) {
                         const int2 jw = bcv[f];
                         atomicAdd(accr + key_col(jw.x), __float2uint_rn(vs * __int_as_float(jw.y)));
                     }
