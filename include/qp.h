@@ -304,8 +304,10 @@ void qp_server_destroy(qp_server* server);
  *                     when T <= 256 and the sums' bound allows its unit;
  *   "cons_chunk_rows" qp_consistency staged form: at most this many rows of
  *                     x per CTA (0: as many as the shared memory holds);
- *   "cons_ctas_per_sm" qp_consistency staged form: CTAs per SM (1 or 2,
- *                     default 2; the shared memory is split between them);
+ *   "cons_ctas_per_sm" qp_consistency staged form: CTAs per SM (1 or 2;
+ *                     the shared memory is split between them; automatic: 2
+ *                     unless their accumulators would hold fewer than 16
+ *                     rows of the longest sequence);
  *   "cons_min_unit"   qp_consistency staged form: the coarsest fixed-point
  *                     unit 2^-u it accepts (default 21); a call whose bound
  *                     on the sums needs a coarser unit runs the row form;

@@ -491,6 +491,7 @@ constexpr int kStBatch = 32;                // z per stage buffer at most (a lan
 constexpr int kMinUnit = 21;                // coarsest fixed-point unit (2^-21) the staged form accepts by default
 constexpr int kStGroup = 1;                 // threads per A entry along a row of B
 constexpr int kStMaxRows = 1024;            // rows of a chunk at most
+constexpr int kStMinRows = 16;              // rows of the longest sequence a chunk should hold (CTAs per SM)
 constexpr int kStSpin = 1 << 22;            // polls of a stage buffer's barrier before the call is failed
 
 // column bands of every matrix and of its transpose (warp per pair, 32
@@ -1030,17 +1031,26 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     int max_rc = 0;
     std::vector<int4> work;
     bool staged = C->tune.cons_form != 0 && cp->T <= kZTab;
-    const int st_ctas = C->tune.cons_ctas_per_sm == 1 ? 1 : 2;      // CTAs of the staged form per SM
-    if (staged) {
-        // shared memory of a CTA: z table, views, two stage buffers,
-        // accumulator rows, row counts (at most kStMaxRows rows per chunk);
-        // less the static shared memory and a margin
-        const int per_cta = std::min(C->smem_optin, C->smem_per_sm / st_ctas - 1024) - 1024;
-        sc.ztab = std::max(1, std::min(cp->T, k));
-        sc.slot_bytes = (per_cta / 5) & ~15;
-        const int fixed = (int)(sizeof(ZEnt) * sc.ztab + sizeof(SView) * 2 * kStBatch) + 2 * sc.slot_bytes +
+    // shared memory of a CTA of the staged form with `ctas` CTAs per SM: z
+    // table, views, two stage buffers, accumulator rows, row counts (at most
+    // kStMaxRows rows per chunk); less the static shared memory and a margin
+    auto stage_cfg = [&](int ctas) {
+        StageCfg c{};
+        const int per_cta = std::min(C->smem_optin, C->smem_per_sm / ctas - 1024) - 1024;
+        c.ztab = std::max(1, std::min(cp->T, k));
+        c.slot_bytes = (per_cta / 5) & ~15;
+        const int fixed = (int)(sizeof(ZEnt) * c.ztab + sizeof(SView) * 2 * kStBatch) + 2 * c.slot_bytes +
                           4 * kStMaxRows;
-        sc.acc_cells = (per_cta - fixed) / 4;
+        c.acc_cells = (per_cta - fixed) / 4;
+        return c;
+    };
+    // two CTAs per SM, unless their accumulators would hold fewer than
+    // kStMinRows rows of the longest sequence (long sequences: measured faster
+    // with one CTA and longer chunks)
+    int st_ctas = C->tune.cons_ctas_per_sm;
+    if (st_ctas <= 0) st_ctas = stage_cfg(2).acc_cells / maxlen >= kStMinRows ? 2 : 1;
+    if (staged) {
+        sc = stage_cfg(st_ctas);
         if (sc.acc_cells < maxlen) staged = false;
     }
     if (staged) {
