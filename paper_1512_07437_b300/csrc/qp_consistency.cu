@@ -182,11 +182,9 @@ __global__ void k_cons_tcount(ConsIn in, int32_t* tcnt) {
     __syncwarp();
     const int32_t* rp = in.rp + in.pro[p];
     const int32_t* col = in.col + in.pno[p];
-    // one row at a time: within a row the columns are distinct
-    for (int i = 0; i < m; ++i) {
-        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) c[col[e]] += 1;
-        __syncwarp();
-    }
+    // every entry at once: integer counts do not depend on the order
+    const int nnz = rp[m];
+    for (int e = lane; e < nnz; e += 32) atomicAdd(&c[col[e]], 1);
 }
 
 // exclusive scan of each pair's transposed row lengths into row pointers
@@ -238,7 +236,7 @@ __global__ void k_cons_tfill(ConsIn in, int32_t* cursor, int2* tcv) {
 
 // the posteriors' entries as (key, value bits) pairs, key = row << 16 |
 // column (lengths are below 2^16), for single 8-byte loads that carry
-// both indices (warp per pair, rows in order)
+// both indices (warp per pair)
 __global__ void k_cons_interleave(ConsIn in, int2* cv) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -247,8 +245,9 @@ __global__ void k_cons_interleave(ConsIn in, int2* cv) {
     const int m = in.len[ab.x];
     const int32_t* rp = in.rp + in.pro[p];
     const int64_t base = in.pno[p];
-    for (int i = 0; i < m; ++i)
-        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32)
+    // a lane per row, 32 rows at a time (rows are short)
+    for (int i = lane; i < m; i += 32)
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
             cv[base + e] = make_int2(pack_key(i, in.col[base + e]), __float_as_int(in.val[base + e]));
 }
 
@@ -924,10 +923,11 @@ __global__ void k_cons_compact(ConsIn in, ConsOut out, const int64_t* pair_nnz_o
         carry += __shfl_sync(FULLM, incl, 31);
     }
     __syncwarp();
-    for (int r = 0; r < m; ++r) {
+    // a lane per row, 32 rows at a time (rows are short)
+    for (int r = lane; r < m; r += 32) {
         const int beg = row_ptr[ro + r], cnt = out.row_cnt[ro + r];
         const int64_t src = out.row_off[ro + r];
-        for (int e = lane; e < cnt; e += 32) {
+        for (int e = 0; e < cnt; ++e) {
             const int2 t = out.pool[src + e];
             col[base + beg + e] = t.x;
             val[base + beg + e] = __int_as_float(t.y);
