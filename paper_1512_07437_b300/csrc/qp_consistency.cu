@@ -491,7 +491,8 @@ constexpr int kMinUnit = 21;                // coarsest fixed-point unit (2^-21)
 constexpr int kStGroup = 1;                 // threads per A entry along a row of B
 constexpr int kStMaxRows = 1024;            // rows of a chunk at most
 constexpr int kStMinRows = 16;              // rows of the longest sequence a chunk should hold (CTAs per SM)
-constexpr int kStSpin = 1 << 22;            // polls of a stage buffer's barrier before the call is failed
+constexpr int kStSpin = 1 << 16;            // waits on a stage buffer's barrier before the call is failed
+constexpr unsigned kStSuspendNs = 20000;    // longest suspension of one wait (ns)
 
 // column bands of every matrix and of its transpose (warp per pair, 32
 // rows at a time): band[r] = (max over rows 0..r of the last column) << 16 |
@@ -556,12 +557,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, u
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// waits for the phase with the given parity: the thread is suspended until
+// the phase completes or about kStSuspendNs pass (no busy polling)
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kStSuspendNs)
         : "memory");
     return ok != 0;
 }
