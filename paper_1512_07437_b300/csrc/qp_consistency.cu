@@ -17,11 +17,21 @@
 // range of the DFS order.
 //
 // Kernels:
-//   k_cons_tree       parent / size / DFS order / R_x from the guide tree's
-//                     joins (one thread: O(k));
-//   k_cons_tcount,    the transposed CSR of every pair (rows of b), built
-//   k_cons_tscan,     row by row so each transposed row lists its entries in
-//   k_cons_tfill      ascending order (deterministic);
+//   k_cons_tree,      parent / size / DFS order / R_x from the guide tree's
+//   k_cons_ranges     joins (one thread: O(k)), then R_x per leaf;
+//   k_cons_tcount,    the transposed CSR of every pair (rows of b); the fill
+//   k_cons_tscan,     walks the rows in order, so each transposed row lists
+//   k_cons_tfill      its entries in ascending order (deterministic);
+//   k_cons_interleave the entries as (row << 16 | column, value) pairs;
+//   staged form (default, T <= 256):
+//   k_cons_stats      the largest value and row sum (the fixed-point unit);
+//   k_cons_bands      per row, the column band of the rows up to / from it;
+//   k_cons_relax_staged  a CTA per row chunk of a pair: warp 0 stages the
+//                     selected z (A's chunk entries, the band of B's rows
+//                     they reach) by TMA bulk copies into two buffers; the
+//                     products go into a dense 32-bit fixed-point
+//                     accumulator in shared memory (see the kernel);
+//   row form (T > 256, or values too large for the staged unit):
 //   k_cons_relax      a CTA per pair, warps over the rows of x: a dense
 //                     accumulator row in shared memory, a Gustavson product
 //                     per z with lanes over (outer entry, inner entry) pairs,
@@ -34,7 +44,8 @@
 //                     (bit-reproducible results) and is exact apart from one
 //                     rounding per product.  No 64-bit conversion per
 //                     product: those run on B300's narrow FP64 pipe;
-//   k_cons_compact    CSR of every pair from the row chunks.
+//   k_cons_pair_nnz,  CSR of every pair from the row chunks.
+//   k_cons_compact
 #include "../../include/qp.h"
 #include "qp_host.h"
 
