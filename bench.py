@@ -168,7 +168,7 @@ def cpu_baseline(fam, prm, budget_s: float, seed: int = 0):
                       f"FP64 log-space, {threads} threads, {dt:.1f} s"}
 
 
-def cpu_consistency(fam, prm, merges, seed: int, n_pairs: int = 3, T: int = 200, h: float = 3.0,
+def cpu_consistency(fam, prm, merges, seed: int, n_pairs: int = 12, T: int = 200, h: float = 3.0,
                     mem_bytes: float = 2.0 * 2**30):
     """The oracle's relaxation (dense FP64 products, numpy) on a few seeded
     pairs of the family that have selected third sequences, over the seeded
