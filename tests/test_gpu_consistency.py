@@ -294,3 +294,81 @@ def test_relaxation_at_c2_lengths_matches_oracle(qp, T):
     assert worst <= TOL, worst
     got.free()
     res.free()
+
+
+@pytest.mark.parametrize("T", [200, 20])
+def test_full_size_sampled_pairs(qp, T):
+    """The 64-sequence benchmark family (200-400 residues, 2016 pairs) at the
+    posterior threshold 0.01, in the launch configuration the benchmark
+    times: three seeded pairs of the relaxed result against the oracle's
+    relaxation of its own posteriors.
+
+    An input entry within 2e-5 of the threshold may be kept on one side and
+    dropped on the other (the posteriors agree to 1e-5).  The oracle bounds
+    what such entries can add to each output cell, with B the matrices of
+    those entries and S the oracle's kept entries:
+        slack = (2 h_xy B_xy + sum_z (B_xz S_zy + S_xz B_zy + B_xz B_zy)) / (2 + |Z|),
+    and the bar is 4e-5 + slack (cells kept on one side only must lie within
+    that of the threshold)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    import torch
+    fam = synth.make_family("c2", 1)
+    theta = 0.01
+    prm = synth.default_params(threshold=theta)
+    d_res = torch.from_numpy(fam.residues).cuda()
+    post = qp.qp_posteriors(d_res, fam.offsets, prm, device=0, out_on_device=True)
+    merges = synth.random_guide_tree(11, fam.k)
+    got = qp.qp_consistency(post, fam.offsets, merges, T=T, threshold=theta, out_on_device=True)
+    assert qp.qp_get_counter("consistency_form") == 1
+    lens = [int(v) for v in fam.lengths]
+    k = fam.k
+    d = oracle.tree_distances(merges, k)
+    rng = np.random.default_rng(17 + T)
+    pl = list(fam.pairs())
+    cand = [(x, y) for x, y in pl if any(z not in (x, y) and max(d[x, z], d[z, y]) <= T for z in range(k))]
+    sample = [cand[i] for i in rng.permutation(len(cand))[:3]]
+    need = set()
+    for x, y in sample:
+        need.add((x, y))
+        for z in range(k):
+            if z not in (x, y) and max(d[x, z], d[z, y]) <= T:
+                need.update({(min(x, z), max(x, z)), (min(z, y), max(z, y))})
+    need = sorted(need)
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        P = dict(zip(need, ex.map(lambda ab: oracle.pair(fam.codes(ab[0]), fam.codes(ab[1]), prm)["P"], need)))
+    S = {ab: np.where(M >= theta, M, 0.0) for ab, M in P.items()}
+    B = {ab: np.where(np.abs(M - theta) <= 2e-5, M, 0.0) for ab, M in P.items()}
+    raw, nz = oracle.consistency(S, lens, merges, T=T, h=3.0, theta=-1.0, pairs=sample)
+
+    def mat(M, a, b):
+        return M[(a, b)] if a < b else M[(b, a)].T
+
+    # the GPU's relaxed matrices of the sampled pairs (device result read back)
+    pro = host(got.array("pair_row_off"))
+    pno = host(got.array("pair_nnz_off"))
+    rp_all = host(got.array("row_ptr"))
+    col = host(got.array("col"))
+    val = host(got.array("val")).astype(np.float64)
+    for x, y in sample:
+        p = x * k - x * (x + 1) // 2 + (y - x - 1)
+        G = np.zeros((lens[x], lens[y]))
+        rp = rp_all[pro[p]:pro[p + 1]]
+        base = int(pno[p])
+        for i in range(lens[x]):
+            G[i, col[base + rp[i]:base + rp[i + 1]]] = val[base + rp[i]:base + rp[i + 1]]
+        Z = [z for z in range(k) if z not in (x, y) and max(d[x, z], d[z, y]) <= T]
+        assert len(Z) == nz[(x, y)] > 0
+        hxy = 1.0 + 2.0 * min(len(Z), 200) / 200
+        slack = 2.0 * hxy * B[(x, y)]
+        for z in Z:
+            slack = slack + mat(B, x, z) @ mat(S, z, y) + mat(S, x, z) @ mat(B, z, y) + mat(B, x, z) @ mat(B, z, y)
+        slack = slack / (2.0 + len(Z))
+        R = raw[(x, y)]
+        bar = TOL + slack
+        kept_ref, kept_gpu = R >= theta, G > 0
+        assert not ((kept_ref != kept_gpu) & (np.abs(R - theta) > bar)).any(), f"pair {(x, y)}: pattern"
+        both = kept_ref & kept_gpu
+        assert (np.abs(G[both] - R[both]) <= bar[both]).all(), f"pair {(x, y)}: values"
+    got.free()
+    post.free()
