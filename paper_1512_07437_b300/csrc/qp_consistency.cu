@@ -89,6 +89,7 @@ struct ConsIn {
     const int32_t* fband;
     const int32_t* tband;
     const int32_t* len;     // [k]
+    const int2* pairs;      // [P] (a, b) of pair p
     const int32_t* leaf_at; // [k] leaf at each DFS position
     const int32_t* pos;     // [k] DFS position of each leaf
     const int32_t* rlo;     // [k] R_x = [rlo, rhi) in DFS positions
@@ -112,17 +113,6 @@ __device__ __forceinline__ int64_t pidx(int a, int b, int k) {
     return (int64_t)a * k - (int64_t)a * (a + 1) / 2 + (b - a - 1);
 }
 
-// (a, b) of linear pair index p (a < b)
-__device__ __forceinline__ int2 pair_of(int64_t p, int k) {
-    // a = the largest a with start(a) <= p, start(a) = a k - a (a + 1) / 2
-    const double kk = 2.0 * k - 1.0;
-    int a = (int)floor((kk - sqrt(kk * kk - 8.0 * (double)p)) * 0.5);
-    if (a < 0) a = 0;
-    while (a > 0 && pidx(a, a + 1, k) > p) --a;
-    while (a + 1 < k - 1 && pidx(a + 1, a + 2, k) <= p) ++a;
-    const int b = (int)(p - pidx(a, a + 1, k)) + a + 1;
-    return make_int2(a, b);
-}
 
 // an entry's row and column in one word (both below 2^16)
 __device__ __forceinline__ int pack_key(int row, int col) { return (row << 16) | col; }
@@ -186,7 +176,7 @@ __global__ void k_cons_tcount(ConsIn in, int32_t* tcnt) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     const int m = in.len[ab.x], n = in.len[ab.y];
     int32_t* c = tcnt + in.tpro[p];
     for (int j = lane; j <= n; j += 32) c[j] = 0;
@@ -203,7 +193,7 @@ __global__ void k_cons_tscan(ConsIn in, int32_t* tcnt, int32_t* trp) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     const int n = in.len[ab.y];
     const int64_t o = in.tpro[p];
     int carry = 0;
@@ -230,7 +220,7 @@ __global__ void k_cons_tfill(ConsIn in, int32_t* cursor, int2* tcv) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     const int m = in.len[ab.x];
     int32_t* cur = cursor + in.tpro[p];
     const int32_t* rp = in.rp + in.pro[p];
@@ -252,7 +242,7 @@ __global__ void k_cons_interleave(ConsIn in, int2* cv) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     const int m = in.len[ab.x];
     const int32_t* rp = in.rp + in.pro[p];
     const int64_t base = in.pno[p];
@@ -321,7 +311,7 @@ __global__ void __launch_bounds__(kConsWarps * 32, 4) k_cons_relax(ConsIn in, Co
     const int64_t p = blockIdx.x;
     if (*tree_status) return;                       // not a tree: the call fails
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int2 xy = pair_of(p, in.k);
+    const int2 xy = in.pairs[p];
     const int x = xy.x, y = xy.y;
     const int m = in.len[x], n = in.len[y];
     unsigned long long* acc = acc_all + (size_t)wid * acc_len;
@@ -440,7 +430,7 @@ __global__ void k_cons_stats(ConsIn in, unsigned* stats) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     float vmax = 0.f, smax = 0.f;
     for (int side = 0; side < 2; ++side) {
         const int rows = in.len[side ? ab.y : ab.x];
@@ -514,7 +504,7 @@ __global__ void k_cons_bands(ConsIn in, int32_t* fband, int32_t* tband) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     for (int side = 0; side < 2; ++side) {
         const int rows = in.len[side ? ab.y : ab.x];
         const int32_t* rp = side ? in.trp + in.tpro[p] : in.rp + in.pro[p];
@@ -656,7 +646,7 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
 
     const int4 w = work[blockIdx.x];
     const int p = w.x, i0 = w.y, i1 = w.z, rc = i1 - i0;
-    const int2 xy = pair_of(p, in.k);
+    const int2 xy = in.pairs[p];
     const int x = xy.x, y = xy.y;
     const int n = in.len[y];
     const int lo = max(in.rlo[x], in.rlo[y]), hi = min(in.rhi[x], in.rhi[y]);
@@ -920,7 +910,7 @@ __global__ void k_cons_compact(ConsIn in, ConsOut out, const int64_t* pair_nnz_o
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P || *out.overflow) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     const int m = in.len[ab.x];
     const int64_t ro = in.pro[p], base = pair_nnz_off[p];
     int carry = 0;
@@ -954,7 +944,7 @@ __global__ void k_cons_pair_nnz(ConsIn in, ConsOut out, int64_t* pair_nnz) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= in.P) return;
-    const int2 ab = pair_of(p, in.k);
+    const int2 ab = in.pairs[p];
     const int m = in.len[ab.x];
     const int64_t ro = in.pro[p];
     long long s = 0;
@@ -992,10 +982,12 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     }
     const int64_t P = (int64_t)k * (k - 1) / 2;
     std::vector<int64_t> tpro(P + 1);
+    std::vector<int2> pairs(P);
     {
         int64_t p = 0;
         for (int a = 0; a < k; ++a)
             for (int b = a + 1; b < k; ++b) {
+                pairs[p] = make_int2(a, b);
                 rows += lens[a] + 1;
                 tpro[p++] = rows_t;
                 rows_t += lens[b] + 1;
@@ -1032,6 +1024,7 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     const size_t o_tcv = take(sizeof(int2) * nnz_in);
     const size_t o_fcv = take(sizeof(int2) * nnz_in);
     const size_t o_len = take(sizeof(int32_t) * k);
+    const size_t o_pairs = take(sizeof(int2) * P);
     const size_t o_mg = take(sizeof(int32_t) * 2 * (k - 1));
     const size_t o_tree = take(sizeof(int32_t) * (size_t)(2 * k - 1) * 6 + sizeof(int32_t) * k * 4);
     const size_t o_cnt = take(sizeof(int32_t) * rows);
@@ -1099,6 +1092,7 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     in.fband = staged ? (const int32_t*)(W + o_fband) : nullptr;
     in.tband = staged ? (const int32_t*)(W + o_tband) : nullptr;
     in.len = (const int32_t*)(W + o_len);
+    in.pairs = (const int2*)(W + o_pairs);
     int32_t* tr = (int32_t*)(W + o_tree);
     const int nn = 2 * k - 1;
     int32_t *parent = tr, *size = tr + nn, *left = tr + 2 * nn, *right = tr + 3 * nn, *stack = tr + 4 * nn,
@@ -1117,6 +1111,7 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     if ((e = cudaMemsetAsync(d_status, 0, 64, st)) != cudaSuccess ||
         (e = up(o_tpro, tpro.data(), sizeof(int64_t) * (P + 1))) != cudaSuccess ||
         (e = up(o_len, lens.data(), sizeof(int32_t) * k)) != cudaSuccess ||
+        (e = up(o_pairs, pairs.data(), sizeof(int2) * P)) != cudaSuccess ||
         (e = cudaMemcpyAsync(W + o_mg, merges, sizeof(int32_t) * 2 * (k - 1),
                              merges_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
