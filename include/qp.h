@@ -308,6 +308,13 @@ void qp_server_destroy(qp_server* server);
  *                     the shared memory is split between them; automatic: 2
  *                     unless their accumulators would hold fewer than 16
  *                     rows of the longest sequence);
+ *   "cons_wait_polls" qp_consistency staged form: waits (each suspends the
+ *                     thread for up to 20 us) on a stage buffer's barrier
+ *                     before the CTA gives up and the call fails with
+ *                     QP_ECUDA (default 65536, about a second);
+ *   "cons_stall_test" testing only: 1 withholds the first batch's arrival,
+ *                     so every CTA's first wait runs out (the call fails with
+ *                     QP_ECUDA and the device stays usable);
  *   "cons_min_unit"   qp_consistency staged form: the coarsest fixed-point
  *                     unit 2^-u it accepts (default 21); a call whose bound
  *                     on the sums needs a coarser unit runs the row form;

@@ -1051,6 +1051,10 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
     } else if (n == "cons_form") {
         if (value > 1) return fail(QP_EINVAL, "cons_form must be 0, 1 or -1");
         C->tune.cons_form = value < 0 ? -1 : (int)value;
+    } else if (n == "cons_wait_polls") {
+        C->tune.cons_wait_polls = value > 0 ? (int)std::min<int64_t>(value, 1 << 20) : 0;
+    } else if (n == "cons_stall_test") {
+        C->tune.cons_stall_test = value > 0 ? 1 : 0;
     } else if (n == "cons_ctas_per_sm") {
         if (value > 2) return fail(QP_EINVAL, "cons_ctas_per_sm must be 1, 2 or 0");
         C->tune.cons_ctas_per_sm = value > 0 ? (int)value : 0;

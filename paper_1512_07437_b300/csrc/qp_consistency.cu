@@ -484,6 +484,8 @@ struct StageCfg {
     int ztab;               // z table entries (>= the selected z of any pair)
     int slot_bytes;         // one of the two stage buffers (a multiple of 16)
     int acc_cells;          // accumulator cells (rows of the chunk x n)
+    int wait_polls;         // waits on a stage buffer's barrier before the CTA gives up
+    int stall_first;        // testing: the first batch's arrival is withheld (its wait runs out)
 };
 
 constexpr int kStThreads = 512;             // 16 warps: one CTA per SM (its shared memory)
@@ -621,6 +623,7 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     __shared__ int bglob[2];                        // the batch is one z read from global memory
     __shared__ int bnext[2];                        // next A entry of the batch a warp takes
     __shared__ int bps[2][kStBatch + 1];            // first A entry of each z of a batch
+    __shared__ int s_nissued;                       // batches issued so far
     if (*tree_status) return;
     if (smem_u32(smem) & 15) {                       // bulk copies need 16-byte aligned buffers
         if (threadIdx.x == 0) atomicExch(stage_err, 1);
@@ -669,6 +672,7 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         bnext[0] = bnext[1] = 0;
+        s_nissued = 0;
     }
     for (int v = lo + tid; v < hi; v += nthr) {
         const int z = in.leaf_at[v];
@@ -730,11 +734,12 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
             bps[s][lane] = nincl - na;
             if (lane == cnt - 1) bps[s][cnt] = nincl;
         }
-        if (lane == 0) { bcount[s] = cnt; bglob[s] = glob0 ? 1 : 0; }
+        if (lane == 0) { bcount[s] = cnt; bglob[s] = glob0 ? 1 : 0; ++s_nissued; }
         __syncwarp();
-        if (lane == 0) mbar_arrive_expect_tx(&bars[s], (unsigned)total);
+        const bool withhold = sc.stall_first && zs == 0;   // testing only
+        if (lane == 0 && !withhold) mbar_arrive_expect_tx(&bars[s], (unsigned)total);
         __syncwarp();
-        if (lane < cnt && !glob0) {
+        if (lane < cnt && !glob0 && !withhold) {
             unsigned char* b = slots + off;
             if (c2) bulk_g2s(b, (const unsigned char*)Z.acv - h2, c2, &bars[s]);
             if (c3) bulk_g2s(b + c2, (const unsigned char*)Z.brp - h3, c3, &bars[s]);
@@ -754,11 +759,12 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     unsigned long long fmas = 0;
     const int lg = lane % G;
     constexpr int kGrab = 32 / G;                    // A entries a warp takes at a time
+    int bail = -1;
     for (int zs = 0, b = 0; zs < nz; ++b) {
         const int s = b & 1;
         bool ok = false;
-        for (int it = 0; it < kStSpin && !ok; ++it) ok = mbar_try_wait(&bars[s], (unsigned)((b >> 1) & 1));
-        if (!ok) atomicExch(stage_err, 1);
+        for (int it = 0; it < sc.wait_polls && !ok; ++it) ok = mbar_try_wait(&bars[s], (unsigned)((b >> 1) & 1));
+        ok = __all_sync(FULLM, ok);                  // a warp skips the batch together if it did not land
         const int cnt = bcount[s];
         const bool glob = bglob[s] != 0;
         const int* ps = bps[s];
@@ -817,12 +823,25 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
             }
         }
         zs += cnt;
-        __syncthreads();                             // buffer s is free again
+        // buffer s is free again; one decision for the whole CTA: a batch
+        // that did not land ends it
+        if (__syncthreads_or(!ok)) { bail = b; break; }
         if (tid == 0) bnext[s] = 0;                  // (its next batch starts after another barrier)
         if (wid == 0 && zq < nz) {
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             zq += issue(zq, s);
         }
+    }
+    if (bail >= 0) {
+        // the call fails; copies still in flight land in this CTA's buffers:
+        // wait for them (again bounded), then leave
+        if (tid == 0) atomicExch(stage_err, 1);
+        for (int bb = bail; bb < s_nissued; ++bb) {
+            bool done = false;
+            for (int it = 0; it < sc.wait_polls && !done; ++it)
+                done = mbar_try_wait(&bars[bb & 1], (unsigned)((bb >> 1) & 1));
+        }
+        return;
     }
 
     // the amplified own signal, in the same units
@@ -1058,6 +1077,8 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     if (st_ctas <= 0) st_ctas = stage_cfg(2).acc_cells / maxlen >= kStMinRows ? 2 : 1;
     if (staged) {
         sc = stage_cfg(st_ctas);
+        sc.wait_polls = C->tune.cons_wait_polls > 0 ? C->tune.cons_wait_polls : kStSpin;
+        sc.stall_first = C->tune.cons_stall_test ? 1 : 0;
         if (sc.acc_cells < maxlen) staged = false;
     }
     if (staged) {

@@ -70,6 +70,8 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int cons_chunk_rows = 0;             // consistency staged form: at most this many rows per CTA (0: by shared memory)
     int cons_min_unit = 0;               // consistency staged form: coarsest unit 2^-u accepted (0: 21)
     int cons_ctas_per_sm = 0;            // consistency staged form: CTAs per SM (1 or 2; 0: 2)
+    int cons_wait_polls = 0;             // consistency staged form: waits on a stage buffer (0: default)
+    int cons_stall_test = 0;             // testing: withhold the first batch's arrival (the wait runs out)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the

@@ -72,7 +72,7 @@ def forms(qp):
     """Restores the automatic choice of the relaxation's form after a test
     that forces one."""
     yield
-    for name in ("cons_form", "cons_chunk_rows", "cons_min_unit"):
+    for name in ("cons_form", "cons_chunk_rows", "cons_min_unit", "cons_wait_polls", "cons_stall_test"):
         qp.qp_set_option(name, -1 if name == "cons_form" else 0, device=0)
 
 
@@ -372,3 +372,28 @@ def test_full_size_sampled_pairs(qp, T):
         assert (np.abs(G[both] - R[both]) <= bar[both]).all(), f"pair {(x, y)}: values"
     got.free()
     post.free()
+
+
+def test_a_stage_wait_that_runs_out_fails_the_call_cleanly(qp, small, forms):
+    """The staged form's waits on its stage buffers are bounded.  A test switch
+    withholds the first batch's arrival, so no CTA's first wait can complete:
+    each CTA gives up after the set number of waits, waits (bounded) for the
+    copies it still has in flight and returns.  The call fails with QP_ECUDA
+    and says why, and the next call on the same device gives the normal
+    result."""
+    fam, res, S, merges = small
+    ref = qp.qp_consistency(res, fam.offsets, merges, T=200)
+    qp.qp_set_option("cons_form", 1)
+    qp.qp_set_option("cons_wait_polls", 64)
+    qp.qp_set_option("cons_stall_test", 1)
+    with pytest.raises(qp.QpError) as e:
+        qp.qp_consistency(res, fam.offsets, merges, T=200)
+    assert e.value.code == 3
+    assert "did not complete" in str(e.value)
+    qp.qp_set_option("cons_stall_test", 0)
+    qp.qp_set_option("cons_wait_polls", 0)
+    got = qp.qp_consistency(res, fam.offsets, merges, T=200)
+    for name in ("pair_row_off", "row_ptr", "pair_nnz_off", "col", "val"):
+        assert np.array_equal(host(got.array(name)), host(ref.array(name))), name
+    got.free()
+    ref.free()
