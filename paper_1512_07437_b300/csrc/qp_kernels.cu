@@ -217,9 +217,11 @@ constexpr long long kPass2Tag = 1LL << 20;         // strip tags of pass 2 start
 constexpr int kSpinLimit = 1 << 22;                 // bounded wait for a progress word
 
 // Waits (warp-uniform) until the progress word reaches need.  A wait that runs
-// out sets the sync guard, so the pair goes to the FP64 form; it never hangs.
+// out sets the sync guard (bit 12), so the pair goes to the FP64 form; it
+// never hangs, and once the guard is set the warp waits no more (the pair's
+// FP32 values are discarded anyway).
 __device__ __forceinline__ void wait_progress(const volatile long long* w, long long need, int& flag) {
-    if (!w) return;
+    if (!w || (flag & (1 << 12))) return;
     int it = 0;
     while (*w < need) {
         if (++it > kSpinLimit) { flag |= (1 << 12); return; }
