@@ -879,6 +879,50 @@ cudaError_t launch_graph(Context* C, cudaStream_t st, const GraphKey& key,
     return cudaGraphLaunch(C->gexec, st);
 }
 
+namespace {
+std::mutex g_host_mu;
+std::multimap<size_t, void*> g_host_spare;    // pinned blocks by size
+size_t g_host_spare_bytes = 0;
+constexpr size_t kHostSpareCap = (size_t)8 << 30;
+constexpr size_t kHostSpareCount = 16;
+}  // namespace
+
+void* take_host_block(size_t bytes, bool* pinned) {
+    {
+        std::lock_guard<std::mutex> g(g_host_mu);
+        auto it = g_host_spare.find(bytes);
+        if (it != g_host_spare.end()) {
+            void* p = it->second;
+            g_host_spare.erase(it);
+            g_host_spare_bytes -= bytes;
+            *pinned = true;
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, bytes) == cudaSuccess && p) {
+        *pinned = true;
+        return p;
+    }
+    cudaGetLastError();
+    *pinned = false;
+    return malloc(bytes);
+}
+
+void give_host_block(void* p, size_t bytes, bool pinned) {
+    if (!p) return;
+    if (!pinned) { free(p); return; }
+    {
+        std::lock_guard<std::mutex> g(g_host_mu);
+        if (g_host_spare_bytes + bytes <= kHostSpareCap && g_host_spare.size() < kHostSpareCount) {
+            g_host_spare.emplace(bytes, p);
+            g_host_spare_bytes += bytes;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
 int to_host(qp_result* r, cudaStream_t st) {
     ResultOwner* own = (ResultOwner*)r->owner_;
     const int64_t P = r->n_pairs;
@@ -900,7 +944,9 @@ int to_host(qp_result* r, cudaStream_t st) {
     };
     size_t tot = 0;
     for (auto& p : parts) tot += align256(p.bytes);
-    char* h = (char*)malloc(std::max<size_t>(tot, 64));
+    const size_t hbytes = std::max<size_t>(tot, 64);
+    bool pinned = false;
+    char* h = (char*)take_host_block(hbytes, &pinned);
     if (!h) return fail(QP_ENOMEM, "host result allocation (%zu bytes) failed", tot);
     size_t o = 0;
     cudaError_t e = cudaSuccess;
@@ -915,7 +961,7 @@ int to_host(qp_result* r, cudaStream_t st) {
         o += align256(p.bytes);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { free(h); return cuda_fail(e, "copy result to host"); }
+    if (e != cudaSuccess) { give_host_block(h, hbytes, pinned); return cuda_fail(e, "copy result to host"); }
     if (own->dev_a || own->dev_b) {
         int rc = QP_OK;
         Context* C = get_context(own->device, &rc);
@@ -929,6 +975,8 @@ int to_host(qp_result* r, cudaStream_t st) {
     }
     own->dev_a = own->dev_b = nullptr;
     own->host = h;
+    own->host_bytes = hbytes;
+    own->host_pinned = pinned;
     own->on_device = false;
     r->on_device = 0;
     return QP_OK;
@@ -952,7 +1000,7 @@ void free_result(qp_result* r) {
             }
             cudaSetDevice(cur);
         }
-        free(own->host);
+        give_host_block(own->host, own->host_bytes, own->host_pinned);
         delete own;
     }
     free(r);

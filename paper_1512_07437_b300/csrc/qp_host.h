@@ -217,8 +217,17 @@ struct ResultOwner {
     void* dev_a = nullptr;   // fixed-size part (ResultLayout)
     void* dev_b = nullptr;   // col / val part
     size_t bytes_a = 0, bytes_b = 0;   // sizes when the blocks may be kept for reuse (else 0)
-    void* host = nullptr;
+    void* host = nullptr;     // host copy (one block: take_host_block)
+    size_t host_bytes = 0;
+    bool host_pinned = false;
 };
+
+// Host blocks of results copied to host memory: pinned (so the copies run at
+// full link speed) and kept after qp_result_free for the next result of the
+// same size, since pinning memory is slow and cudaFreeHost waits for the
+// device.  Plain malloc memory when pinning fails.
+void* take_host_block(size_t bytes, bool* pinned);
+void give_host_block(void* p, size_t bytes, bool pinned);
 
 // Fills the public result from the two device parts (B may be null when nnz = 0
 // is known in advance).  The caller sets nnz, n_fallback, guard_info, kernel_ms.

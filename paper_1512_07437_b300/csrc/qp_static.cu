@@ -80,6 +80,17 @@ int scratch_address(int device, unsigned char** out) {
     return QP_OK;
 }
 
+// Puts the caller's current device back when the call returns.
+struct DeviceRestore {
+    int dev = -1;
+    DeviceRestore() {
+        if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = -1; }
+    }
+    ~DeviceRestore() {
+        if (dev >= 0) cudaSetDevice(dev);
+    }
+};
+
 }  // namespace
 
 extern "C" int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int32_t n,
@@ -88,6 +99,7 @@ extern "C" int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int
                                          int64_t* nnz_out) {
     using namespace qph;
     if (nnz_out) *nnz_out = 0;
+    DeviceRestore restore;
     int rc = validate_params(params);
     if (rc != QP_OK) return rc;
     if (params->precision != QP_F32_SCALED)
@@ -104,6 +116,15 @@ extern "C" int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int
     rc = scratch_address(params->device, &S);
     if (rc != QP_OK) return rc;
     cudaStream_t st = (cudaStream_t)params->stream;
+    // the call copies from host memory on the stack and synchronises the
+    // stream, neither of which a stream capture can hold
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(QP_EINVAL, "qp_pair_posteriors_static cannot run while its stream is being captured");
+    }
 
     Consts* cst = (Consts*)(S + oConsts);
     Status* status = (Status*)(S + oStatus);

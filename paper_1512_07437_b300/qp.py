@@ -311,7 +311,7 @@ def qp_posteriors(residues, offsets, params, out_on_device: bool = False, device
     return Result(out)
 
 
-QP_STATIC_MAX_LEN = 512
+QP_STATIC_MAX_LEN = 512      # the same limit as QP_STATIC_MAX_LEN in qp.h
 
 
 def qp_pair_posteriors_static(residues, m: int, n: int, params, row_ptr, col, val,
@@ -319,16 +319,49 @@ def qp_pair_posteriors_static(residues, m: int, n: int, params, row_ptr, col, va
     """Allocation-free single-pair call (qp_pair_posteriors_static in qp.h).
 
     For callers that may not allocate device memory while they run.  Every
-    array is a caller-owned CUDA tensor: ``residues`` uint8[m + n] (x then y,
-    ASCII), ``row_ptr`` int32[m + 1], ``col`` int32[cap], ``val`` float32[cap],
-    ``pair_out`` float64[4] (MEA score, distance, log Z_hmm, log Z_pf).
-    Returns the number of entries written."""
-    prm = params if isinstance(params, qp_params) else make_params(params, device=device,
-                                                                   stream=stream)
+    array is a caller-owned contiguous CUDA tensor on ``device`` (or on
+    ``params.device`` when ``params`` is a qp_params): ``residues``
+    uint8[m + n] (x then y, ASCII), ``row_ptr`` int32[m + 1], ``col``
+    int32[cap], ``val`` float32[cap], ``pair_out`` float64[4] (MEA score,
+    distance, log Z_hmm, log Z_pf).  The call runs on ``stream``, by default
+    torch's current stream of that device.  Returns the number of entries
+    written."""
+    import torch
+    dev = int(params.device) if isinstance(params, qp_params) else int(device)
+    if stream is None:
+        stream = torch.cuda.current_stream(torch.device("cuda", dev)).cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    if isinstance(params, qp_params):
+        prm = params
+        prm.stream = stream or None
+    else:
+        prm = make_params(params, device=dev, stream=stream)
+
+    def need(t, name, dtype, numel):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise QpError(QP_EINVAL, f"{name} must be a CUDA tensor")
+        if t.device.index != dev:
+            raise QpError(QP_EINVAL, f"{name} is on cuda:{t.device.index}, the call runs on cuda:{dev}")
+        if t.dtype != dtype:
+            raise QpError(QP_EINVAL, f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise QpError(QP_EINVAL, f"{name} must be contiguous")
+        if t.numel() < numel:
+            raise QpError(QP_EINVAL, f"{name} holds {t.numel()} elements, {numel} needed")
+
+    m, n = int(m), int(n)
+    need(residues, "residues", torch.uint8, m + n)
+    need(row_ptr, "row_ptr", torch.int32, m + 1)
+    need(pair_out, "pair_out", torch.float64, 4)
+    cap = 0
+    if col is not None or val is not None:
+        need(col, "col", torch.int32, 0)
+        need(val, "val", torch.float32, 0)
+        cap = min(int(col.numel()), int(val.numel()))
     nnz = ctypes.c_int64(0)
-    cap = int(col.numel()) if col is not None else 0
     rc = lib().qp_pair_posteriors_static(
-        int(residues.data_ptr()), int(m), int(n), ctypes.byref(prm), int(row_ptr.data_ptr()),
+        int(residues.data_ptr()), m, n, ctypes.byref(prm), int(row_ptr.data_ptr()),
         int(col.data_ptr()) if cap else None, int(val.data_ptr()) if cap else None, cap,
         int(pair_out.data_ptr()), ctypes.byref(nnz))
     _check(rc)

@@ -143,3 +143,12 @@ def test_server_without_device_fails_loudly(libqp):
     import paper_1512_07437_b300 as qp
     with pytest.raises(qp.QpError):
         qp.Server(synth.default_params(), 1 << 30)
+
+
+def test_static_limit_matches_header():
+    """The Python binding's copy of QP_STATIC_MAX_LEN must be the header's."""
+    hdr = open(os.path.join(ROOT, "include", "qp.h")).read()
+    m = re.search(r"#define\s+QP_STATIC_MAX_LEN\s+(\d+)", hdr)
+    assert m, "QP_STATIC_MAX_LEN is not defined in qp.h"
+    from paper_1512_07437_b300 import qp as binding
+    assert binding.QP_STATIC_MAX_LEN == int(m.group(1))

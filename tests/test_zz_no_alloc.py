@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import TOL_F32, TOL_LOGZ32, dense_of, host
+from gpu_util import host
 
 pytestmark = pytest.mark.gpu
 
@@ -39,27 +39,24 @@ def _static_call(qp, torch, x, y, prm, cap=None):
     val = torch.full((max(cap, 1),), -7.0, dtype=torch.float32, device="cuda")
     out = torch.full((4,), -7.0, dtype=torch.float64, device="cuda")
     nnz = qp.qp_pair_posteriors_static(res, m, n, prm, row_ptr, col, val, out)
-    rp = row_ptr.cpu().numpy()
-    c = col.cpu().numpy()[:nnz]
-    v = val.cpu().numpy()[:nnz]
-    D = np.zeros((m, n))
-    for i in range(m):
-        D[i, c[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
-    return nnz, rp, D, out.cpu().numpy()
+    return (nnz, row_ptr.cpu().numpy(), col.cpu().numpy()[:nnz], val.cpu().numpy()[:nnz],
+            out.cpu().numpy())
 
 
-def _check_against_qp_posteriors(qp, x, y, prm, nnz, rp, D, out):
+def _check_against_qp_posteriors(qp, x, y, prm, nnz, rp, col, val, out):
+    """Both entry points run the same FP32 kernel on the same inputs, so every
+    output must be identical, bit for bit."""
     fam = synth.family_from_strings([x, y])
     ref = qp.qp_posteriors(fam.residues, fam.offsets, prm, device=0)
-    m, n = len(x), len(y)
-    R = dense_of(ref, 0, m, n)
+    rrp, rcol, rval, _ = ref.pair_csr(0)
     assert nnz == ref.nnz
-    assert rp[0] == 0 and rp[-1] == nnz and (np.diff(rp) >= 0).all()
-    assert np.abs(D - R).max() <= TOL_F32
-    assert abs(out[0] - float(host(ref.mea)[0])) <= TOL_F32 * min(m, n)
-    assert abs(out[1] - float(host(ref.dist64)[0, 1])) <= TOL_F32
-    assert abs(out[2] - float(host(ref.log_z_hmm)[0])) <= TOL_LOGZ32 * max(1.0, abs(out[2]))
-    assert abs(out[3] - float(host(ref.log_z_pf)[0])) <= TOL_LOGZ32 * max(1.0, abs(out[3]))
+    assert np.array_equal(rp, rrp)
+    assert np.array_equal(col, rcol)
+    assert np.array_equal(val.view(np.uint32), rval.view(np.uint32))
+    expect = np.array([float(host(ref.mea)[0]), float(host(ref.dist64)[0, 1]),
+                       float(host(ref.log_z_hmm)[0]), float(host(ref.log_z_pf)[0])])
+    assert np.array_equal(out.view(np.uint64), expect.view(np.uint64)), (out, expect)
+    ref.free()
 
 
 def test_static_entry_matches_qp_posteriors_twice(env):
@@ -70,11 +67,9 @@ def test_static_entry_matches_qp_posteriors_twice(env):
     # anything left in the shared scratch by the first
     pairs = [(fam.seq(0), fam.seq(1)), (fam.seq(3)[:90], fam.seq(2))]
     for x, y in pairs:
-        nnz, rp, D, out = _static_call(qp, torch, x, y, prm)
-        _check_against_qp_posteriors(qp, x, y, prm, nnz, rp, D, out)
+        _check_against_qp_posteriors(qp, x, y, prm, *_static_call(qp, torch, x, y, prm))
     # and the first pair again, after the second
-    nnz, rp, D, out = _static_call(qp, torch, *pairs[0], prm)
-    _check_against_qp_posteriors(qp, *pairs[0], prm, nnz, rp, D, out)
+    _check_against_qp_posteriors(qp, *pairs[0], prm, *_static_call(qp, torch, *pairs[0], prm))
 
 
 def test_static_entry_at_its_size_limit(env):
@@ -87,8 +82,7 @@ def test_static_entry_at_its_size_limit(env):
     y = "".join(synth.ALPHABET[c] for c in synth.evolve(rng, root, 0.3, q)[:limit])
     prm = synth.default_params(threshold=1e-30)
     for _ in range(2):
-        nnz, rp, D, out = _static_call(qp, torch, x, y, prm)
-        _check_against_qp_posteriors(qp, x, y, prm, nnz, rp, D, out)
+        _check_against_qp_posteriors(qp, x, y, prm, *_static_call(qp, torch, x, y, prm))
 
 
 def test_static_entry_rejects_what_it_cannot_hold(env):
@@ -103,3 +97,27 @@ def test_static_entry_rejects_what_it_cannot_hold(env):
     with pytest.raises(qp.QpError) as e:
         _static_call(qp, torch, x, y, synth.default_params(threshold=1e-30), cap=3)
     assert e.value.code == 1 and "too small" in str(e.value)
+
+
+def test_static_entry_refuses_a_capturing_stream(env):
+    """The call synchronises its stream, so a capture cannot hold it: it must
+    refuse cleanly, leave the capture intact and the device usable."""
+    qp, torch = env
+    x, y = "ACDEFGHIKLMNPQRSTVWY" * 3, "ACDEFGHIKLMNPQRSTVWY" * 2
+    prm = synth.default_params(threshold=0.01)
+    s = torch.cuda.Stream()
+    m, n = len(x), len(y)
+    res = torch.from_numpy(np.frombuffer((x + y).encode(), dtype=np.uint8).copy()).cuda()
+    row_ptr = torch.zeros(m + 1, dtype=torch.int32, device="cuda")
+    col = torch.zeros(m * n, dtype=torch.int32, device="cuda")
+    val = torch.zeros(m * n, dtype=torch.float32, device="cuda")
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(qp.QpError) as e:
+        with torch.cuda.graph(g, stream=s):
+            qp.qp_pair_posteriors_static(res, m, n, prm, row_ptr, col, val, out)
+    assert e.value.code == 1 and "captured" in str(e.value)
+    torch.cuda.synchronize()
+    _check_against_qp_posteriors(qp, x, y, prm, *_static_call(qp, torch, x, y, prm))
+    assert torch.cuda.current_device() == 0
