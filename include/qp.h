@@ -190,6 +190,34 @@ typedef struct qp_result {
 int qp_posteriors(const qp_family* family, const qp_params* params,
                   int32_t out_on_device, qp_result** out);
 
+/* The pairs p_begin <= p < p_end of one family (the same computation as
+ * qp_posteriors, restricted to a range of the linear pair order; paper,
+ * Methods, stage I: every pair is independent, so a family's pairs can be
+ * split over several GPUs and the pieces gathered).
+ *   p_begin, p_end : 0 <= p_begin < p_end <= k(k-1)/2, else QP_EINVAL;
+ *   out            : a result of n_pairs = p_end - p_begin pairs, numbered
+ *                    from 0 (local pair q is pair p_begin + q of the family);
+ *                    pair_row_off and pair_nnz_off start at 0 for the first
+ *                    pair of the range; row_ptr, col, val, mea, log totals
+ *                    and flags as for qp_posteriors; dist / dist64 are k x k
+ *                    with only the range's pairs (both triangles) filled and
+ *                    zeros elsewhere, so that the matrices of disjoint ranges
+ *                    add up to the family's.
+ * Every value equals the one qp_posteriors gives for the same pair.  Errors
+ * as for qp_posteriors. */
+int qp_posteriors_range(const qp_family* family, const qp_params* params, int64_t p_begin,
+                        int64_t p_end, int32_t out_on_device, qp_result** out);
+
+/* Equal-work split of a family's pairs over n_parts ranks (host only, no
+ * device needed): bounds[0] = 0 < bounds[1] < ... < bounds[n_parts] =
+ * k(k-1)/2, part i = pairs bounds[i] <= p < bounds[i+1] of the linear order,
+ * each boundary placed where the cumulative work (sum of m n over the pairs
+ * before it) is nearest to i / n_parts of the family's total.
+ *   offsets : HOST int64[k + 1] as in qp_family (every sequence non-empty);
+ *   bounds  : HOST int64[n_parts + 1], written;
+ *   1 <= n_parts <= k(k-1)/2 (every part holds a pair), else QP_EINVAL. */
+int qp_split_pairs(int32_t k, const int64_t* offsets, int32_t n_parts, int64_t* bounds);
+
 /* Releases a result and everything it points to.  NULL is ignored.  Device
  * blocks of a result may be kept by the library for the next call of the same
  * shape: call it after the caller's own work that reads the result (on any
@@ -315,6 +343,10 @@ void qp_server_destroy(qp_server* server);
  *   "cons_stall_test" testing only: 1 withholds the first batch's arrival,
  *                     so every CTA's first wait runs out (the call fails with
  *                     QP_ECUDA and the device stays usable);
+ *   "spin_limit"      testing only: polls (each about 64 ns of sleep) of a
+ *                     warp waiting for the other warp of its pair (wpp = 2)
+ *                     before it gives up and the pair is recomputed by the
+ *                     FP64 form (0: the default, about 4 million);
  *   "cons_min_unit"   qp_consistency staged form: the coarsest fixed-point
  *                     unit 2^-u it accepts (default 21); a call whose bound
  *                     on the sums needs a coarser unit runs the row form;

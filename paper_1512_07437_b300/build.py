@@ -16,9 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 OUT = os.path.join(HERE, "libqp.so")
-SOURCES = ["qp_kernels.cu", "qp_api.cpp", "qp_server.cpp", "qp_static.cu", "qp_tree.cu", "qp_budget.cu",
-           "qp_consistency.cu"]
-HEADERS = ["qp_internal.h", "qp_host.h"]
+SOURCES = ["qp_f32_w1.cu", "qp_f32_w2.cu", "qp_kernels.cu", "qp_api.cpp", "qp_server.cpp", "qp_static.cu",
+           "qp_tree.cu", "qp_budget.cu", "qp_consistency.cu", "qp_split.cpp"]
+HEADERS = ["qp_internal.h", "qp_host.h", "qp_f32.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -185,9 +185,13 @@ int row_capacity(const qp_params* p, int max_len) {
 }
 
 // ------------------------------------------------------------------ planning
-std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
+std::shared_ptr<Plan> build_plan(int k, const int64_t* off, int64_t p0, int64_t p1) {
     auto pl = std::make_shared<Plan>();
     pl->k = k;
+    const int64_t P_all = (int64_t)k * (k - 1) / 2;
+    if (p1 < 0) p1 = P_all;
+    pl->p0 = p0;
+    pl->p1 = p1;
     pl->lens.resize(k);
     int maxL = 0;
     for (int a = 0; a < k; ++a) {
@@ -195,18 +199,24 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
         maxL = std::max<int>(maxL, (int)pl->lens[a]);
     }
     pl->max_len = maxL;
-    const int64_t P = (int64_t)k * (k - 1) / 2;
+    // the plan covers the pairs p0 <= p < p1 of the linear order (all of them
+    // by default), numbered from 0 within the plan
+    const int64_t P = p1 - p0;
     pl->n_pairs = P;
     pl->pairs.resize(P);
     pl->row_off.resize(P + 1);
     pl->strip_off.resize(P + 1);
     pl->work.resize(P);
-    int64_t ro = 0, so = 0, q = 0;
+    int64_t ro = 0, so = 0, q = 0, g = 0;
     int64_t bst = 0, bex = 0;
     double work_sum = 0;
     std::vector<std::pair<int64_t, int32_t>> order(P);
-    for (int a = 0; a < k; ++a) {
-        for (int b = a + 1; b < k; ++b, ++q) {
+    for (int a = 0; a < k && g < p1; ++a) {
+        const int64_t row_pairs = k - 1 - a;
+        if (g + row_pairs <= p0) { g += row_pairs; continue; }    // the whole row of pairs precedes the range
+        for (int b = a + 1; b < k; ++b, ++g) {
+            if (g < p0) continue;
+            if (g >= p1) break;
             const int m = (int)pl->lens[a], n = (int)pl->lens[b];
             pl->pairs[q] = make_int2(a, b);
             pl->row_off[q] = ro;
@@ -222,13 +232,15 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off) {
             pl->work[q] = w;
             order[q] = std::make_pair(-w, (int32_t)q);
             work_sum += (double)w;
+            ++q;
         }
     }
     pl->row_off[P] = ro;
     pl->strip_off[P] = so;
     pl->n_rows = ro;
     pl->n_strips = so;
-    pl->bst_stride = bst;
+    // (the FP32 kernel's ring reads up to kD_ring - 1 blocks past a strip)
+    pl->bst_stride = bst + (int64_t)qpk::kD_ring * qpk::kWarp * qpk::kRmax;
     pl->bex_stride = bex;
     pl->bnd_stride = 2 * (int64_t)(maxL + 1);
     pl->work_sum = work_sum;
@@ -275,18 +287,23 @@ int64_t scratch_budget(const LaunchOverride& t) {
 }
 
 // ------------------------------------------------------------------ result blocks
-constexpr size_t kSpareCap = (size_t)1 << 30;   // bytes of result blocks kept for reuse
-constexpr size_t kSpareCount = 16;
+// Freed result blocks are kept for the next call of the same shape, so that
+// repeated calls see the same addresses and relaunch their captured graph.
+// The most recently freed blocks are kept; the oldest go first when the cache
+// exceeds its bounds.
+constexpr size_t kSpareCap = (size_t)8 << 30;   // bytes of result blocks kept for reuse
+constexpr size_t kSpareCount = 32;
 
 cudaError_t Context::take_block(void** p, size_t bytes, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> g(spare_mu);
-        auto it = spare.find(bytes);
-        if (it != spare.end()) {
-            *p = it->second;
-            spare.erase(it);
-            spare_bytes -= bytes;
-            return cudaSuccess;
+        for (auto it = spare.rbegin(); it != spare.rend(); ++it) {
+            if (it->first == bytes) {
+                *p = it->second;
+                spare.erase(std::next(it).base());
+                spare_bytes -= bytes;
+                return cudaSuccess;
+            }
         }
     }
     cudaError_t e = cudaMallocAsync(p, bytes, st);
@@ -296,15 +313,15 @@ cudaError_t Context::take_block(void** p, size_t bytes, cudaStream_t st) {
 
 void Context::give_block(void* p, size_t bytes) {
     if (!p) return;
-    if (bytes > 0) {
-        std::lock_guard<std::mutex> g(spare_mu);
-        if (spare_bytes + bytes <= kSpareCap && spare.size() < kSpareCount) {
-            spare.emplace(bytes, p);
-            spare_bytes += bytes;
-            return;
-        }
+    if (bytes == 0 || bytes > kSpareCap) { cudaFreeAsync(p, stream); return; }
+    std::lock_guard<std::mutex> g(spare_mu);
+    spare.emplace_back(bytes, p);
+    spare_bytes += bytes;
+    while (spare_bytes > kSpareCap || spare.size() > kSpareCount) {
+        cudaFreeAsync(spare.front().second, stream);
+        spare_bytes -= spare.front().first;
+        spare.pop_front();
     }
-    cudaFreeAsync(p, stream);
 }
 
 // ------------------------------------------------------------------ autotuner key
@@ -373,13 +390,14 @@ cudaError_t call_stream(Context* C, void* user, cudaStream_t* st) {
     return e;
 }
 
-std::shared_ptr<Plan> Context::plan_for(int k, const int64_t* off, int* status) {
-    // cache keyed by the length vector
+std::shared_ptr<Plan> Context::plan_for(int k, const int64_t* off, int* status, int64_t p0, int64_t p1) {
+    // cache keyed by the length vector and the pair range
     std::vector<int64_t> lens(k);
     for (int a = 0; a < k; ++a) lens[a] = off[a + 1] - off[a];
+    if (p1 < 0) p1 = (int64_t)k * (k - 1) / 2;
     for (auto& pl : plans)
-        if (pl->k == k && pl->lens == lens) return pl;
-    auto pl = build_plan(k, off);
+        if (pl->k == k && pl->p0 == p0 && pl->p1 == p1 && pl->lens == lens) return pl;
+    auto pl = build_plan(k, off, p0, p1);
     const int64_t P = pl->n_pairs;
     std::vector<int2> items(P);
     for (int64_t i = 0; i < P; ++i) items[i] = make_int2(0, pl->order[i]);
@@ -429,13 +447,13 @@ void fill_result(qp_result* r, ResultOwner* own, const ResultLayout& L, int k, i
 }
 
 int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
-               qp_result** out) {
+               qp_result** out, int64_t p0, int64_t p1) {
     cudaError_t e;
     const int k = f->k;
     cudaStream_t st;
     if ((e = call_stream(C, prm->stream, &st)) != cudaSuccess) return cuda_fail(e, "stream order");
     int status = QP_OK;
-    auto pl = C->plan_for(k, f->offsets, &status);
+    auto pl = C->plan_for(k, f->offsets, &status, p0, p1);
     if (!pl) return status;
     const int64_t P = pl->n_pairs;
     const int64_t total_res = f->offsets[k];
@@ -499,6 +517,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     Pb.status = (qpk::Status*)C->status.ptr;
     Pb.fallback = (int2*)C->fallback.ptr;
     Pb.max_len = pl->max_len;
+    Pb.spin_limit = C->tune.spin_limit;
     if (!f64) {
         auto occupancy = [&](int v, bool ck, int w = 1) {
             int b = C->tune.blocks_per_sm;
@@ -1028,6 +1047,27 @@ int qp_posteriors(const qp_family* family, const qp_params* params, int32_t out_
     return run_family(C, family, params, out_on_device, out);
 }
 
+int qp_posteriors_range(const qp_family* family, const qp_params* params, int64_t p_begin, int64_t p_end,
+                        int32_t out_on_device, qp_result** out) {
+    using namespace qph;
+    if (!out) return fail(QP_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_family(family);
+    if (rc != QP_OK) return rc;
+    rc = validate_params(params);
+    if (rc != QP_OK) return rc;
+    const int64_t P = (int64_t)family->k * (family->k - 1) / 2;
+    if (!(p_begin >= 0 && p_begin < p_end && p_end <= P))
+        return fail(QP_EINVAL, "pair range [%lld, %lld) is empty or outside [0, %lld)", (long long)p_begin,
+                    (long long)p_end, (long long)P);
+    cudaError_t e = cudaSetDevice(params->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    Context* C = get_context(params->device, &rc);
+    if (!C) return rc;
+    std::lock_guard<std::mutex> g(C->mu);
+    return run_family(C, family, params, out_on_device, out, p_begin, p_end);
+}
+
 void qp_result_free(qp_result* result) { qph::free_result(result); }
 
 int qp_get_counter(int32_t device, const char* name, int64_t* value) {
@@ -1072,6 +1112,10 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
     } else if (n == "wpp") {
         if (value > 0 && value != 1 && value != 2) return fail(QP_EINVAL, "wpp must be 1 or 2");
         C->tune.wpp = value > 0 ? (int)value : 0;
+    } else if (n == "spin_limit") {
+        // testing: polls of a wait for another warp's strip before the pair
+        // is handed to the FP64 form (0 / -1: the default, about 4M)
+        C->tune.spin_limit = value > 0 ? (int)std::min<int64_t>(value, 1 << 30) : 0;
     } else if (n == "graph") {
         C->tune.graph = value != 0;
     } else if (n == "blocks_per_sm") {

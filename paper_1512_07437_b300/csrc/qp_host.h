@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <functional>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -42,6 +43,7 @@ struct HostBuf {                        // pinned host memory
 // Work plan of one family shape (the vector of sequence lengths).
 struct Plan {
     int k = 0;
+    int64_t p0 = 0, p1 = 0;              // the pairs p0 <= p < p1 of the family's linear order
     std::vector<int64_t> lens;
     int max_len = 0;
     int64_t n_pairs = 0, n_rows = 0, n_strips = 0;
@@ -72,6 +74,7 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int cons_ctas_per_sm = 0;            // consistency staged form: CTAs per SM (1 or 2; 0: 2)
     int cons_wait_polls = 0;             // consistency staged form: waits on a stage buffer (0: default)
     int cons_stall_test = 0;             // testing: withhold the first batch's arrival (the wait runs out)
+    int spin_limit = 0;                  // testing: polls of the FP32 kernel's strip waits (0: default)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the
@@ -144,7 +147,7 @@ struct Context {
     // result blocks freed by the caller, kept for the next call of the same
     // shape (same addresses: the captured graph is relaunched as it is)
     std::mutex spare_mu;
-    std::multimap<size_t, void*> spare;
+    std::list<std::pair<size_t, void*>> spare;   // least recently freed first
     size_t spare_bytes = 0;
     cudaError_t take_block(void** p, size_t bytes, cudaStream_t st);
     void give_block(void* p, size_t bytes);
@@ -179,7 +182,7 @@ struct Context {
     LaunchOverride tune;
     std::map<int64_t, TuneEntry> tuner;
     static int64_t tune_key(int64_t n_pairs, int max_len, double work);
-    std::shared_ptr<Plan> plan_for(int k, const int64_t* off, int* status);
+    std::shared_ptr<Plan> plan_for(int k, const int64_t* off, int* status, int64_t p0 = 0, int64_t p1 = -1);
 };
 
 // Device layout of a result's fixed-size part (one allocation): per-pair and
@@ -257,14 +260,14 @@ int validate_params(const qp_params* p);
 void make_raw(const qp_params* p, qpk::RawParams* r);
 void make_coef(const qp_params* p, qpk::Coef* c);
 int row_capacity(const qp_params* p, int max_len);
-std::shared_ptr<Plan> build_plan(int k, const int64_t* off);
+std::shared_ptr<Plan> build_plan(int k, const int64_t* off, int64_t p0 = 0, int64_t p1 = -1);
 Context* get_context(int device, int* status);
 // The stream a call runs on: the caller's, or when it is NULL the library's
 // stream, made to wait first for all work issued so far to the legacy
 // default stream (so inputs written there are complete).
 cudaError_t call_stream(Context* C, void* user, cudaStream_t* st);
 int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
-               qp_result** out);
+               qp_result** out, int64_t p0 = 0, int64_t p1 = -1);
 int to_host(qp_result* r, cudaStream_t st);
 cudaError_t launch_graph(Context* C, cudaStream_t st, const GraphKey& key,
                          const std::function<cudaError_t()>& enqueue);

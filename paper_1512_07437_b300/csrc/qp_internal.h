@@ -7,15 +7,23 @@
 namespace qpk {
 
 constexpr int kWarp = 32;
-#ifndef QP_RMAX
-#define QP_RMAX 4
-#endif
-constexpr int kRmax = QP_RMAX;               // DP rows per lane in a full strip (4 or 8)
-constexpr int kStripRows = kWarp * kRmax;    // 256 DP rows per strip
+constexpr int kRmax = 4;                     // DP rows per lane in a full strip
+constexpr int kStripRows = kWarp * kRmax;    // 128 DP rows per strip
 constexpr int kC = 16;                       // renormalisation period (steps); divides 32
 constexpr int kTab = 21;                     // 20 residues + the empty row/column code
 constexpr int kEmpty = 20;
 constexpr int kNS = 9;                       // FP64 form: values per diagonal slot
+#ifndef QP_RING_DEPTH
+#define QP_RING_DEPTH 4
+#endif
+constexpr int kD_ring = QP_RING_DEPTH;       // FP32 form: depth of the stored-block ring (steps; a power of 2)
+
+// Staging records a lane of the FP32 kernel may hold per strip: at most one
+// per column it sweeps (L + 1), and at most R_max times a row's entry bound
+// (every record holds at least one kept entry of one of its rows).
+__host__ __device__ constexpr int group_capacity(int max_len, int row_cap) {
+    return (max_len + 1) < kRmax * row_cap ? (max_len + 1) : kRmax * row_cap;
+}
 
 // Per-call derived constants, written by k_setup on the device.
 struct Consts {
@@ -133,7 +141,7 @@ struct Problem {
     float2* bst;  int64_t bst_stride;      // stored backward values
     int2* bex;    int64_t bex_stride;      // backward exponents per chunk
     float4* bnd;  int64_t bnd_stride;      // strip boundary rows (2 float4 / column)
-    int2* stg;    int64_t stg_stride;      // staging of entries, [kStripRows][cap]
+    int2* stg;    int64_t stg_stride;      // staging records: 32 lanes x group_capacity x 32 bytes a warp
     // backward boundary rows (bck) and forward ones (bnd), per group of warps
     // sharing a pair: one row per strip when other warps or a recompute read
     // them (checkpointed form, wpp > 1), else one row.  bst / bex: per group
@@ -149,6 +157,8 @@ struct Problem {
     int2* d_stg;  double* d_stg64; int64_t d_stg_stride;
     int32_t f64_all;               // 1: F64 form over the whole item list
     int32_t max_len;
+    int32_t spin_limit;            // polls of a wait for another warp's strip (0: default)
+    int32_t pad_;
 };
 
 // launch wrappers (qp_kernels.cu)
@@ -175,11 +185,15 @@ struct F32Scratch {
         const int64_t strip = (int64_t)kStripRows * (L + 32);
         const int64_t ex = (int64_t)((L + 32 + kC - 1) / kC) * 32;
         const int64_t row = 2 * (int64_t)(L + 1);
-        bst = ckpt ? strip : ns * strip;
+        // pass 2 streams the stored blocks kD - 1 steps ahead of their use;
+        // the blocks past a strip's end are never read (their copies are
+        // zero-filled) but their addresses stay inside the buffer
+        const int64_t pad = (int64_t)kD_ring * kWarp * kRmax;
+        bst = (ckpt ? strip : ns * strip) + pad;
         bex = ckpt ? ex : ns * ex;
         bnd = (wpp > 1 ? ns : 1) * row;
         bck = (ckpt || wpp > 1 ? ns : 1) * row;
-        stg = (int64_t)kStripRows * cap;
+        stg = (int64_t)kWarp * 4 * group_capacity(L, cap);
     }
     // bytes for a grid of `warps` warps
     size_t bytes(int64_t warps) const {

@@ -28,11 +28,12 @@ constexpr size_t oSmall = oFam + al(sizeof(FamDesc));
 constexpr size_t oCodes = oSmall + al(1024);
 constexpr size_t oRowCnt = oCodes + al(2 * kSMaxLen);
 constexpr size_t oBst = oRowCnt + al(sizeof(int32_t) * (kSMaxLen + 1));
-constexpr size_t oBex = oBst + al(sizeof(float2) * (size_t)kSStrips * kStripRows * (kSMaxLen + 32));
+constexpr size_t oBex = oBst + al(sizeof(float2) * ((size_t)kSStrips * kStripRows * (kSMaxLen + 32) +
+                                                    (size_t)kD_ring * kWarp * kRmax));
 constexpr size_t oBnd = oBex + al(sizeof(int2) * (size_t)kSStrips * kSChunks * 32);
 constexpr size_t oBck = oBnd + al(sizeof(float4) * 2 * (size_t)(kSMaxLen + 1));
 constexpr size_t oStg = oBck + al(sizeof(float4) * 2 * (size_t)(kSMaxLen + 1));
-constexpr size_t oPool = oStg + al(sizeof(int2) * (size_t)kStripRows * kSCap);
+constexpr size_t oPool = oStg + al(sizeof(int2) * (size_t)kWarp * 4 * group_capacity(kSMaxLen, kSCap));
 constexpr size_t kSBytes = oPool + al(sizeof(int2) * (size_t)kSMaxLen * kSCap);
 
 // Small per-call tables, copied from the host in one piece (offset oSmall).

@@ -103,6 +103,11 @@ def lib():
         P = ctypes.POINTER
         L.qp_posteriors.argtypes = [P(qp_family), P(qp_params), ctypes.c_int32, P(P(qp_result))]
         L.qp_posteriors.restype = ctypes.c_int
+        L.qp_posteriors_range.argtypes = [P(qp_family), P(qp_params), ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int32, P(P(qp_result))]
+        L.qp_posteriors_range.restype = ctypes.c_int
+        L.qp_split_pairs.argtypes = [ctypes.c_int32, P(ctypes.c_int64), ctypes.c_int32, P(ctypes.c_int64)]
+        L.qp_split_pairs.restype = ctypes.c_int
         L.qp_result_free.argtypes = [P(qp_result)]
         L.qp_result_free.restype = None
         L.qp_last_error.restype = ctypes.c_char_p
@@ -309,6 +314,35 @@ def qp_posteriors(residues, offsets, params, out_on_device: bool = False, device
     del keep
     _check(rc)
     return Result(out)
+
+
+def qp_posteriors_range(residues, offsets, params, p_begin: int, p_end: int, out_on_device: bool = False,
+                        device: int = 0, stream=None, **overrides) -> Result:
+    """The pairs p_begin <= p < p_end of a family (qp_posteriors_range in
+    qp.h): pair q of the result is pair p_begin + q of the family; distances
+    are k x k with only the range's pairs filled."""
+    L = lib()
+    fam, keep = make_family(residues, offsets)
+    prm = params if isinstance(params, qp_params) else make_params(params, device=device,
+                                                                   stream=stream, **overrides)
+    out = ctypes.POINTER(qp_result)()
+    rc = L.qp_posteriors_range(ctypes.byref(fam), ctypes.byref(prm), int(p_begin), int(p_end),
+                               int(bool(out_on_device)), ctypes.byref(out))
+    del keep
+    _check(rc)
+    return Result(out)
+
+
+def qp_split_pairs(offsets, n_parts: int) -> np.ndarray:
+    """Equal-work split of a family's pairs (qp_split_pairs in qp.h; host
+    only): int64 bounds[n_parts + 1], part i = pairs bounds[i] <= p <
+    bounds[i+1]."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    k = int(off.shape[0] - 1)
+    bounds = np.zeros(int(n_parts) + 1, dtype=np.int64)
+    _check(lib().qp_split_pairs(k, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(n_parts),
+                                bounds.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return bounds
 
 
 QP_STATIC_MAX_LEN = 512      # the same limit as QP_STATIC_MAX_LEN in qp.h

@@ -422,3 +422,33 @@ def test_entry_pool_overflow_reruns_the_call(qp):
         qp.qp_set_option("pool_entries", 0)
     ref.free()
     ref_b.free()
+
+
+def test_a_strip_wait_that_runs_out_goes_to_fp64(qp):
+    """Two warps sharing a pair wait for each other's boundary rows with a
+    bounded number of polls.  With the limit cut to one poll (a runtime
+    option; the one-warp kernel the benchmark runs is untouched) the first
+    wait of the second warp runs out before its neighbour has produced the
+    rows it needs: the pair must be flagged (sync guard), recomputed by the
+    FP64 form, and still match the oracle; a normal call on the same device
+    afterwards must succeed in FP32."""
+    fam = synth.star_family(48, 4, (300, 420), 0.3)     # 3-4 strips per pair
+    prm = synth.default_params(threshold=DENSE)
+    try:
+        qp.qp_set_option("wpp", 2)
+        qp.qp_set_option("spin_limit", 1)
+        res = _run(qp, fam, prm)
+    finally:
+        qp.qp_set_option("spin_limit", 0)
+        qp.qp_set_option("wpp", 0)
+    flags = host(res.pair_flags)
+    sync = (flags & (1 << 12)) != 0
+    assert res.n_fallback > 0 and sync.any(), f"no wait ran out: flags {flags}"
+    assert ((flags[sync] & 1) == 1).all(), "a pair whose wait ran out was not recomputed in FP64"
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(res, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32)
+    res.free()
+    again = _run(qp, fam, prm)
+    _no_fallback(again)
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(again, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32)
