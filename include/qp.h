@@ -307,8 +307,8 @@ void qp_server_destroy(qp_server* server);
  *                     tries 2 when pairs are too few to fill the grid;
  *   "graph"           1 (default): run each call as one captured CUDA graph;
  *                     0: plain launches;
- *   "blocks_per_sm", "warps_per_block" (default 2 for qp_posteriors, 4 in
- *                     a server);
+ *   "blocks_per_sm", "warps_per_block" (default for qp_posteriors: 8 for
+ *                     launches of several waves, else 2; 4 in a server);
  *   "scratch_bytes"   device bytes the kernels' scratch may take (default:
  *                     45% of free memory, at most 48 GiB); the stored form is
  *                     chosen while it fits a full grid, else the checkpointed
@@ -343,6 +343,12 @@ void qp_server_destroy(qp_server* server);
  *   "cons_stall_test" testing only: 1 withholds the first batch's arrival,
  *                     so every CTA's first wait runs out (the call fails with
  *                     QP_ECUDA and the device stays usable);
+ *   "tab_copies"      copies of the emission table each block keeps in
+ *                     shared memory: 16 (bank-sliced: lane l reads copy
+ *                     l mod 16, so a half-warp's lookups never share a bank;
+ *                     56 KB) or 1; -1 automatic (16 with blocks of 8 warps
+ *                     when two such blocks fit an SM, else 1).  Results are
+ *                     identical either way;
  *   "spin_limit"      testing only: polls (each about 64 ns of sleep) of a
  *                     warp waiting for the other warp of its pair (wpp = 2)
  *                     before it gives up and the pair is recomputed by the

@@ -167,6 +167,9 @@ void make_coef(const qp_params* p, qpk::Coef* c) {
     c->k_ext = make_float2(c->e1, c->We);
     c->k_mm = make_float2(c->tMM, 1.f);
     c->k_close = make_float2(c->c1, 1.f);
+    c->tab_x = 8;                     // one table copy (see set_tab_copies)
+    c->tab_y = 8 * qpk::kTab;
+    c->spin_limit = 0;
     switch (p->combine) {
         case QP_COMBINE_RMS: c->combine = 0; c->wh = 0.5f; c->wp = 0.5f; break;
         case QP_COMBINE_MEAN: c->combine = 1; c->wh = 0.5f; c->wp = 0.5f; break;
@@ -269,7 +272,7 @@ unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, in
         if (t.variant >= 0 && v != t.variant) continue;
         if (t.wpp > 0 && W != t.wpp) continue;
         // W must divide the block; groups of several warps use named barriers 1, 2
-        if (warps_per_block % W || (W > 1 && warps_per_block / W > 2)) continue;
+        if (warps_per_block % W || (W > 1 && warps_per_block / W > 4)) continue;
         // two warps per pair only while the pairs fill at most half the grid
         // (then they shorten each pair without halving the pairs in flight)
         if (t.wpp <= 0 && W > 1 && (max_strips < W || n_pairs * W > warps_full)) continue;
@@ -499,10 +502,22 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     }
 
     // ---- launch configuration of the FP32 kernel
-    // blocks of 2 warps: finer placement over the SMs than 4 (measured: the
-    // same on large launches, a few per cent better when the pairs fill the
-    // grid about once)
-    const int wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 2;
+    // Launches of several waves: blocks of 8 warps holding the bank-sliced
+    // emission table (kTabCopies copies: conflict-free lookups) when two such
+    // blocks fit an SM's shared memory.  Otherwise blocks of 2 warps with one
+    // table: finer placement over the SMs (a few per cent better when the
+    // pairs fill the grid about once).
+    int wpb = C->tune.warps_per_block;
+    int copies = 1;
+    if (!f64) {
+        const bool big = P >= (int64_t)4 * 16 * C->sm_count;
+        if (wpb <= 0) wpb = big ? 8 : 2;
+        copies = C->tune.tab_copies >= 0 ? C->tune.tab_copies
+                                         : (wpb >= 8 ? qpk::posterior_f32_tab_copies(wpb, pl->max_len, C->smem_per_sm)
+                                                     : 1);
+        if (copies <= 1 && C->tune.warps_per_block <= 0) wpb = 2;
+    }
+    if (wpb <= 0) wpb = 2;
     int variant = 0, cfg = 0, W = 1;
     bool ckpt = false;
     int64_t grid = 1, tkey = 0;
@@ -517,12 +532,15 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     Pb.status = (qpk::Status*)C->status.ptr;
     Pb.fallback = (int2*)C->fallback.ptr;
     Pb.max_len = pl->max_len;
-    Pb.spin_limit = C->tune.spin_limit;
+    Pb.cf.spin_limit = C->tune.spin_limit;
+    Pb.tab_copies = copies > 1 ? qpk::kTabCopies : 1;
+    Pb.cf.tab_x = 8u * (uint32_t)Pb.tab_copies;
+    Pb.cf.tab_y = 8u * (uint32_t)(qpk::kTab * Pb.tab_copies);
     if (!f64) {
         auto occupancy = [&](int v, bool ck, int w = 1) {
             int b = C->tune.blocks_per_sm;
             if (b <= 0) {
-                qpk::posterior_f32_occupancy(wpb, pl->max_len, &b, v, ck, w);
+                qpk::posterior_f32_occupancy(wpb, pl->max_len, &b, v, ck, w, Pb.tab_copies);
                 b = std::max(1, std::min(b, 8));
             }
             return b;
@@ -1112,6 +1130,10 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
     } else if (n == "wpp") {
         if (value > 0 && value != 1 && value != 2) return fail(QP_EINVAL, "wpp must be 1 or 2");
         C->tune.wpp = value > 0 ? (int)value : 0;
+    } else if (n == "tab_copies") {
+        // emission table copies in shared memory: 1, 16 (bank-sliced), or -1 automatic
+        if (value > 1 && value != qpk::kTabCopies) return fail(QP_EINVAL, "tab_copies must be 1, %d or -1", qpk::kTabCopies);
+        C->tune.tab_copies = value < 0 ? -1 : (value == 0 ? -1 : (int)value);
     } else if (n == "spin_limit") {
         // testing: polls of a wait for another warp's strip before the pair
         // is handed to the FP64 form (0 / -1: the default, about 4M)

@@ -265,6 +265,7 @@ enum : int {
 
 __device__ __forceinline__ void wait_progress(const volatile long long* w, long long need, int& flag, int limit) {
     if (!w || (flag & kGuardSync)) return;
+    if (limit <= 0) limit = kSpinLimitDefault;
     int it = 0;
     while (*w < need) {
         if (++it > limit) { flag |= kGuardSync; return; }
@@ -286,7 +287,6 @@ struct PairCtx {
     float4* bck;     // checkpointed form: the backward boundary row of every strip
     int4* stg;       // this lane's staging area: capg records of 32 bytes
     int capg;
-    int spin_limit;
 };
 
 // per-warp shared memory (32-bit shared-window addresses): stored-block ring,
@@ -297,7 +297,9 @@ struct WarpSmem {
     unsigned sy;      // [max_len + 2 kYPad] residue codes
 };
 
-constexpr int kOwBytes = ((kTab * kTab * 8 + 255) / 256) * 256;
+// bytes of the (odds, weight) table with `copies` copies: entry e of copy c
+// at (e * copies + c) * 8
+__host__ __device__ constexpr int tab_bytes(int copies) { return ((kTab * kTab * 8 * copies + 255) / 256) * 256; }
 constexpr int kYPad = 33;   // empty codes before column 1 of the staged residues
 constexpr unsigned kRingSlot = kWarp * kRmax * 8;   // bytes of one ring slot
 
@@ -343,12 +345,14 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     const int row0 = s * kStripRows;
     const bool last_strip = (s == nstrips - 1);
     const bool first_strip = (s == 0);
-    // byte offset of each row's residue within a table row
+    // byte offset of each row's residue within a table row (in this lane's
+    // copy of the table: lane mod copies, 8 bytes apart)
+    const unsigned lane_copy = (8u * (unsigned)lane) & (cf.tab_x - 8u);
     unsigned xo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + lane * R + r;
-        xo[r] = 8u * (unsigned)((i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty);
+        xo[r] = cf.tab_x * (unsigned)((i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty) + lane_copy;
     }
     // carried across steps: the diagonal outflow (B_M, Zm_b) and the
     // horizontal outflows (B_Y, Zf_b), B_Y2 of every row; the vertical
@@ -369,7 +373,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     // its values at column n (every lane starts there)
     int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
     // the row below is written by another warp: wait for its first columns
-    wait_progress(io.wait, io.wait_tag | (64 + kD), flag, c.spin_limit);
+    wait_progress(io.wait, io.wait_tag | (64 + kD), flag, cf.spin_limit);
     if (bnd_in) {
         const float4 v0 = bnd_in[2 * n], v1 = bnd_in[2 * n + 1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
@@ -430,7 +434,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
             // the row below is written by another warp: stay 16 + kD + 32
             // steps behind it (column n - T of the row below is written at
             // the writer's step T + 31 and fetched here kD - 1 steps ahead)
-            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag, c.spin_limit);
+            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag, cf.spin_limit);
             if (io.pub && lane == 0) publish_progress(io.pub, io.pub_tag | t);
             // renormalise: bring the lane's largest carried value into [1, 2)
             float mh = max3f(dDD.x, tV.x, tX2), mp = fmaxf(dDD.y, tV.y);
@@ -501,7 +505,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
                      "@q ld.shared.v4.f32 {%0, %1, %2, %3}, [%6];\n\t@q ld.shared.f32 %4, [%6+16];\n\t}"
                      : "+f"(rDD.x), "+f"(rDD.y), "+f"(rV.x), "+f"(rV.y), "+f"(rX2) : "r"(lane), "r"(eba));
         rDD = __fmul2_rn(rDD, cv); rV = __fmul2_rn(rV, cv); rX2 *= cv.x;
-        const unsigned owr = s_ow + (unsigned)yc_now * (kTab * 8);
+        const unsigned owr = s_ow + (unsigned)yc_now * cf.tab_y;
         float2 D = dDD;
         float2 V = rV;
         float X2b = rX2;
@@ -580,12 +584,14 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
     const bool last_strip = (s == nstrips - 1);
     const bool first_strip = (s == 0);
     // rows outside 1..m get the empty code: their posteriors are 0, below any
-    // threshold, so they never produce an entry
+    // threshold, so they never produce an entry (offsets in this lane's copy
+    // of the table: lane mod copies, 8 bytes apart)
+    const unsigned lane_copy = (8u * (unsigned)lane) & (cf.tab_x - 8u);
     unsigned xo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + lane * R + r;
-        xo[r] = 8u * (unsigned)((i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty);
+        xo[r] = cf.tab_x * (unsigned)((i >= 1 && i <= m) ? (int)__ldg(c.x + i - 1) : kEmpty) + lane_copy;
     }
     // carried across steps: the diagonal outflow (M, Zm) and the horizontal
     // outflows (Y, Zf), Y2 of every row; the vertical outflows (X, Ze), X2 of
@@ -607,7 +613,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
     // its values at column 0 (every lane starts there)
     int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
     // the row above is written by another warp: wait for its first columns
-    wait_progress(io.wait, io.wait_tag | (64 + kD), flag, c.spin_limit);
+    wait_progress(io.wait, io.wait_tag | (64 + kD), flag, cf.spin_limit);
     if (bnd_in) {
         const float4 v0 = bnd_in[0], v1 = bnd_in[1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
@@ -705,7 +711,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
             // steps behind it (column T of the row above is written at the
             // writer's step T + 31 and fetched here kD - 1 steps ahead; a
             // writer publishes its progress every kC steps)
-            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag, c.spin_limit);
+            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag, cf.spin_limit);
             if (io.pub && lane == 31) publish_progress(io.pub, io.pub_tag | t);
             float mh = max3f(uMZ.x, lV.x, lX2), mp = fmaxf(uMZ.y, lV.y);
 #pragma unroll
@@ -778,7 +784,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
             rMZ = make_float2(v0.x, v0.y); rV = make_float2(v0.z, v0.w); rX2 = v1.x; rA = __float_as_int(v1.y);
         }
         rMZ = __fmul2_rn(rMZ, cv); rV = __fmul2_rn(rV, cv); rX2 *= cv.x;
-        const unsigned owr = s_ow + (unsigned)yc_now * (kTab * 8);
+        const unsigned owr = s_ow + (unsigned)yc_now * cf.tab_y;
         // this step's stored backward values of the lane's rows
         float2 bsv[R];
         if (R == 1) {
@@ -957,17 +963,21 @@ struct GroupCtl {
     long long tot[4];
 };
 
-// Barrier of one group.  Groups of 2 warps use named barriers 1 and 2, a group
-// of 4 barrier 1 (literal ids: a register id would reserve all 16 barriers of
-// the block and cost occupancy).
+// Barrier of one group.  Group g of W warps uses named barrier g + 1 (literal
+// ids: a register id would reserve all 16 barriers of the block and cost
+// occupancy); a block holds at most 4 groups.
 __device__ __forceinline__ void group_sync(int gib, int W) {
     if (W == 1) { __syncwarp(); return; }
-    if (gib == 0) asm volatile("bar.sync 1, %0;" ::"r"(32 * W) : "memory");
-    else asm volatile("bar.sync 2, %0;" ::"r"(32 * W) : "memory");
+    switch (gib) {
+        case 0: asm volatile("bar.sync 1, %0;" ::"r"(32 * W) : "memory"); break;
+        case 1: asm volatile("bar.sync 2, %0;" ::"r"(32 * W) : "memory"); break;
+        case 2: asm volatile("bar.sync 3, %0;" ::"r"(32 * W) : "memory"); break;
+        default: asm volatile("bar.sync 4, %0;" ::"r"(32 * W) : "memory"); break;
+    }
 }
 
-__host__ __device__ constexpr size_t posterior_f32_smem_bytes(int warps_per_block, int max_len) {
-    return (size_t)kOwBytes + (size_t)warps_per_block * warp_smem_bytes(max_len) +
+__host__ __device__ constexpr size_t posterior_f32_smem_bytes(int warps_per_block, int max_len, int copies) {
+    return (size_t)tab_bytes(copies) + (size_t)warps_per_block * warp_smem_bytes(max_len) +
            (size_t)warps_per_block * sizeof(GroupCtl);
 }
 
@@ -984,26 +994,29 @@ __host__ __device__ constexpr size_t posterior_f32_smem_bytes(int warps_per_bloc
 // W-th strip (pass 1 from the bottom, pass 2 from the top) and trails the warp
 // of the neighbouring strip through that strip's boundary row and its
 // progress word, so the strips of one pair run concurrently.
-template <int MINB, bool CKPT, int W, bool LIN>
-__global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
+template <bool CKPT, int W, bool LIN>
+__device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     stamp_begin(Pb.status->t_f32);
+    // the table, tab_copies copies side by side (entry e of copy q at e * copies + q)
+    const int copies = Pb.tab_copies > 1 ? kTabCopies : 1;
     float2* s_ow_p = (float2*)s_raw;
-    for (int i = threadIdx.x; i < kTab * kTab; i += blockDim.x) s_ow_p[i] = Pb.cst->ow[i];
+    for (int i = threadIdx.x; i < kTab * kTab * copies; i += blockDim.x) s_ow_p[i] = Pb.cst->ow[i / copies];
     const unsigned s_ow = smem_u32(s_raw);
+    const unsigned tab_end = tab_bytes(copies);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int nwb = blockDim.x >> 5;
     const int gib = wib / W, wig = wib % W;
     WarpSmem ws;
     {
-        const unsigned p = s_ow + kOwBytes + (unsigned)wib * (unsigned)warp_smem_bytes(Pb.max_len);
+        const unsigned p = smem_u32(s_raw) + tab_end + (unsigned)wib * (unsigned)warp_smem_bytes(Pb.max_len);
         ws.ring_b = p;
         ws.ring_e = p + kD * kWarp * kRmax * 8;
         ws.sy = p + kD * kWarp * kRmax * 8 + kD * 32;
     }
-    uint8_t* sy_p = s_raw + kOwBytes + (size_t)wib * warp_smem_bytes(Pb.max_len) + kD * kWarp * kRmax * 8 + kD * 32;
-    GroupCtl* gc = (GroupCtl*)(s_raw + kOwBytes + (size_t)nwb * warp_smem_bytes(Pb.max_len)) + gib;
+    uint8_t* sy_p = s_raw + tab_end + (size_t)wib * warp_smem_bytes(Pb.max_len) + kD * kWarp * kRmax * 8 + kD * 32;
+    GroupCtl* gc = (GroupCtl*)(s_raw + tab_end + (size_t)nwb * warp_smem_bytes(Pb.max_len)) + gib;
     __syncthreads();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t gg = gw / W;
@@ -1015,7 +1028,7 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     c.capg = group_capacity(Pb.max_len, Pb.cap);
     c.stg = (int4*)(Pb.stg + gw * Pb.stg_stride) + (int64_t)lane * 2 * c.capg;
     c.st = Pb.status;
-    c.spin_limit = Pb.spin_limit > 0 ? Pb.spin_limit : kSpinLimitDefault;
+
     // boundary rows: one per strip when other warps or a later recompute read
     // them, else one row reused in place (the writer trails the reader)
     const bool bck_rows = CKPT || W > 1;
@@ -1208,6 +1221,13 @@ __global__ void __launch_bounds__(128, MINB) k_posterior_f32(Problem Pb) {
     }
     stamp_end(Pb.status->t_f32);
 }
+
+// The two occupancy variants: at most 128 registers a thread (16 warps per
+// SM, blocks of up to 8 warps), and at most 168 (12 warps per SM).
+template <bool CKPT, int W, bool LIN>
+__global__ void __launch_bounds__(256, 2) k_posterior_f32_v0(Problem Pb) { posterior_f32_body<CKPT, W, LIN>(Pb); }
+template <bool CKPT, int W, bool LIN>
+__global__ void __maxnreg__(168) k_posterior_f32_v1(Problem Pb) { posterior_f32_body<CKPT, W, LIN>(Pb); }
 
 using F32Kernel = void (*)(Problem);
 

@@ -7,11 +7,11 @@ namespace qpk {
 
 F32Kernel f32_kernel_w1(int variant, bool ckpt, bool lin) {
     if (lin) {
-        if (ckpt) return variant == 1 ? k_posterior_f32<3, true, 1, true> : k_posterior_f32<4, true, 1, true>;
-        return variant == 1 ? k_posterior_f32<3, false, 1, true> : k_posterior_f32<4, false, 1, true>;
+        if (ckpt) return variant == 1 ? k_posterior_f32_v1<true, 1, true> : k_posterior_f32_v0<true, 1, true>;
+        return variant == 1 ? k_posterior_f32_v1<false, 1, true> : k_posterior_f32_v0<false, 1, true>;
     }
-    if (ckpt) return variant == 1 ? k_posterior_f32<3, true, 1, false> : k_posterior_f32<4, true, 1, false>;
-    return variant == 1 ? k_posterior_f32<3, false, 1, false> : k_posterior_f32<4, false, 1, false>;
+    if (ckpt) return variant == 1 ? k_posterior_f32_v1<true, 1, false> : k_posterior_f32_v0<true, 1, false>;
+    return variant == 1 ? k_posterior_f32_v1<false, 1, false> : k_posterior_f32_v0<false, 1, false>;
 }
 
 }  // namespace qpk

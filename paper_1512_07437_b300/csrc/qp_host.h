@@ -75,6 +75,7 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int cons_wait_polls = 0;             // consistency staged form: waits on a stage buffer (0: default)
     int cons_stall_test = 0;             // testing: withhold the first batch's arrival (the wait runs out)
     int spin_limit = 0;                  // testing: polls of the FP32 kernel's strip waits (0: default)
+    int tab_copies = -1;                 // emission table copies (1 or kTabCopies; -1: automatic)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the

@@ -25,6 +25,11 @@ __host__ __device__ constexpr int group_capacity(int max_len, int row_cap) {
     return (max_len + 1) < kRmax * row_cap ? (max_len + 1) : kRmax * row_cap;
 }
 
+// Copies of the (odds, weight) table a block may hold in shared memory: with
+// kTabCopies copies side by side, lane l reads copy l mod kTabCopies and the
+// 8-byte lookups of a half-warp never share a bank.
+constexpr int kTabCopies = 16;
+
 // Per-call derived constants, written by k_setup on the device.
 struct Consts {
     // (odds p(a,b)/(q(a)q(b)), Boltzmann weight exp(s(a,b)/T)), indexed [y][x]
@@ -94,6 +99,11 @@ struct Coef {
     float theta;
     float wh, wp;       // combination weights
     int32_t combine;    // 0 rms-family (sqrt(wh Ph^2 + wp Pp^2)), 1 linear (wh Ph + wp Pp)
+    // FP32 kernel: bytes between table entries of consecutive row / column
+    // residue codes (8 c and 8 kTab c for c table copies), and the polls of a
+    // wait for another warp's strip (0: default)
+    uint32_t tab_x, tab_y;
+    int32_t spin_limit;
 };
 
 // One family resident on the device: inputs, plan and outputs.
@@ -157,7 +167,7 @@ struct Problem {
     int2* d_stg;  double* d_stg64; int64_t d_stg_stride;
     int32_t f64_all;               // 1: F64 form over the whole item list
     int32_t max_len;
-    int32_t spin_limit;            // polls of a wait for another warp's strip (0: default)
+    int32_t tab_copies;            // copies of the emission table in shared memory: 1, or kTabCopies
     int32_t pad_;
 };
 
@@ -173,6 +183,10 @@ cudaError_t launch_encode(const uint8_t* ascii, uint8_t* codes, int64_t n,
 constexpr int kF32Variants = 2;
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block,
                                  cudaStream_t s, int variant = 0);
+// Copies of the emission table for blocks of warps_per_block warps: kTabCopies
+// when two such blocks with that many copies fit one SM's shared memory
+// (smem_per_sm bytes) at sequence length max_len, else 1.
+int posterior_f32_tab_copies(int warps_per_block, int max_len, int smem_per_sm);
 // Scratch of the FP32 kernel for sequences up to L (elements of each buffer
 // per unit: bst / bex per group in the stored form and per warp in the
 // checkpointed form; bnd / bck per group; stg per warp), for wpp warps per pair.
@@ -232,8 +246,8 @@ cudaError_t launch_scan_nnz(const int64_t* pair_nnz, int64_t n_pairs, int64_t* p
                             cudaStream_t s);
 int posterior_f32_regs(int variant = 0, bool ckpt = false);
 int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant = 0,
-                            bool ckpt = false, int wpp = 1);
+                            bool ckpt = false, int wpp = 1, int tab_copies = 1);
 int posterior_f64_occupancy(int* blocks_per_sm);
-size_t posterior_f32_smem(int warps_per_block, int max_len);
+size_t posterior_f32_smem(int warps_per_block, int max_len, int tab_copies = 1);
 
 }  // namespace qpk

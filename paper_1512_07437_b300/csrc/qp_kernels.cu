@@ -148,13 +148,19 @@ int posterior_f32_regs(int variant, bool ckpt) {
     return e == cudaSuccess ? a.numRegs : -1;
 }
 
-size_t posterior_f32_smem(int warps_per_block, int max_len) {
-    return posterior_f32_smem_bytes(warps_per_block, max_len);
+size_t posterior_f32_smem(int warps_per_block, int max_len, int tab_copies) {
+    return posterior_f32_smem_bytes(warps_per_block, max_len, tab_copies > 1 ? kTabCopies : 1);
+}
+
+int posterior_f32_tab_copies(int warps_per_block, int max_len, int smem_per_sm) {
+    // (1 KB of every block's shared memory is reserved by the system)
+    const size_t need = 2 * (posterior_f32_smem(warps_per_block, max_len, kTabCopies) + 1024);
+    return need <= (size_t)smem_per_sm ? kTabCopies : 1;
 }
 
 int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm, int variant, bool ckpt,
-                            int wpp) {
-    const size_t smem = posterior_f32_smem(warps_per_block, max_len);
+                            int wpp, int tab_copies) {
+    const size_t smem = posterior_f32_smem(warps_per_block, max_len, tab_copies);
     const F32Kernel k = f32_kernel(variant, ckpt, wpp);
     set_smem(k, smem);
     set_smem(f32_kernel(variant, ckpt, wpp, true), smem);    // the linear-combination kernel too (no attribute
@@ -164,8 +170,12 @@ int posterior_f32_occupancy(int warps_per_block, int max_len, int* blocks_per_sm
 
 cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block, cudaStream_t s,
                                  int variant) {
-    const size_t smem = posterior_f32_smem(warps_per_block, P.max_len);
+    const size_t smem = posterior_f32_smem(warps_per_block, P.max_len, P.tab_copies);
     if (P.wpp != 1 && P.wpp != 2) return cudaErrorInvalidValue;
+    // at most 8 warps a block (the launch bounds) and 4 groups of several
+    // warps (the named barriers)
+    if (warps_per_block > 8 || warps_per_block % P.wpp || (P.wpp > 1 && warps_per_block / P.wpp > 4))
+        return cudaErrorInvalidValue;
     const F32Kernel k = f32_kernel(variant, P.ckpt != 0, P.wpp, P.cf.combine != 0);
     cudaError_t e = set_smem(k, smem);
     if (e != cudaSuccess) return e;

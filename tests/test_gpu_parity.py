@@ -452,3 +452,31 @@ def test_a_strip_wait_that_runs_out_goes_to_fp64(qp):
     _no_fallback(again)
     for p, (a, b) in enumerate(fam.pairs()):
         compare_pair(again, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32)
+
+
+@pytest.mark.parametrize("wpb,copies,wpp", [(2, 16, 1), (8, 16, 1), (8, 1, 1), (8, 16, 2), (4, 16, 2)])
+def test_table_copies_and_block_shapes_are_bit_identical(qp, wpb, copies, wpp):
+    """The bank-sliced emission table (16 copies), blocks of up to 8 warps and
+    up to 4 groups of 2 warps per block change where values come from, never
+    the values: the result equals the 2-warp-block, one-table, one-warp-per-pair
+    launch bit for bit."""
+    fams = [synth.make_family("c2", 3), synth.family_from_strings(["ACDEFGHIKLMNPQRSTVWY" * 7, "ACDEF",
+                                                                   "WYVTSRQPNMLKIHGFEDCA" * 9])]
+    prm = synth.default_params(threshold=0.01)
+    try:
+        for fam in fams:
+            qp.qp_set_option("warps_per_block", 2)
+            qp.qp_set_option("tab_copies", 1)
+            qp.qp_set_option("wpp", 1)
+            ref = _run(qp, fam, prm)
+            qp.qp_set_option("warps_per_block", wpb)
+            qp.qp_set_option("tab_copies", copies)
+            qp.qp_set_option("wpp", wpp)
+            got = _run(qp, fam, prm)
+            _no_fallback(ref)
+            _no_fallback(got)
+            _same_csr(ref, got)
+    finally:
+        qp.qp_set_option("warps_per_block", 0)
+        qp.qp_set_option("tab_copies", -1)
+        qp.qp_set_option("wpp", 0)
