@@ -271,11 +271,11 @@ unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, in
         const int v = config_variant(cfg), W = config_wpp(cfg);
         if (t.variant >= 0 && v != t.variant) continue;
         if (t.wpp > 0 && W != t.wpp) continue;
-        // W must divide the block; groups of several warps use named barriers 1, 2
+        // W must divide the block; groups of several warps use named barriers 1-4
         if (warps_per_block % W || (W > 1 && warps_per_block / W > 4)) continue;
-        // two warps per pair only while the pairs fill at most half the grid
-        // (then they shorten each pair without halving the pairs in flight)
-        if (t.wpp <= 0 && W > 1 && (max_strips < W || n_pairs * W > warps_full)) continue;
+        // two warps per pair only while the pairs leave warps idle (the spare
+        // warps then double up on the longest pairs)
+        if (t.wpp <= 0 && W > 1 && (max_strips < W || n_pairs >= warps_full)) continue;
         mask |= 1u << cfg;
     }
     return mask ? mask : 1u;
@@ -545,15 +545,13 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             }
             return b;
         };
-        // bytes of a grid of `warps` warps, w warps per pair (the stored form
-        // keeps the plan's tighter per-pair sizes)
+        // bytes of a grid of `warps` warps, w warps per pair (every buffer is
+        // per warp; the stored form keeps the plan's tighter per-pair sizes)
         auto scratch_of = [&](bool ck, int w, int64_t warps) -> int64_t {
             const qpk::F32Scratch sz(pl->max_len, cap, ck, w);
             if (ck) return (int64_t)sz.bytes(warps);
-            const int64_t groups = warps / w;
-            return groups * (int64_t)(sizeof(float2) * pl->bst_stride + sizeof(int2) * pl->bex_stride +
-                                      sizeof(float4) * (sz.bnd + sz.bck)) +
-                   warps * (int64_t)(sizeof(int2) * sz.stg);
+            return warps * (int64_t)(sizeof(float2) * pl->bst_stride + sizeof(int2) * pl->bex_stride +
+                                     sizeof(float4) * (sz.bnd + sz.bck) + sizeof(int2) * sz.stg);
         };
         // stored form unless its scratch for a full grid exceeds the budget;
         // then the checkpointed form, on a grid cut to the budget if need be
@@ -567,18 +565,26 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         cfg = C->tuner[tkey].choose(allowed);
         variant = config_variant(cfg);
         W = config_wpp(cfg);
-        grid = balanced_grid(C->sm_count, occupancy(variant, ckpt, W), (P * W + wpb - 1) / wpb);
+        // with two warps per pair, the spare warps of a launch whose pairs do
+        // not fill the grid double up on the longest pairs (items come longest
+        // first): n_big items run on two warps, the rest on one
+        int64_t n_big = 0;
+        if (W > 1) {
+            const int64_t full_w = (int64_t)C->sm_count * occupancy(variant, ckpt, W) * wpb;
+            n_big = std::max<int64_t>(0, std::min<int64_t>(P, full_w - P));
+        }
+        Pb.n_big = (int32_t)n_big;
+        grid = balanced_grid(C->sm_count, occupancy(variant, ckpt, W), (P + n_big + wpb - 1) / wpb);
         grid = std::min<int64_t>(grid, std::max<int64_t>(1, budget / std::max<int64_t>(1, scratch_of(ckpt, W, wpb))));
         grid = std::max<int64_t>(grid, 1);
-        const int64_t warps = grid * wpb, groups = warps / W;
+        const int64_t warps = grid * wpb;
         const qpk::F32Scratch sz(pl->max_len, cap, ckpt, W);
         const int64_t bst_stride = ckpt ? sz.bst : pl->bst_stride;
         const int64_t bex_stride = ckpt ? sz.bex : pl->bex_stride;
-        const int64_t units = ckpt ? warps : groups;
-        if ((e = C->bst.ensure(sizeof(float2) * bst_stride * units)) != cudaSuccess ||
-            (e = C->bex.ensure(sizeof(int2) * bex_stride * units)) != cudaSuccess ||
-            (e = C->bnd.ensure(sizeof(float4) * sz.bnd * groups)) != cudaSuccess ||
-            (e = C->bck.ensure(sizeof(float4) * sz.bck * groups)) != cudaSuccess ||
+        if ((e = C->bst.ensure(sizeof(float2) * bst_stride * warps)) != cudaSuccess ||
+            (e = C->bex.ensure(sizeof(int2) * bex_stride * warps)) != cudaSuccess ||
+            (e = C->bnd.ensure(sizeof(float4) * sz.bnd * warps)) != cudaSuccess ||
+            (e = C->bck.ensure(sizeof(float4) * sz.bck * warps)) != cudaSuccess ||
             (e = C->stg.ensure(sizeof(int2) * sz.stg * warps)) != cudaSuccess)
             return fail(QP_ENOMEM, "FP32 scratch allocation failed");
         Pb.bst = (float2*)C->bst.ptr; Pb.bst_stride = bst_stride;
@@ -617,6 +623,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             return fail(QP_ENOMEM, "FP64 scratch allocation failed");
         Pb.d_b = (double2*)C->d_b.ptr; Pb.d_b_stride = db;
         Pb.d_diag = (double*)C->d_diag.ptr; Pb.d_diag_stride = 3 * qpk::kNS * L;
+        Pb.f64_smem_diag = qpk::posterior_f64_smem_diag(pl->max_len) ? 1 : 0;
         Pb.d_cnt = (int32_t*)C->d_cnt.ptr; Pb.d_cnt_stride = 5 * L + 8;
         Pb.d_stg = (int2*)C->d_stg.ptr; Pb.d_stg64 = (double*)C->d_stg64.ptr;
         Pb.d_stg_stride = (int64_t)pl->max_len * cap;

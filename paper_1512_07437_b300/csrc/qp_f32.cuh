@@ -187,20 +187,23 @@ __device__ __forceinline__ void stage_record(int4* g, int& ng, int capg, float p
 
 // ---------------------------------------------------------------- progress words
 // Strips of one pair shared by several warps: a warp waits on the progress
-// word of the warp writing its input boundary row.
+// word of the warp writing its input boundary row.  A word holds (strip tag
+// << 32) | steps done.  What a strip waits on and publishes sits in a slot in
+// shared memory (read on the renormalisation steps only, so the sweep keeps
+// one 32-bit address for it).
+struct SyncSlot {
+    long long wait_tag;   // tag of the strip whose row bnd_in is
+    long long pub_tag;    // tag of this strip
+    unsigned wait_addr;   // shared address of the writer's progress word (0: the row is complete)
+    unsigned pub_addr;    // shared address of this warp's progress word (0: nobody waits)
+};
+
 struct StripIO {
     const float4* bnd_in;
     float4* bnd_out;
     float2* bst;
     int2* bex;
-    // the progress word of the warp writing bnd_in and the value that marks
-    // its strip (null: the row is complete), and this warp's own progress
-    // word for bnd_out (null: no reader waits on it).  A word holds
-    // (strip tag << 32) | steps done.
-    const volatile long long* wait;
-    long long wait_tag;
-    volatile long long* pub;
-    long long pub_tag;
+    unsigned sync;        // shared address of this strip's SyncSlot (0: the strip waits on nobody)
 };
 
 constexpr long long kStepsDone = 0x7fffffffLL;     // "strip complete" in a progress word
@@ -216,6 +219,17 @@ __device__ __forceinline__ void wait_progress(const volatile long long* w, long 
 __device__ __forceinline__ void publish_progress(volatile long long* w, long long v) {
     __threadfence_block();
     *w = v;
+}
+
+__device__ __forceinline__ long long lds_vol_s64(unsigned a) {
+    long long v;
+    asm volatile("ld.volatile.shared.s64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned lds_vol_u32(unsigned a) {
+    unsigned v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -272,6 +286,32 @@ __device__ __forceinline__ void wait_progress(const volatile long long* w, long 
         __nanosleep(64);
     }
     __threadfence_block();
+}
+
+// The strip's wait (warp-uniform) until its writer has done `steps` steps of
+// the strip in the slot (nothing without a slot or a writer).
+__device__ __forceinline__ void strip_wait(unsigned slot, long long steps, int& flag, int limit) {
+    if (!slot || (flag & kGuardSync)) return;
+    const unsigned wa = lds_vol_u32(slot + 16);
+    if (!wa) return;
+    const long long need = lds_vol_s64(slot) | steps;
+    if (limit <= 0) limit = kSpinLimitDefault;
+    int it = 0;
+    while (lds_vol_s64(wa) < need) {
+        if (++it > limit) { flag |= kGuardSync; return; }
+        __nanosleep(64);
+    }
+    __threadfence_block();
+}
+
+// Publishes this strip's progress (called by the lane that writes the row).
+__device__ __forceinline__ void strip_publish(unsigned slot, long long steps) {
+    if (!slot) return;
+    const unsigned pa = lds_vol_u32(slot + 20);
+    if (!pa) return;
+    const long long v = lds_vol_s64(slot + 8) | steps;
+    __threadfence_block();
+    asm volatile("st.volatile.shared.s64 [%0], %1;" ::"r"(pa), "l"(v) : "memory");
 }
 
 // ---------------------------------------------------------------- per-warp state
@@ -373,7 +413,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     // its values at column n (every lane starts there)
     int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
     // the row below is written by another warp: wait for its first columns
-    wait_progress(io.wait, io.wait_tag | (64 + kD), flag, cf.spin_limit);
+    strip_wait(io.sync, 64 + kD, flag, cf.spin_limit);
     if (bnd_in) {
         const float4 v0 = bnd_in[2 * n], v1 = bnd_in[2 * n + 1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
@@ -434,8 +474,8 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
             // the row below is written by another warp: stay 16 + kD + 32
             // steps behind it (column n - T of the row below is written at
             // the writer's step T + 31 and fetched here kD - 1 steps ahead)
-            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag, cf.spin_limit);
-            if (io.pub && lane == 0) publish_progress(io.pub, io.pub_tag | t);
+            strip_wait(io.sync, t + 16 + kD + 32, flag, cf.spin_limit);
+            if (lane == 0) strip_publish(io.sync, t);
             // renormalise: bring the lane's largest carried value into [1, 2)
             float mh = max3f(dDD.x, tV.x, tX2), mp = fmaxf(dDD.y, tV.y);
 #pragma unroll
@@ -562,7 +602,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     };
     run_steps(nsteps, t_start, t_end, step);
     cp_async_wait<0>();
-    if (io.pub && lane == 0) publish_progress(io.pub, io.pub_tag | kStepsDone);
+    if (lane == 0) strip_publish(io.sync, kStepsDone);
 }
 
 // ---------------------------------------------------------------- pass 2
@@ -613,7 +653,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
     // its values at column 0 (every lane starts there)
     int eH = 0, eP = 0, eUpH = 0, eUpP = 0;
     // the row above is written by another warp: wait for its first columns
-    wait_progress(io.wait, io.wait_tag | (64 + kD), flag, cf.spin_limit);
+    strip_wait(io.sync, 64 + kD, flag, cf.spin_limit);
     if (bnd_in) {
         const float4 v0 = bnd_in[0], v1 = bnd_in[1];
         eUpH = __float_as_int(v1.z); eUpP = __float_as_int(v1.w);
@@ -711,8 +751,8 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
             // steps behind it (column T of the row above is written at the
             // writer's step T + 31 and fetched here kD - 1 steps ahead; a
             // writer publishes its progress every kC steps)
-            wait_progress(io.wait, io.wait_tag | (t + 16 + kD + 32), flag, cf.spin_limit);
-            if (io.pub && lane == 31) publish_progress(io.pub, io.pub_tag | t);
+            strip_wait(io.sync, t + 16 + kD + 32, flag, cf.spin_limit);
+            if (lane == 31) strip_publish(io.sync, t);
             float mh = max3f(uMZ.x, lV.x, lX2), mp = fmaxf(uMZ.y, lV.y);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -864,7 +904,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
     };
     run_steps(nsteps, t_start, t_end, step);
     cp_async_wait<0>();
-    if (io.pub && lane == 31) publish_progress(io.pub, io.pub_tag | kStepsDone);
+    if (lane == 31) strip_publish(io.sync, kStepsDone);
     // ---- flush this strip's entries into the pool (row-major, columns ascending)
     if (ng > c.capg) {
         flag |= kGuardStage;
@@ -952,6 +992,7 @@ __device__ __forceinline__ void fwd_dispatch(int Rs, const Problem& Pb, unsigned
 // Control block of one group of warps working on one pair (shared memory).
 struct GroupCtl {
     long long prog[4];          // progress word of each warp of the group
+    SyncSlot slot[4];           // what each warp's current strip waits on and publishes
     int q;                      // the group's current work item
     int pad;
     float Zh, Zp;               // pass-1 totals (from the warp of strip 0)
@@ -978,7 +1019,7 @@ __device__ __forceinline__ void group_sync(int gib, int W) {
 
 __host__ __device__ constexpr size_t posterior_f32_smem_bytes(int warps_per_block, int max_len, int copies) {
     return (size_t)tab_bytes(copies) + (size_t)warps_per_block * warp_smem_bytes(max_len) +
-           (size_t)warps_per_block * sizeof(GroupCtl);
+           (size_t)2 * warps_per_block * sizeof(GroupCtl);
 }
 
 // CKPT = false (stored form): pass 1 stores (B_M, Zm_b) of every strip, pass 2
@@ -993,7 +1034,11 @@ __host__ __device__ constexpr size_t posterior_f32_smem_bytes(int warps_per_bloc
 // W warps (1 or 2; Pb.wpp) share a pair: warp w of the group takes every
 // W-th strip (pass 1 from the bottom, pass 2 from the top) and trails the warp
 // of the neighbouring strip through that strip's boundary row and its
-// progress word, so the strips of one pair run concurrently.
+// progress word, so the strips of one pair run concurrently.  With W = 2 only
+// the first Pb.n_big work items (the longest: items come longest first) are
+// shared; once a group draws a later item, its first warp runs that item alone
+// and both warps go on drawing items one warp each.  Scratch is then laid out
+// per warp (a shared item uses the region of its group's first warp).
 template <bool CKPT, int W, bool LIN>
 __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -1016,16 +1061,20 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
         ws.sy = p + kD * kWarp * kRmax * 8 + kD * 32;
     }
     uint8_t* sy_p = s_raw + tab_end + (size_t)wib * warp_smem_bytes(Pb.max_len) + kD * kWarp * kRmax * 8 + kD * 32;
+    // control blocks: one per group, and (W > 1) one per warp for items it runs alone
     GroupCtl* gc = (GroupCtl*)(s_raw + tab_end + (size_t)nwb * warp_smem_bytes(Pb.max_len)) + gib;
+    GroupCtl* gcs = W == 1 ? gc : gc - gib + nwb + wib;
     __syncthreads();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t gg = gw / W;
+    const int64_t gg0 = gw - wig;          // the first warp of the group
     PairCtx c;
-    c.bst = Pb.bst + (CKPT ? gw : gg) * Pb.bst_stride;
-    c.bex = Pb.bex + (CKPT ? gw : gg) * Pb.bex_stride;
-    c.bnd = Pb.bnd + gg * Pb.bnd_stride;
-    c.bck = Pb.bck + gg * Pb.bck_stride;
     c.capg = group_capacity(Pb.max_len, Pb.cap);
+    if (W == 1) {
+        c.bst = Pb.bst + gw * Pb.bst_stride;
+        c.bex = Pb.bex + gw * Pb.bex_stride;
+        c.bnd = Pb.bnd + gw * Pb.bnd_stride;
+        c.bck = Pb.bck + gw * Pb.bck_stride;
+    }
     c.stg = (int4*)(Pb.stg + gw * Pb.stg_stride) + (int64_t)lane * 2 * c.capg;
     c.st = Pb.status;
 
@@ -1034,14 +1083,39 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
     const bool bck_rows = CKPT || W > 1;
     const bool bnd_rows = W > 1;
     volatile long long* my_prog = W > 1 ? &gc->prog[wig] : nullptr;
+    bool solo = W == 1;                    // drawing items one warp each
     for (;;) {
-        if (lane == 0) {
-            if (my_prog) *my_prog = 0;
-            if (wig == 0) gc->q = atomicAdd(&Pb.status->work_f32, 1);
+        int q;
+        if (!solo) {
+            if (lane == 0) {
+                *my_prog = 0;
+                if (wig == 0) gc->q = atomicAdd(&Pb.status->work_f32, 1);
+            }
+            group_sync(gib, W);
+            q = *(volatile int*)&gc->q;
+            if (q >= Pb.n_work) break;
+            if (q >= Pb.n_big) {
+                // a one-warp item: the first warp runs it, then both draw alone
+                solo = true;
+                if (wig != 0) continue;
+            }
+        } else {
+            if (lane == 0) gcs->q = atomicAdd(&Pb.status->work_f32, 1);
+            __syncwarp();
+            q = *(volatile int*)&gcs->q;
+            __syncwarp();
+            if (q >= Pb.n_work) break;
         }
-        group_sync(gib, W);
-        const int q = *(volatile int*)&gc->q;
-        if (q >= Pb.n_work) break;
+        // warps on this item and this warp's place among them
+        const int nw = solo ? 1 : W;
+        const int wg = solo ? 0 : wig;
+        if (W > 1) {
+            const int64_t unit = solo ? gw : gg0;
+            c.bst = Pb.bst + (CKPT ? gw : unit) * Pb.bst_stride;
+            c.bex = Pb.bex + (CKPT ? gw : unit) * Pb.bex_stride;
+            c.bnd = Pb.bnd + unit * Pb.bnd_stride;
+            c.bck = Pb.bck + unit * Pb.bck_stride;
+        }
         const int2 it = Pb.items[q];
         const FamDesc& fd = Pb.fams[it.x];
         const int p = it.y;
@@ -1065,25 +1139,29 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
         }
         __syncwarp();
         int flag = 0;
-        // ---- pass 1: backward, bottom strip first (strip s: warp (ns-1-s) % W)
+        // ---- pass 1: backward, bottom strip first (strip s: warp (ns-1-s) % nw)
         float Zh = 0.f, Zp = 0.f;
         int eZh = 0, eZp = 0;
         const int64_t strip_vals = (int64_t)kStripRows * (n + 32), strip_exps = (int64_t)c.nch * 32;
         const int64_t row_len = 2 * (int64_t)(n + 1);
-        for (int s = nstrips - 1 - wig, seq = 0; s >= 0; s -= W, ++seq) {
+        for (int s = nstrips - 1 - wg, seq = 0; s >= 0; s -= nw, ++seq) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = rows_per_lane(rows_in);
             StripIO io;
             io.bnd_in = (s == nstrips - 1) ? nullptr : c.bck + (bck_rows ? (s + 1) * row_len : 0);
             io.bnd_out = (s == 0) ? nullptr : c.bck + (bck_rows ? s * row_len : 0);
-            io.wait = nullptr; io.pub = nullptr; io.wait_tag = io.pub_tag = 0;
-            if (W > 1) {
-                if (s < nstrips - 1) {
+            io.sync = 0;
+            if (nw > 1) {
+                SyncSlot* sl = &gc->slot[wg];
+                if (lane == 0) {
                     const int ps = nstrips - 2 - s;          // order of strip s + 1 in pass 1
-                    io.wait = &gc->prog[ps % W];
-                    io.wait_tag = (long long)(ps / W + 1) << 32;
+                    sl->wait_addr = s < nstrips - 1 ? smem_u32(&gc->prog[ps % nw]) : 0u;
+                    sl->wait_tag = (long long)(ps / nw + 1) << 32;
+                    sl->pub_addr = s > 0 ? smem_u32((const void*)my_prog) : 0u;
+                    sl->pub_tag = (long long)(seq + 1) << 32;
                 }
-                if (s > 0) { io.pub = my_prog; io.pub_tag = (long long)(seq + 1) << 32; }
+                __syncwarp();
+                io.sync = smem_u32(sl);
             }
             if (CKPT) {
                 io.bst = nullptr;
@@ -1097,12 +1175,14 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
             __syncwarp();
         }
         // the totals come from strip 0 (lane 0 of its warp)
-        if (wig == (nstrips - 1) % W && lane == 0) {
-            gc->Zh = Zh; gc->Zp = Zp; gc->eZh = eZh; gc->eZp = eZp;
+        GroupCtl* cb = nw > 1 ? gc : gcs;
+        if (wg == (nstrips - 1) % nw && lane == 0) {
+            cb->Zh = Zh; cb->Zp = Zp; cb->eZh = eZh; cb->eZp = eZp;
         }
-        group_sync(gib, W);
-        Zh = *(volatile float*)&gc->Zh; Zp = *(volatile float*)&gc->Zp;
-        eZh = *(volatile int*)&gc->eZh; eZp = *(volatile int*)&gc->eZp;
+        if (nw > 1) group_sync(gib, W);
+        else __syncwarp();
+        Zh = *(volatile float*)&cb->Zh; Zp = *(volatile float*)&cb->Zp;
+        eZh = *(volatile int*)&cb->eZh; eZp = *(volatile int*)&cb->eZp;
         // normalise the totals to [1, 2) * 2^e
         if (!(Zh > 0.f) || !(Zp > 0.f) || !(Zh < kBig) || !(Zp < kBig)) flag |= kGuardTotal;
         {
@@ -1117,7 +1197,7 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
         const float2 zfac = LIN ? make_float2(Pb.cf.wh / Zh, Pb.cf.wp / Zp)
                                 : make_float2(sqrtf(Pb.cf.wh) / Zh, sqrtf(Pb.cf.wp) / Zp);
         // ---- pass 2: forward + posterior + threshold + MEA, top strip first
-        // (strip s: warp s % W)
+        // (strip s: warp s % nw)
         const int mn = min(m, n);
         int sA = 30 - (32 - __clz(mn + 1));
         if (sA > 21) sA = 21;
@@ -1125,19 +1205,23 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
         float pmax = 0.f;
         FwdOut fo{0.f, 0.f, 0, 0, 0};
         int64_t pair_tot = 0;
-        for (int s = wig, seq = 0; s < nstrips; s += W, ++seq) {
+        for (int s = wg, seq = 0; s < nstrips; s += nw, ++seq) {
             const int rows_in = min(kStripRows, m + 1 - s * kStripRows);
             const int Rs = rows_per_lane(rows_in);
             StripIO io;
             io.bnd_in = (s == 0) ? nullptr : c.bnd + (bnd_rows ? (s - 1) * row_len : 0);
             io.bnd_out = (s == nstrips - 1) ? nullptr : c.bnd + (bnd_rows ? s * row_len : 0);
-            io.wait = nullptr; io.pub = nullptr; io.wait_tag = io.pub_tag = 0;
-            if (W > 1) {
-                if (s > 0) {
-                    io.wait = &gc->prog[(s - 1) % W];
-                    io.wait_tag = (kPass2Tag + (s - 1) / W + 1) << 32;
+            io.sync = 0;
+            if (nw > 1) {
+                SyncSlot* sl = &gc->slot[wg];
+                if (lane == 0) {
+                    sl->wait_addr = s > 0 ? smem_u32(&gc->prog[(s - 1) % nw]) : 0u;
+                    sl->wait_tag = (kPass2Tag + (s - 1) / nw + 1) << 32;
+                    sl->pub_addr = s < nstrips - 1 ? smem_u32((const void*)my_prog) : 0u;
+                    sl->pub_tag = (kPass2Tag + seq + 1) << 32;
                 }
-                if (s < nstrips - 1) { io.pub = my_prog; io.pub_tag = (kPass2Tag + seq + 1) << 32; }
+                __syncwarp();
+                io.sync = smem_u32(sl);
             }
             if (CKPT) {
                 // the strip's backward values again, from its checkpoint row
@@ -1146,7 +1230,7 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
                 bio.bnd_out = nullptr;
                 bio.bst = c.bst;
                 bio.bex = c.bex;
-                bio.wait = nullptr; bio.pub = nullptr; bio.wait_tag = bio.pub_tag = 0;
+                bio.sync = 0;
                 float dZh = 0.f, dZp = 0.f;
                 int deZh = 0, deZp = 0;
                 bwd_dispatch<true>(Rs, Pb.cf, s_ow, c, ws, s, nstrips, bio, dZh, dZp, deZh, deZp, flag);
@@ -1161,33 +1245,40 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
                               pair_tot, flag);
             __syncwarp();
         }
-        // ---- pair results: partial values of every warp of the group
-        if (wig == (nstrips - 1) % W) {
+        // ---- pair results: partial values of every warp on the item
+        float fZh = 0.f, fZp = 0.f;
+        int feh = 0, fep = 0, Aend = 0;
+        if (wg == (nstrips - 1) % nw) {
             // corner values, held by the lane that owns row m
             const int lastRs = rows_per_lane(min(kStripRows, m + 1 - (nstrips - 1) * kStripRows));
             const int Lend = (m - (nstrips - 1) * kStripRows) / lastRs;
-            const float fZh = __shfl_sync(kFull, fo.Zh, Lend), fZp = __shfl_sync(kFull, fo.Zp, Lend);
-            const int feh = __shfl_sync(kFull, fo.eZh, Lend), fep = __shfl_sync(kFull, fo.eZp, Lend);
-            const int Aend = __shfl_sync(kFull, fo.A, Lend);
-            if (lane == 0) { gc->fZh = fZh; gc->fZp = fZp; gc->feh = feh; gc->fep = fep; gc->fA = Aend; }
+            fZh = __shfl_sync(kFull, fo.Zh, Lend); fZp = __shfl_sync(kFull, fo.Zp, Lend);
+            feh = __shfl_sync(kFull, fo.eZh, Lend); fep = __shfl_sync(kFull, fo.eZp, Lend);
+            Aend = __shfl_sync(kFull, fo.A, Lend);
+            if (nw > 1 && lane == 0) { gc->fZh = fZh; gc->fZp = fZp; gc->feh = feh; gc->fep = fep; gc->fA = Aend; }
         }
         for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(kFull, pmax, o));
         flag = __reduce_or_sync(kFull, flag);
-        if (lane == 0) { gc->flag[wig] = flag; gc->pmax[wig] = pmax; gc->tot[wig] = pair_tot; }
-        group_sync(gib, W);
-        if (wig == 0 && lane == 0) {
-            int fl = 0;
-            float pm = 0.f;
-            int64_t tot = 0;
-            for (int w = 0; w < W; ++w) {
-                fl |= ((volatile int*)gc->flag)[w];
-                pm = fmaxf(pm, ((volatile float*)gc->pmax)[w]);
-                tot += ((volatile long long*)gc->tot)[w];
+        int fl = flag;
+        float pm = pmax;
+        int64_t tot = pair_tot;
+        if (nw > 1) {
+            if (lane == 0) { gc->flag[wg] = flag; gc->pmax[wg] = pmax; gc->tot[wg] = pair_tot; }
+            group_sync(gib, W);
+            if (wg == 0 && lane == 0) {
+                fl = 0; pm = 0.f; tot = 0;
+                for (int w = 0; w < nw; ++w) {
+                    fl |= ((volatile int*)gc->flag)[w];
+                    pm = fmaxf(pm, ((volatile float*)gc->pmax)[w]);
+                    tot += ((volatile long long*)gc->tot)[w];
+                }
+                fZh = *(volatile float*)&gc->fZh; fZp = *(volatile float*)&gc->fZp;
+                feh = *(volatile int*)&gc->feh; fep = *(volatile int*)&gc->fep;
+                Aend = *(volatile int*)&gc->fA;
             }
+        }
+        if (wg == 0 && lane == 0) {
             if (pm > 1.001f) fl |= kGuardPost;
-            const float fZh = *(volatile float*)&gc->fZh, fZp = *(volatile float*)&gc->fZp;
-            const int feh = *(volatile int*)&gc->feh, fep = *(volatile int*)&gc->fep;
-            const int Aend = *(volatile int*)&gc->fA;
             const double ln2 = 0.69314718055994530942;
             const double lzb_h = log((double)Zh) + (double)eZh * ln2;
             const double lzb_p = log((double)Zp) + (double)eZp * ln2;
@@ -1217,7 +1308,8 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
                 if (fd.n_done) { __threadfence(); atomicAdd(fd.n_done, 1); }
             }
         }
-        group_sync(gib, W);
+        if (nw > 1) group_sync(gib, W);
+        else __syncwarp();
     }
     stamp_end(Pb.status->t_f32);
 }

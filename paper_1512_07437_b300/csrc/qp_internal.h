@@ -152,11 +152,11 @@ struct Problem {
     int2* bex;    int64_t bex_stride;      // backward exponents per chunk
     float4* bnd;  int64_t bnd_stride;      // strip boundary rows (2 float4 / column)
     int2* stg;    int64_t stg_stride;      // staging records: 32 lanes x group_capacity x 32 bytes a warp
-    // backward boundary rows (bck) and forward ones (bnd), per group of warps
-    // sharing a pair: one row per strip when other warps or a recompute read
-    // them (checkpointed form, wpp > 1), else one row.  bst / bex: per group
-    // (stored form: every strip of the pair) or per warp (checkpointed form:
-    // one strip).
+    // backward boundary rows (bck) and forward ones (bnd), per warp: one row
+    // per strip when other warps or a recompute read them (checkpointed form,
+    // wpp > 1), else one row.  bst / bex per warp: every strip of the pair
+    // (stored form) or one strip (checkpointed form).  An item shared by a
+    // group uses the buffers of the group's first warp.
     float4* bck;  int64_t bck_stride;
     int32_t ckpt;
     int32_t wpp;                   // warps per pair: 1, or 2 with at most 2 groups per block
@@ -166,9 +166,10 @@ struct Problem {
     int32_t* d_cnt; int64_t d_cnt_stride;  // per-row entry counts and exponents
     int2* d_stg;  double* d_stg64; int64_t d_stg_stride;
     int32_t f64_all;               // 1: F64 form over the whole item list
+    int32_t f64_smem_diag;         // 1: the FP64 form's rotating diagonals in shared memory (else d_diag)
     int32_t max_len;
     int32_t tab_copies;            // copies of the emission table in shared memory: 1, or kTabCopies
-    int32_t pad_;
+    int32_t n_big;                 // wpp = 2: items [0, n_big) are shared by the two warps of a group
 };
 
 // launch wrappers (qp_kernels.cu)
@@ -188,8 +189,7 @@ cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block
 // (smem_per_sm bytes) at sequence length max_len, else 1.
 int posterior_f32_tab_copies(int warps_per_block, int max_len, int smem_per_sm);
 // Scratch of the FP32 kernel for sequences up to L (elements of each buffer
-// per unit: bst / bex per group in the stored form and per warp in the
-// checkpointed form; bnd / bck per group; stg per warp), for wpp warps per pair.
+// per warp), for wpp warps per pair.
 struct F32Scratch {
     int64_t bst, bex, bnd, bck, stg;
     bool ckpt;
@@ -208,15 +208,18 @@ struct F32Scratch {
         bnd = (wpp > 1 ? ns : 1) * row;
         bck = (ckpt || wpp > 1 ? ns : 1) * row;
         stg = (int64_t)kWarp * 4 * group_capacity(L, cap);
+        // (with wpp > 1 every buffer is per warp: a warp may run an item alone)
     }
     // bytes for a grid of `warps` warps
     size_t bytes(int64_t warps) const {
-        const int64_t groups = warps / wpp, units = ckpt ? warps : groups;
-        return (size_t)units * (sizeof(float2) * bst + sizeof(int2) * bex) +
-               (size_t)groups * sizeof(float4) * (bnd + bck) + (size_t)warps * sizeof(int2) * stg;
+        return (size_t)warps * (sizeof(float2) * bst + sizeof(int2) * bex + sizeof(float4) * (bnd + bck) +
+                                sizeof(int2) * stg);
     }
 };
 cudaError_t launch_posterior_f64(const Problem& P, int grid, cudaStream_t s);
+// Whether the FP64 form keeps its rotating diagonals (3 x kNS x (L + 1)
+// doubles) in shared memory at sequence length max_len.
+bool posterior_f64_smem_diag(int max_len);
 cudaError_t launch_compact(const int2* pairs, const int64_t* seq_off,
                            const int64_t* pair_row_off, const int64_t* pair_strip_off,
                            const int32_t* row_cnt, const int64_t* chunk_off, const int2* pool,

@@ -224,9 +224,11 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
     __shared__ int s_q;
     __shared__ unsigned long long s_base;
     const Consts* __restrict__ C = Pb.cst;
+    extern __shared__ double s_diag[];
     const int tid = threadIdx.x, nt = blockDim.x;
     double2* Bd = Pb.d_b + (int64_t)blockIdx.x * Pb.d_b_stride;
-    double* dg = Pb.d_diag + (int64_t)blockIdx.x * Pb.d_diag_stride;
+    // the three rotating diagonals: shared memory when they fit, else global
+    double* dg = Pb.f64_smem_diag ? s_diag : Pb.d_diag + (int64_t)blockIdx.x * Pb.d_diag_stride;
     int32_t* rc = Pb.d_cnt + (int64_t)blockIdx.x * Pb.d_cnt_stride;
     int2* stg = Pb.d_stg + (int64_t)blockIdx.x * Pb.d_stg_stride;
     double* stg64 = Pb.d_stg64 + (int64_t)blockIdx.x * Pb.d_stg_stride;
@@ -327,11 +329,15 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
         int feh = 0, fep = 0;
         const double theta = C->thetad;
         const int comb = C->combine;
+        const double invZh = 1.0 / Zh, invZp = 1.0 / Zp;
         for (int d = 0; d <= m + n; ++d) {
             const int ilo = max(0, d - n), ihi = min(m, d);
             double* cur[9];
             for (int v = 0; v < 9; ++v) cur[v] = slot(d, v);
             const double f2 = pow2d(Fh2 - Fh1), g2 = pow2d(Fp2 - Fp1);
+            // posterior factors of the diagonal: F in units of the previous
+            // diagonal, B in units of its diagonal, over the totals
+            const double sph = ldexp(invZh, Fh1 + EB[d] - eZh), spp = ldexp(invZp, Fp1 + EP[d] - eZp);
             double mh = 0.0, mp = 0.0;
             // the thread for row i is fixed: i = tid (mod nt)
             const int i0 = ilo + ((tid - ilo) % nt + nt) % nt;
@@ -352,9 +358,8 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
                 double A = 0.0;
                 if (i >= 1 && j >= 1) {
                     const double2 b = Bd[(int64_t)i * (n + 1) + j];
-                    // F in units of the previous diagonal, B in units of its diagonal
-                    const double ph = ldexp(FM * b.x / Zh, Fh1 + EB[d] - eZh);
-                    const double pp = ldexp(ZM * b.y / Zp, Fp1 + EP[d] - eZp);
+                    const double ph = FM * b.x * sph;
+                    const double pp = ZM * b.y * spp;
                     double P;
                     if (comb == 0) P = sqrt(0.5 * (ph * ph + pp * pp));
                     else if (comb == 1) P = 0.5 * (ph + pp);
@@ -476,13 +481,26 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
     stamp_end(Pb.status->t_f64);
 }
 
+// Shared memory the FP64 form may use for its diagonals: two CTAs per SM.
+constexpr size_t kF64DiagSmem = 100 * 1024;
+
+static size_t f64_diag_bytes(int max_len) { return sizeof(double) * 3 * kNS * (size_t)(max_len + 1); }
+
+bool posterior_f64_smem_diag(int max_len) { return f64_diag_bytes(max_len) <= kF64DiagSmem; }
+
 int posterior_f64_occupancy(int* blocks_per_sm) {
+    // the attribute is raised once, before any launch (none inside a capture)
+    cudaError_t e = cudaFuncSetAttribute(k_posterior_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kF64DiagSmem);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_posterior_f64,
-                                                              kF64Threads, 0);
+                                                              kF64Threads, kF64DiagSmem);
 }
 
 cudaError_t launch_posterior_f64(const Problem& P, int grid, cudaStream_t s) {
-    k_posterior_f64<<<grid, kF64Threads, 0, s>>>(P);
+    const size_t smem = P.f64_smem_diag ? f64_diag_bytes(P.max_len) : 0;
+    if (smem > kF64DiagSmem) return cudaErrorInvalidValue;
+    k_posterior_f64<<<grid, kF64Threads, smem, s>>>(P);
     return cudaGetLastError();
 }
 

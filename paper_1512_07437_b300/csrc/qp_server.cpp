@@ -230,15 +230,14 @@ int set_scratch(qp_server* S, int L) {
     int cap = 0;
     bool ckpt = false;
     const size_t bytes = scratch_bytes_for(S, L, &warps, S->bps, &cap, &ckpt);
-    // room for one warp per pair (a group is a warp) and for two
+    // room for one warp per pair and for two (every buffer per warp)
     const qpk::F32Scratch s1(L, cap, ckpt, 1), s2(L, cap, ckpt, 2);
     const int64_t L1 = L + 1;
-    const int64_t u1 = warps, u2 = ckpt ? warps : warps / 2;
     struct A { void** p; size_t b; } al[] = {
-        {&S->bst, sizeof(float2) * (size_t)std::max(s1.bst * u1, s2.bst * u2)},
-        {&S->bex, sizeof(int2) * (size_t)std::max(s1.bex * u1, s2.bex * u2)},
-        {&S->bnd, sizeof(float4) * (size_t)std::max(s1.bnd * warps, s2.bnd * (warps / 2))},
-        {&S->bck, sizeof(float4) * (size_t)std::max(s1.bck * warps, s2.bck * (warps / 2))},
+        {&S->bst, sizeof(float2) * (size_t)std::max(s1.bst, s2.bst) * (size_t)warps},
+        {&S->bex, sizeof(int2) * (size_t)std::max(s1.bex, s2.bex) * (size_t)warps},
+        {&S->bnd, sizeof(float4) * (size_t)std::max(s1.bnd, s2.bnd) * (size_t)warps},
+        {&S->bck, sizeof(float4) * (size_t)std::max(s1.bck, s2.bck) * (size_t)warps},
         {&S->stg, sizeof(int2) * (size_t)s1.stg * warps},
         {&S->d_b, sizeof(double2) * (size_t)(L1 * L1) * kF64Grid},
         {&S->d_diag, sizeof(double) * (size_t)(3 * qpk::kNS * L1) * kF64Grid},
@@ -263,7 +262,7 @@ int set_scratch(qp_server* S, int L) {
     return QP_OK;
 }
 
-qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items, int wpp = 1) {
+qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items, int wpp = 1, int64_t n_big = 0) {
     qpk::Problem Pb;
     memset(&Pb, 0, sizeof Pb);
     Pb.cf = S->cf;
@@ -285,9 +284,11 @@ qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items, int wpp = 1) 
     Pb.bck = (float4*)S->bck; Pb.bck_stride = sz.bck;
     Pb.ckpt = S->ckpt ? 1 : 0;
     Pb.wpp = wpp;
+    Pb.n_big = (int32_t)n_big;
     Pb.stg = (int2*)S->stg;   Pb.stg_stride = sz.stg;
     Pb.d_b = (double2*)S->d_b; Pb.d_b_stride = L1 * L1;
     Pb.d_diag = (double*)S->d_diag; Pb.d_diag_stride = 3 * qpk::kNS * L1;
+    Pb.f64_smem_diag = qpk::posterior_f64_smem_diag(L) ? 1 : 0;
     Pb.d_cnt = (int32_t*)S->d_cnt; Pb.d_cnt_stride = 5 * L1 + 8;
     Pb.d_stg = (int2*)S->d_stg; Pb.d_stg64 = (double*)S->d_stg64;
     Pb.d_stg_stride = (int64_t)L * S->cap;
@@ -577,9 +578,13 @@ bool issue(qp_server* S) {
     int bps = 0;
     qpk::posterior_f32_occupancy(kWpb, S->scratch_len, &bps, R.variant, S->ckpt, W);
     bps = std::max(1, std::min(bps, S->bps[R.variant]));
-    int64_t grid = balanced_grid(S->ctx->sm_count, bps, ((int64_t)n_items * W + kWpb - 1) / kWpb);
+    // two warps per pair: the spare warps double up on the longest items
+    // (items come longest first), the rest run on one warp each
+    const int64_t full_w = std::min<int64_t>((int64_t)S->ctx->sm_count * bps * kWpb, S->scratch_warps);
+    const int64_t n_big = W > 1 ? std::max<int64_t>(0, std::min<int64_t>(n_items, full_w - n_items)) : 0;
+    int64_t grid = balanced_grid(S->ctx->sm_count, bps, ((int64_t)n_items + n_big + kWpb - 1) / kWpb);
     grid = std::min<int64_t>(grid, S->scratch_warps / kWpb);
-    const qpk::Problem Pb = base_problem(S, R, n_items, W);
+    const qpk::Problem Pb = base_problem(S, R, n_items, W, n_big);
     cudaEventRecord(R.ev0, S->cs);
     if ((e = qpk::launch_posterior_f32(Pb, (int)grid, kWpb, S->cs, R.variant)) != cudaSuccess) {
         fail_all(S, cuda_fail(e, "k_posterior_f32 launch"), last_error());
