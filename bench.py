@@ -85,7 +85,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="headline only (no c2/c5/serving/stage legs)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--subset", default="", metavar="K:MAXLEN",
+                    help="profiling: only the first K sequences of length <= MAXLEN of the family")
+    ap.add_argument("--variant", type=int, default=-1, help="profiling: force the kernel's register variant")
+    ap.add_argument("--wpp", type=int, default=0, help="profiling: force the warps per pair (1 or 2)")
     return ap.parse_args()
+
+
+def subset_family(fam, spec: str):
+    """The first K sequences of length <= MAXLEN of a family (spec "K:MAXLEN"),
+    a reduced workload of the same family for profiler captures."""
+    k, maxlen = (int(v) for v in spec.split(":"))
+    keep = [a for a in range(fam.k) if fam.lengths[a] <= maxlen][:k]
+    return synth.family_from_strings([fam.seq(a) for a in keep], name=f"{fam.name}-subset")
 
 
 def dist_env():
@@ -631,8 +643,13 @@ def main():
     from paper_1512_07437_b300 import dist as qd
     # every rank works on its own family of the configuration (weak scaling)
     fam = synth.make_family(args.config, qd.rank_seed(args.seed, rank))
+    if args.subset:
+        fam = subset_family(fam, args.subset)
     prm = synth.default_params(threshold=0.01, precision=args.precision)
     config = config_of(args, fam, prm)
+    if args.subset:
+        config["workload"] += f"; profiling subset {args.subset} ({fam.k} sequences)"
+        config["pairs"], config["cells_per_step"] = fam.n_pairs, fam.cells()
     if args.impl == "reference":
         return run_reference(args, fam, prm, rank, config)
 
@@ -648,6 +665,10 @@ def main():
     params = qp.make_params(prm, device=local, stream=stream)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = measured_peaks()
+    if args.variant >= 0:
+        qp.qp_set_option("variant", args.variant, device=local)
+    if args.wpp > 0:
+        qp.qp_set_option("wpp", args.wpp, device=local)
 
     def step_dev():
         return qp.qp_posteriors(d_res, fam.offsets, params, out_on_device=True)
@@ -741,7 +762,7 @@ def main():
         "graph_calls_in_timed_region": graph_calls,
         "clocks": clocks,
     }
-    traffic = recorded_traffic(f"{args.config}-{args.precision}")
+    traffic = None if args.subset else recorded_traffic(f"{args.config}-{args.precision}")
     if args.precision == "f32":
         line["roofline"] = {**posterior_roofline(cells, kernel_ms, sm_count, max_mhz, traffic),
                             "kernel": "k_posterior_f32", "kernel_ms": kernel_ms,
