@@ -89,6 +89,8 @@ def parse():
                     help="profiling: only the first K sequences of length <= MAXLEN of the family")
     ap.add_argument("--variant", type=int, default=-1, help="profiling: force the kernel's register variant")
     ap.add_argument("--wpp", type=int, default=0, help="profiling: force the warps per pair (1 or 2)")
+    ap.add_argument("--wpb", type=int, default=0,
+                    help="profiling: force the block layout (2: one emission table, 8: 16 bank-sliced copies)")
     return ap.parse_args()
 
 
@@ -562,6 +564,12 @@ def event_kernel_ms(qp, step, local, flush, ki, n):
     return out
 
 
+def launch_config(qp, local):
+    """The FP32 kernel's launch configuration the autotuner settled on."""
+    return {k: qp.qp_get_counter(f"f32_{k}", device=local)
+            for k in ("variant", "wpp", "warps_per_block", "tab_copies")}
+
+
 def family_leg(qp, torch, fam, prm, local, stream, flush, steps, warmup, sm_count, max_mhz, key):
     """The stage on one family, device-resident, with its roofline."""
     dev = torch.device("cuda", local)
@@ -587,7 +595,8 @@ def family_leg(qp, torch, fam, prm, local, stream, flush, steps, warmup, sm_coun
     if prm.precision == "f32":
         out["roofline"] = {**posterior_roofline(fam.cells(), kernel_ms, sm_count, max_mhz,
                                                 recorded_traffic(f"{key}-f32")),
-                           "kernel": "k_posterior_f32", "kernel_ms": kernel_ms}
+                           "kernel": "k_posterior_f32", "kernel_ms": kernel_ms,
+                           "launch": launch_config(qp, local)}
     del d_res
     return out
 
@@ -669,12 +678,17 @@ def main():
         qp.qp_set_option("variant", args.variant, device=local)
     if args.wpp > 0:
         qp.qp_set_option("wpp", args.wpp, device=local)
+    if args.wpb > 0:
+        qp.qp_set_option("warps_per_block", args.wpb, device=local)
+        qp.qp_set_option("tab_copies", 16 if args.wpb >= 8 else 1, device=local)
 
     def step_dev():
         return qp.qp_posteriors(d_res, fam.offsets, params, out_on_device=True)
 
     ki = 0 if args.precision == "f32" else 1     # kernel_ms index of the posterior kernel
-    warmup = max(5, args.warmup)          # (the autotuner samples its configurations on the first calls)
+    # (the autotuner samples up to four launch configurations twice each on
+    # the first calls of a launch shape: the warm-up covers them)
+    warmup = max(9, args.warmup)
     for _ in range(warmup):
         step_dev().free()
     torch.cuda.synchronize()
@@ -766,6 +780,7 @@ def main():
     if args.precision == "f32":
         line["roofline"] = {**posterior_roofline(cells, kernel_ms, sm_count, max_mhz, traffic),
                             "kernel": "k_posterior_f32", "kernel_ms": kernel_ms,
+                            "launch": launch_config(qp, local),
                             "kernel_ms_timed_region": statistics.mean(k[ki] for k in kms),
                             "kernel_timing": "CUDA events around the kernel (plain launches); "
                                              "kernel_ms_timed_region: the kernel's own time stamps in "

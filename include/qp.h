@@ -307,8 +307,11 @@ void qp_server_destroy(qp_server* server);
  *                     tries 2 when pairs are too few to fill the grid;
  *   "graph"           1 (default): run each call as one captured CUDA graph;
  *                     0: plain launches;
- *   "blocks_per_sm", "warps_per_block" (default for qp_posteriors: 8 for
- *                     launches of several waves, else 2; 4 in a server);
+ *   "blocks_per_sm", "warps_per_block" (qp_posteriors: by default the
+ *                     autotuner picks blocks of 2 warps with one emission
+ *                     table, or, for launches that fill the grid, blocks of
+ *                     8 warps with 16 table copies; setting this or
+ *                     "tab_copies" fixes the layout; 4 in a server);
  *   "scratch_bytes"   device bytes the kernels' scratch may take (default:
  *                     45% of free memory, at most 48 GiB); the stored form is
  *                     chosen while it fits a full grid, else the checkpointed
@@ -346,8 +349,8 @@ void qp_server_destroy(qp_server* server);
  *   "tab_copies"      copies of the emission table each block keeps in
  *                     shared memory: 16 (bank-sliced: lane l reads copy
  *                     l mod 16, so a half-warp's lookups never share a bank;
- *                     56 KB) or 1; -1 automatic (16 with blocks of 8 warps
- *                     when two such blocks fit an SM, else 1).  Results are
+ *                     56 KB) or 1; -1 automatic (chosen with the block
+ *                     layout, see "warps_per_block").  Results are
  *                     identical either way;
  *   "spin_limit"      testing only: polls (each about 64 ns of sleep) of a
  *                     warp waiting for the other warp of its pair (wpp = 2)
@@ -366,8 +369,10 @@ int qp_set_option(int32_t device, const char* name, int64_t value);
  * was), "plain_calls" (calls with plain launches), "pool_retries" (calls run again because their entries
  * overflowed the entry pool), "consistency_fma" (multiply-adds of the last
  * qp_consistency relaxation), "consistency_form" (form of the last
- * qp_consistency relaxation: 1 staged, 0 row form).  QP_EINVAL for an unknown
- * name or device. */
+ * qp_consistency relaxation: 1 staged, 0 row form), "f32_variant",
+ * "f32_wpp", "f32_warps_per_block", "f32_tab_copies" (launch configuration
+ * of the last qp_posteriors call's FP32 kernel; -1 before the first).
+ * QP_EINVAL for an unknown name or device. */
 int qp_get_counter(int32_t device, const char* name, int64_t* value);
 
 /* Allocation-free variant for callers that cannot allocate device memory.

@@ -265,12 +265,13 @@ int64_t balanced_grid(int sm_count, int blocks_per_sm, int64_t blocks_needed) {
 }
 
 unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, int warps_per_block,
-                         const LaunchOverride& t) {
+                         const LaunchOverride& t, bool wide_layout) {
     unsigned mask = 0;
     for (int cfg = 0; cfg < kTuneConfigs; ++cfg) {
-        const int v = config_variant(cfg), W = config_wpp(cfg);
+        const int v = config_variant(cfg), W = config_wpp(cfg), lay = config_layout(cfg);
         if (t.variant >= 0 && v != t.variant) continue;
         if (t.wpp > 0 && W != t.wpp) continue;
+        if (lay == 1 && (!wide_layout || W > 1)) continue;
         // W must divide the block; groups of several warps use named barriers 1-4
         if (warps_per_block % W || (W > 1 && warps_per_block / W > 4)) continue;
         // two warps per pair only while the pairs leave warps idle (the spare
@@ -502,22 +503,25 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     }
 
     // ---- launch configuration of the FP32 kernel
-    // Launches of several waves: blocks of 8 warps holding the bank-sliced
-    // emission table (kTabCopies copies: conflict-free lookups) when two such
-    // blocks fit an SM's shared memory.  Otherwise blocks of 2 warps with one
-    // table: finer placement over the SMs (a few per cent better when the
-    // pairs fill the grid about once).
-    int wpb = C->tune.warps_per_block;
+    // The autotuner picks the register variant, the warps per pair and the
+    // block layout: blocks of 2 warps with one emission table (finer
+    // placement over the SMs), or, for launches that fill the grid when two
+    // such blocks fit an SM, blocks of 8 warps holding the bank-sliced table
+    // (kTabCopies copies: conflict-free lookups).  The launch knobs
+    // warps_per_block and tab_copies fix the layout instead.
+    const bool layout_forced = C->tune.warps_per_block > 0 || C->tune.tab_copies >= 0;
+    int wpb = 2;
     int copies = 1;
-    if (!f64) {
-        const bool big = P >= (int64_t)4 * 16 * C->sm_count;
-        if (wpb <= 0) wpb = big ? 8 : 2;
-        copies = C->tune.tab_copies >= 0 ? C->tune.tab_copies
-                                         : (wpb >= 8 ? qpk::posterior_f32_tab_copies(wpb, pl->max_len, C->smem_per_sm)
-                                                     : 1);
-        if (copies <= 1 && C->tune.warps_per_block <= 0) wpb = 2;
-    }
-    if (wpb <= 0) wpb = 2;
+    auto set_layout = [&](int lay) {
+        if (layout_forced) {
+            wpb = C->tune.warps_per_block > 0 ? C->tune.warps_per_block : 2;
+            copies = C->tune.tab_copies >= 0 ? C->tune.tab_copies : 1;
+        } else {
+            wpb = lay == 1 ? 8 : 2;
+            copies = lay == 1 ? qpk::kTabCopies : 1;
+        }
+    };
+    set_layout(0);
     int variant = 0, cfg = 0, W = 1;
     bool ckpt = false;
     int64_t grid = 1, tkey = 0;
@@ -533,9 +537,12 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     Pb.fallback = (int2*)C->fallback.ptr;
     Pb.max_len = pl->max_len;
     Pb.cf.spin_limit = C->tune.spin_limit;
-    Pb.tab_copies = copies > 1 ? qpk::kTabCopies : 1;
-    Pb.cf.tab_x = 8u * (uint32_t)Pb.tab_copies;
-    Pb.cf.tab_y = 8u * (uint32_t)(qpk::kTab * Pb.tab_copies);
+    auto set_tables = [&]() {
+        Pb.tab_copies = copies > 1 ? qpk::kTabCopies : 1;
+        Pb.cf.tab_x = 8u * (uint32_t)Pb.tab_copies;
+        Pb.cf.tab_y = 8u * (uint32_t)(qpk::kTab * Pb.tab_copies);
+    };
+    set_tables();
     if (!f64) {
         auto occupancy = [&](int v, bool ck, int w = 1) {
             int b = C->tune.blocks_per_sm;
@@ -560,11 +567,15 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         if (C->tune.ckpt < 0)
             ckpt = scratch_of(false, 1, std::min<int64_t>(warps_full, ((P + wpb - 1) / wpb) * wpb)) > budget;
         const int max_strips = (pl->max_len + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
-        const unsigned allowed = allowed_configs(P, max_strips, warps_full, wpb, C->tune);
+        const bool wide = !layout_forced && P >= warps_full &&
+                          qpk::posterior_f32_tab_copies(8, pl->max_len, C->smem_per_sm) > 1;
+        const unsigned allowed = allowed_configs(P, max_strips, warps_full, wpb, C->tune, wide);
         tkey = Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)ckpt << 62);
         cfg = C->tuner[tkey].choose(allowed);
         variant = config_variant(cfg);
         W = config_wpp(cfg);
+        set_layout(config_layout(cfg));
+        set_tables();
         // with two warps per pair, the spare warps of a launch whose pairs do
         // not fill the grid double up on the longest pairs (items come longest
         // first): n_big items run on two warps, the rest on one
@@ -594,6 +605,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         Pb.ckpt = ckpt ? 1 : 0;
         Pb.wpp = W;
         Pb.stg = (int2*)C->stg.ptr; Pb.stg_stride = sz.stg;
+        C->last_variant = variant; C->last_wpp = W; C->last_wpb = wpb; C->last_copies = Pb.tab_copies;
     }
     // FP64 form: over every pair (plain form), or as the follow-up of the FP32
     // kernel on a small fixed grid that finds its pairs in the fallback list
@@ -1112,6 +1124,10 @@ int qp_get_counter(int32_t device, const char* name, int64_t* value) {
     else if (n == "pool_retries") *value = C->pool_retries;
     else if (n == "consistency_fma") *value = C->cons_fma;
     else if (n == "consistency_form") *value = C->cons_last_form;
+    else if (n == "f32_variant") *value = C->last_variant;
+    else if (n == "f32_wpp") *value = C->last_wpp;
+    else if (n == "f32_warps_per_block") *value = C->last_wpb;
+    else if (n == "f32_tab_copies") *value = C->last_copies;
     else return fail(QP_EINVAL, "unknown counter '%s'", name);
     return QP_OK;
 }

@@ -83,11 +83,14 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
 int64_t scratch_budget(const LaunchOverride& t);
 
 // Launch configurations of the FP32 kernel the autotuner chooses from:
-// config = variant + kF32Variants * w, with w indexing kWpp (warps per pair).
+// config = variant + kF32Variants * (w + 2 * layout), with w indexing kWpp
+// (warps per pair) and layout 0 = blocks of 2 warps with one emission table,
+// 1 = blocks of 8 warps with the bank-sliced table (kTabCopies copies).
 constexpr int kWpp[2] = {1, 2};
-constexpr int kTuneConfigs = qpk::kF32Variants * 2;
+constexpr int kTuneConfigs = qpk::kF32Variants * 2 * 2;
 inline int config_variant(int cfg) { return cfg % qpk::kF32Variants; }
-inline int config_wpp(int cfg) { return kWpp[cfg / qpk::kF32Variants]; }
+inline int config_wpp(int cfg) { return kWpp[(cfg / qpk::kF32Variants) % 2]; }
+inline int config_layout(int cfg) { return cfg / (qpk::kF32Variants * 2); }
 
 // Online choice among the allowed launch configurations, per shape bucket
 // (pair count, longest sequence, mean work): each is timed on kTuneSamples
@@ -115,9 +118,11 @@ struct TuneEntry {
 // Configurations worth trying for a launch of n_pairs pairs whose longest
 // sequence spans max_strips strips, on warps_full resident warps: several
 // warps per pair only when pairs are too few to balance the grid and pairs
-// have strips to share; wpp must divide warps_per_block.
+// have strips to share; wpp must divide warps_per_block.  Layout 1 (8-warp
+// blocks, bank-sliced table) only when wide_layout: the launch fills the grid
+// and two such blocks fit an SM; warps_per_block is layout 0's.
 unsigned allowed_configs(int64_t n_pairs, int max_strips, int64_t warps_full, int warps_per_block,
-                         const LaunchOverride& t);
+                         const LaunchOverride& t, bool wide_layout = false);
 
 // Grid of the persistent FP32 kernel for blocks_needed blocks of work: at most
 // blocks_per_sm per SM, and a multiple of the SM count once it exceeds it.
@@ -166,6 +171,7 @@ struct Context {
     int64_t cons_pool_hint = 0;
     int64_t cons_fma = 0;                // multiply-adds of the last relaxation
     int cons_last_form = -1;             // form of the last relaxation (0 row form, 1 staged form)
+    int last_variant = -1, last_wpp = -1, last_wpb = -1, last_copies = -1;   // last FP32 launch
     cudaEvent_t cons_ev[2] = {};
     // guide tree: working memory kept between calls, pinned staging
     std::mutex tree_mu;
