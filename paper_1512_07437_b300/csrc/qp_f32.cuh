@@ -125,11 +125,18 @@ __device__ __forceinline__ void sts_v4(unsigned a, float4 v) {
 }
 
 // ---------------------------------------------------------------- async copies
-// cp.async moves the stored backward blocks and the boundary row into a small
-// per-warp shared-memory ring kD steps ahead of their use.  Every lane copies
-// and later reads only its own bytes, so waiting on its own copy groups is the
-// only synchronisation needed.  A source size of 0 fills the slot with zeros.
+// cp.async moves the stored backward blocks into a small per-warp
+// shared-memory ring kD steps ahead of their use; every lane copies and later
+// reads only its own bytes, so waiting on its own copy groups is the only
+// synchronisation needed.  The boundary row, which one lane reads, comes in
+// chunks of kBndChunk columns, one 16-byte copy per lane for a whole chunk,
+// issued on the renormalisation steps one chunk ahead into a two-chunk ring;
+// the lanes then meet at a warp barrier before the reading lane uses it.  A
+// source size of 0 fills the slot with zeros.
 constexpr int kD = kD_ring;
+constexpr int kBndChunk = kC;                 // boundary-row columns per chunk (one per step)
+constexpr int kBndSlots = 2 * kBndChunk;      // the two-chunk ring of boundary columns (32 bytes each)
+static_assert(kWarp == 2 * kBndChunk, "a chunk is one 16-byte copy per lane");
 
 __device__ __forceinline__ void cp_async16(unsigned dst, const void* src, int bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
@@ -333,7 +340,7 @@ struct PairCtx {
 // boundary ring, column residues
 struct WarpSmem {
     unsigned ring_b;  // [kD][kWarp * kRmax] float2
-    unsigned ring_e;  // [kD][2] float4
+    unsigned ring_e;  // [kBndSlots][2] float4
     unsigned sy;      // [max_len + 2 kYPad] residue codes
 };
 
@@ -344,7 +351,7 @@ constexpr int kYPad = 33;   // empty codes before column 1 of the staged residue
 constexpr unsigned kRingSlot = kWarp * kRmax * 8;   // bytes of one ring slot
 
 __host__ __device__ constexpr int warp_smem_bytes(int max_len) {
-    return kD * kWarp * kRmax * 8 + kD * 32 + ((max_len + 2 * kYPad + 15) / 16) * 16;
+    return kD * kWarp * kRmax * 8 + kBndSlots * 32 + ((max_len + 2 * kYPad + 15) / 16) * 16;
 }
 
 // Runs steps 0 .. nsteps-1 of a strip: the steps t_a and t_b (-1: none) with
@@ -432,29 +439,32 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     float2* blk = STORE ? io.bst + (int64_t)(n + 31) * (kWarp * R) + (R == 1 ? lane : 2 * lane) : nullptr;
     int2* bex = io.bex;
     const int nsteps = n + 32;
-    // lane 31 streams the boundary row (column n - t at step t) into its ring
+    // lane 31 reads the boundary row (column n - t at step t) from the ring,
+    // slot t mod kBndSlots
     const bool streams = (lane == 31) && (bnd_in != nullptr);
     // lane 0 writes the boundary row above the strip (none above strip 0;
     // the base then points at the staging area and no store is made)
     const int bnd_lane = (lane == 0 && bnd_out != nullptr) ? 1 : 0;
     float4* const bnd_base = bnd_lane ? bnd_out : (float4*)c.stg;
-    auto fetch = [&](int t) {
-        const int jb = n - t;
-        const int sz = (streams && jb >= 0) ? 16 : 0;
-        const float4* src = bnd_in + 2 * max(jb, 0);
-        const unsigned dst = ws.ring_e + 32u * (unsigned)(t & (kD - 1));
-        cp_async16(dst, src, sz);
-        cp_async16(dst + 16, src + 1, sz);
+    // the chunk of steps t0 .. t0 + kBndChunk - 1: lane l copies half l & 1 of
+    // the column of step t0 + l / 2 (zeros left of column 0)
+    auto fetch_chunk = [&](int t0) {
+        const int tl = t0 + (lane >> 1);
+        const int jb = n - tl;
+        const float4* src = bnd_in + 2 * max(jb, 0) + (lane & 1);
+        const unsigned dst = ws.ring_e + 32u * (unsigned)(tl & (kBndSlots - 1)) + 16u * (unsigned)(lane & 1);
+        cp_async16(dst, src, jb >= 0 ? 16 : 0);
         cp_async_commit();
     };
-    // without a strip below, lane 31 reads zeros from a ring slot
+    // without a strip below, lane 31 reads zeros from slot 0
     if (!streams && lane == 31) {
-#pragma unroll
-        for (int q = 0; q < 2 * kD; ++q) sts_v4(ws.ring_e + 16u * q, make_float4(0.f, 0.f, 0.f, 0.f));
+        sts_v4(ws.ring_e, make_float4(0.f, 0.f, 0.f, 0.f));
+        sts_v4(ws.ring_e + 16u, make_float4(0.f, 0.f, 0.f, 0.f));
     }
     if (bnd_in) {
-#pragma unroll
-        for (int t = 0; t < kD - 1; ++t) fetch(t);
+        fetch_chunk(0);
+        cp_async_wait<0>();
+        __syncwarp();
     }
     // column residue of the lane, one step ahead (padded: no range check)
     unsigned ya = ws.sy + (unsigned)(n + 31 - lane + kYPad - 1);
@@ -464,18 +474,21 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     auto step = [&](int t, auto spec) {
         constexpr bool SPEC = decltype(spec)::value;
         const int ph = t & (kC - 1);
-        if (bnd_in) {
-            fetch(t + kD - 1);
-            cp_async_wait<kD - 1>();
-        }
-        const unsigned eba = ws.ring_e + 32u * (unsigned)(streams ? (t & (kD - 1)) : 0);
+        const unsigned eba = ws.ring_e + 32u * (unsigned)(streams ? (t & (kBndSlots - 1)) : 0);
         const int j = n + 31 - lane - t;
         if (ph == 0) {
-            // the row below is written by another warp: stay 16 + kD + 32
-            // steps behind it (column n - T of the row below is written at
-            // the writer's step T + 31 and fetched here kD - 1 steps ahead)
-            strip_wait(io.sync, t + 16 + kD + 32, flag, cf.spin_limit);
+            // the row below is written by another warp: stay 64 steps behind
+            // it (column n - T of the row below is written at the writer's
+            // step T + 31 and fetched here up to 31 steps ahead)
+            strip_wait(io.sync, t + 64, flag, cf.spin_limit);
             if (lane == 0) strip_publish(io.sync, t);
+            // this chunk of the boundary row has landed (issued a chunk ago);
+            // fetch the next one into the other half of the ring
+            if (bnd_in) {
+                cp_async_wait<0>();
+                __syncwarp();
+                fetch_chunk(t + kBndChunk);
+            }
             // renormalise: bring the lane's largest carried value into [1, 2)
             float mh = max3f(dDD.x, tV.x, tX2), mp = fmaxf(dDD.y, tV.y);
 #pragma unroll
@@ -602,6 +615,7 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     };
     run_steps(nsteps, t_start, t_end, step);
     cp_async_wait<0>();
+    __syncwarp();
     if (lane == 0) strip_publish(io.sync, kStepsDone);
 }
 
@@ -694,8 +708,10 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
     // threshold
     int4* grp = c.stg;
     int ng = 0;
-    // ring streams: this lane's stored block of step T, and (lane 0) the
-    // boundary row column T
+    // ring streams: this lane's stored block of step T; lane 0 reads the
+    // boundary row (column T at step T) from the boundary ring, slot
+    // (T - c2 + kBndChunk) mod kBndSlots: chunks start on the renormalisation
+    // steps
     const bool streams = (lane == 0) && (bnd_in != nullptr);
     // lane 31 writes the boundary row below the strip (none below the last;
     // the base then points at the staging area and no store is made)
@@ -717,19 +733,30 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
 #pragma unroll
             for (int h = 0; h < R / 2; ++h) cp_async16(dst + 512u * h, src + 2 * kWarp * h, sz);
         }
-        if (bnd_in) {
-            const int szb = (streams && T <= n) ? 16 : 0;
-            const float4* sb = bnd_in + 2 * min(T, n);
-            const unsigned db = ws.ring_e + 32u * (unsigned)(T & (kD - 1));
-            cp_async16(db, sb, szb);
-            cp_async16(db + 16, sb + 1, szb);
-        }
         cp_async_commit();
     };
-    // lanes without a boundary read zeros from their ring slots
+    // the boundary chunk of steps T0 .. T0 + kBndChunk - 1: lane l copies half
+    // l & 1 of column T0 + l / 2 (zeros outside 0 .. n); it joins the next
+    // copy group
+    auto fetch_chunk = [&](int T0) {
+        const int Tl = T0 + (lane >> 1);
+        const float4* src = bnd_in + 2 * min(max(Tl, 0), n) + (lane & 1);
+        const unsigned dst = ws.ring_e + 32u * (unsigned)((Tl - c2 + kBndChunk) & (kBndSlots - 1)) +
+                             16u * (unsigned)(lane & 1);
+        cp_async16(dst, src, (unsigned)Tl <= (unsigned)n ? 16 : 0);
+    };
+    // lane 0 without a boundary reads zeros from slot 0
     if (!streams && lane == 0) {
-#pragma unroll
-        for (int q = 0; q < 2 * kD; ++q) sts_v4(ws.ring_e + 16u * q, make_float4(0.f, 0.f, 0.f, 0.f));
+        sts_v4(ws.ring_e, make_float4(0.f, 0.f, 0.f, 0.f));
+        sts_v4(ws.ring_e + 16u, make_float4(0.f, 0.f, 0.f, 0.f));
+    }
+    if (bnd_in) {
+        // the chunks before and from the first renormalisation step
+        fetch_chunk(c2 - kBndChunk);
+        fetch_chunk(c2);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
     }
 #pragma unroll
     for (int t = 0; t < kD - 1; ++t) fetch(t);
@@ -743,16 +770,23 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
         cp_async_wait<kD - 1>();
         const unsigned slot = kRingSlot * (unsigned)(t & (kD - 1));
         const unsigned bsa = ring_lane + slot;
-        const unsigned eba = ws.ring_e + (streams ? 32u * (unsigned)(t & (kD - 1)) : 0u);
+        const unsigned eba = ws.ring_e + (streams ? 32u * (unsigned)((t - c2 + kBndChunk) & (kBndSlots - 1)) : 0u);
         const int j = t - lane;
         const int ph = (t - c2) & (kC - 1);
         if (ph == 0) {
-            // the row above is written by another warp: stay 16 + kD + 32
-            // steps behind it (column T of the row above is written at the
-            // writer's step T + 31 and fetched here kD - 1 steps ahead; a
-            // writer publishes its progress every kC steps)
-            strip_wait(io.sync, t + 16 + kD + 32, flag, cf.spin_limit);
+            // the row above is written by another warp: stay 64 steps behind
+            // it (column T of the row above is written at the writer's step
+            // T + 31 and fetched here up to 31 steps ahead; a writer
+            // publishes its progress every kC steps)
+            strip_wait(io.sync, t + 64, flag, cf.spin_limit);
             if (lane == 31) strip_publish(io.sync, t);
+            // this chunk of the boundary row has landed (its group is older
+            // than the kD - 1 the step's wait leaves pending); fetch the next
+            // one into the other half of the ring
+            if (bnd_in) {
+                __syncwarp();
+                fetch_chunk(t + kBndChunk);
+            }
             float mh = max3f(uMZ.x, lV.x, lX2), mp = fmaxf(uMZ.y, lV.y);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -903,6 +937,7 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
                   make_float4(lX2, __int_as_float(Aa[R - 1]), __int_as_float(eH), __int_as_float(eP)));
     };
     run_steps(nsteps, t_start, t_end, step);
+    cp_async_commit();       // a chunk issued on the last step joins no step's group
     cp_async_wait<0>();
     if (lane == 31) strip_publish(io.sync, kStepsDone);
     // ---- flush this strip's entries into the pool (row-major, columns ascending)
@@ -1058,9 +1093,9 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
         const unsigned p = smem_u32(s_raw) + tab_end + (unsigned)wib * (unsigned)warp_smem_bytes(Pb.max_len);
         ws.ring_b = p;
         ws.ring_e = p + kD * kWarp * kRmax * 8;
-        ws.sy = p + kD * kWarp * kRmax * 8 + kD * 32;
+        ws.sy = p + kD * kWarp * kRmax * 8 + kBndSlots * 32;
     }
-    uint8_t* sy_p = s_raw + tab_end + (size_t)wib * warp_smem_bytes(Pb.max_len) + kD * kWarp * kRmax * 8 + kD * 32;
+    uint8_t* sy_p = s_raw + tab_end + (size_t)wib * warp_smem_bytes(Pb.max_len) + kD * kWarp * kRmax * 8 + kBndSlots * 32;
     // control blocks: one per group, and (W > 1) one per warp for items it runs alone
     GroupCtl* gc = (GroupCtl*)(s_raw + tab_end + (size_t)nwb * warp_smem_bytes(Pb.max_len)) + gib;
     GroupCtl* gcs = W == 1 ? gc : gc - gib + nwb + wib;
