@@ -45,9 +45,10 @@
 //
 // Threshold.  The cells of a lane's rows at one step form a group; when the
 // largest posterior of the group reaches the threshold the lane writes the
-// whole group (column and R values, one 20-byte record) to its staging area.
-// At the end of the strip each lane counts and copies its entries row by row
-// into the family's entry pool, in CSR order.
+// whole group (column and R values, one 32-byte record) to its staging area.
+// At the end of the strip each lane counts its entries per row, the warp
+// reserves their place in the family's entry pool, and each lane copies its
+// entries there in CSR order in one pass over its records.
 //
 // Range guards (the pair is recomputed by the FP64 form when one fires), for
 // lanes that own a row of the pair: a carried maximum >= 2^100 or not finite,
@@ -322,6 +323,7 @@ __device__ __forceinline__ void strip_publish(unsigned slot, long long steps) {
 }
 
 // ---------------------------------------------------------------- per-warp state
+struct GroupCtl;
 struct PairCtx {
     const FamDesc* fd;
     Status* st;
@@ -334,6 +336,7 @@ struct PairCtx {
     float4* bck;     // checkpointed form: the backward boundary row of every strip
     int4* stg;       // this lane's staging area: capg records of 32 bytes
     int capg;
+    const struct GroupCtl* pc;   // the warp's control block (flush targets)
 };
 
 // per-warp shared memory (32-bit shared-window addresses): stored-block ring,
@@ -617,6 +620,19 @@ __device__ __forceinline__ void bwd_strip(const Coef& cf, unsigned s_ow, const P
     cp_async_wait<0>();
     __syncwarp();
     if (lane == 0) strip_publish(io.sync, kStepsDone);
+}
+
+// The column and the R values of a staging record (16-byte loads).
+template <int R>
+__device__ __forceinline__ int rec_values(const int4* g, float (&v)[R]) {
+    const int4 a = g[0];
+    if (R == 1) { v[0] = __int_as_float(a.y); }
+    else if (R == 2) { v[0] = __int_as_float(a.y); v[1] = __int_as_float(a.z); }
+    else {
+        const int4 b = g[1];
+        v[0] = __int_as_float(a.y); v[1] = __int_as_float(a.z); v[2] = __int_as_float(a.w); v[R - 1] = __int_as_float(b.x);
+    }
+    return a.x;
 }
 
 // ---------------------------------------------------------------- pass 2
@@ -951,9 +967,10 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
     // (unrolled so that several records' loads are in flight at once)
 #pragma unroll 4
     for (int g = 0; g < ng; ++g) {
-        const float* rec = (const float*)(grp + 2 * g);
+        float v[R];
+        rec_values<R>(grp + 2 * g, v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) cnt[r] += rec[1 + r] >= theta ? 1 : 0;
+        for (int r = 0; r < R; ++r) cnt[r] += v[r] >= theta ? 1 : 0;
     }
     int tot = 0;
 #pragma unroll
@@ -965,32 +982,35 @@ __device__ __forceinline__ void fwd_strip(const Problem& Pb, unsigned s_ow, cons
         if (lane >= o) incl += v;
     }
     const int strip_tot = __shfl_sync(kFull, incl, 31);
-    const FamDesc& fd = *c.fd;
+    const GroupCtl& pc = *c.pc;
     unsigned long long off = 0;
-    if (lane == 0 && strip_tot > 0) off = atomicAdd(fd.pool_used, (unsigned long long)strip_tot);
+    if (lane == 0 && strip_tot > 0) off = atomicAdd(pc.pool_used, (unsigned long long)strip_tot);
     off = __shfl_sync(kFull, off, 0);
-    const bool fits = (int64_t)off + strip_tot <= fd.pool_cap;
+    const bool fits = (int64_t)off + strip_tot <= pc.pool_cap;
     if (!fits) { flag |= kGuardPool; if (lane == 0) atomicExch(&Pb.status->pool_overflow, 1); }
-    const int64_t base = fd.pool_base + (int64_t)off;
+    const int64_t base = pc.pool_base + (int64_t)off;
     int w = incl - tot;
-    const int64_t row_slot = fd.pair_row_off[c.p];
-    int2* pool = fd.pool ? fd.pool : Pb.pool;
+    int2* pool = pc.pool;
+    int2* dst[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = row0 + lane * R + r;
-        if (i >= 1 && i <= m) fd.row_cnt[row_slot + i - 1] = cnt[r];
-        if (fits && cnt[r] > 0) {
-            int2* dst = pool + base + w;
-#pragma unroll 4
-            for (int g = 0; g < ng; ++g) {
-                const int* rec = (const int*)(grp + 2 * g);
-                const float v = __int_as_float(rec[1 + r]);
-                if (v >= theta) { *dst = make_int2(rec[0] - 1, rec[1 + r]); ++dst; }
-            }
-        }
+        if (i >= 1 && i <= m) pc.rowc[i - 1] = cnt[r];
+        dst[r] = pool + base + w;
         w += cnt[r];
     }
-    if (lane == 0) fd.chunk_off[fd.pair_strip_off[c.p] + s] = base;
+    // one pass over the records: every kept value goes to the next place of its row
+    if (fits) {
+#pragma unroll 2
+        for (int g = 0; g < ng; ++g) {
+            float v[R];
+            const int col = rec_values<R>(grp + 2 * g, v) - 1;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (v[r] >= theta) { *dst[r] = make_int2(col, __float_as_int(v[r])); ++dst[r]; }
+        }
+    }
+    if (lane == 0) pc.chunk[s] = base;
     pair_tot += strip_tot;
     __syncwarp();
 }
@@ -1037,6 +1057,12 @@ struct GroupCtl {
     int flag[4];
     float pmax[4];
     long long tot[4];
+    // the pair's flush targets (written once per pair by the warp's lane 0)
+    int2* pool;
+    unsigned long long* pool_used;
+    int64_t* chunk;             // chunk_off of the pair's first strip
+    int32_t* rowc;              // row_cnt of the pair's first row (row i at rowc[i - 1])
+    long long pool_base, pool_cap;
 };
 
 // Barrier of one group.  Group g of W warps uses named barrier g + 1 (literal
@@ -1163,11 +1189,24 @@ __device__ __forceinline__ void posterior_f32_body(const Problem& Pb) {
         c.y = fd.codes + ob;
         c.p = p;
         c.nch = (c.n + 32 + kC - 1) / kC;
+        // what the strip flushes write to, read from shared memory there
+        // (no chain of dependent global loads at the end of every strip)
+        if (lane == 0) {
+            gcs->pool = fd.pool ? fd.pool : Pb.pool;
+            gcs->pool_used = fd.pool_used;
+            gcs->chunk = fd.chunk_off + fd.pair_strip_off[p];
+            gcs->rowc = fd.row_cnt + fd.pair_row_off[p];
+            gcs->pool_base = fd.pool_base;
+            gcs->pool_cap = fd.pool_cap;
+        }
+        c.pc = gcs;
         const int m = c.m, n = c.n;
         const int nstrips = (m + 1 + kStripRows - 1) / kStripRows;
         // the column residues of the pair, staged once, with empty codes on
         // both sides so that every skewed column index reads a valid byte
+        // (four loads of a lane in flight)
         __syncwarp();
+#pragma unroll 4
         for (int i = lane; i < n + 2 * kYPad; i += 32) {
             const int jj = i - kYPad;
             sy_p[i] = (jj >= 0 && jj < n) ? c.y[jj] : (uint8_t)kEmpty;
