@@ -186,22 +186,42 @@ cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block
 // ================================================================ FP64 form
 //
 // Plain FP64 evaluation: one CTA per pair, anti-diagonal wavefront over the
-// (m+1) x (n+1) grid, values of each diagonal rescaled by a power of two so
-// that its largest value is in [1, 2).  Pass 1 (backward) stores (B_M, Zm_b)
-// densely; pass 2 (forward) forms the posteriors, the combination, the
-// threshold and the MEA recurrence on each diagonal.
+// (m+1) x (n+1) grid.  Pass 1 (backward) stores (B_M, Zm_b) densely; pass 2
+// (forward) forms the posteriors, the combination, the threshold and the MEA
+// recurrence on each diagonal.
+//
+// Scaling (per model, per diagonal): a diagonal is computed in the units of
+// its predecessor's largest value ("normalised units"), and stored as it is;
+// its readers bring it to their own units with one power of two per operand
+// (exact), so each diagonal needs one block-wide maximum and one barrier.
+// The stored backward values carry the units they were stored in.
 constexpr int kF64Threads = 256;
+constexpr int kF64Warps = kF64Threads / 32;
 
-__device__ __forceinline__ double pow2d(int e) { return ldexp(1.0, e); }
+// floor(log2 v) for a positive normal double, 0 for 0 (exponent field only)
+__device__ __forceinline__ int exp2_of(double v) {
+    return v > 0.0 ? (int)((__double_as_longlong(v) >> 52) & 0x7ff) - 1023 : 0;
+}
+// 2^e for e in the normal range (clamped to it)
+__device__ __forceinline__ double pow2d(int e) {
+    e = max(-1022, min(1023, e));
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
 
-__device__ double block_max(double v, double* red) {
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+// Largest (mh, mp) over the block: warp maxima go to red[w], and after the
+// barrier every thread reads all of them.  red alternates between two
+// buffers on consecutive diagonals, so one barrier per diagonal suffices.
+__device__ __forceinline__ double2 block_max2(double mh, double mp, double2* red) {
+    for (int o = 16; o; o >>= 1) {
+        mh = fmax(mh, __shfl_xor_sync(FULL, mh, o));
+        mp = fmax(mp, __shfl_xor_sync(FULL, mp, o));
+    }
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = make_double2(mh, mp);
     __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double r = red[0];
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) r = fmax(r, red[i]);
+    double2 r = red[0];
+#pragma unroll
+    for (int i = 1; i < kF64Warps; ++i) { const double2 v = red[i]; r.x = fmax(r.x, v.x); r.y = fmax(r.y, v.y); }
     return r;
 }
 
@@ -219,8 +239,9 @@ __device__ int block_sum(int v, int* red) {
 
 __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
     stamp_begin(Pb.status->t_f64);
-    __shared__ double sred[2][kF64Threads / 32];
-    __shared__ int ired[kF64Threads / 32];
+    __shared__ double2 sred2[2][kF64Warps];
+    __shared__ double sred[2][2];
+    __shared__ int ired[kF64Warps];
     __shared__ int s_q;
     __shared__ unsigned long long s_base;
     const Consts* __restrict__ C = Pb.cst;
@@ -256,27 +277,36 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
         auto slot = [&](int d, int v) -> double* { return dg + ((int64_t)((d % 3 + 3) % 3) * kNS + v) * L; };
         // ---- pass 1: backward over anti-diagonals d = m+n .. 0
         // slot values: 0 B_M, 1 B_X, 2 B_X2, 3 B_Y, 4 B_Y2, 5 Zm_b, 6 Ze_b, 7 Zf_b
-        int Eh1 = 0, Ep1 = 0, Eh2 = 0, Ep2 = 0;   // exponents of diagonals d+1, d+2
+        // units (HMM, PF): stored units of diagonals d+1 (u1) and d+2 (u2),
+        // normalised units of d+1 (v1) = the units diagonal d is computed in
+        int u1h = 0, u1p = 0, u2h = 0, u2p = 0, v1h = 0, v1p = 0;
         double Zh = 0.0, Zp = 0.0;
         int eZh = 0, eZp = 0;
-        int32_t* EB = rc + L;            // [m+n+1] HMM exponents per diagonal
-        int32_t* EP = EB + (2 * L + 2);  // [m+n+1] PF exponents per diagonal
+        int32_t* EB = rc + L;            // [m+n+1] HMM units of the stored diagonal
+        int32_t* EP = EB + (2 * L + 2);  // [m+n+1] PF units of the stored diagonal
         for (int d = m + n; d >= 0; --d) {
             const int ilo = max(0, d - n), ihi = min(m, d);
             double* cur[8];
             for (int v = 0; v < 8; ++v) cur[v] = slot(d, v);
+            const double f1h = pow2d(u1h - v1h), f1p = pow2d(u1p - v1p);
+            const double f2h = pow2d(u2h - v1h), f2p = pow2d(u2p - v1p);
             double mh = 0.0, mp = 0.0;
-            const double f2 = pow2d(Eh2 - Eh1), g2 = pow2d(Ep2 - Ep1);
             for (int i = ilo + tid; i <= ihi; i += nt) {
                 const int j = d - i;
                 double D = 0, Dp = 0, Xb = 0, X2b = 0, Eb = 0, Yb = 0, Y2b = 0, Fb = 0;
                 if (i < m && j < n) {
                     const int o = Y(j + 1) * kTab + X(i + 1);
-                    D = C->oddsd[o] * slot(d + 2, 0)[i + 1] * f2;
-                    Dp = C->wd[o] * slot(d + 2, 5)[i + 1] * g2;
+                    D = C->oddsd[o] * (slot(d + 2, 0)[i + 1] * f2h);
+                    Dp = C->wd[o] * (slot(d + 2, 5)[i + 1] * f2p);
                 }
-                if (i < m) { Xb = slot(d + 1, 1)[i + 1]; X2b = slot(d + 1, 2)[i + 1]; Eb = slot(d + 1, 6)[i + 1]; }
-                if (j < n) { Yb = slot(d + 1, 3)[i]; Y2b = slot(d + 1, 4)[i]; Fb = slot(d + 1, 7)[i]; }
+                if (i < m) {
+                    Xb = slot(d + 1, 1)[i + 1] * f1h; X2b = slot(d + 1, 2)[i + 1] * f1h;
+                    Eb = slot(d + 1, 6)[i + 1] * f1p;
+                }
+                if (j < n) {
+                    Yb = slot(d + 1, 3)[i] * f1h; Y2b = slot(d + 1, 4)[i] * f1h;
+                    Fb = slot(d + 1, 7)[i] * f1p;
+                }
                 double BM = tMM * D + d1 * (Xb + Yb) + d2 * (X2b + Y2b);
                 double BX = c1 * D + e1 * Xb, BX2 = c2 * D + e2 * X2b;
                 double BY = c1 * D + e1 * Yb, BY2 = c2 * D + e2 * Y2b;
@@ -288,66 +318,71 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
                 if (i == 0 && j == 0) {
                     Zh = C->pid[0] * D + C->pid[1] * Xb + C->pid[2] * Yb + C->pid[3] * X2b + C->pid[4] * Y2b;
                     Zp = ZMB;
+                    eZh = v1h; eZp = v1p;
                 }
                 cur[0][i] = BM; cur[1][i] = BX; cur[2][i] = BX2; cur[3][i] = BY; cur[4][i] = BY2;
                 cur[5][i] = ZMB; cur[6][i] = ZEB; cur[7][i] = ZFB;
+                Bd[(int64_t)i * (n + 1) + j] = make_double2(BM, ZMB);
                 mh = fmax(mh, fmax(fmax(BM, BX), fmax(BX2, fmax(BY, BY2))));
                 mp = fmax(mp, fmax(ZMB, fmax(ZEB, ZFB)));
             }
-            const double MH = block_max(mh, sred[0]);
-            const double MP = block_max(mp, sred[1]);
-            int kh = 0, kp = 0;
-            if (d != m + n) {
-                if (MH > 0.0) { frexp(MH, &kh); kh -= 1; }
-                if (MP > 0.0) { frexp(MP, &kp); kp -= 1; }
-            }
-            const double sh = pow2d(-kh), sp = pow2d(-kp);
-            const int Ed = Eh1 + kh, Fd = Ep1 + kp;
-            for (int i = ilo + tid; i <= ihi; i += nt) {
-                const int j = d - i;
-                for (int v = 0; v < 5; ++v) cur[v][i] *= sh;
-                for (int v = 5; v < 8; ++v) cur[v][i] *= sp;
-                Bd[(int64_t)i * (n + 1) + j] = make_double2(cur[0][i], cur[5][i]);
-            }
-            if (tid == 0) { EB[d] = (d == m + n) ? 0 : Ed; EP[d] = (d == m + n) ? 0 : Fd; }
-            if (d == 0 && tid == 0) { eZh = Eh1; eZp = Ep1; }
-            Eh2 = Eh1; Ep2 = Ep1;
-            Eh1 = (d == m + n) ? 0 : Ed; Ep1 = (d == m + n) ? 0 : Fd;
-            __syncthreads();
+            if (tid == 0) { EB[d] = v1h; EP[d] = v1p; }
+            const double2 M = block_max2(mh, mp, sred2[d & 1]);
+            u2h = u1h; u2p = u1p;
+            u1h = v1h; u1p = v1p;
+            v1h += exp2_of(M.x); v1p += exp2_of(M.y);
         }
-        // totals (thread 0 computed them at d = 0, in units of diagonal 1)
+        // totals (thread 0 computed them at d = 0)
         if (tid == 0) { sred[0][0] = Zh; sred[1][0] = Zp; ired[0] = eZh; ired[1] = eZp; }
         __syncthreads();
         Zh = sred[0][0]; Zp = sred[1][0]; eZh = ired[0]; eZp = ired[1];
         __syncthreads();
         // ---- pass 2: forward over d = 0 .. m+n
         // slot values: 0 Mdiag, 1 Xin, 2 X2in, 3 Yin, 4 Y2in, 5 Zd, 6 Ein, 7 Fin, 8 A
+        // units as in pass 1, of diagonals d-1 (u1, v1) and d-2 (u2)
         for (int i = tid; i <= m; i += nt) rc[i] = 0;
         __syncthreads();
-        int Fh1 = 0, Fp1 = 0, Fh2 = 0, Fp2 = 0;
+        u1h = u1p = u2h = u2p = v1h = v1p = 0;
         double fZh = 0, fZp = 0, Aend = 0;
         int feh = 0, fep = 0;
         const double theta = C->thetad;
         const int comb = C->combine;
         const double invZh = 1.0 / Zh, invZp = 1.0 / Zp;
+        // the thread for row i is fixed, i = tid (mod nt); with at most two
+        // rows a thread, the stored backward values of the next diagonal are
+        // loaded one diagonal ahead
+        const bool ahead = (m + 1) <= 2 * nt;
+        auto bload = [&](int i, int d) -> double2 {
+            const int j = d - i;
+            return (i >= 1 && i <= m && j >= 1 && j <= n) ? Bd[(int64_t)i * (n + 1) + j] : make_double2(0.0, 0.0);
+        };
+        double2 bq0 = make_double2(0.0, 0.0), bq1 = bq0;
         for (int d = 0; d <= m + n; ++d) {
             const int ilo = max(0, d - n), ihi = min(m, d);
             double* cur[9];
             for (int v = 0; v < 9; ++v) cur[v] = slot(d, v);
-            const double f2 = pow2d(Fh2 - Fh1), g2 = pow2d(Fp2 - Fp1);
-            // posterior factors of the diagonal: F in units of the previous
-            // diagonal, B in units of its diagonal, over the totals
-            const double sph = ldexp(invZh, Fh1 + EB[d] - eZh), spp = ldexp(invZp, Fp1 + EP[d] - eZp);
+            const double f1h = pow2d(u1h - v1h), f1p = pow2d(u1p - v1p);
+            const double f2h = pow2d(u2h - v1h), f2p = pow2d(u2p - v1p);
+            // posterior factors of the diagonal: F in the diagonal's units
+            // (v1), B in the units it was stored in, over the totals
+            const double sph = ldexp(invZh, v1h + EB[d] - eZh), spp = ldexp(invZp, v1p + EP[d] - eZp);
+            double2 bn0 = make_double2(0.0, 0.0), bn1 = bn0;
+            if (ahead) { bn0 = bload(tid, d + 1); bn1 = bload(tid + nt, d + 1); }
             double mh = 0.0, mp = 0.0;
-            // the thread for row i is fixed: i = tid (mod nt)
             const int i0 = ilo + ((tid - ilo) % nt + nt) % nt;
             for (int i = i0; i <= ihi; i += nt) {
                 const int j = d - i;
                 double Md = 0, Xi = 0, X2i = 0, Yi = 0, Y2i = 0, Zd = 0, Ei = 0, Fi = 0;
                 double Adg = 0, Aup = 0, Alf = 0;
-                if (i >= 1 && j >= 1) { Md = slot(d - 2, 0)[i - 1] * f2; Zd = slot(d - 2, 5)[i - 1] * g2; Adg = slot(d - 2, 8)[i - 1]; }
-                if (i >= 1) { Xi = slot(d - 1, 1)[i - 1]; X2i = slot(d - 1, 2)[i - 1]; Ei = slot(d - 1, 6)[i - 1]; Aup = slot(d - 1, 8)[i - 1]; }
-                if (j >= 1) { Yi = slot(d - 1, 3)[i]; Y2i = slot(d - 1, 4)[i]; Fi = slot(d - 1, 7)[i]; Alf = slot(d - 1, 8)[i]; }
+                if (i >= 1 && j >= 1) { Md = slot(d - 2, 0)[i - 1] * f2h; Zd = slot(d - 2, 5)[i - 1] * f2p; Adg = slot(d - 2, 8)[i - 1]; }
+                if (i >= 1) {
+                    Xi = slot(d - 1, 1)[i - 1] * f1h; X2i = slot(d - 1, 2)[i - 1] * f1h;
+                    Ei = slot(d - 1, 6)[i - 1] * f1p; Aup = slot(d - 1, 8)[i - 1];
+                }
+                if (j >= 1) {
+                    Yi = slot(d - 1, 3)[i] * f1h; Y2i = slot(d - 1, 4)[i] * f1h;
+                    Fi = slot(d - 1, 7)[i] * f1p; Alf = slot(d - 1, 8)[i];
+                }
                 const int o = Y(j) * kTab + X(i);
                 const double FM = C->oddsd[o] * Md, FX = Xi, FX2 = X2i, FY = Yi, FY2 = Y2i;
                 const double ZM = C->wd[o] * Zd, ZE = Ei, ZF = Fi;
@@ -357,7 +392,7 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
                 double nZd = ZM + ZE + ZF, nEi = Wo * ZM + We * ZE, nFi = Wo * ZM + We * ZF;
                 double A = 0.0;
                 if (i >= 1 && j >= 1) {
-                    const double2 b = Bd[(int64_t)i * (n + 1) + j];
+                    const double2 b = ahead ? (i == tid ? bq0 : bq1) : Bd[(int64_t)i * (n + 1) + j];
                     const double ph = FM * b.x * sph;
                     const double pp = ZM * b.y * spp;
                     double P;
@@ -382,26 +417,18 @@ __global__ void __launch_bounds__(kF64Threads) k_posterior_f64(Problem Pb) {
                     fZh = C->taud[0] * FM + C->taud[1] * FX + C->taud[2] * FY + C->taud[3] * FX2 + C->taud[4] * FY2;
                     fZp = ZM + ZE + ZF;
                     Aend = A;
-                    feh = Fh1; fep = Fp1;
+                    feh = v1h; fep = v1p;
                 }
                 cur[0][i] = nMd; cur[1][i] = nXi; cur[2][i] = nX2i; cur[3][i] = nYi; cur[4][i] = nY2i;
                 cur[5][i] = nZd; cur[6][i] = nEi; cur[7][i] = nFi; cur[8][i] = A;
                 mh = fmax(mh, fmax(fmax(nMd, nXi), fmax(nX2i, fmax(nYi, nY2i))));
                 mp = fmax(mp, fmax(nZd, fmax(nEi, nFi)));
             }
-            const double MH = block_max(mh, sred[0]);
-            const double MP = block_max(mp, sred[1]);
-            int kh = 0, kp = 0;
-            if (MH > 0.0) { frexp(MH, &kh); kh -= 1; }
-            if (MP > 0.0) { frexp(MP, &kp); kp -= 1; }
-            const double sh = pow2d(-kh), sp = pow2d(-kp);
-            for (int i = i0; i <= ihi; i += nt) {
-                for (int v = 0; v < 5; ++v) cur[v][i] *= sh;
-                for (int v = 5; v < 8; ++v) cur[v][i] *= sp;
-            }
-            Fh2 = Fh1; Fp2 = Fp1;
-            Fh1 += kh; Fp1 += kp;
-            __syncthreads();
+            bq0 = bn0; bq1 = bn1;
+            const double2 M = block_max2(mh, mp, sred2[d & 1]);
+            u2h = u1h; u2p = u1p;
+            u1h = v1h; u1p = v1p;
+            v1h += exp2_of(M.x); v1p += exp2_of(M.y);
         }
         // gather the corner values from the thread that held row m
         if (tid == m % nt) {
