@@ -89,6 +89,10 @@ def parse():
                     help="profiling: only the first K sequences of length <= MAXLEN of the family")
     ap.add_argument("--variant", type=int, default=-1, help="profiling: force the kernel's register variant")
     ap.add_argument("--wpp", type=int, default=0, help="profiling: force the warps per pair (1 or 2)")
+    ap.add_argument("--ckpt", type=int, default=-1,
+                    help="profiling: force the stored (0) or the checkpointed (1) form of the FP32 kernel")
+    ap.add_argument("--families", type=int, default=0,
+                    help="profiling: serving trace of this many families (default: the C4 trace's 200)")
     ap.add_argument("--wpb", type=int, default=0,
                     help="profiling: force the block layout (2: one emission table, 8: 16 bank-sliced copies)")
     return ap.parse_args()
@@ -469,10 +473,10 @@ def serve_trace(qp, torch, trace, prm, local, time_scale: float, warm_families: 
     }
 
 
-def serving_points(qp, torch, prm, local, rank, sm_count, max_mhz):
+def serving_points(qp, torch, prm, local, rank, sm_count, max_mhz, n_families: int = 0):
     """The C4 trace at its configured arrival rate (the capacity point) and
     stretched to offer LOAD_FRACTION of the capacity measured there."""
-    trace = synth.make_serving_trace(seed=4 + 1000 * rank)
+    trace = synth.make_serving_trace(seed=4 + 1000 * rank, n_families=n_families or None)
     cap = serve_trace(qp, torch, trace, prm, local, 1.0)
     capacity = cap["busy_gcups"] or cap["value"]
     scale = cap["offered_gcups"] / (LOAD_FRACTION * capacity) if capacity else 1.0
@@ -500,7 +504,7 @@ def run_serving(args, rank, world, local):
     prm = synth.default_params(threshold=0.01)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     with ClockSampler(local) as clk:
-        sv = serving_points(qp, torch, prm, local, rank, sm_count, 2032.0)
+        sv = serving_points(qp, torch, prm, local, rank, sm_count, 2032.0, args.families)
     clocks = clk.summary()
     cap, load = sv["capacity_point"], sv["load_point"]
     line = {
@@ -678,6 +682,8 @@ def main():
         qp.qp_set_option("variant", args.variant, device=local)
     if args.wpp > 0:
         qp.qp_set_option("wpp", args.wpp, device=local)
+    if args.ckpt >= 0:
+        qp.qp_set_option("ckpt", args.ckpt, device=local)
     if args.wpb > 0:
         qp.qp_set_option("warps_per_block", args.wpb, device=local)
         qp.qp_set_option("tab_copies", 16 if args.wpb >= 8 else 1, device=local)
