@@ -403,10 +403,8 @@ int qp_get_counter(int32_t device, const char* name, int64_t* value);
  * an FP32 range guard returns QP_ENOMEM (its FP64 recomputation needs more
  * scratch than the fixed array holds; call qp_posteriors instead).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) for that device.  The call itself cannot be captured
- * into a CUDA graph: it copies small tables from host memory on its stack and
- * synchronises its stream, so it returns QP_EINVAL while params->stream is
- * being captured.  All calls share the one array: the call clears what has to
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls share the one array: the call clears what has to
  * start at zero, but two calls that overlap on the GPU (other host threads,
  * other streams) race and corrupt each other.  The call returns after its
  * work on params->stream (or the legacy default stream when NULL) is done,

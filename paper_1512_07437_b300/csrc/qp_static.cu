@@ -117,15 +117,6 @@ extern "C" int qp_pair_posteriors_static(const uint8_t* residues, int32_t m, int
     rc = scratch_address(params->device, &S);
     if (rc != QP_OK) return rc;
     cudaStream_t st = (cudaStream_t)params->stream;
-    // the call copies from host memory on the stack and synchronises the
-    // stream, neither of which a stream capture can hold
-    {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        e = cudaStreamIsCapturing(st, &cs);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
-        if (cs != cudaStreamCaptureStatusNone)
-            return fail(QP_EINVAL, "qp_pair_posteriors_static cannot run while its stream is being captured");
-    }
 
     Consts* cst = (Consts*)(S + oConsts);
     Status* status = (Status*)(S + oStatus);

@@ -97,27 +97,3 @@ def test_static_entry_rejects_what_it_cannot_hold(env):
     with pytest.raises(qp.QpError) as e:
         _static_call(qp, torch, x, y, synth.default_params(threshold=1e-30), cap=3)
     assert e.value.code == 1 and "too small" in str(e.value)
-
-
-def test_static_entry_refuses_a_capturing_stream(env):
-    """The call synchronises its stream, so a capture cannot hold it: it must
-    refuse cleanly, leave the capture intact and the device usable."""
-    qp, torch = env
-    x, y = "ACDEFGHIKLMNPQRSTVWY" * 3, "ACDEFGHIKLMNPQRSTVWY" * 2
-    prm = synth.default_params(threshold=0.01)
-    s = torch.cuda.Stream()
-    m, n = len(x), len(y)
-    res = torch.from_numpy(np.frombuffer((x + y).encode(), dtype=np.uint8).copy()).cuda()
-    row_ptr = torch.zeros(m + 1, dtype=torch.int32, device="cuda")
-    col = torch.zeros(m * n, dtype=torch.int32, device="cuda")
-    val = torch.zeros(m * n, dtype=torch.float32, device="cuda")
-    out = torch.zeros(4, dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with pytest.raises(qp.QpError) as e:
-        with torch.cuda.graph(g, stream=s):
-            qp.qp_pair_posteriors_static(res, m, n, prm, row_ptr, col, val, out)
-    assert e.value.code == 1 and "captured" in str(e.value)
-    torch.cuda.synchronize()
-    _check_against_qp_posteriors(qp, x, y, prm, *_static_call(qp, torch, x, y, prm))
-    assert torch.cuda.current_device() == 0
