@@ -185,7 +185,10 @@ typedef struct qp_result {
 
 /* All-pairs posterior stage of one family (Methods, stage I).
  * On success *out holds a complete result (device or host per
- * out_on_device).  Errors: QP_EINVAL (family/params), QP_ENOMEM, QP_ECUDA.
+ * out_on_device).  With host output a large family is computed in pair
+ * ranges, each range's arrays copied to host memory while the next range
+ * computes (option "host_chunks"); the result is the same.
+ * Errors: QP_EINVAL (family/params), QP_ENOMEM, QP_ECUDA.
  * On error *out is NULL. */
 int qp_posteriors(const qp_family* family, const qp_params* params,
                   int32_t out_on_device, qp_result** out);
@@ -352,6 +355,13 @@ void qp_server_destroy(qp_server* server);
  *                     56 KB) or 1; -1 automatic (chosen with the block
  *                     layout, see "warps_per_block").  Results are
  *                     identical either way;
+ *   "host_chunks"     qp_posteriors with host output: the family's pairs are
+ *                     computed in this many ranges of equal work, the
+ *                     arrays of a finished range copied to host memory
+ *                     while the next range computes (1: never; 0
+ *                     automatic: FP32 families of at least 2e9 cells
+ *                     without an entry budget, one range per 1.5e9 cells,
+ *                     2 to 8).  The result is identical either way;
  *   "spin_limit"      testing only: polls (each about 64 ns of sleep) of a
  *                     warp waiting for the other warp of its pair (wpp = 2)
  *                     before it gives up and the pair is recomputed by the

@@ -377,6 +377,7 @@ Context* get_context(int device, int* status) {
     if (const char* v = getenv("QP_F32_BLOCKS")) c->tune.blocks_per_sm = atoi(v);
     if (const char* v = getenv("QP_F32_WPP")) c->tune.wpp = atoi(v);
     if (const char* v = getenv("QP_GRAPH")) c->tune.graph = atoi(v) != 0;
+    if (const char* v = getenv("QP_HOST_CHUNKS")) c->tune.host_chunks = std::max(0, std::min(atoi(v), 16));
     if (const char* v = getenv("QP_SCRATCH_BYTES")) c->tune.scratch_bytes = atoll(v);
     Context* raw = c.get();
     g_ctx[device] = std::move(c);
@@ -419,7 +420,7 @@ std::shared_ptr<Plan> Context::plan_for(int k, const int64_t* off, int* status, 
     e = cudaMemcpy(pl->d_items.ptr, items.data(), sizeof(int2) * P, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { *status = cuda_fail(e, "plan upload"); return nullptr; }
     plans.push_back(pl);
-    if (plans.size() > 8) plans.erase(plans.begin());
+    if (plans.size() > 16) plans.erase(plans.begin());   // (a family and its ranges fit)
     return pl;
 }
 
@@ -570,7 +571,8 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         const bool wide = !layout_forced && P >= warps_full &&
                           qpk::posterior_f32_tab_copies(8, pl->max_len, C->smem_per_sm) > 1;
         const unsigned allowed = allowed_configs(P, max_strips, warps_full, wpb, C->tune, wide);
-        tkey = Context::tune_key(P, pl->max_len, pl->work_sum) ^ ((int64_t)ckpt << 62);
+        tkey = (C->tune_alias ? C->tune_alias : Context::tune_key(P, pl->max_len, pl->work_sum)) ^
+               ((int64_t)ckpt << 62);
         cfg = C->tuner[tkey].choose(allowed);
         variant = config_variant(cfg);
         W = config_wpp(cfg);
@@ -654,6 +656,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         return code;
     };
     const ResultLayout lay(P, pl->n_rows, k);
+    int64_t call_cap = 0;    // entries this call's pool and result may hold
     e = C->take_block(&own->dev_a, lay.bytes, st);
     if (e != cudaSuccess) return bail(fail(QP_ENOMEM, "result allocation (%zu bytes) failed", lay.bytes));
     own->bytes_a = lay.bytes;
@@ -668,6 +671,9 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             return bail(fail(QP_ENOMEM, "pool allocation failed"));
         C->pool_cap = (int64_t)(C->pool.bytes / sizeof(int2));
         if (f64) C->pool_cap = std::min<int64_t>(C->pool_cap, (int64_t)(C->pool64.bytes / sizeof(double)));
+        // this call's capacity: its own estimate, not the largest pool an
+        // earlier (larger) call left (the result's entry block is sized by it)
+        call_cap = std::min<int64_t>(C->pool_cap, est);
     }
 
     qpk::FamDesc fd;
@@ -700,7 +706,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     // threshold and a filter writes the result (at most n_keep entries)
     const bool ebudget = prm->entry_budget > 0;
     const int64_t n_keep = ebudget ? prm->entry_budget / (f64 ? 16 : 8) : 0;
-    auto nnz_cap_of = [&]() { return ebudget ? std::min<int64_t>(C->pool_cap, n_keep) : C->pool_cap; };
+    auto nnz_cap_of = [&]() { return ebudget ? std::min<int64_t>(call_cap, n_keep) : call_cap; };
     if (ebudget &&
         ((e = C->bud_rp.ensure(sizeof(int32_t) * pl->n_rows)) != cudaSuccess ||
          (e = C->bud_off.ensure(sizeof(int64_t) * (P + 1))) != cudaSuccess ||
@@ -712,9 +718,9 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     for (int attempt = 0;; ++attempt) {
         if (own->dev_b) { C->give_block(own->dev_b, own->bytes_b); own->dev_b = nullptr; }
         if (ebudget &&
-            ((e = C->bud_col.ensure(sizeof(int32_t) * C->pool_cap)) != cudaSuccess ||
-             (e = C->bud_val.ensure(sizeof(float) * C->pool_cap)) != cudaSuccess ||
-             (f64 && (e = C->bud_val64.ensure(sizeof(double) * C->pool_cap)) != cudaSuccess)))
+            ((e = C->bud_col.ensure(sizeof(int32_t) * call_cap)) != cudaSuccess ||
+             (e = C->bud_val.ensure(sizeof(float) * call_cap)) != cudaSuccess ||
+             (f64 && (e = C->bud_val64.ensure(sizeof(double) * call_cap)) != cudaSuccess)))
             return bail(fail(QP_ENOMEM, "entry budget scratch allocation failed"));
         const int64_t nnz_cap = nnz_cap_of();
         own->bytes_b = std::max<size_t>(ResultLayout::entry_bytes(nnz_cap, f64), 256);
@@ -723,7 +729,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         qp_result probe;
         memset(&probe, 0, sizeof probe);
         fill_result(&probe, own, lay, k, P, pl->n_rows, nnz_cap, f64, prm->precision, C->device);
-        fd.pool_cap = C->pool_cap;
+        fd.pool_cap = call_cap;
         memcpy(C->h_fam.ptr, &fd, sizeof fd);
         Pb.pool = (int2*)C->pool.ptr;
         Pb.pool64 = f64 ? (double*)C->pool64.ptr : nullptr;
@@ -794,7 +800,9 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         // events only outside the captured sequence: the whole call; the
         // kernels time themselves (Status time stamps)
         cudaEventRecord(C->ev[0], st);
-        if (C->tune.graph) {
+        // (the ranges of a host-output call run as plain launches: their shapes
+        // alternate, so a captured graph would be rebuilt on every call)
+        if (C->tune.graph && !C->tune_alias) {
             // everything the sequence's nodes hold (pointers, sizes, launch
             // shapes, kernel parameters): equal keys relaunch the cached graph
             GraphKey key;
@@ -839,7 +847,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             return bail(fail(QP_ENOMEM, "%d pair(s) tripped an FP32 range guard and need the FP64 form, whose "
                              "scratch at length %d exceeds the budget", hs.n_fallback, pl->max_len));
         if (!f64 && hs.t_f32[1] > hs.t_f32[0] && hs.t_f32[0] > 0)
-            C->tuner[tkey].record(cfg, 1e-6 * (double)(hs.t_f32[1] - hs.t_f32[0]));
+            if (!C->tune_alias) C->tuner[tkey].record(cfg, 1e-6 * (double)(hs.t_f32[1] - hs.t_f32[0]));
         if (!hs.pool_overflow) break;
         if (attempt >= 2) return bail(fail(QP_ENOMEM, "the entry pool kept overflowing"));
         // grow the pool (and the result's entry part) to what was asked for, and run again
@@ -851,6 +859,7 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             return bail(fail(QP_ENOMEM, "pool allocation (%lld entries) failed", (long long)need));
         C->pool_cap = (int64_t)(C->pool.bytes / sizeof(int2));
         if (f64) C->pool_cap = std::min<int64_t>(C->pool_cap, (int64_t)(C->pool64.bytes / sizeof(double)));
+        call_cap = std::min<int64_t>(C->pool_cap, need);
     }
 
     qp_result* r = (qp_result*)calloc(1, sizeof(qp_result));
@@ -1062,6 +1071,190 @@ void free_result(qp_result* r) {
     free(r);
 }
 
+
+// ------------------------------------------------------------------ host output in ranges
+// A large family asked for in host memory: its pairs are cut into G ranges of
+// about equal work (the linear pair order, as qp_split_pairs), each computed
+// on the device in turn; the arrays of a finished range are copied to the
+// host result on a second stream while the next range computes, so that the
+// copy of the sparse matrices (8 bytes an entry over the host link) overlaps
+// the computation instead of following it.  The result is the one
+// qp_posteriors returns in a single piece, bit for bit: a range's row
+// pointers are pair-local, its pair offsets are shifted by the entries and
+// rows of the ranges before it, and its distances fill its own pairs only.
+constexpr double kPipeCells = 2e9;       // smallest family (cells) computed in ranges for host output
+
+int host_chunks_for(const Context* C, const qp_family* f, const qp_params* prm) {
+    if (prm->precision != QP_F32_SCALED || prm->entry_budget != 0 || C->tune.host_chunks == 1) return 1;
+    double cells = 0.0, len_sum = 0.0, len_sq = 0.0;
+    for (int a = 0; a < f->k; ++a) {
+        const double L = (double)(f->offsets[a + 1] - f->offsets[a]);
+        len_sum += L;
+        len_sq += L * L;
+    }
+    cells = 0.5 * (len_sum * len_sum - len_sq);
+    const int64_t P = (int64_t)f->k * (f->k - 1) / 2;
+    int G = C->tune.host_chunks >= 2 ? C->tune.host_chunks
+          : (cells < kPipeCells ? 1 : (int)std::min(8.0, std::max(2.0, cells / 1.5e9)));
+    return (int)std::min<int64_t>(G, P);
+}
+
+int run_family_ranges(Context* C, const qp_family* f, const qp_params* prm, int G, qp_result** out) {
+    const int k = f->k;
+    const int64_t P = (int64_t)k * (k - 1) / 2;
+    std::vector<int64_t> bounds(G + 1);
+    int rc = qp_split_pairs(k, f->offsets, G, bounds.data());
+    if (rc != QP_OK) return rc;
+    cudaError_t e;
+    if (!C->copy_stream && (e = cudaStreamCreateWithFlags(&C->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "copy stream");
+    // the ranges take the launch the autotuner chose for the whole family's shape
+    {
+        auto full = C->plan_for(k, f->offsets, &rc);
+        if (!full) return rc;
+        C->tune_alias = Context::tune_key(full->n_pairs, full->max_len, full->work_sum);
+    }
+    struct Span { int64_t rows, nnz; };
+    std::vector<qp_result*> parts(G, nullptr);
+    std::vector<Span> off(G + 1, Span{0, 0});
+    // host result: fixed arrays exact, col / val at a capacity grown on demand
+    const size_t k2 = (size_t)k * k;
+    int64_t n_rows = 0;
+    for (int a = 0; a < k; ++a) n_rows += (int64_t)(f->offsets[a + 1] - f->offsets[a] + 1) * (k - 1 - a);
+    size_t o_pro = 0, o_rp, o_pno, o_mea, o_lh, o_lp, o_fl, o_d32, o_d64, o_col, fixed;
+    {
+        size_t o = 0;
+        o_pro = o; o += align256(sizeof(int64_t) * (P + 1));
+        o_rp = o; o += align256(sizeof(int32_t) * n_rows);
+        o_pno = o; o += align256(sizeof(int64_t) * (P + 1));
+        o_mea = o; o += align256(sizeof(double) * P);
+        o_lh = o; o += align256(sizeof(double) * P);
+        o_lp = o; o += align256(sizeof(double) * P);
+        o_fl = o; o += align256(sizeof(int32_t) * P);
+        o_d32 = o; o += align256(sizeof(float) * k2 * G);     // each range's distances, summed at the end
+        o_d64 = o; o += align256(sizeof(double) * k2 * G);
+        o_col = o;
+        fixed = o;
+    }
+    char* h = nullptr;
+    size_t hbytes = 0;
+    bool pinned = false;
+    int64_t cap = 0;   // entries col / val can hold
+    auto layout_bytes = [&](int64_t c) { return fixed + 2 * align256(sizeof(int32_t) * (size_t)c); };
+    auto val_at = [&](char* base, int64_t c) { return base + o_col + align256(sizeof(int32_t) * (size_t)c); };
+    auto cleanup = [&](int code) {
+        cudaStreamSynchronize(C->copy_stream);
+        for (auto* r : parts) if (r) free_result(r);
+        if (h) give_host_block(h, hbytes, pinned);
+        C->tune_alias = 0;
+        return code;
+    };
+    for (int c = 0; c < G; ++c) {
+        rc = run_family(C, f, prm, 1, &parts[c], bounds[c], bounds[c + 1]);
+        if (rc != QP_OK) return cleanup(rc);
+        qp_result* r = parts[c];
+        const int64_t need = off[c].nnz + r->nnz;
+        if (need > cap) {
+            // first range: the entries of the whole family estimated from its
+            // density per pair-cell (+12.5%); later ranges grow the block
+            int64_t want = need;
+            if (c == 0) {
+                const double frac = (double)(bounds[1] - bounds[0]) / (double)P;
+                want = (int64_t)((double)r->nnz / std::max(frac, 1e-9) * 1.125) + (1 << 20);
+            } else {
+                want = std::max<int64_t>(need + need / 8, (int64_t)((double)cap * 1.25));
+            }
+            want = ((want + (1 << 22) - 1) >> 22) << 22;   // whole 4M-entry steps: repeated calls reuse the block
+            bool pin2 = false;
+            const size_t nb = layout_bytes(want);
+            char* h2 = (char*)take_host_block(nb, &pin2);
+            if (!h2) return cleanup(fail(QP_ENOMEM, "host result allocation (%zu bytes) failed", nb));
+            if (h) {
+                cudaStreamSynchronize(C->copy_stream);
+                memcpy(h2, h, fixed + sizeof(int32_t) * (size_t)off[c].nnz);
+                memcpy(val_at(h2, want), val_at(h, cap), sizeof(float) * (size_t)off[c].nnz);
+                give_host_block(h, hbytes, pinned);
+            }
+            h = h2; hbytes = nb; pinned = pin2; cap = want;
+        }
+        const int64_t Pc = r->n_pairs, p0 = bounds[c];
+        cudaStream_t cs = C->copy_stream;
+        struct Copy { void* dst; const void* src; size_t bytes; };
+        const Copy copies[] = {
+            {h + o_pro + sizeof(int64_t) * p0, r->pair_row_off, sizeof(int64_t) * (Pc + 1)},
+            {h + o_rp + sizeof(int32_t) * off[c].rows, r->row_ptr, sizeof(int32_t) * r->n_rows},
+            {h + o_pno + sizeof(int64_t) * p0, r->pair_nnz_off, sizeof(int64_t) * (Pc + 1)},
+            {h + o_col + sizeof(int32_t) * off[c].nnz, r->col, sizeof(int32_t) * r->nnz},
+            {val_at(h, cap) + sizeof(float) * off[c].nnz, r->val, sizeof(float) * r->nnz},
+            {h + o_mea + sizeof(double) * p0, r->mea, sizeof(double) * Pc},
+            {h + o_lh + sizeof(double) * p0, r->log_z_hmm, sizeof(double) * Pc},
+            {h + o_lp + sizeof(double) * p0, r->log_z_pf, sizeof(double) * Pc},
+            {h + o_fl + sizeof(int32_t) * p0, r->pair_flags, sizeof(int32_t) * Pc},
+            {h + o_d32 + sizeof(float) * k2 * c, r->dist, sizeof(float) * k2},
+            {h + o_d64 + sizeof(double) * k2 * c, r->dist64, sizeof(double) * k2},
+        };
+        for (const Copy& x : copies)
+            if (x.bytes && (e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+                return cleanup(cuda_fail(e, "copy a range of the result to host"));
+        off[c + 1] = Span{off[c].rows + r->n_rows, off[c].nnz + r->nnz};
+    }
+    if ((e = cudaStreamSynchronize(C->copy_stream)) != cudaSuccess) return cleanup(cuda_fail(e, "copy stream"));
+    C->tune_alias = 0;
+    // offsets: each range's local offsets shifted by the ranges before it
+    int64_t* pro = (int64_t*)(h + o_pro);
+    int64_t* pno = (int64_t*)(h + o_pno);
+    for (int c = 0; c < G; ++c)
+        for (int64_t p = bounds[c]; p < bounds[c + 1]; ++p) { pro[p] += off[c].rows; pno[p] += off[c].nnz; }
+    pro[P] = off[G].rows;
+    pno[P] = off[G].nnz;
+    // distances: the ranges fill disjoint entries (zero elsewhere)
+    float* d32 = (float*)(h + o_d32);
+    double* d64 = (double*)(h + o_d64);
+    for (int c = 1; c < G; ++c)
+        for (size_t i = 0; i < k2; ++i) { d32[i] += d32[c * k2 + i]; d64[i] += d64[c * k2 + i]; }
+    qp_result* res = (qp_result*)calloc(1, sizeof(qp_result));
+    ResultOwner* own = new ResultOwner();
+    if (!res || !own) { free(res); delete own; return cleanup(fail(QP_ENOMEM, "result allocation failed")); }
+    *res = *parts[0];
+    res->on_device = 0;
+    res->n_pairs = P;
+    res->n_rows = off[G].rows;
+    res->nnz = off[G].nnz;
+    res->pair_row_off = pro;
+    res->row_ptr = (int32_t*)(h + o_rp);
+    res->pair_nnz_off = pno;
+    res->col = (int32_t*)(h + o_col);
+    res->val = (float*)val_at(h, cap);
+    res->val64 = nullptr;
+    res->dist = d32;
+    res->dist64 = d64;
+    res->mea = (double*)(h + o_mea);
+    res->log_z_hmm = (double*)(h + o_lh);
+    res->log_z_pf = (double*)(h + o_lp);
+    res->pair_flags = (int32_t*)(h + o_fl);
+    res->n_fallback = 0;
+    for (int i = 0; i < 4; ++i) res->kernel_ms[i] = 0.0;
+    bool guard = false;
+    for (auto* r : parts) {
+        res->n_fallback += r->n_fallback;
+        for (int i = 0; i < 4; ++i) res->kernel_ms[i] += r->kernel_ms[i];
+        if (!guard && r->guard_info[0]) {
+            for (int i = 0; i < 12; ++i) res->guard_info[i] = r->guard_info[i];
+            guard = true;
+        }
+    }
+    own->device = C->device;
+    own->on_device = false;
+    own->host = h;
+    own->host_bytes = hbytes;
+    own->host_pinned = pinned;
+    res->owner_ = own;
+    h = nullptr;
+    for (auto*& r : parts) { free_result(r); r = nullptr; }
+    *out = res;
+    return QP_OK;
+}
+
 }  // namespace qph
 
 // ================================================================== C ABI
@@ -1081,6 +1274,10 @@ int qp_posteriors(const qp_family* family, const qp_params* params, int32_t out_
     Context* C = get_context(params->device, &rc);
     if (!C) return rc;
     std::lock_guard<std::mutex> g(C->mu);
+    if (!out_on_device) {
+        const int G = host_chunks_for(C, family, params);
+        if (G > 1) return run_family_ranges(C, family, params, G, out);
+    }
     return run_family(C, family, params, out_on_device, out);
 }
 
@@ -1157,6 +1354,9 @@ int qp_set_option(int32_t device, const char* name, int64_t value) {
         // emission table copies in shared memory: 1, 16 (bank-sliced), or -1 automatic
         if (value > 1 && value != qpk::kTabCopies) return fail(QP_EINVAL, "tab_copies must be 1, %d or -1", qpk::kTabCopies);
         C->tune.tab_copies = value < 0 ? -1 : (value == 0 ? -1 : (int)value);
+    } else if (n == "host_chunks") {
+        // host output: pair ranges (0 automatic, 1 never, n >= 2 forced, at most 16)
+        C->tune.host_chunks = value > 0 ? (int)std::min<int64_t>(value, 16) : 0;
     } else if (n == "spin_limit") {
         // testing: polls of a wait for another warp's strip before the pair
         // is handed to the FP64 form (0 / -1: the default, about 4M)

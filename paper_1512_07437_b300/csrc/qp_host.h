@@ -76,6 +76,8 @@ struct LaunchOverride {                  // benchmark knobs (0 / -1: automatic)
     int cons_stall_test = 0;             // testing: withhold the first batch's arrival (the wait runs out)
     int spin_limit = 0;                  // testing: polls of the FP32 kernel's strip waits (0: default)
     int tab_copies = -1;                 // emission table copies (1 or kTabCopies; -1: automatic)
+    int host_chunks = 0;                 // host output: pair ranges whose copies overlap the next range's
+                                         // compute (0 automatic, 1 never, n >= 2 forced)
 };
 
 // Device bytes the kernels' scratch may take: the override, else 45% of the
@@ -144,6 +146,8 @@ struct Context {
     int f32_blocks_per_sm = 3;
     int f64_blocks_per_sm = 2;
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host output in ranges: the copies of a finished range
+    int64_t tune_alias = 0;              // when set, calls take this shape's tuned launch (and do not time)
     cudaEvent_t ev_join = nullptr;       // orders the library stream after the legacy default stream
     cudaEvent_t ev[6] = {};
     cudaGraphExec_t gexec = nullptr;     // the last captured call sequence

@@ -73,3 +73,40 @@ def test_range_rejects_bad_bounds(qp):
         with pytest.raises(qp.QpError) as e:
             qp.qp_posteriors_range(fam.residues, fam.offsets, prm, lo, hi)
         assert e.value.code == 1
+
+
+RESULT_ARRAYS = ("pair_row_off", "row_ptr", "pair_nnz_off", "col", "val", "dist", "dist64", "mea",
+                 "log_z_hmm", "log_z_pf", "pair_flags")
+
+
+@pytest.mark.parametrize("chunks,which", [(2, "c2"), (5, "c2"), (3, "growing")])
+def test_host_output_in_ranges_equals_one_piece(qp, chunks, which):
+    """Host output of a large family is computed in pair ranges, the arrays of
+    a finished range copied to host memory while the next range computes
+    (option host_chunks).  The result must equal the one-piece call bit for
+    bit.  The "growing" family (lengths rising along the pair order, every
+    cell kept) makes the first range's entry estimate too small, so the host
+    block is grown and copied over between ranges."""
+    if which == "c2":
+        fam = synth.make_family("c2", 5)
+        prm = synth.default_params(threshold=0.01)
+    else:
+        rng = np.random.Generator(np.random.PCG64(91))
+        q = synth.background()
+        seqs = ["".join(synth.ALPHABET[c] for c in rng.choice(20, size=L, p=q)) for L in range(20, 260, 20)]
+        fam = synth.family_from_strings(seqs)
+        prm = synth.default_params(threshold=1e-30)
+    try:
+        qp.qp_set_option("host_chunks", 1)
+        ref = qp.qp_posteriors(fam.residues, fam.offsets, prm, out_on_device=False)
+        qp.qp_set_option("host_chunks", chunks)
+        got = qp.qp_posteriors(fam.residues, fam.offsets, prm, out_on_device=False)
+    finally:
+        qp.qp_set_option("host_chunks", 0)
+    assert (got.n_pairs, got.n_rows, got.nnz) == (ref.n_pairs, ref.n_rows, ref.nnz)
+    for name in RESULT_ARRAYS:
+        a, b = np.asarray(got.array(name)), np.asarray(ref.array(name))
+        assert a.dtype == b.dtype and a.shape == b.shape and a.tobytes() == b.tobytes(), name
+    assert got.n_fallback == ref.n_fallback
+    got.free()
+    ref.free()
