@@ -16,7 +16,9 @@ the p50/p99 family latency of the serving loop.
           flushed (256 MiB write) before every step, outside the timed window.
   e2e   : host to host through the public API: residues from pinned host
           memory, qp_posteriors with host output (CSR, distances, MEA scores,
-          log totals and flags all copied back to host memory); wall time.
+          log totals and flags all copied back to host memory; the library
+          overlaps the copies of a large family with its computation by
+          running it in pair ranges); wall time.
   e2e_csr_on_device : the same with the CSR left on the device and only the
           distance matrix read back (the guide tree's input).
   latency_ms / serving : the serving loop (qp_server_*: memory-admitted,
