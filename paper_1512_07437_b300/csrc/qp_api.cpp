@@ -1083,6 +1083,7 @@ void free_result(qp_result* r) {
 // pointers are pair-local, its pair offsets are shifted by the entries and
 // rows of the ranges before it, and its distances fill its own pairs only.
 constexpr double kPipeCells = 2e9;       // smallest family (cells) computed in ranges for host output
+constexpr double kRangeRatio = 0.7;      // work of a range over the one before it
 
 int host_chunks_for(const Context* C, const qp_family* f, const qp_params* prm) {
     if (prm->precision != QP_F32_SCALED || prm->entry_budget != 0 || C->tune.host_chunks == 1) return 1;
@@ -1102,9 +1103,33 @@ int host_chunks_for(const Context* C, const qp_family* f, const qp_params* prm) 
 int run_family_ranges(Context* C, const qp_family* f, const qp_params* prm, int G, qp_result** out) {
     const int k = f->k;
     const int64_t P = (int64_t)k * (k - 1) / 2;
+    // ranges shrinking by kRangeRatio along the pair order: a range's copy
+    // (about 0.7 of its compute time at C3's density) then fits under the
+    // next range's compute, and the last copy, which nothing hides, is short
     std::vector<int64_t> bounds(G + 1);
-    int rc = qp_split_pairs(k, f->offsets, G, bounds.data());
-    if (rc != QP_OK) return rc;
+    {
+        std::vector<double> cum(P + 1);
+        cum[0] = 0.0;
+        int64_t q = 0;
+        for (int a = 0; a < k; ++a)
+            for (int b = a + 1; b < k; ++b, ++q)
+                cum[q + 1] = cum[q] + (double)(f->offsets[a + 1] - f->offsets[a]) * (double)(f->offsets[b + 1] - f->offsets[b]);
+        const double total = cum[P];
+        const double norm = (1.0 - std::pow(kRangeRatio, G)) / (1.0 - kRangeRatio);
+        bounds[0] = 0;
+        bounds[G] = P;
+        double acc = 0.0, w = 1.0;
+        for (int c = 1; c < G; ++c) {
+            acc += w / norm;
+            w *= kRangeRatio;
+            // the first boundary whose prefix work reaches the target, every range non-empty
+            int64_t b = std::lower_bound(cum.begin(), cum.end(), acc * total) - cum.begin();
+            b = std::max<int64_t>(b, bounds[c - 1] + 1);
+            b = std::min<int64_t>(b, P - (G - c));
+            bounds[c] = b;
+        }
+    }
+    int rc = QP_OK;
     cudaError_t e;
     if (!C->copy_stream && (e = cudaStreamCreateWithFlags(&C->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "copy stream");
@@ -1131,8 +1156,8 @@ int run_family_ranges(Context* C, const qp_family* f, const qp_params* prm, int 
         o_lh = o; o += align256(sizeof(double) * P);
         o_lp = o; o += align256(sizeof(double) * P);
         o_fl = o; o += align256(sizeof(int32_t) * P);
-        o_d32 = o; o += align256(sizeof(float) * k2 * G);     // each range's distances, summed at the end
-        o_d64 = o; o += align256(sizeof(double) * k2 * G);
+        o_d32 = o; o += align256(sizeof(float) * k2);
+        o_d64 = o; o += align256(sizeof(double) * k2);
         o_col = o;
         fixed = o;
     }
@@ -1190,8 +1215,6 @@ int run_family_ranges(Context* C, const qp_family* f, const qp_params* prm, int 
             {h + o_lh + sizeof(double) * p0, r->log_z_hmm, sizeof(double) * Pc},
             {h + o_lp + sizeof(double) * p0, r->log_z_pf, sizeof(double) * Pc},
             {h + o_fl + sizeof(int32_t) * p0, r->pair_flags, sizeof(int32_t) * Pc},
-            {h + o_d32 + sizeof(float) * k2 * c, r->dist, sizeof(float) * k2},
-            {h + o_d64 + sizeof(double) * k2 * c, r->dist64, sizeof(double) * k2},
         };
         for (const Copy& x : copies)
             if (x.bytes && (e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
@@ -1207,11 +1230,23 @@ int run_family_ranges(Context* C, const qp_family* f, const qp_params* prm, int 
         for (int64_t p = bounds[c]; p < bounds[c + 1]; ++p) { pro[p] += off[c].rows; pno[p] += off[c].nnz; }
     pro[P] = off[G].rows;
     pno[P] = off[G].nnz;
-    // distances: the ranges fill disjoint entries (zero elsewhere)
+    // distances from the MEA scores: d = 1 - A / min(m, n), the kernels'
+    // expression in the same FP64 operations, so the values are the same bits
     float* d32 = (float*)(h + o_d32);
     double* d64 = (double*)(h + o_d64);
-    for (int c = 1; c < G; ++c)
-        for (size_t i = 0; i < k2; ++i) { d32[i] += d32[c * k2 + i]; d64[i] += d64[c * k2 + i]; }
+    memset(d32, 0, sizeof(float) * k2);
+    memset(d64, 0, sizeof(double) * k2);
+    {
+        const double* mea = (const double*)(h + o_mea);
+        int64_t q = 0;
+        for (int a = 0; a < k; ++a)
+            for (int b = a + 1; b < k; ++b, ++q) {
+                const int64_t la = f->offsets[a + 1] - f->offsets[a], lb = f->offsets[b + 1] - f->offsets[b];
+                const double d = 1.0 - mea[q] / (double)std::min(la, lb);
+                d64[(size_t)a * k + b] = d64[(size_t)b * k + a] = d;
+                d32[(size_t)a * k + b] = d32[(size_t)b * k + a] = (float)d;
+            }
+    }
     qp_result* res = (qp_result*)calloc(1, sizeof(qp_result));
     ResultOwner* own = new ResultOwner();
     if (!res || !own) { free(res); delete own; return cleanup(fail(QP_ENOMEM, "result allocation failed")); }
