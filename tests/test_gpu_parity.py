@@ -1,7 +1,7 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Tolerances: FP32 scaled form <= 1e-5 on every posterior and distance (the
-spec bar); FP64 plain form <= 1e-9.  Sparse patterns must match
+stage's accuracy bar); FP64 plain form <= 1e-9.  Sparse patterns must match
 wherever |P - theta| > 1e-5.  FP32 results must come from the FP32 kernel:
 the tests assert that no pair was handed to the FP64 form unless stated.
 """
