@@ -371,7 +371,7 @@ Context* get_context(int device, int* status) {
     if (e != cudaSuccess) { *status = cuda_fail(e, "cudaEventCreate"); return nullptr; }
     int bps64 = 0;
     qpk::posterior_f64_occupancy(&bps64);
-    c->f64_blocks_per_sm = std::max(1, std::min(bps64, 2));
+    c->f64_blocks_per_sm = std::max(1, std::min(bps64, 4));
     if (const char* v = getenv("QP_F32_VARIANT")) c->tune.variant = atoi(v);
     if (const char* v = getenv("QP_F32_CKPT")) c->tune.ckpt = atoi(v);
     if (const char* v = getenv("QP_F32_BLOCKS")) c->tune.blocks_per_sm = atoi(v);

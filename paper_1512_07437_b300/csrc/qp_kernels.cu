@@ -195,7 +195,7 @@ cudaError_t launch_posterior_f32(const Problem& P, int grid, int warps_per_block
 // its readers bring it to their own units with one power of two per operand
 // (exact), so each diagonal needs one block-wide maximum and one barrier.
 // The stored backward values carry the units they were stored in.
-constexpr int kF64Threads = 256;
+constexpr int kF64Threads = 128;
 constexpr int kF64Warps = kF64Threads / 32;
 
 // floor(log2 v) for a positive normal double, 0 for 0 (exponent field only)
