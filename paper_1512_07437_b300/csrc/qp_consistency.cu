@@ -26,11 +26,13 @@
 //   staged form (default, T <= 256):
 //   k_cons_stats      the largest value and row sum (the fixed-point unit);
 //   k_cons_bands      per row, the column band of the rows up to / from it;
-//   k_cons_relax_staged  a CTA per row chunk of a pair: warp 0 stages the
-//                     selected z (A's chunk entries, the band of B's rows
-//                     they reach) by TMA bulk copies into two buffers; the
-//                     products go into a dense 32-bit fixed-point
-//                     accumulator in shared memory (see the kernel);
+//   k_cons_relax_staged  a CTA per row chunk of a pair: a producer warp
+//                     stages the selected z (A's chunk entries, the band of
+//                     B's rows they reach) by TMA bulk copies into two
+//                     buffers, each refilled as soon as every warp is done
+//                     with it; the products go into a dense 32-bit
+//                     fixed-point accumulator in shared memory (see the
+//                     kernel);
 //   row form (T > 256, or values too large for the staged unit):
 //   k_cons_relax      a CTA per pair, warps over the rows of x: a dense
 //                     accumulator row in shared memory, a Gustavson product
@@ -493,7 +495,7 @@ constexpr int kStBatch = 32;                // z per stage buffer at most (a lan
 constexpr int kMinUnit = 21;                // coarsest fixed-point unit (2^-21) the staged form accepts by default
 constexpr int kStGroup = 1;                 // threads per A entry along a row of B
 constexpr int kStMaxRows = 1024;            // rows of a chunk at most
-constexpr int kStMinRows = 16;              // rows of the longest sequence a chunk should hold (CTAs per SM)
+constexpr int kStMinRows = 32;              // rows of the longest sequence a chunk should hold (CTAs per SM)
 constexpr int kStSpin = 1 << 16;            // waits on a stage buffer's barrier before the call is failed
 constexpr unsigned kStSuspendNs = 20000;    // longest suspension of one wait (ns)
 
@@ -594,12 +596,16 @@ __device__ __forceinline__ int bulk_span(const void* g, int bytes, int* head) {
 }
 
 // Relaxation of rows i0 .. i1 - 1 of one pair (a work item) with the
-// selected z staged in shared memory.  Warp 0 produces: its lanes take one
-// z each of the next batch, a warp scan packs as many as fit into a stage
+// selected z staged in shared memory.  A producer warp's lanes take one z
+// each of the next batch, a warp scan packs as many as fit into a stage
 // buffer, and each lane issues the TMA bulk copies of its z (A's entries of
 // the chunk, B's row pointers and entries), completing on the buffer's
 // barrier; a z larger than a buffer is read from global memory.  Two
-// buffers: the next batch lands while this one is multiplied.  The batch's
+// buffers: the next batch lands while this one is multiplied.  Warp 0
+// issues the first two batches; after that the last warp to finish a batch
+// issues the batch after next into its buffer, so no warp waits at a
+// CTA-wide barrier between batches (a warp waits only for a batch to land).
+// The batch's
 // A entries (t, v) are numbered through, G threads per entry (the key of an
 // entry holds its row, so no search is needed); the threads of an entry run
 // along row t of B and add v * S_zy(t, j) into the chunk's dense
@@ -624,7 +630,12 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     __shared__ int bnext[2];                        // next A entry of the batch a warp takes
     __shared__ int bps[2][kStBatch + 1];            // first A entry of each z of a batch
     __shared__ int s_nissued;                       // batches issued so far
+    __shared__ int bdone[2];                        // warps done with the buffer's current batch
+    __shared__ int s_zq;                            // first z not yet issued
+    __shared__ int s_bail;                          // a stage wait ran out: every warp leaves
     if (*tree_status) return;
+    // a CTA whose stage wait ran out has failed the call: the rest leave at once
+    if (*(volatile int32_t*)stage_err) return;
     if (smem_u32(smem) & 15) {                       // bulk copies need 16-byte aligned buffers
         if (threadIdx.x == 0) atomicExch(stage_err, 1);
         return;
@@ -672,7 +683,9 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         bnext[0] = bnext[1] = 0;
+        bdone[0] = bdone[1] = 0;
         s_nissued = 0;
+        s_bail = 0;
     }
     for (int v = lo + tid; v < hi; v += nthr) {
         const int z = in.leaf_at[v];
@@ -748,10 +761,10 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         return cnt;
     };
 
-    int zq = 0;                                      // producer: first z not yet issued
     if (wid == 0 && nz > 0) {
-        zq = issue(0, 0);
+        int zq = issue(0, 0);
         if (zq < nz) zq += issue(zq, 1);
+        if (lane == 0) s_zq = zq;
     }
     for (int c = tid; c < rc * n; c += nthr) acc[c] = 0u;
     __syncthreads();
@@ -763,13 +776,21 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     for (int zs = 0, b = 0; zs < nz; ++b) {
         const int s = b & 1;
         bool ok = false;
-        for (int it = 0; it < sc.wait_polls && !ok; ++it) ok = mbar_try_wait(&bars[s], (unsigned)((b >> 1) & 1));
-        ok = __all_sync(FULLM, ok);                  // a warp skips the batch together if it did not land
+        for (int it = 0; it < sc.wait_polls && !ok; ++it) {
+            ok = mbar_try_wait(&bars[s], (unsigned)((b >> 1) & 1));
+            if (!ok && *(volatile int*)&s_bail) break;   // another warp gave up
+        }
+        ok = __all_sync(FULLM, ok);                  // one decision for the warp
+        if (!ok) {
+            if (lane == 0) atomicExch(&s_bail, 1);
+            bail = b;
+            break;
+        }
         const int cnt = bcount[s];
         const bool glob = bglob[s] != 0;
         const int* ps = bps[s];
         const SView* vt = views + s * kStBatch;
-        const int na_all = ok ? ps[cnt] : 0;
+        const int na_all = ps[cnt];
         // the batch's A entries, numbered through its z, taken kGrab at a
         // time by whichever warp is free
         for (;;) {
@@ -823,24 +844,43 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
             }
         }
         zs += cnt;
-        // buffer s is free again; one decision for the whole CTA: a batch
-        // that did not land ends it
-        if (__syncthreads_or(!ok)) { bail = b; break; }
-        if (tid == 0) bnext[s] = 0;                  // (its next batch starts after another barrier)
-        if (wid == 0 && zq < nz) {
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            zq += issue(zq, s);
+        // this warp is done with buffer s; the last warp to finish the batch
+        // refills it with the batch after next while the others go on with
+        // the next one (no CTA-wide barrier per batch).  Fences order the
+        // warps' reads of the buffer before the refill's copies.
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&bdone[s], 1) == nwarps - 1;
+        }
+        if (__shfl_sync(FULLM, last, 0)) {
+            __threadfence_block();
+            const int zq = *(volatile int*)&s_zq;
+            if (lane == 0) { bdone[s] = 0; bnext[s] = 0; }
+            if (zq < nz) {
+                __syncwarp();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                const int c = issue(zq, s);
+                if (lane == 0) s_zq = zq + c;
+            }
+            __syncwarp();
         }
     }
-    if (bail >= 0) {
+    if (__syncthreads_or(bail >= 0)) {
         // the call fails; copies still in flight land in this CTA's buffers:
-        // wait for them (again bounded), then leave
-        if (tid == 0) atomicExch(stage_err, 1);
-        for (int bb = bail; bb < s_nissued; ++bb) {
-            bool done = false;
-            for (int it = 0; it < sc.wait_polls && !done; ++it)
-                done = mbar_try_wait(&bars[bb & 1], (unsigned)((bb >> 1) & 1));
+        // wait (again bounded) for the last batch issued into each buffer
+        // (a later batch is only issued once the earlier one has landed),
+        // then leave
+        if (tid == 0) {
+            atomicExch(stage_err, 1);
+            for (int bb = s_nissued - 1; bb >= 0 && bb >= s_nissued - 2; --bb) {
+                bool done = false;
+                for (int it = 0; it < sc.wait_polls && !done; ++it)
+                    done = mbar_try_wait(&bars[bb & 1], (unsigned)((bb >> 1) & 1));
+            }
         }
+        __syncthreads();
         return;
     }
 
@@ -1071,8 +1111,11 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
         return c;
     };
     // two CTAs per SM, unless their accumulators would hold fewer than
-    // kStMinRows rows of the longest sequence (long sequences: measured faster
-    // with one CTA and longer chunks)
+    // kStMinRows rows of the longest sequence: shorter chunks re-stage more of
+    // every z's band and repeat the per-chunk work more often.  Measured: 64
+    // sequences of 200-400 (36 rows with two CTAs) run faster with two; 500
+    // of 150-500 (26 rows) and 100 of 2000-4000 (3) with one CTA and chunks
+    // twice as long
     int st_ctas = C->tune.cons_ctas_per_sm;
     if (st_ctas <= 0) st_ctas = stage_cfg(2).acc_cells / maxlen >= kStMinRows ? 2 : 1;
     if (staged) {
