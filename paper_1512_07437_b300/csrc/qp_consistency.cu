@@ -633,6 +633,7 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     __shared__ int bdone[2];                        // warps done with the buffer's current batch
     __shared__ int s_zq;                            // first z not yet issued
     __shared__ int s_bail;                          // a stage wait ran out: every warp leaves
+    __shared__ int s_clo, s_chi;                    // columns the chunk's sums can reach
     if (*tree_status) return;
     // a CTA whose stage wait ran out has failed the call: the rest leave at once
     if (*(volatile int32_t*)stage_err) return;
@@ -686,7 +687,11 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         bdone[0] = bdone[1] = 0;
         s_nissued = 0;
         s_bail = 0;
+        const MatRef own = mat_of(in, x, y);
+        s_clo = own.band[i0] & 0xffff;
+        s_chi = own.band[i1 - 1] >> 16;
     }
+    int cmn = 0x7fffffff, cmx = -1;                  // columns of this thread's staged bands
     for (int v = lo + tid; v < hi; v += nthr) {
         const int z = in.leaf_at[v];
         if (z == x || z == y) continue;
@@ -701,12 +706,25 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
             const int t0 = A.band[i0] & 0xffff, t1 = (A.band[i1 - 1] >> 16) + 1;
             e.bt0 = t0; e.nbr = t1 - t0;
             e.b0 = B.rp[t0]; e.nb = B.rp[t1] - e.b0;
+            cmn = min(cmn, B.band[t0] & 0xffff);
+            cmx = max(cmx, B.band[t1 - 1] >> 16);
         }
         e.brp = B.rp + e.bt0;
         e.bcv = B.cv + e.b0;
         zt[slot] = e;
     }
     __syncthreads();
+    // the columns the chunk's sums can reach: those of its own rows and of
+    // every staged band of B (nothing outside them is zeroed or scanned)
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        cmn = min(cmn, __shfl_xor_sync(FULLM, cmn, d));
+        cmx = max(cmx, __shfl_xor_sync(FULLM, cmx, d));
+    }
+    if (lane == 0 && cmx >= 0) {
+        atomicMin(&s_clo, cmn);
+        atomicMax(&s_chi, cmx);
+    }
 
     // producer (warp 0): the batch of z starting at zs into buffer s;
     // returns its size (the same in every lane).  A z larger than a buffer
@@ -766,7 +784,11 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         if (zq < nz) zq += issue(zq, 1);
         if (lane == 0) s_zq = zq;
     }
-    for (int c = tid; c < rc * n; c += nthr) acc[c] = 0u;
+    __syncthreads();
+    // (a threshold that rounds to 0 in FP32 keeps every cell)
+    const int clo = theta > 0.f ? max(s_clo, 0) : 0, chi = theta > 0.f ? min(s_chi, n - 1) : n - 1;
+    for (int r = wid; r < rc; r += nwarps)
+        for (int j = clo + lane; j <= chi; j += 32) acc[r * n + j] = 0u;
     __syncthreads();
 
     unsigned long long fmas = 0;
@@ -900,9 +922,9 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
     for (int r = wid; r < rc; r += nwarps) {
         const unsigned* ar = acc + r * n;
         int kept = 0;
-        for (int j0 = 0; j0 < n; j0 += 32) {
+        for (int j0 = clo; j0 <= chi; j0 += 32) {
             const int j = j0 + lane;
-            const bool keep = j < n && (__uint2float_rn(ar[j]) * inv_unit) * scale >= theta;
+            const bool keep = j <= chi && (__uint2float_rn(ar[j]) * inv_unit) * scale >= theta;
             kept += __popc(__ballot_sync(FULLM, keep));
         }
         if (lane == 0) rcnt[r] = kept;
@@ -938,10 +960,10 @@ __global__ void __launch_bounds__(kStThreads, MINB) k_cons_relax_staged(ConsIn i
         const int64_t off = (int64_t)base + rcnt[r];
         int wpos = 0;
         const unsigned below = (1u << lane) - 1u;
-        for (int j0 = 0; j0 < n; j0 += 32) {
+        for (int j0 = clo; j0 <= chi; j0 += 32) {
             const int j = j0 + lane;
-            const float v = j < n ? (__uint2float_rn(ar[j]) * inv_unit) * scale : 0.0f;
-            const bool keep = j < n && v >= theta;
+            const float v = j <= chi ? (__uint2float_rn(ar[j]) * inv_unit) * scale : 0.0f;
+            const bool keep = j <= chi && v >= theta;
             const unsigned mk = __ballot_sync(FULLM, keep);
             if (keep && base != ~0ull) out.pool[off + wpos + __popc(mk & below)] = make_int2(j, __float_as_int(v));
             wpos += __popc(mk);
