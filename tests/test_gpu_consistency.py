@@ -72,7 +72,8 @@ def forms(qp):
     """Restores the automatic choice of the relaxation's form after a test
     that forces one."""
     yield
-    for name in ("cons_form", "cons_chunk_rows", "cons_min_unit", "cons_wait_polls", "cons_stall_test"):
+    for name in ("cons_form", "cons_chunk_rows", "cons_min_unit", "cons_wait_polls", "cons_stall_test",
+                 "cons_ctas_per_sm"):
         qp.qp_set_option(name, -1 if name == "cons_form" else 0, device=0)
 
 
@@ -238,6 +239,32 @@ def test_forms_agree_beyond_the_stage_buffers(qp, forms):
     assert fma["row"] == fma["staged"] == fma["chunked"] > 0
     for name in ("staged", "chunked"):
         assert _compare_entries(got["row"], got[name], 2e-3, 1e-6) <= 1e-6, name
+
+
+def test_staged_launch_shapes_are_bit_identical(qp, forms):
+    """The staged form with one or two CTAs per SM (chunks of different
+    heights) and with 3-row chunks gives the same result bit for bit: every
+    sum is exact in the fixed-point unit, whatever the chunking, the order of
+    the products, or which warp refills a stage buffer."""
+    import torch
+    fam = synth.star_family(41, 24, (150, 420), 0.35)
+    prm = synth.default_params(threshold=0.01)
+    post = qp.qp_posteriors(torch.from_numpy(fam.residues).cuda(), fam.offsets, prm, device=0, out_on_device=True)
+    merges = synth.random_guide_tree(8, fam.k)
+    got = {}
+    for name, ctas, chunk in (("two", 2, 0), ("one", 1, 0), ("rows3", 2, 3)):
+        qp.qp_set_option("cons_form", 1)
+        qp.qp_set_option("cons_ctas_per_sm", ctas)
+        qp.qp_set_option("cons_chunk_rows", chunk)
+        r = qp.qp_consistency(post, fam.offsets, merges, T=200, threshold=0.01)
+        assert qp.qp_get_counter("consistency_form") == 1
+        got[name] = {a: host(r.array(a)).copy() for a in ("pair_row_off", "row_ptr", "pair_nnz_off", "col", "val")}
+        r.free()
+    post.free()
+    assert got["two"]["col"].size > 0
+    for name in ("one", "rows3"):
+        for a in got["two"]:
+            assert np.array_equal(got["two"][a], got[name][a]), (name, a)
 
 
 def test_staged_form_hands_a_coarse_unit_to_the_row_form(qp, small, forms):
