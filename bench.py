@@ -69,8 +69,9 @@ CONFIG_DESC = {
 }
 # the sources of k_posterior_f32: a DRAM-traffic figure in profiles/ holds
 # only while they are unchanged
-KERNEL_SOURCES = ["paper_1512_07437_b300/csrc/qp_kernels.cu", "paper_1512_07437_b300/csrc/qp_f32.cuh",
-                  "paper_1512_07437_b300/csrc/qp_internal.h"]
+# the translation units of k_posterior_f32 (its traffic record is keyed to them)
+KERNEL_SOURCES = ["paper_1512_07437_b300/csrc/qp_f32.cuh", "paper_1512_07437_b300/csrc/qp_f32_w1.cu",
+                  "paper_1512_07437_b300/csrc/qp_f32_w2.cu", "paper_1512_07437_b300/csrc/qp_internal.h"]
 LOAD_FRACTION = 0.70           # offered load of the serving load point, of measured capacity
 METRIC = "posterior-stage GCUPS and p50/p99 family latency, FP32 batched vs plain FP64"
 
