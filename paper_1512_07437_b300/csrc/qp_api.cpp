@@ -737,11 +737,14 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
         // timed: CUDA events around the posterior kernels (plain launches only:
         // a captured sequence carries none)
         bool timed = false;
+        bool start_in_enqueue = false;   // plain launches: the start event follows the input copies
         auto enqueue = [&]() -> cudaError_t {
             cudaError_t x;
             if ((x = cudaMemcpyAsync(C->off.ptr, C->h_off.ptr, sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-                (x = cudaMemcpyAsync(C->fam.ptr, C->h_fam.ptr, sizeof fd, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-                (x = cudaMemsetAsync(C->status.ptr, 0, sizeof(qpk::Status), st)) != cudaSuccess ||
+                (x = cudaMemcpyAsync(C->fam.ptr, C->h_fam.ptr, sizeof fd, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return x;
+            if (start_in_enqueue) cudaEventRecord(C->ev[0], st);
+            if ((x = cudaMemsetAsync(C->status.ptr, 0, sizeof(qpk::Status), st)) != cudaSuccess ||
                 (x = cudaMemcpyAsync(A + lay.o_pro, pl->d_row_off.ptr, sizeof(int64_t) * (P + 1), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
                 (x = cudaMemsetAsync(A + lay.o_dist, 0, sizeof(float) * (size_t)k * k, st)) != cudaSuccess ||
                 (x = cudaMemsetAsync(A + lay.o_d64, 0, sizeof(double) * (size_t)k * k, st)) != cudaSuccess ||
@@ -798,8 +801,16 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
             return cudaSuccess;
         };
         // events only outside the captured sequence: the whole call; the
-        // kernels time themselves (Status time stamps)
-        cudaEventRecord(C->ev[0], st);
+        // kernels time themselves (Status time stamps).  Plain launches record
+        // the start after their first input copies.  Measured on B300: when the
+        // event record was the first command on the stream after the previous
+        // range's synchronisation, while the copy stream still held that
+        // range's device-to-host copies, the stream waited for those copies
+        // (each range of a host-output call with device-resident residues
+        // took about 13 ms longer: 105 against 68 ms for the 500-sequence
+        // family); with a copy first it did not.
+        if (C->tune.graph && !C->tune_alias) cudaEventRecord(C->ev[0], st);
+        else start_in_enqueue = true;
         // (the ranges of a host-output call run as plain launches: their shapes
         // alternate, so a captured graph would be rebuilt on every call)
         if (C->tune.graph && !C->tune_alias) {
