@@ -496,6 +496,7 @@ constexpr int kMinUnit = 21;                // coarsest fixed-point unit (2^-21)
 constexpr int kStGroup = 1;                 // threads per A entry along a row of B
 constexpr int kStMaxRows = 1024;            // rows of a chunk at most
 constexpr int kStMinRows = 32;              // rows of the longest sequence a chunk should hold (CTAs per SM)
+constexpr int kStLongRows = 16;             // below this many rows per chunk, smaller stage buffers
 constexpr int kStSpin = 1 << 16;            // waits on a stage buffer's barrier before the call is failed
 constexpr unsigned kStSuspendNs = 20000;    // longest suspension of one wait (ns)
 
@@ -1122,11 +1123,11 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     // shared memory of a CTA of the staged form with `ctas` CTAs per SM: z
     // table, views, two stage buffers, accumulator rows, row counts (at most
     // kStMaxRows rows per chunk); less the static shared memory and a margin
-    auto stage_cfg = [&](int ctas) {
+    auto stage_cfg = [&](int ctas, int slot_div) {
         StageCfg c{};
         const int per_cta = std::min(C->smem_optin, C->smem_per_sm / ctas - 1024) - 1024;
         c.ztab = std::max(1, std::min(cp->T, k));
-        c.slot_bytes = (per_cta / 5) & ~15;
+        c.slot_bytes = (per_cta / slot_div) & ~15;
         const int fixed = (int)(sizeof(ZEnt) * c.ztab + sizeof(SView) * 2 * kStBatch) + 2 * c.slot_bytes +
                           4 * kStMaxRows;
         c.acc_cells = (per_cta - fixed) / 4;
@@ -1139,9 +1140,16 @@ extern "C" int qp_consistency(const qp_result* post, const int64_t* offsets, con
     // of 150-500 (26 rows) and 100 of 2000-4000 (3) with one CTA and chunks
     // twice as long
     int st_ctas = C->tune.cons_ctas_per_sm;
-    if (st_ctas <= 0) st_ctas = stage_cfg(2).acc_cells / maxlen >= kStMinRows ? 2 : 1;
+    if (st_ctas <= 0) st_ctas = stage_cfg(2, 5).acc_cells / maxlen >= kStMinRows ? 2 : 1;
+    // each stage buffer a fifth of the CTA's shared memory, or an eighth when
+    // the accumulator would otherwise hold fewer than kStLongRows rows of the
+    // longest sequence: longer chunks then gain more than smaller batches
+    // cost.  Measured: 100 sequences of 2000-4000 (7.6 rows) 253 -> 232 ms;
+    // 500 of 150-500 (94 rows) keep a fifth (277 ms with an eighth, 198 with
+    // a fifth)
+    const int slot_div = stage_cfg(st_ctas, 5).acc_cells / maxlen >= kStLongRows ? 5 : 8;
     if (staged) {
-        sc = stage_cfg(st_ctas);
+        sc = stage_cfg(st_ctas, slot_div);
         sc.wait_polls = C->tune.cons_wait_polls > 0 ? C->tune.cons_wait_polls : kStSpin;
         sc.stall_first = C->tune.cons_stall_test ? 1 : 0;
         if (sc.acc_cells < maxlen) staged = false;
