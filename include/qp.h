@@ -340,14 +340,15 @@ void qp_server_destroy(qp_server* server);
  *                     x per CTA (0: as many as the shared memory holds);
  *   "cons_ctas_per_sm" qp_consistency staged form: CTAs per SM (1 or 2;
  *                     the shared memory is split between them; automatic: 2
- *                     unless their accumulators would hold fewer than 16
+ *                     unless their accumulators would hold fewer than 32
  *                     rows of the longest sequence);
  *   "cons_wait_polls" qp_consistency staged form: waits (each suspends the
  *                     thread for up to 20 us) on a stage buffer's barrier
- *                     before the CTA gives up and the call fails with
- *                     QP_ECUDA (default 65536, about a second);
+ *                     before a warp gives up; its CTA then leaves, CTAs
+ *                     that start later leave at once, and the call fails
+ *                     with QP_ECUDA (default 65536, about a second);
  *   "cons_stall_test" testing only: 1 withholds the first batch's arrival,
- *                     so every CTA's first wait runs out (the call fails with
+ *                     so the first waits run out (the call fails with
  *                     QP_ECUDA and the device stays usable);
  *   "tab_copies"      copies of the emission table each block keeps in
  *                     shared memory: 16 (bank-sliced: lane l reads copy
