@@ -79,14 +79,16 @@ RESULT_ARRAYS = ("pair_row_off", "row_ptr", "pair_nnz_off", "col", "val", "dist"
                  "log_z_hmm", "log_z_pf", "pair_flags")
 
 
-@pytest.mark.parametrize("chunks,which", [(2, "c2"), (5, "c2"), (3, "growing")])
-def test_host_output_in_ranges_equals_one_piece(qp, chunks, which):
+@pytest.mark.parametrize("chunks,which,on_device", [(2, "c2", False), (5, "c2", False), (3, "growing", False),
+                                                     (4, "c2", True)])
+def test_host_output_in_ranges_equals_one_piece(qp, chunks, which, on_device):
     """Host output of a large family is computed in pair ranges, the arrays of
     a finished range copied to host memory while the next range computes
     (option host_chunks).  The result must equal the one-piece call bit for
     bit.  The "growing" family (lengths rising along the pair order, every
     cell kept) makes the first range's entry estimate too small, so the host
-    block is grown and copied over between ranges."""
+    block is grown and copied over between ranges.  One case passes the
+    residues already on the device (no upload starts a range)."""
     if which == "c2":
         fam = synth.make_family("c2", 5)
         prm = synth.default_params(threshold=0.01)
@@ -96,11 +98,15 @@ def test_host_output_in_ranges_equals_one_piece(qp, chunks, which):
         seqs = ["".join(synth.ALPHABET[c] for c in rng.choice(20, size=L, p=q)) for L in range(20, 260, 20)]
         fam = synth.family_from_strings(seqs)
         prm = synth.default_params(threshold=1e-30)
+    res = fam.residues
+    if on_device:
+        import torch
+        res = torch.from_numpy(fam.residues).cuda()
     try:
         qp.qp_set_option("host_chunks", 1)
         ref = qp.qp_posteriors(fam.residues, fam.offsets, prm, out_on_device=False)
         qp.qp_set_option("host_chunks", chunks)
-        got = qp.qp_posteriors(fam.residues, fam.offsets, prm, out_on_device=False)
+        got = qp.qp_posteriors(res, fam.offsets, prm, out_on_device=False)
     finally:
         qp.qp_set_option("host_chunks", 0)
     assert (got.n_pairs, got.n_rows, got.nnz) == (ref.n_pairs, ref.n_rows, ref.nnz)
