@@ -241,6 +241,31 @@ def test_forms_agree_beyond_the_stage_buffers(qp, forms):
         assert _compare_entries(got["row"], got[name], 2e-3, 1e-6) <= 1e-6, name
 
 
+def test_forms_agree_on_long_sequences(qp, forms):
+    """Sequences of 2000-2600 residues: one CTA's accumulator holds fewer
+    than 16 rows of the longest, so the staged form takes stage buffers of
+    an eighth of its shared memory and reads more z from global memory.  It
+    agrees with the row form within 1e-6 (both sum the same products in
+    fixed point) and counts the same multiply-adds."""
+    import torch
+    fam = synth.star_family(29, 6, (2000, 2600), 0.3)
+    prm = synth.default_params(threshold=0.01)
+    post = qp.qp_posteriors(torch.from_numpy(fam.residues).cuda(), fam.offsets, prm, device=0, out_on_device=True)
+    merges = synth.random_guide_tree(3, fam.k)
+    lens = [int(v) for v in fam.lengths]
+    got, fma = {}, {}
+    for name, form in (("row", 0), ("staged", 1)):
+        qp.qp_set_option("cons_form", form)
+        r = qp.qp_consistency(post, fam.offsets, merges, T=200, threshold=0.01, out_on_device=True)
+        assert qp.qp_get_counter("consistency_form") == form
+        fma[name] = qp.qp_get_counter("consistency_fma")
+        got[name] = _entries(r, fam.k, lens)
+        r.free()
+    post.free()
+    assert fma["row"] == fma["staged"] > 0
+    assert _compare_entries(got["row"], got["staged"], 0.01, 1e-6) <= 1e-6
+
+
 def test_staged_launch_shapes_are_bit_identical(qp, forms):
     """The staged form with one or two CTAs per SM (chunks of different
     heights) and with 3-row chunks gives the same result bit for bit: every
