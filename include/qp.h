@@ -188,6 +188,10 @@ typedef struct qp_result {
  * out_on_device).  With host output a large family is computed in pair
  * ranges, each range's arrays copied to host memory while the next range
  * computes (option "host_chunks"); the result is the same.
+ * Lengths: 1 to 2^20 residues; with FP32 precision at most the device's
+ * limit, the counter "f32_max_len" (each warp stages its pair's column
+ * residues in shared memory: about 108,000 on B300), else QP_EINVAL before
+ * anything runs.
  * Errors: QP_EINVAL (family/params), QP_ENOMEM, QP_ECUDA.
  * On error *out is NULL. */
 int qp_posteriors(const qp_family* family, const qp_params* params,
@@ -251,8 +255,10 @@ void qp_result_free(qp_result* result);
  *                      memory, 1: results stay in device memory (and no
  *                      longer count against the budget once polled).
  *   qp_server_submit : copies the family; returns a ticket.  QP_EINVAL for a
- *                      malformed family, a residue outside the alphabet, or
- *                      a family that can never fit the budget.
+ *                      malformed family, a residue outside the alphabet, a
+ *                      sequence longer than the server's FP32 launches take
+ *                      (blocks of four warps: about half of "f32_max_len"),
+ *                      or a family that can never fit the budget.
  *   qp_server_poll   : waits up to timeout_ms (0: no wait, <0: forever) for
  *                      the ticket; QP_ENOTREADY / QP_ETIMEOUT when not done.
  *                      On success the caller owns *out (qp_result_free); a
@@ -382,7 +388,8 @@ int qp_set_option(int32_t device, const char* name, int64_t value);
  * qp_consistency relaxation), "consistency_form" (form of the last
  * qp_consistency relaxation: 1 staged, 0 row form), "f32_variant",
  * "f32_wpp", "f32_warps_per_block", "f32_tab_copies" (launch configuration
- * of the last qp_posteriors call's FP32 kernel; -1 before the first).
+ * of the last qp_posteriors call's FP32 kernel; -1 before the first),
+ * "f32_max_len" (the longest sequence the FP32 form takes on the device).
  * QP_EINVAL for an unknown name or device. */
 int qp_get_counter(int32_t device, const char* name, int64_t* value);
 

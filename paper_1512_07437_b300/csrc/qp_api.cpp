@@ -384,6 +384,32 @@ Context* get_context(int device, int* status) {
     return raw;
 }
 
+int f32_max_len(const Context* C, int warps_per_block) {
+    const size_t cap = (size_t)C->smem_optin;
+    if (qpk::posterior_f32_smem(warps_per_block, 1, 1) > cap) return 0;
+    int lo = 1, hi = (int)kMaxLen;
+    while (lo < hi) {
+        const int mid = lo + (hi - lo + 1) / 2;
+        if (qpk::posterior_f32_smem(warps_per_block, mid, 1) <= cap) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// the FP32 form's length limit for a family (blocks of two warps, the
+// smallest the autotuner launches)
+static int check_f32_lengths(const Context* C, const qp_family* f, const qp_params* prm) {
+    if (prm->precision != QP_F32_SCALED) return QP_OK;
+    const int lim = f32_max_len(C, 2);
+    for (int a = 0; a < f->k; ++a) {
+        const int64_t L = f->offsets[a + 1] - f->offsets[a];
+        if (L > lim)
+            return fail(QP_EINVAL, "sequence %d has %lld residues; the FP32 form takes at most %d on this device",
+                        a, (long long)L, lim);
+    }
+    return QP_OK;
+}
+
 cudaError_t call_stream(Context* C, void* user, cudaStream_t* st) {
     if (user) {
         *st = (cudaStream_t)user;
@@ -615,7 +641,15 @@ int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out
     int f64_grid;
     {
         const int64_t L = pl->max_len + 1;
-        const int64_t db = L * L;
+        // the stored backward values of a pair take (m + 1)(n + 1) cells: at
+        // most the product of the two longest lengths (+1 each), which for a
+        // family with one very long sequence is far below L * L
+        int64_t l1 = 0, l2 = 0;
+        for (int a = 0; a < k; ++a) {
+            const int64_t la = f->offsets[a + 1] - f->offsets[a];
+            if (la > l1) { l2 = l1; l1 = la; } else if (la > l2) l2 = la;
+        }
+        const int64_t db = (l1 + 1) * (l2 + 1);
         const int64_t per_cta = (int64_t)(sizeof(double2) * db + sizeof(double) * 3 * qpk::kNS * L +
                                           sizeof(int32_t) * (5 * L + 8) +
                                           (sizeof(int2) + sizeof(double)) * (int64_t)pl->max_len * cap);
@@ -1319,6 +1353,7 @@ int qp_posteriors(const qp_family* family, const qp_params* params, int32_t out_
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     Context* C = get_context(params->device, &rc);
     if (!C) return rc;
+    if ((rc = check_f32_lengths(C, family, params)) != QP_OK) return rc;
     std::lock_guard<std::mutex> g(C->mu);
     if (!out_on_device) {
         const int G = host_chunks_for(C, family, params);
@@ -1344,6 +1379,7 @@ int qp_posteriors_range(const qp_family* family, const qp_params* params, int64_
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     Context* C = get_context(params->device, &rc);
     if (!C) return rc;
+    if ((rc = check_f32_lengths(C, family, params)) != QP_OK) return rc;
     std::lock_guard<std::mutex> g(C->mu);
     return run_family(C, family, params, out_on_device, out, p_begin, p_end);
 }
@@ -1371,6 +1407,7 @@ int qp_get_counter(int32_t device, const char* name, int64_t* value) {
     else if (n == "f32_wpp") *value = C->last_wpp;
     else if (n == "f32_warps_per_block") *value = C->last_wpb;
     else if (n == "f32_tab_copies") *value = C->last_copies;
+    else if (n == "f32_max_len") *value = f32_max_len(C, 2);
     else return fail(QP_EINVAL, "unknown counter '%s'", name);
     return QP_OK;
 }

@@ -277,6 +277,12 @@ Context* get_context(int device, int* status);
 // stream, made to wait first for all work issued so far to the legacy
 // default stream (so inputs written there are complete).
 cudaError_t call_stream(Context* C, void* user, cudaStream_t* st);
+
+// Longest sequence the FP32 form takes on the context's device with blocks of
+// warps_per_block warps: every warp stages its pair's column residues in
+// shared memory, so such a block must fit the per-block opt-in shared memory
+// (0 when not even a one-residue block fits).
+int f32_max_len(const Context* C, int warps_per_block);
 int run_family(Context* C, const qp_family* f, const qp_params* prm, int32_t out_on_device,
                qp_result** out, int64_t p0 = 0, int64_t p1 = -1);
 int to_host(qp_result* r, cudaStream_t st);

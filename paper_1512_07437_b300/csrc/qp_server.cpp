@@ -966,6 +966,16 @@ int qp_server_submit(qp_server* S, const qp_family* family, uint64_t* ticket) {
     int rc = validate_family(family);
     if (rc != QP_OK) return rc;
     if (family->residues_on_device) return fail(QP_EINVAL, "the server takes host-resident families");
+    {
+        // the server's FP32 launches use blocks of kWpb warps
+        const int lim = f32_max_len(S->ctx, kWpb);
+        for (int a = 0; a < family->k; ++a) {
+            const int64_t L = family->offsets[a + 1] - family->offsets[a];
+            if (L > lim)
+                return fail(QP_EINVAL, "sequence %d has %lld residues; the server takes at most %d on this device",
+                            a, (long long)L, lim);
+        }
+    }
     const double t_submit = now_s();
     const int k = family->k;
     const int64_t total = family->offsets[k];

@@ -195,6 +195,36 @@ def test_invalid_residue_is_rejected(qp):
     assert e.value.code == 1
 
 
+def test_longest_supported_sequence(qp):
+    """The FP32 form's length limit on this device (every warp stages its
+    pair's column residues in shared memory, in blocks of two warps): a
+    family holding a sequence of exactly that length runs and matches the
+    oracle, as columns (20 x L) and as rows (L x 30, hundreds of strips); one
+    residue more is rejected with QP_EINVAL before anything runs."""
+    lim = qp.qp_get_counter("f32_max_len")
+    assert 10_000 < lim <= (1 << 20), lim
+    rng = np.random.Generator(np.random.PCG64(2718))
+    q = synth.background()
+    long_seq = "".join(synth.ALPHABET[c] for c in rng.choice(20, size=lim, p=q))
+    # the short sequences are copies of two stretches of the long one (one
+    # letter changed), so each pair has an alignment band far into it
+    a0, b0 = lim // 2, lim - 40
+    s1 = long_seq[a0:a0 + 20]
+    s1 = s1[:7] + ("A" if s1[7] != "A" else "C") + s1[8:]
+    s2 = long_seq[b0:b0 + 30]
+    fam = synth.family_from_strings([s1, long_seq, s2])
+    prm = synth.default_params(threshold=0.01)
+    res = _run(qp, fam, prm)
+    assert res.nnz > 0
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(res, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
+    res.free()
+    over = synth.family_from_strings([s1, long_seq + "A", s2])
+    with pytest.raises(qp.QpError) as e:
+        _run(qp, over, prm)
+    assert e.value.code == 1
+
+
 def test_long_pairs_stay_in_fp32(qp):
     """Pairs of 500-700 residues (four to six strips): the per-lane exponents
     must follow the values down the strip chain, so no range guard fires."""
