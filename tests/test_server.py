@@ -212,6 +212,12 @@ def test_cancel_poll_and_errors(qp):
         with pytest.raises(qp.QpError) as e:
             srv.submit(bad, small.offsets)
         assert e.value.code == 1
+        # a sequence longer than the FP32 form takes (the server's blocks of
+        # four warps take less than qp_posteriors' two) is refused at submit
+        too_long = synth.family_from_strings(["ACDEFGHIK", "A" * (qp.qp_get_counter("f32_max_len") + 1)])
+        with pytest.raises(qp.QpError) as e:
+            srv.submit(too_long.residues, too_long.offsets)
+        assert e.value.code == 1
         st = srv.stats()
         assert st["cancelled"] == 1 and st["completed"] == 2 and st["resident"] == 0
     finally:
