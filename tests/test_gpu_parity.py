@@ -369,6 +369,46 @@ def test_large_family_sampled_pairs(qp):
         compare_pair(res, fam, int(q), a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
 
 
+def test_millions_of_short_pairs(qp):
+    """3000 sequences of 8-24 residues: 4.5 million pairs in one launch (far
+    more work items than the C3 family's 124,750).  A seeded sample of 300
+    pairs against the oracle (totals, MEA, distance, entry count), the
+    distance matrix symmetric with a zero diagonal, and offsets that add up."""
+    import os
+    import oracle
+    fam = synth.star_family(101, 3000, (12, 20), 0.3, keep=(8, 24))
+    k = fam.k
+    prm = synth.default_params(threshold=0.01)
+    res = _run(qp, fam, prm)
+    P = k * (k - 1) // 2
+    assert res.n_pairs == P
+    _no_fallback(res)
+    L = np.asarray(fam.lengths)
+    rng = np.random.Generator(np.random.PCG64(12))
+    a_s = rng.integers(0, k - 1, size=300)
+    b_s = np.array([int(rng.integers(a + 1, k)) for a in a_s])
+    sample = a_s * k - a_s * (a_s + 1) // 2 + (b_s - a_s - 1)
+    ref = oracle.pairs(fam, list(zip(a_s.tolist(), b_s.tolist())), prm, threads=os.cpu_count())
+    lzh, lzp = host(res.log_z_hmm), host(res.log_z_pf)
+    mea, dist = host(res.mea), host(res.dist64)
+    pno, pro = host(res.pair_nnz_off), host(res.pair_row_off)
+    mn = np.minimum(L[a_s], L[b_s])
+    assert np.all(np.abs(lzh[sample] - ref["logz_hmm"]) <= TOL_LOGZ32 * np.abs(ref["logz_hmm"]))
+    assert np.all(np.abs(lzp[sample] - ref["logz_pf"]) <= TOL_LOGZ32 * np.abs(ref["logz_pf"]))
+    assert np.all(np.abs(mea[sample] - ref["mea"]) <= TOL_F32 * mn)
+    assert np.abs(dist[a_s, b_s] - ref["dist"]).max() <= TOL_F32
+    nnz = pno[sample + 1] - pno[sample]
+    assert np.all(np.abs(nnz - ref["nnz"]) <= 2), np.abs(nnz - ref["nnz"]).max()
+    d = host(res.dist)
+    assert np.array_equal(d, d.T) and (np.diag(d) == 0).all()
+    # rows: m + 1 per pair (a's length), entries: the last offset
+    assert int(pro[-1]) == int(sum((L[a] + 1) * (k - 1 - a) for a in range(k)))
+    assert int(pno[-1]) == int(res.nnz) and np.all(np.diff(pno) >= 0)
+    for q in range(3):
+        a, b = int(a_s[q]), int(b_s[q])
+        compare_pair(res, fam, int(sample[q]), a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
+
+
 @pytest.mark.parametrize("wpp", [2])
 @pytest.mark.parametrize("ckpt", [0, 1])
 def test_warps_per_pair_equal_one(qp, wpp, ckpt):
