@@ -213,7 +213,6 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off, int64_t p0, int64_t 
     int64_t ro = 0, so = 0, q = 0, g = 0;
     int64_t bst = 0, bex = 0;
     double work_sum = 0;
-    std::vector<std::pair<int64_t, int32_t>> order(P);
     for (int a = 0; a < k && g < p1; ++a) {
         const int64_t row_pairs = k - 1 - a;
         if (g + row_pairs <= p0) { g += row_pairs; continue; }    // the whole row of pairs precedes the range
@@ -233,7 +232,6 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off, int64_t p0, int64_t 
             const int last = (m + 1 - (ns - 1) * qpk::kStripRows + 31) / 32;
             const int64_t w = ((int64_t)(ns - 1) * qpk::kRmax + (last <= 1 ? 1 : last <= 2 ? 2 : last <= 4 ? 4 : 8)) * (n + 32);
             pl->work[q] = w;
-            order[q] = std::make_pair(-w, (int32_t)q);
             work_sum += (double)w;
             ++q;
         }
@@ -247,10 +245,38 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off, int64_t p0, int64_t 
     pl->bex_stride = bex;
     pl->bnd_stride = 2 * (int64_t)(maxL + 1);
     pl->work_sum = work_sum;
-    // longest first keeps the persistent workers balanced (greedy LPT)
-    std::stable_sort(order.begin(), order.end());
-    pl->order.resize(P);
-    for (int64_t i = 0; i < P; ++i) pl->order[i] = order[i].second;
+    // longest first keeps the persistent workers balanced (greedy LPT): a
+    // stable LSD radix sort by decreasing work, ties in pair order, linear in
+    // the pair count (a comparison sort took 0.6 s for 4.5 million pairs)
+    {
+        int64_t maxw = 0;
+        for (int64_t i = 0; i < P; ++i) maxw = std::max(maxw, pl->work[i]);
+        std::vector<uint64_t> key(P), key2(P);
+        std::vector<int32_t> idx(P), idx2(P);
+        for (int64_t i = 0; i < P; ++i) {
+            key[i] = (uint64_t)(maxw - pl->work[i]);
+            idx[i] = (int32_t)i;
+        }
+        int bits = 0;
+        while (bits < 63 && (maxw >> bits) != 0) ++bits;
+        constexpr int kDigit = 11;
+        constexpr uint64_t kMask = (1u << kDigit) - 1;
+        std::vector<int64_t> cnt((size_t)1 << kDigit);
+        for (int shift = 0; shift < bits; shift += kDigit) {
+            std::fill(cnt.begin(), cnt.end(), 0);
+            for (int64_t i = 0; i < P; ++i) ++cnt[(key[i] >> shift) & kMask];
+            int64_t run = 0;
+            for (auto& c : cnt) { const int64_t t = c; c = run; run += t; }
+            for (int64_t i = 0; i < P; ++i) {
+                const int64_t d = cnt[(key[i] >> shift) & kMask]++;
+                key2[d] = key[i];
+                idx2[d] = idx[i];
+            }
+            key.swap(key2);
+            idx.swap(idx2);
+        }
+        pl->order.swap(idx);
+    }
     return pl;
 }
 
