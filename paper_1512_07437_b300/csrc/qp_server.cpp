@@ -150,6 +150,7 @@ struct qp_server {
     int cap = 0;
     int64_t scratch_warps = 0;
     int bps[qpk::kF32Variants] = {};
+    int f64_grid = 0;            // CTAs of the FP64 follow-up (its scratch holds that many pairs)
     size_t scratch_bytes = 0;
     bool ckpt = false;               // checkpointed form of the FP32 kernel
     void *bst = nullptr, *bex = nullptr, *bnd = nullptr, *bck = nullptr, *stg = nullptr;
@@ -177,6 +178,19 @@ struct qp_server {
 
 namespace {
 
+// CTAs of the FP64 follow-up for sequences up to L: kF64Grid, fewer when
+// their scratch would pass kF64Scratch (each CTA holds a whole pair's
+// stored backward values, (L + 1)^2 of them), at least one
+constexpr int64_t kF64Scratch = (int64_t)2 << 30;
+int64_t f64_cta_bytes(int L, int cap) {
+    const int64_t L1 = L + 1;
+    return (int64_t)(sizeof(double2) * L1 * L1 + sizeof(double) * 3 * qpk::kNS * L1 + sizeof(int32_t) * (5 * L1 + 8) +
+                     (sizeof(int2) + sizeof(double)) * (int64_t)L * cap);
+}
+int f64_grid_for(int L, int cap) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kF64Grid, kF64Scratch / f64_cta_bytes(L, cap)));
+}
+
 // Device bytes of the kernels' scratch for sequences up to L.  The stored
 // form is used while its scratch takes at most a third of the budget, else
 // the checkpointed form.
@@ -202,9 +216,7 @@ size_t scratch_bytes_for(const qp_server* S, int L, int64_t* warps_out, int* bps
         if (ckpt || S->ctx->tune.ckpt == 0 || (S->ctx->tune.ckpt < 0 && b <= S->budget / 3)) break;
         ckpt = true;
     }
-    const int64_t L1 = L + 1;
-    b += (size_t)kF64Grid * (sizeof(double2) * L1 * L1 + sizeof(double) * 3 * qpk::kNS * L1 +
-                             sizeof(int32_t) * (5 * L1 + 8) + (sizeof(int2) + sizeof(double)) * (size_t)L * cap);
+    b += (size_t)f64_grid_for(L, cap) * (size_t)f64_cta_bytes(L, cap);
     if (warps_out) *warps_out = warps;
     if (cap_out) *cap_out = cap;
     if (ckpt_out) *ckpt_out = ckpt;
@@ -233,17 +245,18 @@ int set_scratch(qp_server* S, int L) {
     // room for one warp per pair and for two (every buffer per warp)
     const qpk::F32Scratch s1(L, cap, ckpt, 1), s2(L, cap, ckpt, 2);
     const int64_t L1 = L + 1;
+    const size_t f64g = (size_t)f64_grid_for(L, cap);
     struct A { void** p; size_t b; } al[] = {
         {&S->bst, sizeof(float2) * (size_t)std::max(s1.bst, s2.bst) * (size_t)warps},
         {&S->bex, sizeof(int2) * (size_t)std::max(s1.bex, s2.bex) * (size_t)warps},
         {&S->bnd, sizeof(float4) * (size_t)std::max(s1.bnd, s2.bnd) * (size_t)warps},
         {&S->bck, sizeof(float4) * (size_t)std::max(s1.bck, s2.bck) * (size_t)warps},
         {&S->stg, sizeof(int2) * (size_t)s1.stg * warps},
-        {&S->d_b, sizeof(double2) * (size_t)(L1 * L1) * kF64Grid},
-        {&S->d_diag, sizeof(double) * (size_t)(3 * qpk::kNS * L1) * kF64Grid},
-        {&S->d_cnt, sizeof(int32_t) * (size_t)(5 * L1 + 8) * kF64Grid},
-        {&S->d_stg, sizeof(int2) * (size_t)L * cap * kF64Grid},
-        {&S->d_stg64, sizeof(double) * (size_t)L * cap * kF64Grid},
+        {&S->d_b, sizeof(double2) * (size_t)(L1 * L1) * f64g},
+        {&S->d_diag, sizeof(double) * (size_t)(3 * qpk::kNS * L1) * f64g},
+        {&S->d_cnt, sizeof(int32_t) * (size_t)(5 * L1 + 8) * f64g},
+        {&S->d_stg, sizeof(int2) * (size_t)L * cap * f64g},
+        {&S->d_stg64, sizeof(double) * (size_t)L * cap * f64g},
     };
     for (auto& a : al) {
         cudaError_t e = cudaMallocAsync(a.p, std::max<size_t>(a.b, 256), S->cs);
@@ -256,6 +269,7 @@ int set_scratch(qp_server* S, int L) {
     }
     S->scratch_len = L;
     S->scratch_warps = warps;
+    S->f64_grid = (int)f64g;
     S->cap = cap;
     S->ckpt = ckpt;
     S->scratch_bytes = bytes;
@@ -266,6 +280,7 @@ qpk::Problem base_problem(qp_server* S, const Rec& R, int n_items, int wpp = 1, 
     qpk::Problem Pb;
     memset(&Pb, 0, sizeof Pb);
     Pb.cf = S->cf;
+    Pb.cf.spin_limit = S->ctx->tune.spin_limit;   // testing knob of the two-warp form (0: default)
     Pb.cst = S->d_cst;
     Pb.fams = S->d_fams;
     Pb.items = R.d_items;
@@ -667,7 +682,7 @@ void retire(qp_server* S, int ri) {
         R.per_fam_f64.assign(fb.begin(), fb.end());
         const qpk::Problem Pb = base_problem(S, R, (int)R.items.size());
         cudaEventRecord(R.ev0, S->cs);
-        e = qpk::launch_posterior_f64(Pb, std::min(hs.n_fallback, kF64Grid), S->cs);
+        e = qpk::launch_posterior_f64(Pb, std::min(hs.n_fallback, S->f64_grid), S->cs);
         if (e != cudaSuccess) {
             fail_all(S, cuda_fail(e, "k_posterior_f64 launch"), last_error());
             release_items(S, R.per_fam_f64);

@@ -277,3 +277,30 @@ def test_serving_trace_sampled_pairs(qp):
         pno = host(r.pair_nnz_off)
         assert abs(int(pno[p + 1] - pno[p]) - int(ref["nnz"][0])) <= 2
         r.free()
+
+
+def test_fp64_follow_up_in_the_server(qp):
+    """Pairs that the FP32 form hands to FP64 are recomputed by the server's
+    FP64 follow-up launch.  Two warps per pair with the strip-wait limit cut
+    to one poll (runtime testing knobs of the two-warp form) make waits run
+    out; the flagged pairs must be recomputed in FP64 and match the oracle."""
+    fam = synth.star_family(48, 4, (300, 420), 0.3)     # 3-4 strips per pair
+    prm = synth.default_params(threshold=1e-4)
+    try:
+        qp.qp_set_option("wpp", 2)
+        qp.qp_set_option("spin_limit", 1)
+        srv = qp.Server(prm, 16 << 30)
+        try:
+            r = srv.poll(srv.submit(fam.residues, fam.offsets), 120000)
+        finally:
+            srv.destroy()
+    finally:
+        qp.qp_set_option("spin_limit", 0)
+        qp.qp_set_option("wpp", 0)
+    flags = host(r.pair_flags)
+    sync = (flags & (1 << 12)) != 0
+    assert r.n_fallback > 0 and sync.any(), f"no wait ran out: flags {flags}"
+    assert ((flags[sync] & 1) == 1).all(), "a pair whose wait ran out was not recomputed in FP64"
+    for p, (a, b) in enumerate(fam.pairs()):
+        compare_pair(r, fam, p, a, b, prm, TOL_F32, TOL_LOGZ32, dense=False)
+    r.free()
