@@ -216,25 +216,31 @@ std::shared_ptr<Plan> build_plan(int k, const int64_t* off, int64_t p0, int64_t 
     for (int a = 0; a < k && g < p1; ++a) {
         const int64_t row_pairs = k - 1 - a;
         if (g + row_pairs <= p0) { g += row_pairs; continue; }    // the whole row of pairs precedes the range
-        for (int b = a + 1; b < k; ++b, ++g) {
-            if (g < p0) continue;
-            if (g >= p1) break;
-            const int m = (int)pl->lens[a], n = (int)pl->lens[b];
+        // what depends on x = sequence a alone: its strips, and the rows per
+        // lane summed over them
+        const int m = (int)pl->lens[a];
+        const int ns = (m + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
+        const int last = (m + 1 - (ns - 1) * qpk::kStripRows + 31) / 32;
+        const int64_t rows_per_lane = (int64_t)(ns - 1) * qpk::kRmax + (last <= 1 ? 1 : last <= 2 ? 2 : last <= 4 ? 4 : 8);
+        const int b0 = std::max<int64_t>(a + 1, a + 1 + (p0 - g));
+        const int b1 = (int)std::min<int64_t>(k, a + 1 + (p1 - g));
+        int64_t n_max = 0, n_sum = 0;      // columns + skew of the row's pairs
+        for (int b = b0; b < b1; ++b, ++q) {
+            const int64_t nn = pl->lens[b] + 32;
             pl->pairs[q] = make_int2(a, b);
             pl->row_off[q] = ro;
             pl->strip_off[q] = so;
-            const int ns = (m + 1 + qpk::kStripRows - 1) / qpk::kStripRows;
             ro += m + 1;
             so += ns;
-            bst = std::max<int64_t>(bst, (int64_t)ns * qpk::kStripRows * (n + 32));
-            bex = std::max<int64_t>(bex, (int64_t)ns * ((n + 32 + qpk::kC - 1) / qpk::kC) * 32);
-            // swept lane-steps of the pair: strips x (columns + skew) x rows per lane
-            const int last = (m + 1 - (ns - 1) * qpk::kStripRows + 31) / 32;
-            const int64_t w = ((int64_t)(ns - 1) * qpk::kRmax + (last <= 1 ? 1 : last <= 2 ? 2 : last <= 4 ? 4 : 8)) * (n + 32);
-            pl->work[q] = w;
-            work_sum += (double)w;
-            ++q;
+            // swept lane-steps of the pair: rows per lane over the strips x (columns + skew)
+            pl->work[q] = rows_per_lane * nn;
+            n_max = std::max(n_max, nn);
+            n_sum += nn;
         }
+        g += row_pairs;
+        bst = std::max<int64_t>(bst, (int64_t)ns * qpk::kStripRows * n_max);
+        bex = std::max<int64_t>(bex, (int64_t)ns * ((n_max + qpk::kC - 1) / qpk::kC) * 32);
+        work_sum += (double)(rows_per_lane * n_sum);    // exact per row
     }
     pl->row_off[P] = ro;
     pl->strip_off[P] = so;
